@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the parareal + splitting solver on one node.
+
+One step = one complete solve of the workload to tolerance through the C ABI:
+the sequential coarse sweep, every parareal iteration (batched fine propagator
+over all slices, coarse chain with the fused correction, increment test) until
+the stopping rule fires.  Inputs are resident in HBM before the timed region.
+
+value    unknown-updates/s over the K timed solves (all ranks): interior unknowns
+         advanced by one FIE step, summed over the fine and coarse work executed.
+e2e      the same through ps_run_parareal_host with the initial state in pinned host
+         memory and U_N copied back every step.
+roofline the dominant kernel's algorithmic bytes (or flops) per launch over its
+         average CUDA-event duration in the timed region, against the measured peak.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+Multi-GPU (torchrun): every rank solves its own copy (replicas, weak scaling); only the
+timing uses collectives.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "unknown-updates/s & HBM roofline % of split sweeps; time-to-tol vs plain FP64 GPU"
+UNIT = "unknown-updates/s"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return pk, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 FMA issue rate of this GB300 pool, measured with a dependent-free DFMA loop
+# (152 SMs x 256 threads x 8 chains): 0.595e12 FMA/s = 1.19 TFLOP/s (FMA = 2 flops).
+FP64_PEAK_TFLOPS = 1.19
+
+
+def workload(name):
+    from paper_2502_08370_gb300 import workloads as wl
+    if name == "heat3d_255":
+        return wl.heat3d_255()
+    if name == "heat2d_63":
+        return wl.heat2d_63()
+    if name.startswith("heat3d_"):
+        return wl.heat3d_255(n=int(name.split("_")[1]))
+    raise SystemExit(f"unknown workload {name}")
+
+
+def dist_setup(backend):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend)
+    return rank, ws
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_problem(ps, torch, cfg, precision, timing):
+    grid = ps.Grid(cfg["n"])
+    a = None if cfg["a"] is None else torch.as_tensor(cfg["a"]).cuda()
+    src = None if cfg["src"] is None else torch.as_tensor(cfg["src"]).cuda()
+    op = ps.Operator(grid, a=a, c=cfg["c"], src=src, src_t=cfg["src_t"])
+    sp = ps.Splitting(op, cfg["split"], cfg.get("boxes", (1, 1)), cfg.get("overlap", 0.0))
+    prob = ps.Problem(sp, cfg["T"], cfg["N"], cfg["g"], cfg["s"], precision=precision, timing=timing)
+    prob._keep = (grid, op, sp, a, src)
+    return prob
+
+
+def cpu_sample(cfg, seconds):
+    """The oracle, as it stands, on a bounded sample: whole fine FIE steps of one slice."""
+    import numpy as np
+
+    import oracle as orc
+    orp = orc.Problem(cfg["n"], a=cfg["a"], c=cfg["c"], src=cfg["src"], src_t=cfg["src_t"], split=cfg["split"],
+                      boxes=cfg.get("boxes", (1, 1)), overlap=cfg.get("overlap", 0.0))
+    tau = cfg["T"] / cfg["N"] / cfg["s"]
+    u = np.ascontiguousarray(cfg["u0"], dtype=np.float64)
+    t = time.perf_counter()
+    u = orc.propagate(orp, tau, 1, u, t0=0)
+    one = time.perf_counter() - t
+    steps = max(1, int(seconds / max(one, 1e-6)))
+    t = time.perf_counter()
+    orc.propagate(orp, tau, steps, u, t0=1)
+    dt = time.perf_counter() - t
+    nt = int(np.prod(cfg["n"]))
+    grid = "x".join(str(v) for v in cfg["n"])
+    return {"value": steps * nt / dt, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+            "sample": f"{steps} fine FIE steps of one {grid} slice ({len(cfg['n'])} line-solve substeps each), "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, cfg, rank, ws):
+    """The oracle as it stands: each step is one fine FIE step of one slice of the workload."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle as orc
+    orc.build()
+    orp = orc.Problem(cfg["n"], a=cfg["a"], c=cfg["c"], src=cfg["src"], src_t=cfg["src_t"], split=cfg["split"],
+                      boxes=cfg.get("boxes", (1, 1)), overlap=cfg.get("overlap", 0.0))
+    tau = cfg["T"] / cfg["N"] / cfg["s"]
+    u = np.ascontiguousarray(cfg["u0"], dtype=np.float64)
+    for w in range(args.warmup):
+        u = orc.propagate(orp, tau, 1, u, t0=w)
+    t = time.perf_counter()
+    for k in range(args.steps):
+        u = orc.propagate(orp, tau, 1, u, t0=args.warmup + k)
+    dt = time.perf_counter() - t
+    nt = int(np.prod(cfg["n"]))
+    value = args.steps * nt / dt
+    grid = "x".join(str(v) for v in cfg["n"])
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args, cfg),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+                             "sample": f"each step: one fine FIE step ({len(cfg['n'])} line-solve substeps) of one "
+                                       f"{grid} slice of the workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args, cfg):
+    grid = "x".join(str(v) for v in cfg["n"])
+    return {"workload": args.workload, "grid": grid, "splitting": cfg["split"], "N_slices": cfg["N"],
+            "coarse_steps": cfg["g"], "fine_steps": cfg["s"], "T": cfg["T"], "tol": cfg["tol"],
+            "precision": args.precision,
+            "l2": "inputs larger than L2 (every step streams all slice states, > 20 GB)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="heat3d_255")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 time-to-tolerance run")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    cfg = workload(args.workload)
+
+    if args.impl == "reference":
+        rank, ws = dist_setup("gloo")
+        run_reference(args, cfg, rank, ws)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_2502_08370_gb300 as ps
+    from paper_2502_08370_gb300 import build as psbuild
+    rank, ws = dist_setup("nccl")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if rank == 0:
+        psbuild.build()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    ps.lib()
+
+    prob = make_problem(ps, torch, cfg, args.precision, timing=2)
+    u0 = torch.as_tensor(cfg["u0"]).cuda()
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        prob.run(u0, cfg["tol"])
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    updates = 0.0
+    launches = 0
+    iters = []
+    kern = {}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if sampler:
+        sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        iters.append(prob.run(u0, cfg["tol"]))
+        st = prob.stats()
+        updates += st["unknown_updates"]
+        launches += st["kernel_launches"]
+        for name, k in prob.kernel_times().items():
+            acc = kern.setdefault(name, dict(launches=0, ms=0.0, bytes=0.0, flops=0.0))
+            for key in acc:
+                acc[key] += k[key]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, updates], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_max, updates_all = float(mx[0]), float(sm[1])
+    else:
+        ms_max, updates_all = ms, updates
+    value = updates_all / (ms_max / 1000.0)
+    uN_mixed = prob.state(cfg["N"]).cpu().numpy()
+
+    # dominant kernel and its roofline
+    pk, pk_kind = load_peaks()
+    dom_name, dom = max(kern.items(), key=lambda kv: kv[1]["ms"])
+    per_launch_ms = dom["ms"] / dom["launches"]
+    is_f64 = dom_name.endswith("f64") or "f64+" in dom_name
+    if is_f64:
+        achieved = dom["flops"] / dom["launches"] / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None}
+    else:
+        achieved = dom["bytes"] / dom["launches"] / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None}
+    roof.update({"kernel": dom_name, "launches_timed": dom["launches"], "ms_per_launch": per_launch_ms,
+                 "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
+                 "share_of_step": dom["ms"] / ms, "peak_source": pk_kind})
+    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                   "GB/s": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1),
+                   "TFLOP/s": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 4)}
+               for k, v in sorted(kern.items(), key=lambda kv: -kv[1]["ms"])}
+
+    # end to end through the host entry point (pinned host buffers)
+    nt = int(np.prod(cfg["n"]))
+    u0h = torch.as_tensor(cfg["u0"]).contiguous().pin_memory()
+    uNh = torch.empty_like(u0h).pin_memory()
+    prob_e2e = prob
+    prob_e2e.run_host(u0h, uNh, cfg["tol"])
+    torch.cuda.synchronize()
+    barrier()
+    e2e_upd = 0.0
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        prob_e2e.run_host(u0h, uNh, cfg["tol"])
+        e2e_upd += prob_e2e.stats()["unknown_updates"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_wall = time.perf_counter() - t0
+    barrier()
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms, e2e_upd], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        e2e_ms, e2e_upd = float(mx[0]), float(sm[1])
+    e2e = {"value": e2e_upd / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": 8 * nt,
+           "d2h_bytes_per_step": 8 * nt, "wall_s": e2e_wall}
+
+    # plain FP64 GPU method: time to tolerance at the same tolerance, and the accuracy gap
+    compare = None
+    if not args.no_compare and args.precision != "fp64":
+        del prob
+        torch.cuda.empty_cache()
+        p64 = make_problem(ps, torch, cfg, "fp64", timing=1)
+        p64.run(u0, cfg["tol"])
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        c0.record(stream)
+        for _ in range(reps):
+            it64 = p64.run(u0, cfg["tol"])
+        c1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = c0.elapsed_time(c1) / reps
+        uN64 = p64.state(cfg["N"]).cpu().numpy()
+        err = float(np.abs(uN_mixed - uN64).max() / max(np.abs(uN64).max(), 1e-300))
+        compare = {"fp64_ms_to_tol": ms64, "fp64_iters": it64, "ms_to_tol": ms / args.steps,
+                   "iters": iters[-1], "speedup_vs_fp64": ms64 / (ms / args.steps),
+                   "rel_maxnorm_diff_UN_vs_fp64": err,
+                   "fp64_unknown_updates_per_s": p64.stats()["unknown_updates"] / (ms64 / 1000.0)}
+        del p64
+
+    cpu = None
+    if rank == 0 and ws == 1:
+        import oracle as orc
+        orc.build()
+        cpu = cpu_sample(cfg, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+                "config": config_of(args, cfg), "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roof, "cpu_baseline": cpu, "time_to_tol": compare, "parareal_iterations": iters,
+                "kernels": kernels}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * ps.h -- C ABI of the GB300 parareal + splitting solver.
+ *
+ * Method: Arraras, Gaspar, Jimenez-Ciga, Portero, "Space-time parallel
+ * iterative solvers for the integration of parabolic problems",
+ * arXiv 2502.08370.  The library integrates
+ *     u_t = div(a grad u) - c u + f   on the unit square / cube,
+ *     u = 0 on the boundary                         (Sec. 2.1, eq. cont_problem)
+ * discretised by second-order finite differences on a uniform grid of
+ * interior nodes (Sec. 2.2, eq. semidisc_prob; Sec. 5), split either by
+ * dimension (x/y/z) or by a partition of unity over overlapping boxes
+ * (Sec. 2.1), advanced by fractional implicit Euler steps (Sec. 2.2,
+ * eq. FIE_method) used as both propagators of the parareal iteration
+ * (Sec. 3, Parareal/FIE-FIE of Sec. 4).
+ *
+ * Conventions for every entry point:
+ *  - Return value: PS_OK (0) or a PS_ERR_* code; ps_last_error() gives a
+ *    message for the calling thread's last failure.  No entry point aborts.
+ *  - Arrays are dense, x fastest: a state has nx*ny*nz doubles (interior
+ *    nodes, boundary values are the implicit zero Dirichlet data); a nodal
+ *    coefficient has (nx+2)*(ny+2)*(nz+2) doubles (boundary included).
+ *    nz = 1 in 2-D.
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller; the
+ *    library reads or writes them on the given stream and never frees them.
+ *    Pointers named *_host are host pointers (pinned or pageable).
+ *  - `stream` is a cudaStream_t passed as uintptr_t (0 = legacy default).
+ *    Work is enqueued on it; functions that return host data synchronise it.
+ *  - Handles are opaque, owned by the library, freed by the matching
+ *    *_destroy.  A problem keeps pointers to its splittings, a splitting to
+ *    its operator, an operator to its grid: destroy in reverse order.
+ *  - The library allocates its own device workspaces with cudaMalloc at
+ *    handle creation (PS_ERR_OOM when that fails) and frees them on destroy.
+ */
+#ifndef PS_H
+#define PS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PS_OK 0
+#define PS_ERR_INVALID 1        /* bad argument or state */
+#define PS_ERR_CUDA 2           /* a CUDA runtime call failed (message has the CUDA error) */
+#define PS_ERR_OOM 3            /* device allocation failed */
+#define PS_ERR_NONFINITE 4      /* a NaN/Inf appeared in the parareal correction */
+#define PS_ERR_DEVICE_TIMEOUT 5 /* a device-side wait ran out of its iteration budget */
+#define PS_ERR_UNSUPPORTED 6    /* combination not implemented (e.g. 3-D DD splitting) */
+
+#define PS_SPLIT_DIM 0 /* dimensional splitting, M = d substeps x, y(, z) (Sec. 2.1) */
+#define PS_SPLIT_DD 1  /* domain-decomposition splitting, 2-D, M = #colours (Sec. 2.1) */
+
+#define PS_PREC_FP64 0  /* every solve in FP64 */
+#define PS_PREC_MIXED 1 /* fine-propagator line solves in FP32; coarse propagator, the
+                           parareal correction, the increments and the test in FP64 */
+
+#define PS_SCHED_AUTO 0   /* library default for dimensional line solves */
+#define PS_SCHED_THOMAS 1 /* one thread per line, Thomas/LDL^T recurrences */
+#define PS_SCHED_PCR 2    /* one warp per line, parallel cyclic reduction */
+
+typedef struct ps_grid ps_grid;
+typedef struct ps_operator ps_operator;
+typedef struct ps_splitting ps_splitting;
+typedef struct ps_problem ps_problem;
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* ps_last_error(void);
+/* ABI version (major*100 + minor). */
+int ps_version(void);
+
+/* ---- grid: unit box, n[d] interior nodes, h_d = 1/(n[d]+1) (Sec. 2.2) ---------------- */
+/* dim = 2 or 3; n[0..dim-1] >= 1 (n[2] ignored in 2-D).  PS_ERR_INVALID otherwise. */
+int ps_grid_create(int dim, const int n[3], ps_grid** out);
+int ps_grid_destroy(ps_grid* g);
+
+/* ---- operator L u = div(a grad u) - c u + f (Sec. 2.1, eq. cont_problem) -------------- */
+/* a_nodal_dev: nodal diffusion (boundary included) or NULL for a = 1; must be > 0.
+ * c >= 0: reaction.  src_dev: spatial source on interior nodes or NULL (f = 0).
+ * src_t_host: time factors f(x,t) = src(x) * src_t[j] at the fine times t_j = j*dt,
+ * j = 0..src_t_len-1, or NULL (factor 1).  The arrays are copied; the caller may
+ * free them after the call.  The edge coefficient is a_{i+1/2} = (a_i + a_{i+1})/2. */
+int ps_operator_create(const ps_grid* g, const double* a_nodal_dev, double c, const double* src_dev,
+                       const double* src_t_host, int src_t_len, uintptr_t stream, ps_operator** out);
+int ps_operator_destroy(ps_operator* op);
+
+/* ---- splitting L = L_1 + ... + L_M (Sec. 2.1) ----------------------------------------- */
+typedef struct {
+  int boxes[2];   /* boxes per direction (>= 1; a direction with 1 box is not split) */
+  double overlap; /* overlap width beta in [0,1] units, centred on every core boundary */
+} ps_dd_params;
+/* kind = PS_SPLIT_DIM (dd ignored) or PS_SPLIT_DD (2-D only; colours
+ * (bx%2, by%2) = (0,0),(1,0),(0,1),(1,1) applied in that order; cos^2 ramps). */
+int ps_splitting_create(const ps_operator* op, int kind, const ps_dd_params* dd, ps_splitting** out);
+int ps_splitting_destroy(ps_splitting* sp);
+
+/* ---- parareal problem (Sec. 3) ----------------------------------------------------------- */
+typedef struct {
+  int precision; /* PS_PREC_FP64 or PS_PREC_MIXED */
+  int schedule;  /* PS_SCHED_* for the fine line solves */
+  int timing;    /* 1: per-phase CUDA events (ps_problem_stats); 2: also per-kernel
+                    events (ps_problem_kernel_times) */
+  int dd_slices_per_block; /* DD subdomain solves: slices (one warp each) per CTA, 1..8; 0 = 2 */
+  int reserved[4];
+} ps_params;
+
+/* fine, coarse: splittings of the same operator used by F and G (coarse = NULL: use
+ * fine).  T > 0; N slices; G = g_steps FIE steps of DeltaT/g_steps; F = f_steps FIE
+ * steps of dt = DeltaT/f_steps; f_steps % g_steps == 0.  Builds the substep factors
+ * of (I - tau A_j) for both step sizes on the device (FP64) and allocates the slice
+ * states: (N+1) U, N Gold, N F-results (+ N FP32 work states in PS_PREC_MIXED). */
+int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, double T, int N, int g_steps,
+                      int f_steps, const ps_params* params, uintptr_t stream, ps_problem** out);
+int ps_problem_destroy(ps_problem* p);
+
+/* Parareal from u0_dev: U_0 = u0, U^0 by a sequential coarse sweep, then
+ * U_{n+1}^{k} = F(U_n^{k-1}) + (G(U_n^{k}) - G(U_n^{k-1})) for k = 1, 2, ...
+ * Stops at the first k with inc_k = max_{n>=1} ||U_n^k - U_n^{k-1}||_inf < tol, at
+ * k = N (then U is the sequential fine solution), or at k = max_iter (<= 0: N).
+ * *iters_out = k.  Reaching k = N is not an error.  Slices n < k-1 whose input
+ * did not change are not recomputed (their result is bitwise the same). */
+int ps_run_parareal(ps_problem* p, const double* u0_dev, double tol, int max_iter, uintptr_t stream,
+                    int* iters_out);
+/* Same from host memory: copies u0_host in, runs, copies U_N out to uN_host. */
+int ps_run_parareal_host(ps_problem* p, const double* u0_host, double* uN_host, double tol, int max_iter,
+                         uintptr_t stream, int* iters_out);
+/* Copy U_slice (0..N) of the last run to out_dev. */
+int ps_get_state(const ps_problem* p, int slice, double* out_dev, uintptr_t stream);
+/* inc_k for k = 1..len of the last run; len = min(iterations, cap). */
+int ps_get_history(const ps_problem* p, double* inc_host, int cap, int* len);
+
+/* Sequential fine solution (the plain comparator): U_out_dev gets (N+1) states at T_n. */
+int ps_run_fine_sequential(ps_problem* p, const double* u0_dev, double* U_out_dev, uintptr_t stream);
+/* Sequential coarse solution U_n = G^n(u0), (N+1) states. */
+int ps_run_coarse_sequential(ps_problem* p, const double* u0_dev, double* U_out_dev, uintptr_t stream);
+
+/* Building blocks on one state x_dev (in place), for testing the kernels.
+ * which = 0: fine propagator's step size and splitting, 1: coarse.
+ * ps_substep_solve: x <- (I - tau A_m)^{-1} x (one internal stage of eq. FIE_method).
+ * ps_propagate: nsteps FIE steps; step q ends at fine time index t0 + (q+1)*tstride. */
+int ps_substep_solve(ps_problem* p, int which, int m, double* x_dev, uintptr_t stream);
+int ps_propagate(ps_problem* p, int which, int nsteps, int t0, int tstride, double* x_dev, uintptr_t stream);
+
+typedef struct {
+  int iterations;          /* k of the last run */
+  double unknown_updates;  /* interior unknowns advanced by one FIE step, summed over the run */
+  double ms_total;         /* device time of the last run (events; timing != 0) */
+  double ms_fine;          /* of which F phases */
+  double ms_coarse;        /* of which the initial sweep, G phases and corrections */
+  int kernel_launches;     /* kernels this library launched in the last run */
+} ps_stats;
+int ps_problem_stats(const ps_problem* p, ps_stats* out);
+
+/* Per-kernel-kind device times of the last run, recorded when params.timing >= 2 with a
+ * CUDA event pair around every launch on the run's stream.  name: "<phase>.<axis>.<type>"
+ * (phase F = fine, G = coarse; +corr / +init when the parareal correction / initial sweep
+ * is fused in).  bytes / flops: algorithmic traffic and FP work summed over the launches
+ * (each sweep reads its right-hand side and writes its result once, reads the factors once
+ * per launch; 5 flops per unknown per sweep, FMA = 2).  len = number of kinds (<= cap). */
+typedef struct {
+  char name[32];
+  int launches;
+  double ms;
+  double bytes;
+  double flops;
+} ps_kernel_time;
+int ps_problem_kernel_times(const ps_problem* p, ps_kernel_time* out, int cap, int* len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PS_H */

@@ -1,0 +1,275 @@
+"""GB300 parareal + splitting solver (arXiv 2502.08370) -- Python binding.
+
+The numerical work runs in the CUDA library ``_lib/libps.so`` (C ABI declared
+in ``include/ps.h``); this module only loads it and marshals arguments.  Device
+arrays are torch tensors (float64, CUDA, contiguous); torch provides the
+memory and the streams.  There is no CPU fallback: every call fails loudly
+when the library or a CUDA device is missing.
+
+Function names follow the C ABI: ``ps_grid_create`` etc. are exposed as raw
+calls on :func:`lib`, and :class:`Grid`, :class:`Operator`, :class:`Splitting`
+and :class:`Problem` own the corresponding handles.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libps.so")
+
+PS_OK = 0
+ERRORS = {1: "PS_ERR_INVALID", 2: "PS_ERR_CUDA", 3: "PS_ERR_OOM", 4: "PS_ERR_NONFINITE",
+          5: "PS_ERR_DEVICE_TIMEOUT", 6: "PS_ERR_UNSUPPORTED"}
+PS_SPLIT_DIM, PS_SPLIT_DD = 0, 1
+PS_PREC_FP64, PS_PREC_MIXED = 0, 1
+PS_SCHED_AUTO, PS_SCHED_THOMAS, PS_SCHED_PCR = 0, 1, 2
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _DD(C.Structure):
+    _fields_ = [("boxes", C.c_int * 2), ("overlap", C.c_double)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("precision", C.c_int), ("schedule", C.c_int), ("timing", C.c_int), ("dd_slices_per_block", C.c_int),
+                ("reserved", C.c_int * 4)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("unknown_updates", C.c_double), ("ms_total", C.c_double),
+                ("ms_fine", C.c_double), ("ms_coarse", C.c_double), ("kernel_launches", C.c_int)]
+
+
+class _KTime(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int), ("ms", C.c_double), ("bytes", C.c_double),
+                ("flops", C.c_double)]
+
+
+_VP = C.c_void_p
+_I = C.c_int
+_D = C.c_double
+_U = C.c_uint64
+_IP = C.POINTER(C.c_int)
+
+# name -> argtypes (every entry point returns int status unless listed in _RESTYPE)
+SIGNATURES = {
+    "ps_last_error": [],
+    "ps_version": [],
+    "ps_grid_create": [_I, C.POINTER(C.c_int * 3), C.POINTER(_VP)],
+    "ps_grid_destroy": [_VP],
+    "ps_operator_create": [_VP, _VP, _D, _VP, _VP, _I, _U, C.POINTER(_VP)],
+    "ps_operator_destroy": [_VP],
+    "ps_splitting_create": [_VP, _I, C.POINTER(_DD), C.POINTER(_VP)],
+    "ps_splitting_destroy": [_VP],
+    "ps_problem_create": [_VP, _VP, _D, _I, _I, _I, C.POINTER(_Params), _U, C.POINTER(_VP)],
+    "ps_problem_destroy": [_VP],
+    "ps_run_parareal": [_VP, _VP, _D, _I, _U, _IP],
+    "ps_run_parareal_host": [_VP, _VP, _VP, _D, _I, _U, _IP],
+    "ps_get_state": [_VP, _I, _VP, _U],
+    "ps_get_history": [_VP, _VP, _I, _IP],
+    "ps_run_fine_sequential": [_VP, _VP, _VP, _U],
+    "ps_run_coarse_sequential": [_VP, _VP, _VP, _U],
+    "ps_substep_solve": [_VP, _I, _I, _VP, _U],
+    "ps_propagate": [_VP, _I, _I, _I, _I, _VP, _U],
+    "ps_problem_stats": [_VP, C.POINTER(_Stats)],
+    "ps_problem_kernel_times": [_VP, C.POINTER(_KTime), _I, _IP],
+}
+_RESTYPE = {"ps_last_error": C.c_char_p}
+
+
+def lib():
+    """Load libps.so (built by ``build.build()``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run paper_2502_08370_gb300.build.build())")
+            h = C.CDLL(LIB_PATH)
+            for name, args in SIGNATURES.items():
+                f = getattr(h, name)
+                f.argtypes = args
+                f.restype = _RESTYPE.get(name, C.c_int)
+            _lib = h
+    return _lib
+
+
+def check(rc):
+    if rc != PS_OK:
+        raise PsError(rc, lib().ps_last_error().decode())
+
+
+def _dev_ptr(t, n=None):
+    """Pointer of a contiguous float64 CUDA tensor (optionally checking its element count)."""
+    if t is None:
+        return None
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"expected {n} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Grid:
+    def __init__(self, n):
+        n = tuple(int(v) for v in n)
+        self.dim = len(n)
+        self.n = n
+        self.nt = 1
+        for v in n:
+            self.nt *= v
+        arr = (C.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+        h = _VP()
+        check(lib().ps_grid_create(self.dim, C.byref(arr), C.byref(h)))
+        self._h = h
+
+    @property
+    def shape(self):
+        return tuple(reversed(self.n))
+
+    @property
+    def nodal_size(self):
+        s = 1
+        for v in self.n:
+            s *= v + 2
+        return s
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().ps_grid_destroy(self._h)
+            self._h = None
+
+
+class Operator:
+    """u_t = div(a grad u) - c u + src(x) src_t(t); a nodal incl. boundary (None: a = 1)."""
+
+    def __init__(self, grid: Grid, a=None, c=0.0, src=None, src_t=None, stream=None):
+        import numpy as np
+        self.grid = grid
+        st = None
+        if src_t is not None:
+            st = np.ascontiguousarray(src_t, dtype=np.float64)
+        h = _VP()
+        check(lib().ps_operator_create(grid._h, _dev_ptr(a, grid.nodal_size), float(c), _dev_ptr(src, grid.nt),
+                                       None if st is None else st.ctypes.data_as(_VP), 0 if st is None else st.size,
+                                       _stream(stream), C.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().ps_operator_destroy(self._h)
+            self._h = None
+
+
+class Splitting:
+    def __init__(self, op: Operator, kind="dim", boxes=(1, 1), overlap=0.0):
+        self.op = op
+        dd = _DD((C.c_int * 2)(*boxes), float(overlap))
+        h = _VP()
+        check(lib().ps_splitting_create(op._h, PS_SPLIT_DIM if kind == "dim" else PS_SPLIT_DD, C.byref(dd),
+                                        C.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().ps_splitting_destroy(self._h)
+            self._h = None
+
+
+class Problem:
+    """Parareal problem: G = g FIE steps of T/(N g), F = s FIE steps of T/(N s) (Sec. 3)."""
+
+    def __init__(self, fine: Splitting, T, N, g, s, coarse: Splitting = None, precision="fp64",
+                 schedule=PS_SCHED_AUTO, timing=False, dd_slices_per_block=0, stream=None):
+        self.fine, self.coarse = fine, coarse
+        self.grid = fine.op.grid
+        self.N = int(N)
+        prm = _Params(PS_PREC_FP64 if precision == "fp64" else PS_PREC_MIXED, int(schedule), int(timing),
+                      int(dd_slices_per_block))
+        h = _VP()
+        check(lib().ps_problem_create(fine._h, None if coarse is None else coarse._h, float(T), int(N), int(g),
+                                      int(s), C.byref(prm), _stream(stream), C.byref(h)))
+        self._h = h
+
+    def run(self, u0, tol, max_iter=0, stream=None):
+        it = C.c_int(0)
+        check(lib().ps_run_parareal(self._h, _dev_ptr(u0, self.grid.nt), float(tol), int(max_iter), _stream(stream),
+                                    C.byref(it)))
+        return it.value
+
+    def run_host(self, u0_host, uN_host, tol, max_iter=0, stream=None):
+        """u0_host/uN_host: contiguous float64 CPU tensors (pinned for async copies)."""
+        it = C.c_int(0)
+        check(lib().ps_run_parareal_host(self._h, C.c_void_p(u0_host.data_ptr()), C.c_void_p(uN_host.data_ptr()),
+                                         float(tol), int(max_iter), _stream(stream), C.byref(it)))
+        return it.value
+
+    def state(self, n, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.grid.shape, dtype=torch.float64, device="cuda")
+        check(lib().ps_get_state(self._h, int(n), _dev_ptr(out, self.grid.nt), _stream(stream)))
+        return out
+
+    def history(self):
+        import numpy as np
+        buf = np.zeros(max(self.N, 1))
+        ln = C.c_int(0)
+        check(lib().ps_get_history(self._h, buf.ctypes.data_as(_VP), buf.size, C.byref(ln)))
+        return buf[:ln.value].copy()
+
+    def fine_sequential(self, u0, stream=None):
+        import torch
+        out = torch.empty((self.N + 1,) + self.grid.shape, dtype=torch.float64, device="cuda")
+        check(lib().ps_run_fine_sequential(self._h, _dev_ptr(u0, self.grid.nt), _dev_ptr(out), _stream(stream)))
+        return out
+
+    def coarse_sequential(self, u0, stream=None):
+        import torch
+        out = torch.empty((self.N + 1,) + self.grid.shape, dtype=torch.float64, device="cuda")
+        check(lib().ps_run_coarse_sequential(self._h, _dev_ptr(u0, self.grid.nt), _dev_ptr(out), _stream(stream)))
+        return out
+
+    def substep_solve(self, which, m, x, stream=None):
+        check(lib().ps_substep_solve(self._h, int(which), int(m), _dev_ptr(x, self.grid.nt), _stream(stream)))
+        return x
+
+    def propagate(self, which, nsteps, x, t0=0, tstride=1, stream=None):
+        check(lib().ps_propagate(self._h, int(which), int(nsteps), int(t0), int(tstride), _dev_ptr(x, self.grid.nt),
+                                 _stream(stream)))
+        return x
+
+    def stats(self):
+        s = _Stats()
+        check(lib().ps_problem_stats(self._h, C.byref(s)))
+        return dict(iterations=s.iterations, unknown_updates=s.unknown_updates, ms_total=s.ms_total,
+                    ms_fine=s.ms_fine, ms_coarse=s.ms_coarse, kernel_launches=s.kernel_launches)
+
+    def kernel_times(self):
+        """Per-kernel-kind times of the last run (needs timing=2): name -> dict."""
+        buf = (_KTime * 64)()
+        ln = C.c_int(0)
+        check(lib().ps_problem_kernel_times(self._h, buf, 64, C.byref(ln)))
+        return {buf[i].name.decode(): dict(launches=buf[i].launches, ms=buf[i].ms, bytes=buf[i].bytes,
+                                           flops=buf[i].flops) for i in range(ln.value)}
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().ps_problem_destroy(self._h)
+            self._h = None

@@ -1,0 +1,676 @@
+// ps_capi.cu -- handles, the parareal driver and the C ABI declared in include/ps.h.
+//
+// Parareal (Sec. 3) with FIE propagators (Sec. 2.2, eq. FIE_method):
+//   U_0 = u0,  U_{n+1}^0 = G(U_n^0),
+//   U_{n+1}^k = F(U_n^{k-1}) + (G(U_n^k) - G(U_n^{k-1})),  k = 1, 2, ...
+// F of every slice runs in one batched launch per substep (all slices at once); the
+// coarse chain runs slice after slice with the correction fused into its last sweep.
+// Finite termination (Sec. 3): U_n^k = U_n^{k-1} for n <= k-1, so the correction of
+// slice k-1 has an exactly zero bracket and slices n < k-1 are unchanged; the driver
+// skips that work, which leaves every value bitwise as the full iteration computes it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "ps_dd.h"
+
+using namespace ps;
+
+struct ps_grid {
+  Geom g;
+};
+
+struct ps_operator {
+  const ps_grid* grid = nullptr;
+  DevBuf<double> a;
+  DevBuf<double> src;
+  DevBuf<double> src_t;
+  int src_t_len = 0;
+  double c = 0.0;
+};
+
+struct ps_splitting {
+  const ps_operator* op = nullptr;
+  int kind = PS_SPLIT_DIM;
+  ps_dd_params dd{};
+  int M = 0;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    f();
+    return PS_OK;
+  } catch (const Error& e) {
+    return fail(e.code, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(PS_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(PS_ERR_INVALID, e.what());
+  }
+}
+
+inline cudaStream_t S(uintptr_t s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// One propagator: `steps` FIE steps of size tau per slice; step q of slice n ends at fine
+// time index n*s + (q+1)*tstride.
+struct Prop {
+  const ps_splitting* sp = nullptr;
+  double tau = 0.0;
+  int steps = 1;
+  int tstride = 1;
+  bool f32 = false;
+  std::vector<std::unique_ptr<LineFactors>> dim;
+  std::unique_ptr<DDFactors> dd;
+};
+
+// Per-launch CUDA events around the library's kernels (params.timing == 2), resolved at
+// the host synchronisation points and summed per kernel kind.
+struct KernelTimer {
+  struct Kind {
+    std::string name;
+    int launches = 0;
+    double ms = 0.0, bytes = 0.0, flops = 0.0;
+  };
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  struct Mark {
+    int kind;
+    double bytes, flops;
+  };
+  std::vector<Mark> marks;
+  std::vector<Kind> kinds;
+  cudaStream_t st = nullptr;
+  ~KernelTimer() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+  int kind_id(const std::string& name) {
+    for (size_t i = 0; i < kinds.size(); ++i)
+      if (kinds[i].name == name) return (int)i;
+    kinds.push_back(Kind{name});
+    return (int)kinds.size() - 1;
+  }
+  void begin(cudaStream_t s) {
+    if (!on) return;
+    st = s;
+    size_t need = 2 * (marks.size() + 1);
+    while (pool.size() < need) {
+      cudaEvent_t e;
+      PS_CUDA(cudaEventCreate(&e));
+      pool.push_back(e);
+    }
+    PS_CUDA(cudaEventRecord(pool[2 * marks.size()], s));
+  }
+  void end(const std::string& name, double bytes, double flops) {
+    if (!on) return;
+    PS_CUDA(cudaEventRecord(pool[2 * marks.size() + 1], st));
+    marks.push_back(Mark{kind_id(name), bytes, flops});
+  }
+  // call after the stream was synchronised
+  void resolve() {
+    for (size_t i = 0; i < marks.size(); ++i) {
+      float ms = 0.f;
+      PS_CUDA(cudaEventElapsedTime(&ms, pool[2 * i], pool[2 * i + 1]));
+      Kind& k = kinds[marks[i].kind];
+      k.launches++;
+      k.ms += ms;
+      k.bytes += marks[i].bytes;
+      k.flops += marks[i].flops;
+    }
+    marks.clear();
+  }
+  void reset() {
+    marks.clear();
+    kinds.clear();
+  }
+};
+
+}  // namespace
+
+struct ps_problem {
+  const ps_splitting* fine = nullptr;
+  const ps_splitting* coarse = nullptr;
+  const ps_operator* op = nullptr;
+  Geom g;
+  double T = 1.0;
+  int N = 1, gs = 1, fs = 1;
+  ps_params prm{};
+  Prop F, G;
+  DevBuf<double> U, Fout, Gold, gtmp;
+  DevBuf<float> W;
+  DevBuf<unsigned long long> inc;
+  DevBuf<int> flag;
+  unsigned long long* h_inc = nullptr;
+  int* h_flag = nullptr;
+  std::vector<double> hist;
+  int iters = 0;
+  double updates = 0.0;
+  int launches = 0;
+  float ms_total = 0, ms_fine = 0, ms_coarse = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  KernelTimer kt;
+  ~ps_problem() {
+    if (h_inc) cudaFreeHost(h_inc);
+    if (h_flag) cudaFreeHost(h_flag);
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+void build_prop(ps_problem* p, Prop& P, const ps_splitting* sp, double tau, int steps, int tstride, bool f32,
+                cudaStream_t st) {
+  P.sp = sp;
+  P.tau = tau;
+  P.steps = steps;
+  P.tstride = tstride;
+  P.f32 = f32;
+  const ps_operator* op = sp->op;
+  if (sp->kind == PS_SPLIT_DIM) {
+    for (int m = 0; m < p->g.dim; ++m) {
+      auto f = std::make_unique<LineFactors>();
+      factor_dim(p->g, m, op->a.p, op->c / p->g.dim, tau, *f, f32, st);
+      P.dim.push_back(std::move(f));
+    }
+  } else {
+    if (f32) throw Error(PS_ERR_UNSUPPORTED, "DD splitting runs in FP64 only");
+    P.dd = std::make_unique<DDFactors>();
+    dd_factor(p->g, sp->dd, op->a.p, op->c, tau, *P.dd, st);
+  }
+}
+
+SourceArgs source_for(const ps_problem* p, const Prop& P, int t0, int tslice) {
+  SourceArgs sa;
+  if (!p->op->src.p) return sa;
+  sa.src = p->op->src.p;
+  sa.src_t = p->op->src_t.p;
+  sa.t0 = t0;
+  sa.tstride = tslice;
+  sa.tau = P.tau;
+  return sa;
+}
+
+// One FP64 FIE step of propagator P on nsl consecutive states: in -> out (out may alias in).
+// The source of slice j of the launch is taken at fine time index t0 + j*tslice.  When
+// corr.mode != 0 the last sweep of the step carries the parareal correction instead of
+// writing out.
+const char* kAxis[3] = {"x", "y", "z"};
+
+// Algorithmic bytes and flops of one sweep launch: read the right-hand side, write the
+// result (bytes_in + bytes_out per unknown), read the factors once (they are shared by all
+// slices of the launch), read the source when it is added, and for the fused correction
+// read Fout, Gold and U_{n+1} and write Gold and U_{n+1}.  Flops: 5 per unknown (FMA
+// forward, MUL + FMA backward, FMA = 2) plus 2 for the source.
+void sweep_cost(const ps_problem* p, const LineFactors& f, int nsl, int bin, int bout, int bc, bool src, int corr,
+                double* bytes, double* flops) {
+  const double nt = (double)p->g.nt;
+  double b = nsl * nt * (bin + bout);
+  b += (f.var ? nt : (double)p->g.n[f.m]) * 2.0 * bc;
+  if (src) b += nt * 8.0;
+  if (corr == 1) b += nt * 40.0 - nsl * nt * bout;
+  if (corr == 2) b += nt * 16.0 - nsl * nt * bout;
+  *bytes = b;
+  *flops = nsl * nt * (5.0 + (src ? 2.0 : 0.0));
+}
+
+// DD step: right-hand side (and copy in -> out), the colour solves in place, and the
+// correction as a separate pass over the slice (it touches every node, not only boxes).
+void fie_step_dd(ps_problem* p, Prop& P, int nsl, const double* in, double* out, int t0, int tslice,
+                 const CorrArgs& corr, cudaStream_t st, const char* phase) {
+  const int M = P.sp->M;
+  const double nt = (double)p->g.nt;
+  SourceArgs sa = source_for(p, P, t0, tslice);
+  if (in != out || sa.src) {
+    p->kt.begin(st);
+    dd_rhs(p->g, nsl, in, out, sa, st);
+    if (p->kt.on) p->kt.end(std::string(phase) + ".rhs.f64", nsl * nt * 16.0 + (sa.src ? nt * 8.0 : 0.0), 0.0);
+    p->launches++;
+  }
+  const int spb = p->prm.dd_slices_per_block > 0 ? p->prm.dd_slices_per_block : 2;
+  for (int c = 0; c < M; ++c) {
+    p->kt.begin(st);
+    dd_solve(p->g, nsl, *P.dd, c, out, spb, st);
+    if (p->kt.on) {
+      const auto& pl = P.dd->plan;
+      const double w = pl.nodes[c] > 0 ? pl.fac_entries[c] / (2.0 * pl.nodes[c]) - 1.0 : 0.0;
+      p->kt.end(std::string(phase) + ".dd" + std::to_string(c) + ".f64", nsl * pl.nodes[c] * 16.0 + pl.fac_entries[c] * 8.0,
+                nsl * pl.nodes[c] * 4.0 * w);
+    }
+    p->launches++;
+  }
+  if (corr.mode != 0) {
+    p->kt.begin(st);
+    dd_correct(p->g, out, corr, st);
+    if (p->kt.on) p->kt.end(std::string(phase) + (corr.mode == 1 ? ".corr.f64" : ".init.f64"), nt * 48.0, 0.0);
+    p->launches++;
+  }
+}
+
+void fie_step64(ps_problem* p, Prop& P, int nsl, const double* in, double* out, int t0, int tslice,
+                const CorrArgs& corr, cudaStream_t st, const char* phase) {
+  if (P.sp->kind == PS_SPLIT_DD) {
+    fie_step_dd(p, P, nsl, in, out, t0, tslice, corr, st, phase);
+    return;
+  }
+  const int M = P.sp->M;
+  for (int m = 0; m < M; ++m) {
+    SourceArgs sa = m == 0 ? source_for(p, P, t0, tslice) : SourceArgs{};
+    const double* src_state = m == 0 ? in : out;
+    const bool epi = (m == M - 1 && corr.mode != 0);
+    double bytes = 0, flops = 0;
+    if (p->kt.on) sweep_cost(p, *P.dim[m], nsl, 8, 8, 8, sa.src != nullptr, epi ? corr.mode : 0, &bytes, &flops);
+    p->kt.begin(st);
+    if (epi)
+      sweep_dim<double, double>(p->g, nsl, *P.dim[m], false, src_state, out, sa, corr, out, st);
+    else
+      sweep_dim<double, double>(p->g, nsl, *P.dim[m], false, src_state, out, sa, CorrArgs{}, nullptr, st);
+    if (p->kt.on)
+      p->kt.end(std::string(phase) + "." + kAxis[m] + ".f64" + (epi ? (corr.mode == 1 ? "+corr" : "+init") : ""),
+                bytes, flops);
+    p->launches++;
+  }
+}
+
+// F (s fine steps) on nsl consecutive slices starting at absolute slice n_first.
+void run_F(ps_problem* p, int n_first, int nsl, const double* in, double* out, cudaStream_t st) {
+  Prop& P = p->F;
+  const int M = P.sp->M;
+  if (!P.f32) {
+    for (int j = 0; j < P.steps; ++j)
+      fie_step64(p, P, nsl, j == 0 ? in : out, out, n_first * p->fs + (j + 1) * P.tstride, p->fs, CorrArgs{}, st,
+                 "F");
+  } else {
+    float* W = p->W.p;
+    for (int j = 0; j < P.steps; ++j) {
+      for (int m = 0; m < M; ++m) {
+        const bool first = (j == 0 && m == 0), last = (j == P.steps - 1 && m == M - 1);
+        SourceArgs sa = m == 0 ? source_for(p, P, n_first * p->fs + (j + 1) * P.tstride, p->fs) : SourceArgs{};
+        const LineFactors& f = *P.dim[m];
+        double bytes = 0, flops = 0;
+        if (p->kt.on) sweep_cost(p, f, nsl, first ? 8 : 4, last ? 8 : 4, 4, sa.src != nullptr, 0, &bytes, &flops);
+        p->kt.begin(st);
+        if (first && last) sweep_dim<double, double>(p->g, nsl, f, true, in, out, sa, CorrArgs{}, nullptr, st);
+        else if (first) sweep_dim<double, float>(p->g, nsl, f, true, in, W, sa, CorrArgs{}, nullptr, st);
+        else if (last) sweep_dim<float, double>(p->g, nsl, f, true, W, out, sa, CorrArgs{}, nullptr, st);
+        else sweep_dim<float, float>(p->g, nsl, f, true, W, W, sa, CorrArgs{}, nullptr, st);
+        if (p->kt.on) p->kt.end(std::string("F.") + kAxis[m] + ".f32", bytes, flops);
+        p->launches++;
+      }
+    }
+  }
+  p->updates += (double)nsl * P.steps * (double)p->g.nt;
+}
+
+// G on slice n from `in`; the last sweep carries `corr` (mode 0: result left in gtmp).
+void run_G(ps_problem* p, int n, const double* in, const CorrArgs& corr, cudaStream_t st) {
+  Prop& P = p->G;
+  for (int q = 0; q < P.steps; ++q) {
+    CorrArgs c = (q == P.steps - 1) ? corr : CorrArgs{};
+    fie_step64(p, P, 1, q == 0 ? in : p->gtmp.p, p->gtmp.p, n * p->fs + (q + 1) * P.tstride, 0, c, st, "G");
+  }
+  p->updates += (double)P.steps * (double)p->g.nt;
+}
+
+CorrArgs corr_args(ps_problem* p, int mode, int n) {
+  CorrArgs c;
+  c.mode = mode;
+  const long long nt = p->g.nt;
+  c.U_next = p->U.p + (n + 1) * nt;
+  c.Fout = p->Fout.p + n * nt;
+  c.Gold = p->Gold.p + n * nt;
+  c.inc = p->inc.p;
+  c.nonfinite = p->flag.p;
+  return c;
+}
+
+void check_state_len(const ps_problem* p, int slice) {
+  PS_REQUIRE(slice >= 0 && slice <= p->N, "slice out of range");
+}
+
+void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStream_t st, int* iters_out) {
+  const long long nt = p->g.nt;
+  const int N = p->N;
+  if (max_iter <= 0 || max_iter > N) max_iter = N;
+  p->hist.clear();
+  p->updates = 0;
+  p->launches = 0;
+  p->ms_total = p->ms_fine = p->ms_coarse = 0;
+  const bool timing = p->prm.timing != 0;
+  p->kt.on = p->prm.timing >= 2;
+  p->kt.reset();
+  if (timing) PS_CUDA(cudaEventRecord(p->ev[0], st));
+  PS_CUDA(cudaMemcpyAsync(p->U.p, u0, sizeof(double) * nt, cudaMemcpyDeviceToDevice, st));
+  PS_CUDA(cudaMemsetAsync(p->flag.p, 0, sizeof(int), st));
+  // k = 0: sequential coarse sweep, U_{n+1}^0 = G(U_n^0), Gold_n = G(U_n^0)
+  for (int n = 0; n < N; ++n) run_G(p, n, p->U.p + n * nt, corr_args(p, 2, n), st);
+  int k = 0;
+  while (k < max_iter) {
+    ++k;
+    const int nlo = k - 1;
+    PS_CUDA(cudaMemsetAsync(p->inc.p, 0, sizeof(unsigned long long), st));
+    if (timing) PS_CUDA(cudaEventRecord(p->ev[1], st));
+    run_F(p, nlo, N - nlo, p->U.p + nlo * nt, p->Fout.p + nlo * nt, st);
+    if (timing) PS_CUDA(cudaEventRecord(p->ev[2], st));
+    // slice k-1: U_k^k = F(U_{k-1}^{k-1}) exactly (its G bracket is zero)
+    copy_with_increment(nt, p->Fout.p + nlo * nt, p->U.p + k * nt, p->inc.p, p->flag.p, st);
+    p->launches++;
+    for (int n = k; n < N; ++n) run_G(p, n, p->U.p + n * nt, corr_args(p, 1, n), st);
+    if (timing) PS_CUDA(cudaEventRecord(p->ev[3], st));
+    PS_CUDA(cudaMemcpyAsync(p->h_inc, p->inc.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaMemcpyAsync(p->h_flag, p->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    p->kt.resolve();
+    if (timing) {
+      float a = 0, b = 0;
+      PS_CUDA(cudaEventElapsedTime(&a, p->ev[1], p->ev[2]));
+      PS_CUDA(cudaEventElapsedTime(&b, p->ev[2], p->ev[3]));
+      p->ms_fine += a;
+      p->ms_coarse += b;
+    }
+    double inc;
+    unsigned long long bits = *p->h_inc;
+    std::memcpy(&inc, &bits, sizeof inc);
+    p->hist.push_back(inc);
+    if (*p->h_flag) {
+      p->iters = k;
+      throw Error(PS_ERR_NONFINITE, "non-finite value in the parareal correction at iteration " + std::to_string(k));
+    }
+    if (inc < tol) break;
+  }
+  if (timing) {
+    PS_CUDA(cudaEventRecord(p->ev[1], st));
+    PS_CUDA(cudaEventSynchronize(p->ev[1]));
+    PS_CUDA(cudaEventElapsedTime(&p->ms_total, p->ev[0], p->ev[1]));
+  }
+  p->iters = k;
+  if (iters_out) *iters_out = k;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ps_last_error(void) { return g_last_error.c_str(); }
+int ps_version(void) { return 100; }
+
+int ps_grid_create(int dim, const int n[3], ps_grid** out) {
+  return guarded([&] {
+    PS_REQUIRE(out && n, "null argument");
+    PS_REQUIRE(dim == 2 || dim == 3, "dim must be 2 or 3");
+    auto g = std::make_unique<ps_grid>();
+    g->g.dim = dim;
+    long long nt = 1;
+    for (int d = 0; d < 3; ++d) {
+      int v = d < dim ? n[d] : 1;
+      PS_REQUIRE(v >= 1 && v <= (1 << 20), "grid size out of range");
+      g->g.n[d] = v;
+      nt *= v;
+    }
+    g->g.nt = nt;
+    *out = g.release();
+  });
+}
+
+int ps_grid_destroy(ps_grid* g) {
+  delete g;
+  return PS_OK;
+}
+
+int ps_operator_create(const ps_grid* g, const double* a_nodal_dev, double c, const double* src_dev,
+                       const double* src_t_host, int src_t_len, uintptr_t stream, ps_operator** out) {
+  return guarded([&] {
+    PS_REQUIRE(g && out, "null argument");
+    PS_REQUIRE(c >= 0.0 && std::isfinite(c), "c must be finite and >= 0");
+    PS_REQUIRE(!src_t_host || src_t_len > 0, "src_t_len must be positive");
+    auto op = std::make_unique<ps_operator>();
+    op->grid = g;
+    op->c = c;
+    cudaStream_t st = S(stream);
+    const Geom& G = g->g;
+    if (a_nodal_dev) {
+      long long na = (long long)(G.n[0] + 2) * (G.n[1] + 2) * (G.dim == 3 ? G.n[2] + 2 : 1);
+      op->a.alloc(na);
+      PS_CUDA(cudaMemcpyAsync(op->a.p, a_nodal_dev, sizeof(double) * na, cudaMemcpyDeviceToDevice, st));
+    }
+    if (src_dev) {
+      op->src.alloc(G.nt);
+      PS_CUDA(cudaMemcpyAsync(op->src.p, src_dev, sizeof(double) * G.nt, cudaMemcpyDeviceToDevice, st));
+      if (src_t_host) {
+        op->src_t.alloc(src_t_len);
+        op->src_t_len = src_t_len;
+        PS_CUDA(cudaMemcpyAsync(op->src_t.p, src_t_host, sizeof(double) * src_t_len, cudaMemcpyHostToDevice, st));
+      }
+    }
+    PS_CUDA(cudaStreamSynchronize(st));
+    *out = op.release();
+  });
+}
+
+int ps_operator_destroy(ps_operator* op) {
+  delete op;
+  return PS_OK;
+}
+
+int ps_splitting_create(const ps_operator* op, int kind, const ps_dd_params* dd, ps_splitting** out) {
+  return guarded([&] {
+    PS_REQUIRE(op && out, "null argument");
+    auto sp = std::make_unique<ps_splitting>();
+    sp->op = op;
+    sp->kind = kind;
+    const Geom& G = op->grid->g;
+    if (kind == PS_SPLIT_DIM) {
+      sp->M = G.dim;
+    } else if (kind == PS_SPLIT_DD) {
+      PS_REQUIRE(dd, "DD splitting needs ps_dd_params");
+      if (G.dim != 2) throw Error(PS_ERR_UNSUPPORTED, "DD splitting is implemented in 2-D");
+      PS_REQUIRE(dd->boxes[0] >= 1 && dd->boxes[1] >= 1, "boxes must be >= 1");
+      PS_REQUIRE(dd->overlap >= 0.0, "overlap must be >= 0");
+      sp->dd = *dd;
+      sp->M = (dd->boxes[0] > 1 ? 2 : 1) * (dd->boxes[1] > 1 ? 2 : 1);
+    } else {
+      throw Error(PS_ERR_INVALID, "unknown splitting kind");
+    }
+    *out = sp.release();
+  });
+}
+
+int ps_splitting_destroy(ps_splitting* sp) {
+  delete sp;
+  return PS_OK;
+}
+
+int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, double T, int N, int g_steps,
+                      int f_steps, const ps_params* params, uintptr_t stream, ps_problem** out) {
+  return guarded([&] {
+    PS_REQUIRE(fine && out, "null argument");
+    if (!coarse) coarse = fine;
+    PS_REQUIRE(coarse->op == fine->op, "coarse and fine splittings must share the operator");
+    PS_REQUIRE(T > 0 && std::isfinite(T), "T must be positive");
+    PS_REQUIRE(N >= 1 && g_steps >= 1 && f_steps >= 1, "N, g_steps, f_steps must be >= 1");
+    PS_REQUIRE(f_steps % g_steps == 0, "f_steps must be a multiple of g_steps");
+    auto p = std::make_unique<ps_problem>();
+    p->fine = fine;
+    p->coarse = coarse;
+    p->op = fine->op;
+    p->g = fine->op->grid->g;
+    p->T = T;
+    p->N = N;
+    p->gs = g_steps;
+    p->fs = f_steps;
+    if (params) p->prm = *params;
+    PS_REQUIRE(p->prm.precision == PS_PREC_FP64 || p->prm.precision == PS_PREC_MIXED, "unknown precision");
+    if (p->op->src_t.p)
+      PS_REQUIRE(p->op->src_t_len >= N * f_steps + 1, "src_t must cover the fine times 0..N*f_steps");
+    cudaStream_t st = S(stream);
+    const bool mixed = p->prm.precision == PS_PREC_MIXED;
+    build_prop(p.get(), p->F, fine, T / N / f_steps, f_steps, 1, mixed, st);
+    build_prop(p.get(), p->G, coarse, T / N / g_steps, g_steps, f_steps / g_steps, false, st);
+    const long long nt = p->g.nt;
+    p->U.alloc((size_t)(N + 1) * nt);
+    p->Fout.alloc((size_t)N * nt);
+    p->Gold.alloc((size_t)N * nt);
+    p->gtmp.alloc((size_t)nt);
+    if (mixed) p->W.alloc((size_t)N * nt);
+    p->inc.alloc(1);
+    p->flag.alloc(1);
+    PS_CUDA(cudaMallocHost(&p->h_inc, sizeof(unsigned long long)));
+    PS_CUDA(cudaMallocHost(&p->h_flag, sizeof(int)));
+    for (auto& e : p->ev) PS_CUDA(cudaEventCreate(&e));
+    PS_CUDA(cudaStreamSynchronize(st));
+    *out = p.release();
+  });
+}
+
+int ps_problem_destroy(ps_problem* p) {
+  delete p;
+  return PS_OK;
+}
+
+int ps_run_parareal(ps_problem* p, const double* u0_dev, double tol, int max_iter, uintptr_t stream,
+                    int* iters_out) {
+  return guarded([&] {
+    PS_REQUIRE(p && u0_dev, "null argument");
+    do_run(p, u0_dev, tol, max_iter, S(stream), iters_out);
+  });
+}
+
+int ps_run_parareal_host(ps_problem* p, const double* u0_host, double* uN_host, double tol, int max_iter,
+                         uintptr_t stream, int* iters_out) {
+  return guarded([&] {
+    PS_REQUIRE(p && u0_host && uN_host, "null argument");
+    cudaStream_t st = S(stream);
+    const long long nt = p->g.nt;
+    // u0 is staged in the coarse scratch state, which the run copies to U_0 before using it
+    PS_CUDA(cudaMemcpyAsync(p->gtmp.p, u0_host, sizeof(double) * nt, cudaMemcpyHostToDevice, st));
+    do_run(p, p->gtmp.p, tol, max_iter, st, iters_out);
+    PS_CUDA(cudaMemcpyAsync(uN_host, p->U.p + (long long)p->N * nt, sizeof(double) * nt, cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+int ps_get_state(const ps_problem* p, int slice, double* out_dev, uintptr_t stream) {
+  return guarded([&] {
+    PS_REQUIRE(p && out_dev, "null argument");
+    check_state_len(p, slice);
+    const long long nt = p->g.nt;
+    PS_CUDA(cudaMemcpyAsync(out_dev, p->U.p + slice * nt, sizeof(double) * nt, cudaMemcpyDeviceToDevice, S(stream)));
+  });
+}
+
+int ps_get_history(const ps_problem* p, double* inc_host, int cap, int* len) {
+  return guarded([&] {
+    PS_REQUIRE(p && len, "null argument");
+    int n = std::min<int>(cap, (int)p->hist.size());
+    for (int i = 0; i < n; ++i) inc_host[i] = p->hist[i];
+    *len = n;
+  });
+}
+
+int ps_run_fine_sequential(ps_problem* p, const double* u0_dev, double* U_out_dev, uintptr_t stream) {
+  return guarded([&] {
+    PS_REQUIRE(p && u0_dev && U_out_dev, "null argument");
+    cudaStream_t st = S(stream);
+    const long long nt = p->g.nt;
+    p->updates = 0;
+    p->launches = 0;
+    PS_CUDA(cudaMemcpyAsync(U_out_dev, u0_dev, sizeof(double) * nt, cudaMemcpyDeviceToDevice, st));
+    for (int n = 0; n < p->N; ++n) run_F(p, n, 1, U_out_dev + n * nt, U_out_dev + (n + 1) * nt, st);
+    PS_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+int ps_run_coarse_sequential(ps_problem* p, const double* u0_dev, double* U_out_dev, uintptr_t stream) {
+  return guarded([&] {
+    PS_REQUIRE(p && u0_dev && U_out_dev, "null argument");
+    cudaStream_t st = S(stream);
+    const long long nt = p->g.nt;
+    PS_CUDA(cudaMemcpyAsync(U_out_dev, u0_dev, sizeof(double) * nt, cudaMemcpyDeviceToDevice, st));
+    for (int n = 0; n < p->N; ++n) {
+      run_G(p, n, U_out_dev + n * nt, CorrArgs{}, st);
+      PS_CUDA(cudaMemcpyAsync(U_out_dev + (n + 1) * nt, p->gtmp.p, sizeof(double) * nt, cudaMemcpyDeviceToDevice, st));
+    }
+    PS_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+int ps_substep_solve(ps_problem* p, int which, int m, double* x_dev, uintptr_t stream) {
+  return guarded([&] {
+    PS_REQUIRE(p && x_dev, "null argument");
+    PS_REQUIRE(which == 0 || which == 1, "which must be 0 (fine) or 1 (coarse)");
+    Prop& P = which == 0 ? p->F : p->G;
+    PS_REQUIRE(m >= 0 && m < P.sp->M, "substep out of range");
+    if (P.sp->kind == PS_SPLIT_DD) {
+      dd_solve(p->g, 1, *P.dd, m, x_dev, 1, S(stream));
+      return;
+    }
+    sweep_dim<double, double>(p->g, 1, *P.dim[m], P.f32, x_dev, x_dev, SourceArgs{}, CorrArgs{}, nullptr, S(stream));
+  });
+}
+
+int ps_propagate(ps_problem* p, int which, int nsteps, int t0, int tstride, double* x_dev, uintptr_t stream) {
+  return guarded([&] {
+    PS_REQUIRE(p && x_dev && nsteps >= 0, "bad argument");
+    PS_REQUIRE(which == 0 || which == 1, "which must be 0 (fine) or 1 (coarse)");
+    Prop& P = which == 0 ? p->F : p->G;
+    if (p->op->src_t.p)
+      PS_REQUIRE(t0 >= 0 && t0 + (long long)nsteps * tstride < p->op->src_t_len, "time index outside src_t");
+    cudaStream_t st = S(stream);
+    for (int q = 0; q < nsteps; ++q) {
+      const int te = t0 + (q + 1) * tstride;
+      if (!P.f32) {
+        fie_step64(p, P, 1, x_dev, x_dev, te, 0, CorrArgs{}, st, which == 0 ? "F" : "G");
+      } else {
+        for (int m = 0; m < P.sp->M; ++m) {
+          SourceArgs sa = m == 0 ? source_for(p, P, te, 0) : SourceArgs{};
+          sweep_dim<double, double>(p->g, 1, *P.dim[m], true, x_dev, x_dev, sa, CorrArgs{}, nullptr, st);
+        }
+      }
+    }
+  });
+}
+
+int ps_problem_stats(const ps_problem* p, ps_stats* out) {
+  return guarded([&] {
+    PS_REQUIRE(p && out, "null argument");
+    out->iterations = p->iters;
+    out->unknown_updates = p->updates;
+    out->ms_total = p->ms_total;
+    out->ms_fine = p->ms_fine;
+    out->ms_coarse = p->ms_coarse;
+    out->kernel_launches = p->launches;
+  });
+}
+
+int ps_problem_kernel_times(const ps_problem* p, ps_kernel_time* out, int cap, int* len) {
+  return guarded([&] {
+    PS_REQUIRE(p && len && (out || cap == 0), "null argument");
+    int n = std::min<int>(cap, (int)p->kt.kinds.size());
+    for (int i = 0; i < n; ++i) {
+      const auto& k = p->kt.kinds[i];
+      std::memset(out[i].name, 0, sizeof out[i].name);
+      std::strncpy(out[i].name, k.name.c_str(), sizeof out[i].name - 1);
+      out[i].launches = k.launches;
+      out[i].ms = k.ms;
+      out[i].bytes = k.bytes;
+      out[i].flops = k.flops;
+    }
+    *len = n;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,54 @@
+// ps_dd.h -- internal declarations of the domain-decomposition splitting (ps_dd.cu).
+#pragma once
+
+#include <vector>
+
+#include "ps_internal.h"
+
+namespace ps {
+
+// One box of a colour: nodes [x0, x0+wx) x [y0, y0+wy) (1-based interior indices), ordered
+// with the shorter extent fastest; lead = that extent = the half-bandwidth of its block.
+struct DDBox {
+  int bx, by;         // box indices; colour = (bx % 2) + (Bx > 1 ? 2 : 1) * (by % 2)
+  int x0, y0;         // first node
+  int xfast;          // 1: x fastest (lead = wx), 0: y fastest (lead = wy)
+  int lead;           // half-bandwidth
+  int n;              // nodes in the box
+  int pad;
+  long long offset;   // of the box's factors in DDFactors::fac (2 * n * (lead + 1) doubles)
+};
+
+struct DDGeomArgs {
+  int nx, ny, Bx, By;
+  const double* a;    // nodal coefficient or null
+  double c, tau, overlap;
+};
+
+struct DDPlan {
+  int M = 0;
+  int max_lead = 0;
+  long long fac_len = 0;
+  std::vector<std::vector<DDBox>> colours;
+  std::vector<double> nodes, fac_entries;  // per colour: box nodes, factor doubles
+};
+
+struct DDFactors {
+  DDPlan plan;
+  double tau = 0.0;
+  DevBuf<double> fac;
+  DevBuf<int> status;
+  std::vector<DevBuf<DDBox>> dev_boxes;
+  DDFactors() = default;
+  DDFactors(const DDFactors&) = delete;
+};
+
+void dd_plan(const Geom& g, const ps_dd_params& dd, DDPlan& plan);
+void dd_factor(const Geom& g, const ps_dd_params& dd, const double* a_nodal, double c, double tau, DDFactors& f,
+               cudaStream_t st);
+void dd_solve(const Geom& g, int nslices, const DDFactors& f, int colour, double* state, int slices_per_block,
+              cudaStream_t st);
+void dd_rhs(const Geom& g, int nslices, const double* in, double* out, const SourceArgs& sa, cudaStream_t st);
+void dd_correct(const Geom& g, const double* gstate, const CorrArgs& ca, cudaStream_t st);
+
+}  // namespace ps

@@ -1,0 +1,351 @@
+// ps_dim.cu -- dimensional-splitting kernels: substep factor setup, batched line solves
+// with the fused right-hand side and the fused parareal correction.
+//
+// One substep of eq. FIE_method (Sec. 2.2) solves (I - tau A_m) x = b where, with the
+// dimensional splitting of Sec. 2.1, A_m couples only nodes on a line along x_m: every
+// line is an independent symmetric tridiagonal system (Sec. 2.2: "essentially
+// one-dimensional uncoupled systems").  We factor each line once per step size as
+// L D L^T (setup, FP64) and solve with two recurrences:
+//     forward   y_i = b_i - l_i y_{i-1}
+//     backward  x_i = r_i y_i - l_{i+1} x_{i+1},        r_i = 1/D_i
+// All time slices are solved in one launch: the batch is (slice x line).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "ps_internal.h"
+
+namespace ps {
+namespace {
+
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------------------
+// a1: LDL^T factors of (I - tau A_m) along every line of direction m.
+// Row i of the line: diag 1 + tau (a_{i-1/2} + a_{i+1/2}) / h^2 + tau c/M,
+// off-diagonal (i, i+1) = -tau a_{i+1/2} / h^2, a_{i+1/2} = (a_i + a_{i+1}) / 2 (nodal a).
+// One thread per line; lines = 1 when the coefficients are constant (var = 0).
+__global__ void factor_dim_kernel(int dim, int nx, int ny, int nz, int m, const double* __restrict__ a,
+                                  double cM, double tau, double* __restrict__ l, double* __restrict__ r,
+                                  float* __restrict__ l32, float* __restrict__ r32, long long lines, int var) {
+  long long L = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= lines) return;
+  const int nm = m == 0 ? nx : (m == 1 ? ny : nz);
+  const long long S = m == 0 ? 1LL : (m == 1 ? (long long)nx : (long long)nx * ny);
+  const long long base = (m == 0) ? L * nx : (L / S) * S * nm + (L % S);
+  const int x0 = (int)(base % nx);
+  const long long t = base / nx;
+  const int y0 = (int)(t % ny);
+  const int z0 = (int)(t / ny);
+  const double h = 1.0 / (nm + 1);
+  const double h2 = h * h;
+  const long long as = m == 0 ? 1LL : (m == 1 ? (long long)(nx + 2) : (long long)(nx + 2) * (ny + 2));
+  const long long a0 = dim == 3 ? ((long long)(z0 + 1) * (ny + 2) + (y0 + 1)) * (nx + 2) + (x0 + 1)
+                                : (long long)(y0 + 1) * (nx + 2) + (x0 + 1);
+  double dprev = 1.0, offprev = 0.0;
+  for (int i = 0; i < nm; ++i) {
+    double ai = a ? a[a0 + i * as] : 1.0;
+    double am = a ? 0.5 * (ai + a[a0 + (i - 1) * as]) : 1.0;
+    double ap = a ? 0.5 * (ai + a[a0 + (i + 1) * as]) : 1.0;
+    double diag = 1.0 + tau * (am + ap) / h2 + tau * cM;
+    double li = 0.0, di = diag;
+    if (i > 0) {
+      li = offprev / dprev;
+      di = diag - li * offprev;
+    }
+    long long idx = var ? base + i * S : (long long)i;
+    double ri = 1.0 / di;
+    l[idx] = li;
+    r[idx] = ri;
+    if (l32) {
+      l32[idx] = (float)li;
+      r32[idx] = (float)ri;
+    }
+    dprev = di;
+    offprev = -tau * ap / h2;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T to(double v);
+template <>
+__device__ __forceinline__ double to<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float to<float>(double v) { return (float)v; }
+
+// ---------------------------------------------------------------------------------------
+// a2 + a3: x-direction substep (lines are contiguous rows).  A block stages R whole rows in
+// shared memory with coalesced loads (adding tau * src * src_t on the way in when SRC), R
+// threads run the two recurrences in shared memory, and the block writes the rows back
+// coalesced.  ld = row pitch in shared memory, odd so that thread t's row start t*ld hits
+// distinct banks.
+template <typename Tin, typename Tout, typename Tc, bool VAR, bool SRC>
+__global__ void __launch_bounds__(kThreads) sweep_x_kernel(const Tin* in, Tout* out, long long rows, int nx,
+                                                          int ld, int R, long long rows_per_slice,
+                                                          const Tc* __restrict__ fl, const Tc* __restrict__ fr,
+                                                          SourceArgs sa) {
+  extern __shared__ unsigned char smem_raw[];
+  Tc* sm = reinterpret_cast<Tc*>(smem_raw);
+  const long long row0 = (long long)blockIdx.x * R;
+  const int nrows = (int)min((long long)R, rows - row0);
+  const long long g0 = row0 * nx;
+  const int total = nrows * nx;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    int rr = e / nx;
+    int cc = e - rr * nx;
+    Tc v = (Tc)in[g0 + e];
+    if (SRC) {
+      long long row = row0 + rr;
+      long long sl = row / rows_per_slice;
+      long long ris = row - sl * rows_per_slice;
+      double ft = sa.src_t ? sa.src_t[sa.t0 + sl * sa.tstride] : 1.0;
+      v = v + to<Tc>(sa.tau * sa.src[ris * nx + cc] * ft);
+    }
+    sm[rr * ld + cc] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nrows) {
+    Tc* x = sm + threadIdx.x * ld;
+    long long ris = (row0 + threadIdx.x) % rows_per_slice;
+    const Tc* L = fl + (VAR ? ris * nx : 0);
+    const Tc* Rr = fr + (VAR ? ris * nx : 0);
+    Tc y = x[0];
+    for (int i = 1; i < nx; ++i) {
+      y = x[i] - L[i] * y;
+      x[i] = y;
+    }
+    Tc xn = Rr[nx - 1] * y;
+    x[nx - 1] = xn;
+    for (int i = nx - 2; i >= 0; --i) {
+      xn = Rr[i] * x[i] - L[i + 1] * xn;
+      x[i] = xn;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    int rr = e / nx;
+    int cc = e - rr * nx;
+    out[g0 + e] = (Tout)sm[rr * ld + cc];
+  }
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
+  // nonnegative doubles order like their bit patterns
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// ---------------------------------------------------------------------------------------
+// a3/a4: y- or z-direction substep, one thread per line; consecutive threads take
+// consecutive x so every access of a warp is one coalesced row segment.  The forward
+// recurrence stores y_i in `tmp` (the output, or the coarse scratch state; its type is the
+// output type, which holds the recurrence type exactly), the backward one reads it back.  EPI = 1 fuses the parareal correction of Sec. 3 into the backward
+// recurrence of the last sweep of a coarse step:
+//     U_{n+1} <- Fout + (g - Gold),  Gold <- g,  inc <- max(inc, |U_{n+1}^new - U_{n+1}^old|)
+// EPI = 2 is the initial coarse sweep: U_{n+1} <- g, Gold <- g.
+template <typename Tin, typename Tout, typename Tc, bool VAR, bool SRC, int EPI>
+__global__ void __launch_bounds__(kThreads) sweep_strided_kernel(const Tin* in, Tout* out, Tout* tmp, long long lines,
+                                                                int nm, long long S, long long nt,
+                                                                const Tc* __restrict__ fl, const Tc* __restrict__ fr,
+                                                                SourceArgs sa, CorrArgs ca) {
+  const long long L = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double my_inc = 0.0;
+  bool bad = false;
+  if (L < lines) {
+    const long long outer = L / S;
+    const long long base = outer * S * nm + (L - outer * S);
+    const long long sl = base / nt;
+    const long long pos = base - sl * nt;  // position inside the slice
+    const Tc* Lf = fl + (VAR ? pos : 0);
+    const Tc* Rf = fr + (VAR ? pos : 0);
+    const long long fs = VAR ? S : 1;
+    double ft = 0.0;
+    if (SRC) ft = sa.tau * (sa.src_t ? sa.src_t[sa.t0 + sl * sa.tstride] : 1.0);
+    Tc y = (Tc)in[base];
+    if (SRC) y = y + to<Tc>(ft * sa.src[pos]);
+    tmp[base] = (Tout)y;
+    for (int i = 1; i < nm; ++i) {
+      Tc b = (Tc)in[base + i * S];
+      if (SRC) b = b + to<Tc>(ft * sa.src[pos + i * S]);
+      y = b - Lf[i * fs] * y;
+      tmp[base + i * S] = (Tout)y;
+    }
+    Tc xn = Rf[(nm - 1) * fs] * y;
+    for (int i = nm - 1; i >= 0; --i) {
+      if (i < nm - 1) xn = Rf[i * fs] * (Tc)tmp[base + i * S] - Lf[(i + 1) * fs] * xn;
+      const long long gi = base + i * S;
+      if (EPI == 0) {
+        out[gi] = (Tout)xn;
+      } else {
+        const long long si = pos + i * S;  // coarse steps run on one slice
+        const double g = (double)xn;
+        if (EPI == 1) {
+          const double unew = ca.Fout[si] + (g - ca.Gold[si]);
+          const double d = fabs(unew - ca.U_next[si]);
+          if (!isfinite(unew)) bad = true;
+          my_inc = fmax(my_inc, d);
+          ca.Gold[si] = g;
+          ca.U_next[si] = unew;
+        } else {
+          if (!isfinite(g)) bad = true;
+          ca.Gold[si] = g;
+          ca.U_next[si] = g;
+        }
+      }
+    }
+  }
+  if (EPI == 1) {
+    for (int o = 16; o > 0; o >>= 1) my_inc = fmax(my_inc, __shfl_xor_sync(0xffffffffu, my_inc, o));
+    if ((threadIdx.x & 31) == 0 && my_inc > 0.0) atomic_max_nonneg(ca.inc, my_inc);
+  }
+  if (EPI != 0) {
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(ca.nonfinite, 1);
+  }
+}
+
+__global__ void copy_inc_kernel(long long n, const double* __restrict__ src, double* __restrict__ dst,
+                                unsigned long long* inc, int* nonfinite) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double my = 0.0;
+  bool bad = false;
+  for (; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = src[i];
+    my = fmax(my, fabs(v - dst[i]));
+    if (!isfinite(v)) bad = true;
+    dst[i] = v;
+  }
+  for (int o = 16; o > 0; o >>= 1) my = fmax(my, __shfl_xor_sync(0xffffffffu, my, o));
+  if ((threadIdx.x & 31) == 0 && my > 0.0) atomic_max_nonneg(inc, my);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(nonfinite, 1);
+}
+
+int g_max_smem = 0;
+int max_dyn_smem() {
+  if (!g_max_smem) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  return g_max_smem;
+}
+
+template <typename Tin, typename Tout, typename Tc, bool VAR, bool SRC>
+void launch_x(const Geom& g, int nslices, const Tc* fl, const Tc* fr, const Tin* in, Tout* out, const SourceArgs& sa,
+              cudaStream_t st) {
+  const int nx = g.n[0];
+  const long long rows_per_slice = g.nt / nx;
+  const long long rows = rows_per_slice * nslices;
+  const int ld = (nx % 2) ? nx : nx + 1;
+  const int budget = 96 * 1024;
+  int R = std::max(1, std::min(sizeof(Tc) == 8 ? 32 : 64, budget / (int)(ld * sizeof(Tc))));
+  size_t smem = (size_t)R * ld * sizeof(Tc);
+  if ((int)smem > max_dyn_smem()) throw Error(PS_ERR_UNSUPPORTED, "x-line too long for shared memory");
+  auto kern = sweep_x_kernel<Tin, Tout, Tc, VAR, SRC>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem()));
+    attr_set = true;
+  }
+  long long blocks = (rows + R - 1) / R;
+  kern<<<(unsigned)blocks, kThreads, smem, st>>>(in, out, rows, nx, ld, R, rows_per_slice, fl, fr, sa);
+  PS_CUDA(cudaGetLastError());
+}
+
+template <typename Tin, typename Tout, typename Tc, bool VAR, bool SRC, int EPI>
+void launch_strided(const Geom& g, int m, int nslices, const Tc* fl, const Tc* fr, const Tin* in, Tout* out, Tout* tmp,
+                    const SourceArgs& sa, const CorrArgs& ca, cudaStream_t st) {
+  const int nm = g.n[m];
+  const long long S = g.stride(m);
+  const long long lines = (g.nt / nm) * nslices;
+  long long blocks = (lines + kThreads - 1) / kThreads;
+  sweep_strided_kernel<Tin, Tout, Tc, VAR, SRC, EPI>
+      <<<(unsigned)blocks, kThreads, 0, st>>>(in, out, tmp, lines, nm, S, g.nt, fl, fr, sa, ca);
+  PS_CUDA(cudaGetLastError());
+}
+
+template <typename Tin, typename Tout, typename Tc>
+void dispatch(const Geom& g, int nslices, const LineFactors& f, const Tc* fl, const Tc* fr, const Tin* in, Tout* out,
+              const SourceArgs& sa, const CorrArgs& ca, Tout* tmp, cudaStream_t st) {
+  static_assert(sizeof(Tout) >= sizeof(Tc), "the output type must hold the recurrence type");
+  const bool var = f.var != 0, src = sa.src != nullptr;
+  if (f.m == 0) {
+    PS_REQUIRE(ca.mode == 0, "the correction is fused into a y/z sweep only");
+    if (var) {
+      if (src) launch_x<Tin, Tout, Tc, true, true>(g, nslices, fl, fr, in, out, sa, st);
+      else launch_x<Tin, Tout, Tc, true, false>(g, nslices, fl, fr, in, out, sa, st);
+    } else {
+      if (src) launch_x<Tin, Tout, Tc, false, true>(g, nslices, fl, fr, in, out, sa, st);
+      else launch_x<Tin, Tout, Tc, false, false>(g, nslices, fl, fr, in, out, sa, st);
+    }
+    return;
+  }
+  Tout* t = tmp ? tmp : out;
+#define PS_STRIDED(V, S_, E) launch_strided<Tin, Tout, Tc, V, S_, E>(g, f.m, nslices, fl, fr, in, out, t, sa, ca, st)
+  if (ca.mode == 0) {
+    if (var) { if (src) PS_STRIDED(true, true, 0); else PS_STRIDED(true, false, 0); }
+    else { if (src) PS_STRIDED(false, true, 0); else PS_STRIDED(false, false, 0); }
+  } else if (ca.mode == 1) {
+    if (var) { if (src) PS_STRIDED(true, true, 1); else PS_STRIDED(true, false, 1); }
+    else { if (src) PS_STRIDED(false, true, 1); else PS_STRIDED(false, false, 1); }
+  } else {
+    if (var) { if (src) PS_STRIDED(true, true, 2); else PS_STRIDED(true, false, 2); }
+    else { if (src) PS_STRIDED(false, true, 2); else PS_STRIDED(false, false, 2); }
+  }
+#undef PS_STRIDED
+}
+
+}  // namespace
+
+void factor_dim(const Geom& g, int m, const double* a_nodal, double c_over_M, double tau, LineFactors& f,
+                bool want_f32, cudaStream_t st) {
+  const int nm = g.n[m];
+  f.m = m;
+  f.var = a_nodal ? 1 : 0;
+  const size_t cnt = f.var ? (size_t)g.nt : (size_t)nm;
+  f.l64.alloc(cnt);
+  f.r64.alloc(cnt);
+  if (want_f32) {
+    f.l32.alloc(cnt);
+    f.r32.alloc(cnt);
+  }
+  const long long lines = f.var ? g.nt / nm : 1;
+  long long blocks = (lines + 127) / 128;
+  factor_dim_kernel<<<(unsigned)blocks, 128, 0, st>>>(g.dim, g.n[0], g.n[1], g.dim == 3 ? g.n[2] : 1, m, a_nodal,
+                                                      c_over_M, tau, f.l64.p, f.r64.p, want_f32 ? f.l32.p : nullptr,
+                                                      want_f32 ? f.r32.p : nullptr, lines, f.var);
+  PS_CUDA(cudaGetLastError());
+}
+
+template <typename Tin, typename Tout>
+void sweep_dim(const Geom& g, int nslices, const LineFactors& f, bool fp32, const Tin* in, Tout* out,
+               const SourceArgs& sa, const CorrArgs& ca, double* tmp, cudaStream_t st) {
+  if (fp32) {
+    PS_REQUIRE(f.l32.p != nullptr, "FP32 factors missing");
+    PS_REQUIRE(ca.mode == 0 && tmp == nullptr, "the FP32 sweeps carry no correction");
+    dispatch<Tin, Tout, float>(g, nslices, f, f.l32.p, f.r32.p, in, out, sa, ca, nullptr, st);
+  } else {
+    if constexpr (sizeof(Tout) == 8) {
+      dispatch<Tin, Tout, double>(g, nslices, f, f.l64.p, f.r64.p, in, out, sa, ca, reinterpret_cast<Tout*>(tmp), st);
+    } else {
+      throw Error(PS_ERR_INVALID, "an FP64 sweep needs an FP64 output");
+    }
+  }
+}
+
+template void sweep_dim<double, double>(const Geom&, int, const LineFactors&, bool, const double*, double*,
+                                        const SourceArgs&, const CorrArgs&, double*, cudaStream_t);
+template void sweep_dim<double, float>(const Geom&, int, const LineFactors&, bool, const double*, float*,
+                                       const SourceArgs&, const CorrArgs&, double*, cudaStream_t);
+template void sweep_dim<float, float>(const Geom&, int, const LineFactors&, bool, const float*, float*,
+                                      const SourceArgs&, const CorrArgs&, double*, cudaStream_t);
+template void sweep_dim<float, double>(const Geom&, int, const LineFactors&, bool, const float*, double*,
+                                       const SourceArgs&, const CorrArgs&, double*, cudaStream_t);
+
+void copy_with_increment(long long nt, const double* src, double* dst, unsigned long long* inc, int* nonfinite,
+                         cudaStream_t st) {
+  long long blocks = std::min<long long>((nt + 255) / 256, 152 * 8);
+  copy_inc_kernel<<<(unsigned)blocks, 256, 0, st>>>(nt, src, dst, inc, nonfinite);
+  PS_CUDA(cudaGetLastError());
+}
+
+}  // namespace ps

@@ -1,0 +1,118 @@
+// ps_internal.h -- internal declarations of the CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/ps.h"
+
+namespace ps {
+
+// Error carried from a failing call to the C boundary, which turns it into a status.
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define PS_CUDA(call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      throw ::ps::Error(e_ == cudaErrorMemoryAllocation ? PS_ERR_OOM : PS_ERR_CUDA,             \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                    \
+  } while (0)
+#define PS_REQUIRE(cond, msg) \
+  do {                        \
+    if (!(cond)) throw ::ps::Error(PS_ERR_INVALID, msg); \
+  } while (0)
+
+// Device buffer owned by a handle.
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) {
+    o.p = nullptr;
+    o.n = 0;
+  }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) {
+      reset();
+      p = o.p;
+      n = o.n;
+      o.p = nullptr;
+      o.n = 0;
+    }
+    return *this;
+  }
+  ~DevBuf() { reset(); }
+  void alloc(size_t count) {
+    reset();
+    if (count == 0) return;
+    PS_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    n = count;
+  }
+  void reset() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+// Factors of one dimensional substep (I - tau A_m) = L D L^T along every line of direction m:
+// l[i] = L_{i,i-1} (l at the first node of a line is 0), r[i] = 1/D_i.
+// var = 0: all lines share one factor vector of length n_m (constant coefficients);
+// var = 1: one value per interior node in the state layout.
+struct LineFactors {
+  int m = 0;
+  int var = 0;
+  DevBuf<double> l64, r64;
+  DevBuf<float> l32, r32;
+};
+
+// Geometry of a state on the grid (x fastest).
+struct Geom {
+  int dim = 2;
+  int n[3] = {1, 1, 1};
+  long long nt = 0;
+  long long stride(int m) const { return m == 0 ? 1LL : (m == 1 ? (long long)n[0] : (long long)n[0] * n[1]); }
+};
+
+// Source term f = src(x) * src_t(t_j) handed to the sweeps that form the right-hand side.
+struct SourceArgs {
+  const double* src = nullptr;    // interior field or null (no source)
+  const double* src_t = nullptr;  // device table of time factors or null (factor 1)
+  int t0 = 0;                     // time index of the first slice of the launch
+  int tstride = 0;                // added per slice of the launch
+  double tau = 0.0;
+};
+
+// Epilogue of the last sweep of a coarse step (the parareal correction, Sec. 3).
+struct CorrArgs {
+  int mode = 0;                      // 0 none, 1 correction, 2 initial sweep (U = Gold = g)
+  double* U_next = nullptr;          // U_{n+1}: old value in, new value out
+  const double* Fout = nullptr;      // F(U_n^{k-1})
+  double* Gold = nullptr;            // G(U_n^{k-1}) in, G(U_n^k) out
+  unsigned long long* inc = nullptr; // running max |U^k - U^{k-1}| as bits of a nonnegative double
+  int* nonfinite = nullptr;          // set to 1 when a non-finite value appears
+};
+
+// Launchers (ps_dim.cu).  `in` and `out` may alias (in-place sweeps).  nslices states of
+// geometry g are stored back to back.  Tin/Tout are double or float; the recurrences run in
+// double when fp32 == false and in float otherwise.
+void factor_dim(const Geom& g, int m, const double* a_nodal, double c_over_M, double tau, LineFactors& f,
+                bool want_f32, cudaStream_t st);
+template <typename Tin, typename Tout>
+void sweep_dim(const Geom& g, int nslices, const LineFactors& f, bool fp32, const Tin* in, Tout* out,
+               const SourceArgs& srcargs, const CorrArgs& corr, double* tmp, cudaStream_t st);
+void copy_with_increment(long long nt, const double* src, double* dst, unsigned long long* inc, int* nonfinite,
+                         cudaStream_t st);
+
+}  // namespace ps

@@ -1,0 +1,196 @@
+"""GPU parity of the dimensional-splitting path against the FP64 CPU oracle.
+
+Every call goes through the C ABI (libps.so) via the thin binding.  FP64 results
+must match the oracle to 1e-12 in relative max-norm with equal parareal
+iteration counts; the FP32 line-solve form must stay within the bound stated in
+``mixed_bound`` (C * s * N * M * 2^-24 relative, C = 4).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as orc
+from paper_2502_08370_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+RTOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def ps():
+    from paper_2502_08370_gb300 import build
+    build.build()
+    import paper_2502_08370_gb300 as ps
+    return ps
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def relmax(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def make(ps, n, a=None, c=0.0, src=None, src_t=None, T=1.0, N=4, g=1, s=4, precision="fp64", split="dim",
+         boxes=(1, 1), overlap=0.0):
+    grid = ps.Grid(n)
+    op = ps.Operator(grid, a=None if a is None else dev(a), c=c, src=None if src is None else dev(src), src_t=src_t)
+    sp = ps.Splitting(op, split, boxes, overlap)
+    prob = ps.Problem(sp, T, N, g, s, precision=precision)
+    prob._keep = (grid, op, sp)
+    orp = orc.Problem(n, a=a, c=c, src=src, src_t=src_t, split=split, boxes=boxes, overlap=overlap)
+    return prob, orp
+
+
+def mixed_bound(s, N, M):
+    return 4.0 * s * N * M * 2.0 ** -24
+
+
+SIZES = [(1, 1), (2, 3), (7, 5), (33, 31), (64, 17), (5, 4, 3), (17, 9, 12), (1, 6, 2)]
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("variable", [False, True])
+def test_substep_solve_matches_oracle(ps, n, variable):
+    rng = np.random.default_rng(hash((n, variable)) % 2 ** 32)
+    a = np.exp(0.5 * rng.standard_normal([v + 2 for v in reversed(n)])) if variable else None
+    prob, orp = make(ps, n, a=a, c=0.3, T=0.7, N=3, g=1, s=5)
+    b = rng.standard_normal(n[::-1])
+    for which, tau in ((0, 0.7 / 3 / 5), (1, 0.7 / 3)):
+        for m in range(len(n)):
+            x = dev(b)
+            prob.substep_solve(which, m, x)
+            ref = orc.substep_solve(orp, m, tau, b)
+            assert relmax(x.cpu().numpy(), ref) < RTOL64, (which, m)
+
+
+@pytest.mark.parametrize("n", [(9, 8), (6, 5, 7), (255, 3)])
+def test_propagate_with_source_matches_oracle(ps, n):
+    rng = np.random.default_rng(7)
+    a = np.exp(0.3 * rng.standard_normal([v + 2 for v in reversed(n)]))
+    N, s = 3, 4
+    src = rng.standard_normal(n[::-1])
+    src_t = np.cos(0.3 * np.arange(N * s + 1))
+    prob, orp = make(ps, n, a=a, c=0.1, src=src, src_t=src_t, T=0.5, N=N, g=2, s=s)
+    u = rng.standard_normal(n[::-1])
+    x = dev(u)
+    prob.propagate(0, 5, x, t0=2, tstride=1)
+    ref = orc.propagate(orp, 0.5 / N / s, 5, u, t0=2, tstride=1)
+    assert relmax(x.cpu().numpy(), ref) < RTOL64
+    x = dev(u)
+    prob.propagate(1, 2, x, t0=0, tstride=2)
+    ref = orc.propagate(orp, 0.5 / N / 2, 2, u, t0=0, tstride=2)
+    assert relmax(x.cpu().numpy(), ref) < RTOL64
+
+
+def test_parareal_heat2d_63_full_size(ps):
+    """63x63, N = 16, s = 64, tol 1e-10: equal iteration count, states within 1e-12."""
+    cfg = wl.heat2d_63()
+    prob, orp = make(ps, cfg["n"], T=cfg["T"], N=cfg["N"], g=1, s=cfg["s"])
+    it = prob.run(dev(cfg["u0"]), cfg["tol"])
+    U_ref, h_ref, it_ref = orc.parareal(orp, cfg["T"], cfg["N"], 1, cfg["s"], cfg["u0"], cfg["tol"])
+    assert it == it_ref == 12
+    hist = prob.history()
+    np.testing.assert_allclose(hist, h_ref, rtol=1e-6, atol=1e-14)
+    for n in range(cfg["N"] + 1):
+        assert relmax(prob.state(n).cpu().numpy(), U_ref[n]) < RTOL64, n
+
+
+@pytest.mark.parametrize("n,N,s,g", [((15, 13, 11), 6, 8, 1), ((31, 29), 8, 16, 2), ((20, 9, 6), 5, 6, 3)])
+def test_parareal_variable_coefficient_source(ps, n, N, s, g):
+    rng = np.random.default_rng(11)
+    a = np.exp(0.4 * rng.standard_normal([v + 2 for v in reversed(n)]))
+    src = rng.standard_normal(n[::-1])
+    src_t = 1.0 + np.sin(np.arange(N * s + 1) * 0.2)
+    prob, orp = make(ps, n, a=a, c=0.5, src=src, src_t=src_t, T=0.4, N=N, g=g, s=s)
+    u0 = rng.standard_normal(n[::-1])
+    tol = 1e-9
+    it = prob.run(dev(u0), tol)
+    U_ref, h_ref, it_ref = orc.parareal(orp, 0.4, N, g, s, u0, tol)
+    assert it == it_ref
+    for j in range(N + 1):
+        assert relmax(prob.state(j).cpu().numpy(), U_ref[j]) < RTOL64, j
+
+
+def test_finite_termination_bitwise_on_gpu(ps):
+    """U_n^k equals the GPU's own sequential fine solution bitwise for n <= k (Sec. 3)."""
+    rng = np.random.default_rng(12)
+    n, N, s = (21, 19), 6, 5
+    a = np.exp(0.4 * rng.standard_normal((n[1] + 2, n[0] + 2)))
+    prob, _ = make(ps, n, a=a, src=rng.standard_normal(n[::-1]), T=0.3, N=N, g=1, s=s)
+    u0 = dev(rng.standard_normal(n[::-1]))
+    fine = prob.fine_sequential(u0).cpu().numpy()
+    for k in range(1, N + 1):
+        it = prob.run(u0, 0.0, max_iter=k)
+        assert it == k
+        for j in range(k + 1):
+            assert np.array_equal(prob.state(j).cpu().numpy(), fine[j]), (k, j)
+
+
+def test_coarse_sequential_matches_oracle(ps):
+    cfg = wl.heat3d_255(n=15, N=4, s=6)
+    prob, orp = make(ps, cfg["n"], a=cfg["a"], src=cfg["src"], T=1.0, N=4, g=1, s=6)
+    U = prob.coarse_sequential(dev(cfg["u0"])).cpu().numpy()
+    ref = orc.coarse_sequential(orp, 1.0, 4, 1, 6, cfg["u0"])
+    assert relmax(U, ref) < RTOL64
+
+
+@pytest.mark.parametrize("n,N,s", [((33, 31), 8, 16), ((15, 14, 13), 6, 8)])
+def test_mixed_precision_within_stated_bound(ps, n, N, s):
+    """FP32 line solves in F; result vs the FP64 oracle within C s N M 2^-24 (C = 4)."""
+    rng = np.random.default_rng(13)
+    a = np.exp(0.3 * rng.standard_normal([v + 2 for v in reversed(n)]))
+    src = rng.standard_normal(n[::-1])
+    prob, orp = make(ps, n, a=a, src=src, T=1.0, N=N, g=1, s=s, precision="mixed")
+    u0 = rng.standard_normal(n[::-1])
+    it = prob.run(dev(u0), 1e-8)
+    U_ref, _, it_ref = orc.parareal(orp, 1.0, N, 1, s, u0, 1e-8)
+    assert abs(it - it_ref) <= 1
+    err = relmax(prob.state(N).cpu().numpy(), U_ref[N])
+    assert err < mixed_bound(s, N, len(n)), err
+    # the mixed fixed point is the mixed fine solution: k = N reproduces it bitwise
+    u0d = dev(u0)
+    fine = prob.fine_sequential(u0d).cpu().numpy()
+    prob.run(u0d, 0.0, max_iter=N)
+    assert np.array_equal(prob.state(N).cpu().numpy(), fine[N])
+
+
+def test_host_entry_point_matches_device_entry_point(ps):
+    cfg = wl.heat2d_63(n=31, N=8, s=16)
+    prob, _ = make(ps, cfg["n"], T=1.0, N=8, g=1, s=16)
+    it = prob.run(dev(cfg["u0"]), 1e-10)
+    ref = prob.state(8).cpu().numpy()
+    u0h = torch.as_tensor(cfg["u0"]).contiguous().pin_memory()
+    uNh = torch.empty_like(u0h).pin_memory()
+    it2 = prob.run_host(u0h, uNh, 1e-10)
+    assert it == it2 and np.array_equal(uNh.numpy(), ref)
+
+
+def test_invalid_arguments_are_rejected(ps):
+    grid = ps.Grid((5, 5))
+    op = ps.Operator(grid)
+    sp = ps.Splitting(op)
+    with pytest.raises(ps.PsError) as e:
+        ps.Problem(sp, 1.0, 4, 3, 8)  # f_steps % g_steps != 0
+    assert e.value.code == 1
+    with pytest.raises(ps.PsError):
+        ps.Problem(sp, -1.0, 4, 1, 8)
+    prob = ps.Problem(sp, 1.0, 4, 1, 8)
+    with pytest.raises(ps.PsError):
+        prob.state(5)
+    with pytest.raises(ValueError):
+        prob.run(torch.zeros(3, dtype=torch.float64, device="cuda"), 1e-8)
+
+
+def test_nonfinite_input_is_reported(ps):
+    prob, _ = make(ps, (9, 9), N=4, s=4)
+    u0 = np.ones((9, 9))
+    u0[3, 3] = np.nan
+    with pytest.raises(ps.PsError) as e:
+        prob.run(dev(u0), 1e-8)
+    assert e.value.code == 4
