@@ -355,7 +355,7 @@ def main():
         del p64
 
     cpu = None
-    if rank == 0 and ws == 1:
+    if rank == 0 and ws == 1 and args.cpu_seconds > 0:
         import oracle as orc
         orc.build()
         cpu = cpu_sample(cfg, args.cpu_seconds)

@@ -102,7 +102,11 @@ typedef struct {
   int timing;    /* 1: per-phase CUDA events (ps_problem_stats); 2: also per-kernel
                     events (ps_problem_kernel_times) */
   int dd_slices_per_block; /* DD subdomain solves: slices (one warp each) per CTA, 1..8; 0 = 2 */
-  int reserved[4];
+  int tile_positions;      /* fine line solves: line positions per TMA tile (1, 2, 4); 0 = auto */
+  int tile_pipeline;       /* fine line solves: 1 persistent double-buffered CTAs, 2 one tile per
+                              CTA, 0 = auto */
+  int tile_slots;          /* fine line solves: time slices per TMA tile (16, 32, 64); 0 = auto */
+  int reserved[1];
 } ps_params;
 
 /* fine, coarse: splittings of the same operator used by F and G (coarse = NULL: use

@@ -42,7 +42,8 @@ class _DD(C.Structure):
 
 class _Params(C.Structure):
     _fields_ = [("precision", C.c_int), ("schedule", C.c_int), ("timing", C.c_int), ("dd_slices_per_block", C.c_int),
-                ("reserved", C.c_int * 4)]
+                ("tile_positions", C.c_int), ("tile_pipeline", C.c_int), ("tile_slots", C.c_int),
+                ("reserved", C.c_int * 1)]
 
 
 class _Stats(C.Structure):
@@ -196,12 +197,13 @@ class Problem:
     """Parareal problem: G = g FIE steps of T/(N g), F = s FIE steps of T/(N s) (Sec. 3)."""
 
     def __init__(self, fine: Splitting, T, N, g, s, coarse: Splitting = None, precision="fp64",
-                 schedule=PS_SCHED_AUTO, timing=False, dd_slices_per_block=0, stream=None):
+                 schedule=PS_SCHED_AUTO, timing=False, dd_slices_per_block=0, tile_positions=0, tile_pipeline=0,
+                 tile_slots=0, stream=None):
         self.fine, self.coarse = fine, coarse
         self.grid = fine.op.grid
         self.N = int(N)
         prm = _Params(PS_PREC_FP64 if precision == "fp64" else PS_PREC_MIXED, int(schedule), int(timing),
-                      int(dd_slices_per_block))
+                      int(dd_slices_per_block), int(tile_positions), int(tile_pipeline), int(tile_slots))
         h = _VP()
         check(lib().ps_problem_create(fine._h, None if coarse is None else coarse._h, float(T), int(N), int(g),
                                       int(s), C.byref(prm), _stream(stream), C.byref(h)))

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "ps_dd.h"
+#include "ps_tile.h"
 
 using namespace ps;
 
@@ -76,6 +77,7 @@ struct Prop {
   bool f32 = false;
   std::vector<std::unique_ptr<LineFactors>> dim;
   std::unique_ptr<DDFactors> dd;
+  TilePlan tiles[3];  // fine propagator, dimensional splitting: one TMA plan per direction
 };
 
 // Per-launch CUDA events around the library's kernels (params.timing == 2), resolved at
@@ -151,7 +153,12 @@ struct ps_problem {
   ps_params prm{};
   Prop F, G;
   DevBuf<double> U, Fout, Gold, gtmp;
-  DevBuf<float> W;
+  DevBuf<float> W;      // fine working state, slice-interleaved (FP32 line solves)
+  DevBuf<double> W64;   // same for FP64 line solves
+  int S_pad = 0;        // slots of the interleaved layout
+  DevBuf<int> tmo;      // set by a kernel whose bounded wait ran out
+  DevBuf<float> srcrow32;   // fine source rows along x, line-major (tile sweeps)
+  DevBuf<double> srcrow64;
   DevBuf<unsigned long long> inc;
   DevBuf<int> flag;
   unsigned long long* h_inc = nullptr;
@@ -201,6 +208,7 @@ SourceArgs source_for(const ps_problem* p, const Prop& P, int t0, int tslice) {
   sa.src_t = p->op->src_t.p;
   sa.t0 = t0;
   sa.tstride = tslice;
+  sa.src_t_len = p->op->src_t_len;
   sa.tau = P.tau;
   return sa;
 }
@@ -286,32 +294,48 @@ void fie_step64(ps_problem* p, Prop& P, int nsl, const double* in, double* out, 
   }
 }
 
-// F (s fine steps) on nsl consecutive slices starting at absolute slice n_first.
-void run_F(ps_problem* p, int n_first, int nsl, const double* in, double* out, cudaStream_t st) {
+// F (s fine steps) on nsl consecutive slices starting at absolute slice n_first.  With the
+// dimensional splitting the slices are packed into the interleaved working state, every
+// substep is one TMA tile sweep over all of them, and the result is unpacked into `out`.
+template <typename T>
+void run_F_tiles(ps_problem* p, int n_first, int nsl, const double* in, double* out, cudaStream_t st) {
   Prop& P = p->F;
   const int M = P.sp->M;
-  if (!P.f32) {
+  T* W = sizeof(T) == 4 ? reinterpret_cast<T*>(p->W.p) : reinterpret_cast<T*>(p->W64.p);
+  const double nt = (double)p->g.nt;
+  const char* tn = sizeof(T) == 4 ? "f32" : "f64";
+  p->kt.begin(st);
+  to_interleaved<T>(p->g, in, W, p->S_pad, n_first, nsl, st);
+  if (p->kt.on) p->kt.end(std::string("F.pack.") + tn, nsl * nt * (8.0 + sizeof(T)), 0.0);
+  p->launches++;
+  for (int j = 0; j < P.steps; ++j) {
+    for (int m = 0; m < M; ++m) {
+      SourceArgs sa = m == 0 ? source_for(p, P, j + 1, p->fs) : SourceArgs{};
+      const LineFactors& f = *P.dim[m];
+      double bytes = 0, flops = 0;
+      if (p->kt.on) sweep_cost(p, f, nsl, sizeof(T), sizeof(T), sizeof(T), sa.src != nullptr, 0, &bytes, &flops);
+      p->kt.begin(st);
+      const T* srow = sizeof(T) == 4 ? reinterpret_cast<const T*>(p->srcrow32.p) : reinterpret_cast<const T*>(p->srcrow64.p);
+      tile_sweep<T>(p->g, P.tiles[m], f, p->S_pad, n_first, nsl, sa, srow, p->tmo.p, st);
+      if (p->kt.on) p->kt.end(std::string("F.") + kAxis[m] + "." + tn, bytes, flops);
+      p->launches++;
+    }
+  }
+  p->kt.begin(st);
+  from_interleaved<T>(p->g, W, out, p->S_pad, n_first, nsl, st);
+  if (p->kt.on) p->kt.end(std::string("F.unpack.") + tn, nsl * nt * (8.0 + sizeof(T)), 0.0);
+  p->launches++;
+}
+
+void run_F(ps_problem* p, int n_first, int nsl, const double* in, double* out, cudaStream_t st) {
+  Prop& P = p->F;
+  if (P.sp->kind == PS_SPLIT_DIM) {
+    if (P.f32) run_F_tiles<float>(p, n_first, nsl, in, out, st);
+    else run_F_tiles<double>(p, n_first, nsl, in, out, st);
+  } else {
     for (int j = 0; j < P.steps; ++j)
       fie_step64(p, P, nsl, j == 0 ? in : out, out, n_first * p->fs + (j + 1) * P.tstride, p->fs, CorrArgs{}, st,
                  "F");
-  } else {
-    float* W = p->W.p;
-    for (int j = 0; j < P.steps; ++j) {
-      for (int m = 0; m < M; ++m) {
-        const bool first = (j == 0 && m == 0), last = (j == P.steps - 1 && m == M - 1);
-        SourceArgs sa = m == 0 ? source_for(p, P, n_first * p->fs + (j + 1) * P.tstride, p->fs) : SourceArgs{};
-        const LineFactors& f = *P.dim[m];
-        double bytes = 0, flops = 0;
-        if (p->kt.on) sweep_cost(p, f, nsl, first ? 8 : 4, last ? 8 : 4, 4, sa.src != nullptr, 0, &bytes, &flops);
-        p->kt.begin(st);
-        if (first && last) sweep_dim<double, double>(p->g, nsl, f, true, in, out, sa, CorrArgs{}, nullptr, st);
-        else if (first) sweep_dim<double, float>(p->g, nsl, f, true, in, W, sa, CorrArgs{}, nullptr, st);
-        else if (last) sweep_dim<float, double>(p->g, nsl, f, true, W, out, sa, CorrArgs{}, nullptr, st);
-        else sweep_dim<float, float>(p->g, nsl, f, true, W, W, sa, CorrArgs{}, nullptr, st);
-        if (p->kt.on) p->kt.end(std::string("F.") + kAxis[m] + ".f32", bytes, flops);
-        p->launches++;
-      }
-    }
   }
   p->updates += (double)nsl * P.steps * (double)p->g.nt;
 }
@@ -356,6 +380,7 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
   if (timing) PS_CUDA(cudaEventRecord(p->ev[0], st));
   PS_CUDA(cudaMemcpyAsync(p->U.p, u0, sizeof(double) * nt, cudaMemcpyDeviceToDevice, st));
   PS_CUDA(cudaMemsetAsync(p->flag.p, 0, sizeof(int), st));
+  PS_CUDA(cudaMemsetAsync(p->tmo.p, 0, sizeof(int), st));
   // k = 0: sequential coarse sweep, U_{n+1}^0 = G(U_n^0), Gold_n = G(U_n^0)
   for (int n = 0; n < N; ++n) run_G(p, n, p->U.p + n * nt, corr_args(p, 2, n), st);
   int k = 0;
@@ -373,7 +398,13 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
     if (timing) PS_CUDA(cudaEventRecord(p->ev[3], st));
     PS_CUDA(cudaMemcpyAsync(p->h_inc, p->inc.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaMemcpyAsync(p->h_flag, p->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaMemcpyAsync(p->h_flag + 1, p->tmo.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaStreamSynchronize(st));
+    if (p->h_flag[1]) {
+      p->iters = k;
+      if (p->h_flag[1] == 2) throw Error(PS_ERR_CUDA, "a tile's shared-memory buffer was not 128-byte aligned");
+      throw Error(PS_ERR_DEVICE_TIMEOUT, "a TMA tile load did not arrive within its wait limit");
+    }
     p->kt.resolve();
     if (timing) {
       float a = 0, b = 0;
@@ -525,11 +556,44 @@ int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, doub
     p->Fout.alloc((size_t)N * nt);
     p->Gold.alloc((size_t)N * nt);
     p->gtmp.alloc((size_t)nt);
-    if (mixed) p->W.alloc((size_t)N * nt);
     p->inc.alloc(1);
+    p->tmo.alloc(1);
+    if (fine->kind == PS_SPLIT_DIM) {
+      const int elem = mixed ? 4 : 8;
+      const int TS = mixed ? 32 : 16;
+      p->S_pad = (N + TS - 1) / TS * TS;
+      void* W = nullptr;
+      if (mixed) {
+        p->W.alloc((size_t)p->S_pad * nt);
+        W = p->W.p;
+      } else {
+        p->W64.alloc((size_t)p->S_pad * nt);
+        W = p->W64.p;
+      }
+      PS_CUDA(cudaMemsetAsync(W, 0, (size_t)p->S_pad * nt * elem, st));
+      Geom g3 = p->g;
+      if (g3.dim == 2) g3.n[2] = 1;
+      for (int m = 0; m < p->g.dim; ++m) {
+        tile_plan(g3, p->S_pad, elem, m, p->F.tiles[m], W, p->prm.tile_positions,
+                  p->prm.tile_pipeline == 0 ? 0 : (p->prm.tile_pipeline == 1 ? 1 : 0), p->prm.tile_slots);
+        factor_lines(g3, *p->F.dim[m], mixed, st);
+      }
+      if (p->op->src.p) {
+        const size_t rows = (size_t)(nt / g3.n[0]) * ((g3.n[0] + 3) & ~3);
+        void* out;
+        if (mixed) {
+          p->srcrow32.alloc(rows);
+          out = p->srcrow32.p;
+        } else {
+          p->srcrow64.alloc(rows);
+          out = p->srcrow64.p;
+        }
+        source_rows(g3, p->op->src.p, out, elem, st);
+      }
+    }
     p->flag.alloc(1);
     PS_CUDA(cudaMallocHost(&p->h_inc, sizeof(unsigned long long)));
-    PS_CUDA(cudaMallocHost(&p->h_flag, sizeof(int)));
+    PS_CUDA(cudaMallocHost(&p->h_flag, 2 * sizeof(int)));
     for (auto& e : p->ev) PS_CUDA(cudaEventCreate(&e));
     PS_CUDA(cudaStreamSynchronize(st));
     *out = p.release();

@@ -371,8 +371,9 @@ void dd_factor(const Geom& g, const ps_dd_params& dd, const double* a_nodal, dou
   int dev = 0, maxsm = 0;
   PS_CUDA(cudaGetDevice(&dev));
   PS_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if ((int)smem > maxsm) throw Error(PS_ERR_UNSUPPORTED, "DD box too wide for the shared-memory factorisation");
-  PS_CUDA(cudaFuncSetAttribute(dd_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+  // the kernel also holds one static double
+  if ((int)smem + 64 > maxsm) throw Error(PS_ERR_UNSUPPORTED, "DD box too wide for the shared-memory factorisation");
+  PS_CUDA(cudaFuncSetAttribute(dd_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int c = 0; c < f.plan.M; ++c) {
     auto& boxes = f.plan.colours[c];
     f.dev_boxes[c].alloc(boxes.size());

@@ -54,7 +54,7 @@ __global__ void factor_dim_kernel(int dim, int nx, int ny, int nz, int m, const 
       li = offprev / dprev;
       di = diag - li * offprev;
     }
-    long long idx = var ? base + i * S : (long long)i;
+    long long idx = !var ? (long long)i : (m == 0 ? (long long)i * lines + L : base + i * S);
     double ri = 1.0 / di;
     l[idx] = li;
     r[idx] = ri;
@@ -107,19 +107,48 @@ __global__ void __launch_bounds__(kThreads) sweep_x_kernel(const Tin* in, Tout* 
   __syncthreads();
   if (threadIdx.x < nrows) {
     Tc* x = sm + threadIdx.x * ld;
-    long long ris = (row0 + threadIdx.x) % rows_per_slice;
-    const Tc* L = fl + (VAR ? ris * nx : 0);
-    const Tc* Rr = fr + (VAR ? ris * nx : 0);
+    // factors: transposed layout (entry (row, i) at i * rows_per_slice + row)
+    const long long ris = (row0 + threadIdx.x) % rows_per_slice;
+    const Tc* L = fl + (VAR ? ris : 0);
+    const Tc* Rr = fr + (VAR ? ris : 0);
+    const long long fs = VAR ? rows_per_slice : 1;
+    // chunks of K elements: the shared-memory and factor loads of a chunk issue together
+    constexpr int K = 8;
     Tc y = x[0];
-    for (int i = 1; i < nx; ++i) {
-      y = x[i] - L[i] * y;
-      x[i] = y;
+    for (int i0 = 1; i0 < nx; i0 += K) {
+      Tc b[K], l[K];
+#pragma unroll
+      for (int u = 0; u < K; ++u) {
+        const int i = i0 + u;
+        b[u] = i < nx ? x[i] : Tc(0);
+        l[u] = i < nx ? L[i * fs] : Tc(0);
+      }
+#pragma unroll
+      for (int u = 0; u < K; ++u) {
+        if (i0 + u < nx) {
+          y = b[u] - l[u] * y;
+          x[i0 + u] = y;
+        }
+      }
     }
-    Tc xn = Rr[nx - 1] * y;
-    x[nx - 1] = xn;
-    for (int i = nx - 2; i >= 0; --i) {
-      xn = Rr[i] * x[i] - L[i + 1] * xn;
-      x[i] = xn;
+    Tc xn = y;
+    for (int i0 = nx - 1; i0 >= 0; i0 -= K) {
+      Tc yy[K], r[K], l[K];
+#pragma unroll
+      for (int u = 0; u < K; ++u) {
+        const int i = i0 - u;
+        yy[u] = i >= 0 ? x[i] : Tc(0);
+        r[u] = i >= 0 ? Rr[i * fs] : Tc(0);
+        l[u] = (i >= 0 && i + 1 < nx) ? L[(i + 1) * fs] : Tc(0);
+      }
+#pragma unroll
+      for (int u = 0; u < K; ++u) {
+        const int i = i0 - u;
+        if (i >= 0) {
+          xn = (i == nx - 1) ? r[u] * yy[u] : r[u] * yy[u] - l[u] * xn;
+          x[i] = xn;
+        }
+      }
     }
   }
   __syncthreads();
@@ -161,35 +190,74 @@ __global__ void __launch_bounds__(kThreads) sweep_strided_kernel(const Tin* in, 
     const long long fs = VAR ? S : 1;
     double ft = 0.0;
     if (SRC) ft = sa.tau * (sa.src_t ? sa.src_t[sa.t0 + sl * sa.tstride] : 1.0);
+    // forward recurrence; the loads of each chunk of K elements are issued together
+    constexpr int K = 8;
     Tc y = (Tc)in[base];
     if (SRC) y = y + to<Tc>(ft * sa.src[pos]);
     tmp[base] = (Tout)y;
-    for (int i = 1; i < nm; ++i) {
-      Tc b = (Tc)in[base + i * S];
-      if (SRC) b = b + to<Tc>(ft * sa.src[pos + i * S]);
-      y = b - Lf[i * fs] * y;
-      tmp[base + i * S] = (Tout)y;
+    for (int i0 = 1; i0 < nm; i0 += K) {
+      Tc b[K], l[K];
+#pragma unroll
+      for (int u = 0; u < K; ++u) {
+        const int i = i0 + u;
+        b[u] = i < nm ? (Tc)in[base + i * S] : Tc(0);
+        l[u] = i < nm ? Lf[i * fs] : Tc(0);
+        if (SRC) b[u] = b[u] + (i < nm ? to<Tc>(ft * sa.src[pos + i * S]) : Tc(0));
+      }
+#pragma unroll
+      for (int u = 0; u < K; ++u) {
+        if (i0 + u < nm) {
+          y = b[u] - l[u] * y;
+          tmp[base + (i0 + u) * S] = (Tout)y;
+        }
+      }
     }
-    Tc xn = Rf[(nm - 1) * fs] * y;
-    for (int i = nm - 1; i >= 0; --i) {
-      if (i < nm - 1) xn = Rf[i * fs] * (Tc)tmp[base + i * S] - Lf[(i + 1) * fs] * xn;
-      const long long gi = base + i * S;
-      if (EPI == 0) {
-        out[gi] = (Tout)xn;
-      } else {
-        const long long si = pos + i * S;  // coarse steps run on one slice
-        const double g = (double)xn;
-        if (EPI == 1) {
-          const double unew = ca.Fout[si] + (g - ca.Gold[si]);
-          const double d = fabs(unew - ca.U_next[si]);
-          if (!isfinite(unew)) bad = true;
-          my_inc = fmax(my_inc, d);
-          ca.Gold[si] = g;
-          ca.U_next[si] = unew;
-        } else {
-          if (!isfinite(g)) bad = true;
-          ca.Gold[si] = g;
-          ca.U_next[si] = g;
+    // backward recurrence (chunks of KB), with the correction of Sec. 3 fused when EPI != 0
+    constexpr int KB = 4;
+    Tc xn = y;
+    for (int i0 = nm - 1; i0 >= 0; i0 -= KB) {
+      Tc yy[KB], r[KB], l[KB];
+      double fo[KB], go[KB], uo[KB];
+#pragma unroll
+      for (int u = 0; u < KB; ++u) {
+        const int i = i0 - u;
+        const bool ok = i >= 0;
+        yy[u] = ok ? (Tc)tmp[base + i * S] : Tc(0);
+        r[u] = ok ? Rf[i * fs] : Tc(0);
+        l[u] = (ok && i + 1 < nm) ? Lf[(i + 1) * fs] : Tc(0);
+        if (EPI != 0) {
+          const long long si = pos + (long long)(ok ? i : 0) * S;
+          go[u] = ok ? ca.Gold[si] : 0.0;
+          if (EPI == 1) {
+            fo[u] = ok ? ca.Fout[si] : 0.0;
+            uo[u] = ok ? ca.U_next[si] : 0.0;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < KB; ++u) {
+        const int i = i0 - u;
+        if (i >= 0) {
+          xn = (i == nm - 1) ? r[u] * yy[u] : r[u] * yy[u] - l[u] * xn;
+          const long long gi = base + i * S;
+          if (EPI == 0) {
+            out[gi] = (Tout)xn;
+          } else {
+            const long long si = pos + i * S;  // coarse steps run on one slice
+            const double g = (double)xn;
+            if (EPI == 1) {
+              const double unew = fo[u] + (g - go[u]);
+              const double d = fabs(unew - uo[u]);
+              if (!isfinite(unew)) bad = true;
+              my_inc = fmax(my_inc, d);
+              ca.Gold[si] = g;
+              ca.U_next[si] = unew;
+            } else {
+              if (!isfinite(g)) bad = true;
+              ca.Gold[si] = g;
+              ca.U_next[si] = g;
+            }
+          }
         }
       }
     }

@@ -69,12 +69,17 @@ struct DevBuf {
 // Factors of one dimensional substep (I - tau A_m) = L D L^T along every line of direction m:
 // l[i] = L_{i,i-1} (l at the first node of a line is 0), r[i] = 1/D_i.
 // var = 0: all lines share one factor vector of length n_m (constant coefficients);
-// var = 1: one value per interior node in the state layout.
+// var = 1: one value per interior node, in the state layout for m = 1, 2 and transposed
+// for m = 0 (entry (line, i) at i * (nt / nx) + line, line = z*ny + y), so that the threads
+// of a warp, which walk consecutive x-lines, read consecutive addresses.
 struct LineFactors {
   int m = 0;
   int var = 0;
   DevBuf<double> l64, r64;
   DevBuf<float> l32, r32;
+  // line-major copies [line][L rounded up to 4] for the fine propagator's tile sweeps
+  DevBuf<double> lt64, rt64;
+  DevBuf<float> lt32, rt32;
 };
 
 // Geometry of a state on the grid (x fastest).
@@ -91,6 +96,7 @@ struct SourceArgs {
   const double* src_t = nullptr;  // device table of time factors or null (factor 1)
   int t0 = 0;                     // time index of the first slice of the launch
   int tstride = 0;                // added per slice of the launch
+  int src_t_len = 0;              // entries of src_t
   double tau = 0.0;
 };
 

@@ -1,0 +1,745 @@
+// ps_tile.cu -- the fine propagator's batched line solves on the slice-interleaved layout.
+//
+// During a fine phase every time slice advances with the same step size, so all slices
+// share the substep factors.  The fine working state is kept interleaved,
+//     W[z][y][x][s]   (slice index fastest, S_pad slots),
+// which turns every direction x, y, z into a batch of strided lines whose 32 consecutive
+// slices form one warp: a warp walks 32 lines that share every factor (one broadcast
+// load) and whose elements at one line position are one 128-/256-byte row.
+//
+// A CTA owns a tile of TS slices x P positions of a second axis x the whole line (L nodes).
+// The tile moves between HBM and shared memory by TMA (cp.async.bulk.tensor, one load and
+// one store per 256-node chunk of the line), its factors and source are staged in shared
+// memory, and TS*P threads run the two recurrences of the L D L^T solve in shared memory:
+//     forward   y_i = b_i - l_i y_{i-1}
+//     backward  x_i = r_i y_i - l_{i+1} x_{i+1}
+// so each element is read from and written to HBM exactly once per substep.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "ps_tile.h"
+
+namespace ps {
+namespace {
+
+constexpr unsigned long long kWaitNs = 500000000ULL;  // a tile gives up on its TMA load after 0.5 s
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits for phase `parity` of the barrier; returns false when kWaitNs have passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+      "[%2];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int c0, int c1, int c2, int c3) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_addr(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_commit_and_drain() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Tile geometry shared by host and device.
+struct TileArgs {
+  int axis;          // 0 = x, 1 = y, 2 = z: direction of the lines
+  int L;             // line length (n_axis)
+  int nb;            // extent of the paired axis b (P positions per tile)
+  int P, TS;         // positions and slices per tile
+  int n[3];          // nx, ny, nz
+  int s_lo, s_hi;    // slice groups [s_lo, s_hi) of TS slots each
+  int nbt;           // tiles along b
+  int chunks;        // TMA chunks along the line (box extent <= 256)
+  int chunk;         // nodes per chunk
+  int var;           // factors per node (1) or shared by all lines (0)
+  long long rows_x;  // ny*nz: leading dimension of the transposed x-factors
+  const void* fl;       // factor rows l of every line: [line][Lp], line = c * nb + b
+  const void* fr;       // factor rows r, same layout
+  const void* srcrow;   // source rows (x-lines of a step's first substep) [line][Lp] or null
+  int Lp;               // row length: L rounded up to 4, zero padded
+  const double* src;    // non-null when the source is added
+  const double* src_t;  // time factors or null
+  int t_first, t_slice; // time index of slot s: t_first + s * t_slice
+  int src_t_len;
+  double tau;
+  int* err;
+};
+
+// Offset of element i of line (slot-in-tile s, position p) in the tile's shared memory,
+// which mirrors the TMA box order (slice fastest, then x, y, z of the box).
+__device__ __forceinline__ int tile_off(const TileArgs& a, int s, int p, int i) {
+  return a.axis == 0 ? (p * a.L + i) * a.TS + s : (i * a.P + p) * a.TS + s;
+}
+
+// 1-D bulk copy global -> shared, completing on `bar` (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+// Bytes the factor (and source) rows of a tile add to its barrier's transaction count.
+template <typename T, bool SRC>
+__device__ __forceinline__ uint32_t side_bytes(const TileArgs& a, int nvalid) {
+  return (uint32_t)((SRC ? 3 : 2) * nvalid * a.Lp * (int)sizeof(T));
+}
+// Factor (and source) rows of the tile's valid positions: nvalid consecutive lines.
+template <typename T, bool SRC>
+__device__ __forceinline__ void issue_side_loads(const TileArgs& a, int b0, int c, int nvalid, T* fl_s, T* fr_s,
+                                                 T* src_s, uint64_t* bar) {
+  const long long row = (long long)c * a.nb + b0;
+  const uint32_t bytes = (uint32_t)(nvalid * a.Lp * (int)sizeof(T));
+  bulk_load(fl_s, reinterpret_cast<const T*>(a.fl) + row * a.Lp, bytes, bar);
+  bulk_load(fr_s, reinterpret_cast<const T*>(a.fr) + row * a.Lp, bytes, bar);
+  if (SRC) bulk_load(src_s, reinterpret_cast<const T*>(a.srcrow) + row * a.Lp, bytes, bar);
+}
+// tau * src_t at the end time of the step, for interleaved slot `slot`.
+template <typename T>
+__device__ __forceinline__ T slot_time_factor(const TileArgs& a, int slot) {
+  const int ti = a.t_first + slot * a.t_slice;
+  const double f = a.src_t ? (ti >= 0 && ti < a.src_t_len ? a.src_t[ti] : 0.0) : 1.0;
+  return (T)(a.tau * f);
+}
+
+// V adjacent slots of one line position, as one vector access (V * sizeof(T) bytes).
+template <typename T, int V>
+struct alignas(sizeof(T) * V) VecT {
+  T v[V];
+};
+// Four consecutive factors (16- or 32-byte aligned rows, padded with zeros past L).
+template <typename T>
+struct alignas(sizeof(T) * 4) Quad {
+  T q[4];
+};
+
+// The two recurrences of the L D L^T solve for V lines (adjacent slots, one thread) held
+// in shared memory, element i of the V lines at x + i*st.  Factors are shared by the V
+// lines and read four at a time; l_0 = 0 and the zero padding past L make the first and
+// last steps uniform:
+//     forward   y_i = b_i - l_i y_{i-1}            (y_{-1} = 0)
+//     backward  x_i = r_i y_i - l_{i+1} x_{i+1}    (x_L = 0, l_L = 0)
+// The source, when present, enters the right-hand side: b_i += src_i * ft[v].
+template <typename T, int V, bool SRC>
+__device__ __forceinline__ void line_solve(T* x, int st, int L, const T* Lf, const T* Rf, const T* S, const T* ft) {
+  using VT = VecT<T, V>;
+  using QT = Quad<T>;
+  T y[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) y[v] = T(0);
+  const int nq = L / 4;
+  for (int c = 0; c < nq; ++c) {
+    const int i0 = 4 * c;
+    const QT l4 = *reinterpret_cast<const QT*>(Lf + i0);
+    QT s4;
+    if (SRC) s4 = *reinterpret_cast<const QT*>(S + i0);
+    VT b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) b[u] = *reinterpret_cast<const VT*>(x + (i0 + u) * st);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        T bb = b[u].v[v];
+        if (SRC) bb = bb + s4.q[u] * ft[v];
+        y[v] = bb - l4.q[u] * y[v];
+        b[u].v[v] = y[v];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) *reinterpret_cast<VT*>(x + (i0 + u) * st) = b[u];
+  }
+  for (int i = 4 * nq; i < L; ++i) {
+    VT b = *reinterpret_cast<const VT*>(x + i * st);
+    const T li = Lf[i];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      T bb = b.v[v];
+      if (SRC) bb = bb + S[i] * ft[v];
+      y[v] = bb - li * y[v];
+      b.v[v] = y[v];
+    }
+    *reinterpret_cast<VT*>(x + i * st) = b;
+  }
+  T xn[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) xn[v] = T(0);
+  T lnext = T(0);  // l_{i+1} for the step at i
+  for (int i = L - 1; i >= 4 * nq; --i) {
+    VT yy = *reinterpret_cast<const VT*>(x + i * st);
+    const T ri = Rf[i];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      xn[v] = ri * yy.v[v] - lnext * xn[v];
+      yy.v[v] = xn[v];
+    }
+    *reinterpret_cast<VT*>(x + i * st) = yy;
+    lnext = Lf[i];
+  }
+  for (int c = nq - 1; c >= 0; --c) {
+    const int i0 = 4 * c;
+    const QT r4 = *reinterpret_cast<const QT*>(Rf + i0);
+    const QT l4 = *reinterpret_cast<const QT*>(Lf + i0);
+    VT yy[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) yy[u] = *reinterpret_cast<const VT*>(x + (i0 + u) * st);
+#pragma unroll
+    for (int u = 3; u >= 0; --u) {
+      const T l1 = u == 3 ? lnext : l4.q[u + 1];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        xn[v] = r4.q[u] * yy[u].v[v] - l1 * xn[v];
+        yy[u].v[v] = xn[v];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) *reinterpret_cast<VT*>(x + (i0 + u) * st) = yy[u];
+    lnext = l4.q[0];
+  }
+}
+
+template <typename T, int V, bool SRC>
+__global__ void tile_sweep_kernel(const __grid_constant__ CUtensorMap map, TileArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // carve: [tile data | factors l | factors r | source | barrier]; factor rows hold Lp =
+  // L rounded up to 4 entries (zero padded) and start 32-byte aligned
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  const int lines = a.TS * a.P;
+  const int Lp = a.Lp;
+  T* fl_s = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(tile + (size_t)lines * a.L) + 31) & ~(uintptr_t)31);
+  T* fr_s = fl_s + (size_t)a.P * Lp;
+  T* src_s = fr_s + (size_t)a.P * Lp;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(
+      (reinterpret_cast<uintptr_t>(src_s + (SRC ? (size_t)a.P * Lp : 0)) + 15) & ~(uintptr_t)15);
+
+  // tile coordinates: blockIdx.x -> (slice group, b block, c)
+  int t = blockIdx.x;
+  const int ngroups = a.s_hi - a.s_lo;
+  const int g = a.s_lo + t % ngroups;
+  t /= ngroups;
+  const int bt = t % a.nbt;
+  const int c = t / a.nbt;
+  const int s0 = g * a.TS, b0 = bt * a.P;
+
+  const int tid = threadIdx.x;
+  const int nvalid = min(a.P, a.nb - b0);  // positions of this tile inside the grid
+  // once a tile has timed out the launch is abandoned: later tiles start no copies
+  __shared__ int s_abort;
+  if (tid == 0) {
+    s_abort = *reinterpret_cast<volatile int*>(a.err);
+    // TMA tensor copies need 128-byte aligned shared-memory destinations
+    if (smem_addr(tile) & 127) {
+      atomicExch(a.err, 2);
+      s_abort = 1;
+    }
+  }
+  __syncthreads();
+  if (s_abort) return;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (a.axis == 0) {
+      // x-lines: one box (TS slots x chunk nodes) per position and chunk
+      mbar_expect_tx(bar, (uint32_t)(nvalid * a.L * a.TS * (int)sizeof(T)) + side_bytes<T, SRC>(a, nvalid));
+      issue_side_loads<T, SRC>(a, b0, c, nvalid, fl_s, fr_s, src_s, bar);
+      for (int p = 0; p < nvalid; ++p)
+        for (int k = 0; k < a.chunks; ++k) {
+          const int i0 = k * a.chunk;
+          tma_load_4d(tile + ((size_t)p * a.L + i0) * a.TS, &map, bar, s0, i0, b0 + p, c);
+        }
+    } else {
+      // y/z-lines: one box (TS slots x P positions x chunk nodes) per chunk
+      mbar_expect_tx(bar, (uint32_t)(lines * a.L * (int)sizeof(T)) + side_bytes<T, SRC>(a, nvalid));
+      issue_side_loads<T, SRC>(a, b0, c, nvalid, fl_s, fr_s, src_s, bar);
+      for (int k = 0; k < a.chunks; ++k) {
+        const int i0 = k * a.chunk;
+        T* dst = tile + (size_t)i0 * a.P * a.TS;
+        if (a.axis == 1) tma_load_4d(dst, &map, bar, s0, b0, i0, c);
+        else tma_load_4d(dst, &map, bar, s0, b0, c, i0);
+      }
+    }
+  }
+  __syncthreads();
+  if (!mbar_wait(bar, 0)) {
+    if (tid == 0) atomicExch(a.err, 1);
+    return;
+  }
+  const int per_row = a.TS / V;  // threads per line position
+  const int s = (tid % per_row) * V, p = tid / per_row;
+  if (p < a.P && b0 + p < a.nb) {
+    T ft[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) ft[v] = SRC ? slot_time_factor<T>(a, s0 + s + v) : T(0);
+    line_solve<T, V, SRC>(tile + tile_off(a, s, p, 0), a.axis == 0 ? a.TS : a.P * a.TS, a.L, fl_s + p * Lp,
+                          fr_s + p * Lp, src_s + p * Lp, ft);
+  }
+  fence_async_smem();
+  __syncthreads();
+  if (tid == 0) {
+    if (a.axis == 0) {
+      for (int p = 0; p < nvalid; ++p)
+        for (int k = 0; k < a.chunks; ++k) {
+          const int i0 = k * a.chunk;
+          tma_store_4d(&map, tile + ((size_t)p * a.L + i0) * a.TS, s0, i0, b0 + p, c);
+        }
+    } else {
+      for (int k = 0; k < a.chunks; ++k) {
+        const int i0 = k * a.chunk;
+        const T* srcp = tile + (size_t)i0 * a.P * a.TS;
+        if (a.axis == 1) tma_store_4d(&map, srcp, s0, b0, i0, c);
+        else tma_store_4d(&map, srcp, s0, b0, c, i0);
+      }
+    }
+    tma_store_commit_and_drain();
+  }
+}
+
+// Tile t -> (first slot, first paired position, fixed coordinate).
+__device__ __forceinline__ void tile_coords(const TileArgs& a, int t, int* s0, int* b0, int* c) {
+  const int ngroups = a.s_hi - a.s_lo;
+  *s0 = (a.s_lo + t % ngroups) * a.TS;
+  t /= ngroups;
+  *b0 = (t % a.nbt) * a.P;
+  *c = t / a.nbt;
+}
+
+template <typename T, bool SRC>
+__device__ __forceinline__ void issue_tile_load(const CUtensorMap* map, const TileArgs& a, T* buf, T* fl_s, T* fr_s,
+                                                T* src_s, uint64_t* bar, int t) {
+  int s0, b0, c;
+  tile_coords(a, t, &s0, &b0, &c);
+  const int nvalid = min(a.P, a.nb - b0);
+  if (a.axis == 0) {
+    mbar_expect_tx(bar, (uint32_t)(nvalid * a.L * a.TS * (int)sizeof(T)) + side_bytes<T, SRC>(a, nvalid));
+    issue_side_loads<T, SRC>(a, b0, c, nvalid, fl_s, fr_s, src_s, bar);
+    for (int p = 0; p < nvalid; ++p)
+      for (int k = 0; k < a.chunks; ++k) {
+        const int i0 = k * a.chunk;
+        tma_load_4d(buf + ((size_t)p * a.L + i0) * a.TS, map, bar, s0, i0, b0 + p, c);
+      }
+  } else {
+    mbar_expect_tx(bar, (uint32_t)(a.TS * a.P * a.L * (int)sizeof(T)) + side_bytes<T, SRC>(a, nvalid));
+    issue_side_loads<T, SRC>(a, b0, c, nvalid, fl_s, fr_s, src_s, bar);
+    for (int k = 0; k < a.chunks; ++k) {
+      const int i0 = k * a.chunk;
+      T* dst = buf + (size_t)i0 * a.P * a.TS;
+      if (a.axis == 1) tma_load_4d(dst, map, bar, s0, b0, i0, c);
+      else tma_load_4d(dst, map, bar, s0, b0, c, i0);
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void issue_tile_store(const CUtensorMap* map, const TileArgs& a, const T* buf, int t) {
+  int s0, b0, c;
+  tile_coords(a, t, &s0, &b0, &c);
+  const int nvalid = min(a.P, a.nb - b0);
+  if (a.axis == 0) {
+    for (int p = 0; p < nvalid; ++p)
+      for (int k = 0; k < a.chunks; ++k) {
+        const int i0 = k * a.chunk;
+        tma_store_4d(map, buf + ((size_t)p * a.L + i0) * a.TS, s0, i0, b0 + p, c);
+      }
+  } else {
+    for (int k = 0; k < a.chunks; ++k) {
+      const int i0 = k * a.chunk;
+      const T* srcp = buf + (size_t)i0 * a.P * a.TS;
+      if (a.axis == 1) tma_store_4d(map, srcp, s0, b0, i0, c);
+      else tma_store_4d(map, srcp, s0, b0, c, i0);
+    }
+  }
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// Persistent form: each CTA walks tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... with two
+// shared-memory stages, so the TMA load of tile k+1 (and the store of tile k-1) run while
+// tile k is solved.  Thread 0 alone polls a stage's barrier (bounded by kWaitNs) and
+// shares the outcome; on a timeout the CTA records the error, drains the other stage's
+// load (bounded) and returns.
+template <typename T, int V, bool SRC>
+__global__ void tile_sweep_pipe_kernel(const __grid_constant__ CUtensorMap map, TileArgs a, int ntiles) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int lines = a.TS * a.P;
+  const int Lp = a.Lp;
+  const size_t tile_elems = (size_t)lines * a.L;
+  const size_t side = (size_t)a.P * Lp;
+  T* buf0 = reinterpret_cast<T*>(smem_raw);
+  // per stage: l, r (and source) of the tile's positions, rows of Lp entries, 32-byte aligned
+  T* fac0 = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(buf0 + 2 * tile_elems) + 31) & ~(uintptr_t)31);
+  const size_t fac_stride = SRC ? 3 * side : 2 * side;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(
+      (reinterpret_cast<uintptr_t>(fac0 + 2 * fac_stride) + 15) & ~(uintptr_t)15);
+  __shared__ int s_ok;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_ok = *reinterpret_cast<volatile int*>(a.err) ? 0 : 1;
+    if (smem_addr(buf0) & 127) {  // TMA tensor destinations must be 128-byte aligned
+      atomicExch(a.err, 2);
+      s_ok = 0;
+    }
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (!s_ok) return;
+  if (tid == 0) {
+    if (blockIdx.x < ntiles)
+      issue_tile_load<T, SRC>(&map, a, buf0, fac0, fac0 + side, fac0 + 2 * side, &bars[0], blockIdx.x);
+    if (blockIdx.x + gridDim.x < ntiles)
+      issue_tile_load<T, SRC>(&map, a, buf0 + tile_elems, fac0 + fac_stride, fac0 + fac_stride + side,
+                              fac0 + fac_stride + 2 * side, &bars[1], blockIdx.x + gridDim.x);
+  }
+  int k = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+    const int stage = k & 1;
+    const uint32_t parity = (k >> 1) & 1;
+    T* buf = buf0 + stage * tile_elems;
+    T* fl_s = fac0 + stage * fac_stride;
+    T* fr_s = fl_s + side;
+    T* src_s = fr_s + side;
+    int s0, b0, c;
+    tile_coords(a, t, &s0, &b0, &c);
+    if (tid == 0) s_ok = mbar_wait(&bars[stage], parity) ? 1 : 0;
+    __syncthreads();
+    if (!s_ok) {
+      if (tid == 0) {
+        atomicExch(a.err, 1);
+        if (t + (int)gridDim.x < ntiles) mbar_wait(&bars[stage ^ 1], (k + 1) >> 1 & 1);
+      }
+      return;
+    }
+    if (tid != 0) mbar_wait(&bars[stage], parity);  // completed: acquires the tile's bytes
+    const int per_row = a.TS / V;
+    const int s = (tid % per_row) * V, p = tid / per_row;
+    if (p < a.P && b0 + p < a.nb) {
+      T ft[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) ft[v] = SRC ? slot_time_factor<T>(a, s0 + s + v) : T(0);
+      line_solve<T, V, SRC>(buf + tile_off(a, s, p, 0), a.axis == 0 ? a.TS : a.P * a.TS, a.L, fl_s + p * Lp,
+                            fr_s + p * Lp, src_s + p * Lp, ft);
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      issue_tile_store(&map, a, buf, t);
+      const int t2 = t + 2 * (int)gridDim.x;
+      if (t2 < ntiles) {
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // the stage may be refilled
+        issue_tile_load<T, SRC>(&map, a, buf, fl_s, fr_s, src_s, &bars[stage], t2);
+      }
+    }
+  }
+  if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// U (slice-major, FP64, slices [s_first, s_first+nsl)) <-> W (interleaved, S_pad slots).
+template <typename T>
+__global__ void to_interleaved_kernel(const double* __restrict__ U, T* __restrict__ W, long long nt, int S_pad,
+                                      int s_first, int nsl) {
+  __shared__ double tile[32][33];
+  const long long pos0 = (long long)blockIdx.x * 32;
+  const int sl0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int sl = sl0 + r;
+    const long long pos = pos0 + threadIdx.x;
+    tile[r][threadIdx.x] = (sl < nsl && pos < nt) ? U[(long long)sl * nt + pos] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const long long pos = pos0 + r;
+    const int sl = sl0 + threadIdx.x;
+    if (sl < nsl && pos < nt) W[pos * S_pad + s_first + sl] = (T)tile[threadIdx.x][r];
+  }
+}
+template <typename T>
+__global__ void from_interleaved_kernel(const T* __restrict__ W, double* __restrict__ U, long long nt, int S_pad,
+                                        int s_first, int nsl) {
+  __shared__ double tile[32][33];
+  const long long pos0 = (long long)blockIdx.x * 32;
+  const int sl0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const long long pos = pos0 + r;
+    const int sl = sl0 + threadIdx.x;
+    tile[r][threadIdx.x] = (sl < nsl && pos < nt) ? (double)W[pos * S_pad + s_first + sl] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int sl = sl0 + r;
+    const long long pos = pos0 + threadIdx.x;
+    if (sl < nsl && pos < nt) U[(long long)sl * nt + pos] = tile[threadIdx.x][r];
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    PS_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !f) throw Error(PS_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+
+}  // namespace
+
+// Chooses the tile shape of one direction and encodes its tensor map.
+void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void* W, int positions, int pipe,
+               int slots) {
+  const int L = g.n[axis];
+  tp.axis = axis;
+  tp.L = L;
+  // slots per tile: 256-byte rows of slots when the slot count allows, else 128-byte rows
+  // 32 slots per tile (128-byte rows in FP32, 256-byte rows in FP64): measured best on
+  // 255^3 x 64 slices among 16/32/64 slots and 1/2/4 positions
+  tp.TS = S_pad % 32 == 0 ? 32 : 128 / elem;
+  if (slots > 0) {
+    // requested slots per tile: a divisor of S_pad whose rows are a multiple of 128 bytes,
+    // so that every TMA destination in the tile (rows, positions, chunks) is 128-byte
+    // aligned as tensor copies require
+    int ts = slots;
+    while (ts > 1 && S_pad % ts != 0) ts /= 2;
+    if ((ts * elem) % 128 == 0 && S_pad % ts == 0) tp.TS = ts;
+  }
+  PS_REQUIRE((tp.TS * elem) % 128 == 0, "tile rows must be a multiple of 128 bytes");
+  tp.pipe = pipe < 0 ? 1 : pipe;
+  const int stages = tp.pipe ? 2 : 1;
+  const size_t budget = tp.pipe ? 72 * 1024 : 96 * 1024;  // per CTA, so that 2-3 CTAs share an SM
+  const int nb = g.n[axis == 0 ? 1 : 0];  // the paired axis: y for x-lines, x otherwise
+  if (positions > 0) {
+    tp.P = positions >= 4 ? 4 : (positions >= 2 ? 2 : 1);
+    // fewer positions when the paired axis is short or the stages would not fit in shared memory
+    while (tp.P > 1 && (tp.P > nb || (size_t)stages * tp.TS * tp.P * L * elem > 200 * 1024)) tp.P /= 2;
+  } else {
+    tp.P = 1;
+    while (tp.P < 4 && tp.P * 2 <= nb && (size_t)stages * tp.TS * (tp.P * 2) * L * elem <= budget) tp.P *= 2;
+  }
+  // a TMA box extent is at most 256: split the line into the fewest equal chunks
+  tp.chunks = (L + 255) / 256;
+  while (L % tp.chunks) ++tp.chunks;
+  tp.chunk = L / tp.chunks;
+  // globals: dims (S_pad, nx, ny, nz), strides in bytes of dims 1..3
+  cuuint64_t dims[4] = {(cuuint64_t)S_pad, (cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
+  cuuint64_t strides[3] = {(cuuint64_t)S_pad * elem, (cuuint64_t)S_pad * elem * g.n[0],
+                           (cuuint64_t)S_pad * elem * g.n[0] * g.n[1]};
+  cuuint32_t box[4] = {(cuuint32_t)tp.TS, 1, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  if (axis == 0) {
+    box[1] = tp.chunk;
+  } else if (axis == 1) {
+    box[1] = tp.P;
+    box[2] = tp.chunk;
+  } else {
+    box[1] = tp.P;
+    box[3] = tp.chunk;
+  }
+  CUresult r = encode_fn()(&tp.map, elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, W,
+                           dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(PS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  const int lines = tp.TS * tp.P;
+  const int Lp = (L + 3) & ~3;
+  tp.V = (elem == 4 && tp.TS >= 32) ? 2 : 1;  // slots per thread: FP32 threads take two adjacent lines
+  // stages x (tile + factor rows l, r) + alignment + barriers; the source, when added, takes
+  // one more factor row per position and stage
+  tp.smem = (size_t)stages * ((size_t)lines * L * elem + 2 * (size_t)tp.P * Lp * elem + 64) + 64;
+  tp.threads = lines / tp.V;
+  int dev = 0, maxsm = 0;
+  PS_CUDA(cudaGetDevice(&dev));
+  PS_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  // the x-sweep of a step's first substep also stages the source: P * L more per stage
+  if (tp.smem + (size_t)stages * tp.P * Lp * elem + 256 > (size_t)maxsm)
+    throw Error(PS_ERR_UNSUPPORTED, "fine line tile does not fit in shared memory (line too long)");
+}
+
+template <typename T>
+void tile_sweep(const Geom& g, const TilePlan& tp, const LineFactors& f, int S_pad, int s_first, int nsl,
+                const SourceArgs& sa, const T* srcrow, int* err, cudaStream_t st) {
+  TileArgs a{};
+  a.axis = tp.axis;
+  a.L = tp.L;
+  a.P = tp.P;
+  a.TS = tp.TS;
+  a.n[0] = g.n[0];
+  a.n[1] = g.n[1];
+  a.n[2] = g.n[2];
+  const int other[3][2] = {{1, 2}, {0, 2}, {0, 1}};  // (b, c) axes per line axis
+  const int bax = other[tp.axis][0], cax = other[tp.axis][1];
+  a.nb = g.n[bax];
+  a.nbt = (a.nb + tp.P - 1) / tp.P;
+  a.s_lo = s_first / tp.TS;
+  a.s_hi = (s_first + nsl + tp.TS - 1) / tp.TS;
+  a.chunks = tp.chunks;
+  a.chunk = tp.chunk;
+  a.var = f.var;
+  a.rows_x = (long long)g.n[1] * g.n[2];
+  a.Lp = (tp.L + 3) & ~3;
+  if (sizeof(T) == 4) {
+    a.fl = f.lt32.p;
+    a.fr = f.rt32.p;
+  } else {
+    a.fl = f.lt64.p;
+    a.fr = f.rt64.p;
+  }
+  a.src = sa.src;
+  a.srcrow = srcrow;
+  a.src_t = sa.src_t;
+  a.t_first = sa.t0;
+  a.t_slice = sa.tstride;
+  a.src_t_len = sa.src_t_len;
+  PS_REQUIRE(a.fl && a.fr, "line-major factors of the sweep's precision are missing");
+  PS_REQUIRE(!sa.src || srcrow, "line-major source rows are missing");
+  a.tau = sa.tau;
+  a.err = err;
+  const long long tiles = (long long)(a.s_hi - a.s_lo) * a.nbt * g.n[cax];
+  const bool src = sa.src != nullptr;
+  PS_REQUIRE(!src || tp.axis == 0, "the source enters with the x-substep");
+  const int stages = tp.pipe ? 2 : 1;
+  const int Lp = (tp.L + 3) & ~3;
+  const size_t smem = tp.smem + (src ? (size_t)stages * tp.P * Lp * sizeof(T) : 0);
+  if (!tp.pipe) {
+    auto kern = tp.V == 2 ? (src ? tile_sweep_kernel<T, 2, true> : tile_sweep_kernel<T, 2, false>)
+                          : (src ? tile_sweep_kernel<T, 1, true> : tile_sweep_kernel<T, 1, false>);
+    PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)tiles, tp.threads, smem, st>>>(tp.map, a);
+  } else {
+    auto kern = tp.V == 2 ? (src ? tile_sweep_pipe_kernel<T, 2, true> : tile_sweep_pipe_kernel<T, 2, false>)
+                          : (src ? tile_sweep_pipe_kernel<T, 1, true> : tile_sweep_pipe_kernel<T, 1, false>);
+    PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0, dev = 0, sms = 0;
+    PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tp.threads, smem));
+    PS_CUDA(cudaGetDevice(&dev));
+    PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    per_sm = std::max(per_sm, 1);
+    const long long grid = std::min<long long>(tiles, (long long)per_sm * sms);
+    kern<<<(unsigned)grid, tp.threads, smem, st>>>(tp.map, a, (int)tiles);
+  }
+  PS_CUDA(cudaGetLastError());
+}
+
+template void tile_sweep<float>(const Geom&, const TilePlan&, const LineFactors&, int, int, int, const SourceArgs&,
+                                const float*, int*, cudaStream_t);
+template void tile_sweep<double>(const Geom&, const TilePlan&, const LineFactors&, int, int, int, const SourceArgs&,
+                                 const double*, int*, cudaStream_t);
+
+// Line-major copies [line][Lp] (zero padded) of a direction's factors, in the tile's
+// precision.  Line numbering: c * n_b + b, with (b, c) = (y, z) for x-lines, (x, z) for
+// y-lines, (x, y) for z-lines.
+template <typename T>
+__global__ void line_major_kernel(const T* __restrict__ l, const T* __restrict__ r, T* __restrict__ lt,
+                                  T* __restrict__ rt, int axis, int nx, int ny, int nz, long long lines, int L, int Lp,
+                                  int var) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= lines * Lp) return;
+  const long long line = e / Lp;
+  const int i = (int)(e - line * Lp);
+  T lv = T(0), rv = T(0);
+  if (i < L) {
+    long long idx;
+    if (!var) idx = i;
+    else if (axis == 0) idx = (long long)i * lines + line;  // transposed x-factors: [i][z*ny + y]
+    else if (axis == 1) {
+      const long long z = line / nx, x = line % nx;
+      idx = (z * ny + i) * nx + x;
+    } else {
+      const long long y = line / nx, x = line % nx;
+      idx = ((long long)i * ny + y) * nx + x;
+    }
+    lv = l[idx];
+    rv = r[idx];
+  }
+  lt[e] = lv;
+  rt[e] = rv;
+}
+__global__ void src_rows_kernel(const double* __restrict__ src, void* out, int elem, long long rows, int nx, int Lp) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * Lp) return;
+  const long long row = e / Lp;
+  const int i = (int)(e - row * Lp);
+  const double v = i < nx ? src[row * nx + i] : 0.0;
+  if (elem == 4) reinterpret_cast<float*>(out)[e] = (float)v;
+  else reinterpret_cast<double*>(out)[e] = v;
+}
+
+void factor_lines(const Geom& g, LineFactors& f, bool fp32, cudaStream_t st) {
+  const int m = f.m, L = g.n[m], Lp = (L + 3) & ~3;
+  const long long lines = g.nt / L;
+  const long long total = lines * Lp;
+  const unsigned blocks = (unsigned)((total + 255) / 256);
+  if (fp32) {
+    f.lt32.alloc((size_t)total);
+    f.rt32.alloc((size_t)total);
+    line_major_kernel<float><<<blocks, 256, 0, st>>>(f.l32.p, f.r32.p, f.lt32.p, f.rt32.p, m, g.n[0], g.n[1], g.n[2],
+                                                     lines, L, Lp, f.var);
+  } else {
+    f.lt64.alloc((size_t)total);
+    f.rt64.alloc((size_t)total);
+    line_major_kernel<double><<<blocks, 256, 0, st>>>(f.l64.p, f.r64.p, f.lt64.p, f.rt64.p, m, g.n[0], g.n[1],
+                                                      g.n[2], lines, L, Lp, f.var);
+  }
+  PS_CUDA(cudaGetLastError());
+}
+
+void source_rows(const Geom& g, const double* src, void* out, int elem, cudaStream_t st) {
+  const int Lp = (g.n[0] + 3) & ~3;
+  const long long rows = g.nt / g.n[0];
+  const long long total = rows * Lp;
+  src_rows_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(src, out, elem, rows, g.n[0], Lp);
+  PS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void to_interleaved(const Geom& g, const double* U, T* W, int S_pad, int s_first, int nsl, cudaStream_t st) {
+  dim3 grid((unsigned)((g.nt + 31) / 32), (unsigned)((nsl + 31) / 32));
+  to_interleaved_kernel<T><<<grid, dim3(32, 8), 0, st>>>(U, W, g.nt, S_pad, s_first, nsl);
+  PS_CUDA(cudaGetLastError());
+}
+template <typename T>
+void from_interleaved(const Geom& g, const T* W, double* U, int S_pad, int s_first, int nsl, cudaStream_t st) {
+  dim3 grid((unsigned)((g.nt + 31) / 32), (unsigned)((nsl + 31) / 32));
+  from_interleaved_kernel<T><<<grid, dim3(32, 8), 0, st>>>(W, U, g.nt, S_pad, s_first, nsl);
+  PS_CUDA(cudaGetLastError());
+}
+template void to_interleaved<float>(const Geom&, const double*, float*, int, int, int, cudaStream_t);
+template void to_interleaved<double>(const Geom&, const double*, double*, int, int, int, cudaStream_t);
+template void from_interleaved<float>(const Geom&, const float*, double*, int, int, int, cudaStream_t);
+template void from_interleaved<double>(const Geom&, const double*, double*, int, int, int, cudaStream_t);
+
+}  // namespace ps

@@ -1,0 +1,38 @@
+// ps_tile.h -- fine-propagator sweeps on the slice-interleaved layout (ps_tile.cu).
+#pragma once
+
+#include <cuda.h>
+
+#include "ps_internal.h"
+
+namespace ps {
+
+// Tile shape and TMA tensor map of one sweep direction over W[z][y][x][S_pad].
+struct TilePlan {
+  CUtensorMap map;
+  int axis = 0, L = 0, TS = 32, P = 1, chunks = 1, chunk = 0, threads = 0;
+  int V = 1;         // adjacent slots (lines) per thread
+  int pipe = 1;      // persistent double-buffered CTAs (1) or one tile per CTA (0)
+  int ctas_per_sm = 1;
+  size_t smem = 0;   // dynamic shared memory per CTA without the source staging
+};
+
+// positions: 1, 2 or 4 line positions per tile (0 = largest that fits); pipe: 1 persistent
+// double-buffered, 0 one tile per CTA, -1 auto.
+void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void* W, int positions = 0, int pipe = -1,
+               int slots = 0);
+// One substep along tp.axis on slots [s_first, s_first + nsl) (whole TS-slot groups are
+// processed).  `err` is set when a tile's TMA load does not arrive within the wait limit.
+template <typename T>
+void tile_sweep(const Geom& g, const TilePlan& tp, const LineFactors& f, int S_pad, int s_first, int nsl,
+                const SourceArgs& sa, const T* srcrow, int* err, cudaStream_t st);
+// Line-major, zero-padded copies of a direction's factors for the tile sweeps (f.lt*, f.rt*).
+void factor_lines(const Geom& g, LineFactors& f, bool fp32, cudaStream_t st);
+// Source rows along x, line-major [z*ny + y][Lp], in precision elem (4 or 8 bytes).
+void source_rows(const Geom& g, const double* src, void* out, int elem, cudaStream_t st);
+template <typename T>
+void to_interleaved(const Geom& g, const double* U, T* W, int S_pad, int s_first, int nsl, cudaStream_t st);
+template <typename T>
+void from_interleaved(const Geom& g, const T* W, double* U, int S_pad, int s_first, int nsl, cudaStream_t st);
+
+}  // namespace ps
