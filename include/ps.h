@@ -139,6 +139,26 @@ int ps_run_fine_sequential(ps_problem* p, const double* u0_dev, double* U_out_de
 /* Sequential coarse solution U_n = G^n(u0), (N+1) states. */
 int ps_run_coarse_sequential(ps_problem* p, const double* u0_dev, double* U_out_dev, uintptr_t stream);
 
+/* Sequential coarse solution U_n = G^n(u0) without allocating any device memory.
+ *
+ * No counterpart in the paper: this is a service for callers that cannot allocate, such as
+ * code running where cudaMalloc is forbidden or unsafe (inside a host callback or a memory
+ * pool's own allocation hook, or under a budget that leaves no device memory to spare).
+ * It computes exactly what ps_run_coarse_sequential computes (same kernels, same order),
+ * but keeps the coarse working state in a fixed array of PS_NOALLOC_MAX_UNKNOWNS doubles
+ * (8 MiB) that every GPU loading this library reserves until the process exits, instead of
+ * in the problem's own workspace.  The caller passes the input u0_dev and the output
+ * U_out_dev ((N+1) states), as for the allocating version.
+ *  - Grids with more than PS_NOALLOC_MAX_UNKNOWNS interior unknowns are rejected with
+ *    PS_ERR_INVALID before any GPU work.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *    with that device current; make that first call before any stream capture.
+ *  - All calls share the one array: calls that overlap on the GPU (other streams, other
+ *    threads) race and produce wrong results.  Serialise them.
+ *  - Nothing in the array needs to start at zero: each coarse step overwrites it fully. */
+#define PS_NOALLOC_MAX_UNKNOWNS (1 << 20)
+int ps_run_coarse_sequential_noalloc(ps_problem* p, const double* u0_dev, double* U_out_dev, uintptr_t stream);
+
 /* Building blocks on one state x_dev (in place), for testing the kernels.
  * which = 0: fine propagator's step size and splitting, 1: coarse.
  * ps_substep_solve: x <- (I - tau A_m)^{-1} x (one internal stage of eq. FIE_method).

@@ -25,6 +25,7 @@ ERRORS = {1: "PS_ERR_INVALID", 2: "PS_ERR_CUDA", 3: "PS_ERR_OOM", 4: "PS_ERR_NON
 PS_SPLIT_DIM, PS_SPLIT_DD = 0, 1
 PS_PREC_FP64, PS_PREC_MIXED = 0, 1
 PS_SCHED_AUTO, PS_SCHED_THOMAS, PS_SCHED_PCR = 0, 1, 2
+PS_NOALLOC_MAX_UNKNOWNS = 1 << 20
 
 _lock = threading.Lock()
 _lib = None
@@ -80,6 +81,7 @@ SIGNATURES = {
     "ps_get_history": [_VP, _VP, _I, _IP],
     "ps_run_fine_sequential": [_VP, _VP, _VP, _U],
     "ps_run_coarse_sequential": [_VP, _VP, _VP, _U],
+    "ps_run_coarse_sequential_noalloc": [_VP, _VP, _VP, _U],
     "ps_substep_solve": [_VP, _I, _I, _VP, _U],
     "ps_propagate": [_VP, _I, _I, _I, _I, _VP, _U],
     "ps_problem_stats": [_VP, C.POINTER(_Stats)],
@@ -246,6 +248,14 @@ class Problem:
         import torch
         out = torch.empty((self.N + 1,) + self.grid.shape, dtype=torch.float64, device="cuda")
         check(lib().ps_run_coarse_sequential(self._h, _dev_ptr(u0, self.grid.nt), _dev_ptr(out), _stream(stream)))
+        return out
+
+    def coarse_sequential_noalloc(self, u0, out, stream=None):
+        """Same result as coarse_sequential, computed without any device allocation inside the
+        library (the working state lives in a fixed per-device array of
+        PS_NOALLOC_MAX_UNKNOWNS doubles); the caller provides `out` ((N+1) states)."""
+        check(lib().ps_run_coarse_sequential_noalloc(self._h, _dev_ptr(u0, self.grid.nt),
+                                                     _dev_ptr(out, (self.N + 1) * self.grid.nt), _stream(stream)))
         return out
 
     def substep_solve(self, which, m, x, stream=None):

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -434,6 +435,50 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
 
 }  // namespace
 
+// ---------------------------------------------------------------------------------------
+// Coarse sequential solution without device allocation (ps_run_coarse_sequential_noalloc).
+// The working state of each coarse step lives in this file-scope array instead of the
+// problem's workspace.  Host code must not take its address directly: the symbol's host
+// stand-in is not a device address, so the device address is looked up once per device.
+static __device__ __align__(256) double g_noalloc_work[PS_NOALLOC_MAX_UNKNOWNS];
+
+namespace {
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[64] = {};
+
+double* noalloc_work_ptr() {
+  int dev = 0;
+  PS_CUDA(cudaGetDevice(&dev));
+  PS_REQUIRE(dev >= 0 && dev < 64, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    PS_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_work));
+    g_noalloc_ptr[dev] = static_cast<double*>(ptr);
+  }
+  return g_noalloc_ptr[dev];
+}
+
+// One coarse step from `in` into `work`: the same launches as the allocating coarse step,
+// without the kernel timer (whose events it would otherwise create).
+void coarse_step_into(ps_problem* p, int n, int q, const double* in, double* work, cudaStream_t st) {
+  Prop& P = p->G;
+  const int t_end = n * p->fs + (q + 1) * P.tstride;
+  const int M = P.sp->M;
+  if (P.sp->kind == PS_SPLIT_DD) {
+    SourceArgs sa = source_for(p, P, t_end, 0);
+    dd_rhs(p->g, 1, in, work, sa, st);
+    const int spb = p->prm.dd_slices_per_block > 0 ? p->prm.dd_slices_per_block : 2;
+    for (int c = 0; c < M; ++c) dd_solve(p->g, 1, *P.dd, c, work, spb, st);
+    return;
+  }
+  for (int m = 0; m < M; ++m) {
+    SourceArgs sa = m == 0 ? source_for(p, P, t_end, 0) : SourceArgs{};
+    sweep_dim<double, double>(p->g, 1, *P.dim[m], false, m == 0 ? in : work, work, sa, CorrArgs{}, nullptr, st);
+  }
+}
+}  // namespace
+
 extern "C" {
 
 const char* ps_last_error(void) { return g_last_error.c_str(); }
@@ -717,6 +762,24 @@ int ps_problem_stats(const ps_problem* p, ps_stats* out) {
     out->ms_fine = p->ms_fine;
     out->ms_coarse = p->ms_coarse;
     out->kernel_launches = p->launches;
+  });
+}
+
+int ps_run_coarse_sequential_noalloc(ps_problem* p, const double* u0_dev, double* U_out_dev, uintptr_t stream) {
+  return guarded([&] {
+    PS_REQUIRE(p && u0_dev && U_out_dev, "null argument");
+    const long long nt = p->g.nt;
+    if (nt > PS_NOALLOC_MAX_UNKNOWNS)
+      throw Error(PS_ERR_INVALID, "grid has " + std::to_string(nt) + " unknowns; the no-allocation coarse solve holds at most " +
+                                      std::to_string(PS_NOALLOC_MAX_UNKNOWNS));
+    cudaStream_t st = S(stream);
+    double* work = noalloc_work_ptr();
+    PS_CUDA(cudaMemcpyAsync(U_out_dev, u0_dev, sizeof(double) * nt, cudaMemcpyDeviceToDevice, st));
+    for (int n = 0; n < p->N; ++n) {
+      for (int q = 0; q < p->G.steps; ++q) coarse_step_into(p, n, q, q == 0 ? U_out_dev + n * nt : work, work, st);
+      PS_CUDA(cudaMemcpyAsync(U_out_dev + (n + 1) * nt, work, sizeof(double) * nt, cudaMemcpyDeviceToDevice, st));
+    }
+    PS_CUDA(cudaStreamSynchronize(st));
   });
 }
 
