@@ -106,7 +106,8 @@ typedef struct {
   int tile_pipeline;       /* fine line solves: 1 persistent double-buffered CTAs, 2 one tile per
                               CTA, 0 = auto */
   int tile_slots;          /* fine line solves: time slices per TMA tile (16, 32, 64); 0 = auto */
-  int reserved[1];
+  int tol_mode;            /* stopping test: 0 = max_n ||U_n^k - U_n^{k-1}||_inf < tol (absolute);
+                              1 = max_n ||U_n^k - U_n^{k-1}||_inf / ||U_n^k||_inf < tol (per slice) */
 } ps_params;
 
 /* fine, coarse: splittings of the same operator used by F and G (coarse = NULL: use
@@ -138,6 +139,28 @@ int ps_get_history(const ps_problem* p, double* inc_host, int cap, int* len);
 int ps_run_fine_sequential(ps_problem* p, const double* u0_dev, double* U_out_dev, uintptr_t stream);
 /* Sequential coarse solution U_n = G^n(u0), (N+1) states. */
 int ps_run_coarse_sequential(ps_problem* p, const double* u0_dev, double* U_out_dev, uintptr_t stream);
+
+/* Replace the nodal diffusion coefficient (same layout as at ps_operator_create, which must
+ * have been given one) and rebuild the problem's substep factors for both step sizes.  The
+ * operator is shared: other problems built on it see the new coefficient after their own
+ * update call. */
+int ps_problem_update_coefficients(ps_problem* p, const double* a_nodal_dev, uintptr_t stream);
+
+/* Vector-Jacobian product of the last parareal run (no counterpart in the paper; the
+ * transpose of the FIE steps).  With U_N the sequential fine solution from u0 and the
+ * coefficient a, and g = gN_dev an upstream gradient dL/dU_N, returns dL/du0 = J_u0^T g and
+ * dL/da = J_a^T g (nodal, boundary included; NULL to skip).  The slice-boundary adjoints
+ * lambda_n = F^T lambda_{n+1}, lambda_N = g, come from a parareal iteration with the
+ * transposed propagators (substeps in reverse order, no source) run backwards in time to
+ * the per-slice relative tolerance `tol` (max_iter <= 0: N); the coefficient gradient then
+ * recomputes the fine steps inside every slice from the forward checkpoints U_n (all slices
+ * at once, FP64) and accumulates -tau (nu_Q - nu_P)(w_Q - w_P)/h^2 over every edge of every
+ * substep, half to each end node.  Needs a preceding ps_run_parareal on this problem (its
+ * states are the checkpoints, so run it to a tight tolerance, e.g. tol_mode = 1); FP64
+ * precision and dimensional splitting for the coefficient gradient.  The problem's states
+ * are the forward ones again on return; *iters_out = adjoint parareal iterations. */
+int ps_adjoint_vjp(ps_problem* p, const double* gN_dev, double tol, int max_iter, double* grad_u0_dev,
+                   double* grad_a_dev, uintptr_t stream, int* iters_out);
 
 /* Sequential coarse solution U_n = G^n(u0) without allocating any device memory.
  *

@@ -44,7 +44,7 @@ class _DD(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("precision", C.c_int), ("schedule", C.c_int), ("timing", C.c_int), ("dd_slices_per_block", C.c_int),
                 ("tile_positions", C.c_int), ("tile_pipeline", C.c_int), ("tile_slots", C.c_int),
-                ("reserved", C.c_int * 1)]
+                ("tol_mode", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -85,6 +85,8 @@ SIGNATURES = {
     "ps_substep_solve": [_VP, _I, _I, _VP, _U],
     "ps_propagate": [_VP, _I, _I, _I, _I, _VP, _U],
     "ps_problem_stats": [_VP, C.POINTER(_Stats)],
+    "ps_problem_update_coefficients": [_VP, _VP, _U],
+    "ps_adjoint_vjp": [_VP, _VP, _D, _I, _VP, _VP, _U, _IP],
     "ps_problem_kernel_times": [_VP, C.POINTER(_KTime), _I, _IP],
 }
 _RESTYPE = {"ps_last_error": C.c_char_p}
@@ -200,12 +202,13 @@ class Problem:
 
     def __init__(self, fine: Splitting, T, N, g, s, coarse: Splitting = None, precision="fp64",
                  schedule=PS_SCHED_AUTO, timing=False, dd_slices_per_block=0, tile_positions=0, tile_pipeline=0,
-                 tile_slots=0, stream=None):
+                 tile_slots=0, tol_mode=0, stream=None):
         self.fine, self.coarse = fine, coarse
         self.grid = fine.op.grid
         self.N = int(N)
         prm = _Params(PS_PREC_FP64 if precision == "fp64" else PS_PREC_MIXED, int(schedule), int(timing),
-                      int(dd_slices_per_block), int(tile_positions), int(tile_pipeline), int(tile_slots))
+                      int(dd_slices_per_block), int(tile_positions), int(tile_pipeline), int(tile_slots),
+                      int(tol_mode))
         h = _VP()
         check(lib().ps_problem_create(fine._h, None if coarse is None else coarse._h, float(T), int(N), int(g),
                                       int(s), C.byref(prm), _stream(stream), C.byref(h)))
@@ -273,6 +276,22 @@ class Problem:
         return dict(iterations=s.iterations, unknown_updates=s.unknown_updates, ms_total=s.ms_total,
                     ms_fine=s.ms_fine, ms_coarse=s.ms_coarse, kernel_launches=s.kernel_launches)
 
+    def update_coefficients(self, a, stream=None):
+        """Replace the nodal coefficient and rebuild the substep factors."""
+        check(lib().ps_problem_update_coefficients(self._h, _dev_ptr(a, self.grid.nodal_size), _stream(stream)))
+
+    def vjp(self, gN, tol, max_iter=0, want_a=True, stream=None):
+        """(dL/du0, dL/da) for the upstream gradient gN = dL/dU_N of the last run."""
+        import torch
+        gu = torch.empty(self.grid.shape, dtype=torch.float64, device="cuda")
+        ga = torch.empty(tuple(v + 2 for v in reversed(self.grid.n)), dtype=torch.float64, device="cuda") \
+            if want_a else None
+        it = C.c_int(0)
+        check(lib().ps_adjoint_vjp(self._h, _dev_ptr(gN, self.grid.nt), float(tol), int(max_iter), _dev_ptr(gu),
+                                   _dev_ptr(ga), _stream(stream), C.byref(it)))
+        self.last_adjoint_iters = it.value
+        return gu, ga
+
     def kernel_times(self):
         """Per-kernel-kind times of the last run (needs timing=2): name -> dict."""
         buf = (_KTime * 64)()
@@ -285,3 +304,24 @@ class Problem:
         if getattr(self, "_h", None):
             lib().ps_problem_destroy(self._h)
             self._h = None
+
+
+def parareal_solve(problem: "Problem", u0, a, tol, adjoint_tol=None):
+    """U_N of the parareal solve as a differentiable function of u0 and the nodal
+    coefficient a (torch.autograd.Function backed by ps_run_parareal and ps_adjoint_vjp)."""
+    import torch
+
+    class _Solve(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, u0_, a_):
+            problem.update_coefficients(a_.detach().contiguous())
+            problem.run(u0_.detach().contiguous(), tol)
+            return problem.state(problem.N).clone()
+
+        @staticmethod
+        def backward(ctx, gN):
+            gu, ga = problem.vjp(gN.detach().contiguous(), adjoint_tol if adjoint_tol is not None else tol,
+                                 want_a=ctx.needs_input_grad[1])
+            return gu, ga
+
+    return _Solve.apply(u0, a)

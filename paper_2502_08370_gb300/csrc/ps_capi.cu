@@ -18,6 +18,7 @@
 #include <string>
 #include <vector>
 
+#include "ps_adjoint.h"
 #include "ps_dd.h"
 #include "ps_tile.h"
 
@@ -160,6 +161,14 @@ struct ps_problem {
   DevBuf<int> tmo;      // set by a kernel whose bounded wait ran out
   DevBuf<float> srcrow32;   // fine source rows along x, line-major (tile sweeps)
   DevBuf<double> srcrow64;
+  DevBuf<unsigned long long> sstats;  // per slice {max |U^k - U^{k-1}|, max |U^k|}, slices 0..N
+  unsigned long long* h_sstats = nullptr;
+  bool transposed = false;  // propagate with the transposed steps (substeps reversed, no source)
+  bool have_forward = false;
+  // adjoint workspaces (allocated by the first ps_adjoint_vjp with a coefficient gradient)
+  DevBuf<double> Uchk, snap, Lam, gedge[3];
+  TilePlan adj_tiles[3];
+  bool adj_ready = false;
   DevBuf<unsigned long long> inc;
   DevBuf<int> flag;
   unsigned long long* h_inc = nullptr;
@@ -172,6 +181,7 @@ struct ps_problem {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   KernelTimer kt;
   ~ps_problem() {
+    if (h_sstats) cudaFreeHost(h_sstats);
     if (h_inc) cudaFreeHost(h_inc);
     if (h_flag) cudaFreeHost(h_flag);
     for (auto& e : ev)
@@ -204,7 +214,7 @@ void build_prop(ps_problem* p, Prop& P, const ps_splitting* sp, double tau, int 
 
 SourceArgs source_for(const ps_problem* p, const Prop& P, int t0, int tslice) {
   SourceArgs sa;
-  if (!p->op->src.p) return sa;
+  if (!p->op->src.p || p->transposed) return sa;  // the transposed (adjoint) steps carry no source
   sa.src = p->op->src.p;
   sa.src_t = p->op->src_t.p;
   sa.t0 = t0;
@@ -251,7 +261,8 @@ void fie_step_dd(ps_problem* p, Prop& P, int nsl, const double* in, double* out,
     p->launches++;
   }
   const int spb = p->prm.dd_slices_per_block > 0 ? p->prm.dd_slices_per_block : 2;
-  for (int c = 0; c < M; ++c) {
+  for (int q = 0; q < M; ++q) {
+    const int c = p->transposed ? M - 1 - q : q;
     p->kt.begin(st);
     dd_solve(p->g, nsl, *P.dd, c, out, spb, st);
     if (p->kt.on) {
@@ -277,10 +288,15 @@ void fie_step64(ps_problem* p, Prop& P, int nsl, const double* in, double* out, 
     return;
   }
   const int M = P.sp->M;
-  for (int m = 0; m < M; ++m) {
-    SourceArgs sa = m == 0 ? source_for(p, P, t0, tslice) : SourceArgs{};
-    const double* src_state = m == 0 ? in : out;
-    const bool epi = (m == M - 1 && corr.mode != 0);
+  const bool tr = p->transposed;
+  // the transposed step ends with the x-substep, whose kernel carries no epilogue: then the
+  // correction runs as its own pass over the slice
+  const bool fuse = corr.mode != 0 && !tr;
+  for (int q = 0; q < M; ++q) {
+    const int m = tr ? M - 1 - q : q;
+    SourceArgs sa = q == 0 ? source_for(p, P, t0, tslice) : SourceArgs{};
+    const double* src_state = q == 0 ? in : out;
+    const bool epi = (q == M - 1 && fuse);
     double bytes = 0, flops = 0;
     if (p->kt.on) sweep_cost(p, *P.dim[m], nsl, 8, 8, 8, sa.src != nullptr, epi ? corr.mode : 0, &bytes, &flops);
     p->kt.begin(st);
@@ -291,6 +307,12 @@ void fie_step64(ps_problem* p, Prop& P, int nsl, const double* in, double* out, 
     if (p->kt.on)
       p->kt.end(std::string(phase) + "." + kAxis[m] + ".f64" + (epi ? (corr.mode == 1 ? "+corr" : "+init") : ""),
                 bytes, flops);
+    p->launches++;
+  }
+  if (corr.mode != 0 && !fuse) {
+    p->kt.begin(st);
+    dd_correct(p->g, out, corr, st);
+    if (p->kt.on) p->kt.end(std::string(phase) + (corr.mode == 1 ? ".corr.f64" : ".init.f64"), p->g.nt * 48.0, 0.0);
     p->launches++;
   }
 }
@@ -310,8 +332,9 @@ void run_F_tiles(ps_problem* p, int n_first, int nsl, const double* in, double* 
   if (p->kt.on) p->kt.end(std::string("F.pack.") + tn, nsl * nt * (8.0 + sizeof(T)), 0.0);
   p->launches++;
   for (int j = 0; j < P.steps; ++j) {
-    for (int m = 0; m < M; ++m) {
-      SourceArgs sa = m == 0 ? source_for(p, P, j + 1, p->fs) : SourceArgs{};
+    for (int q = 0; q < M; ++q) {
+      const int m = p->transposed ? M - 1 - q : q;
+      SourceArgs sa = q == 0 ? source_for(p, P, j + 1, p->fs) : SourceArgs{};
       const LineFactors& f = *P.dim[m];
       double bytes = 0, flops = 0;
       if (p->kt.on) sweep_cost(p, f, nsl, sizeof(T), sizeof(T), sizeof(T), sa.src != nullptr, 0, &bytes, &flops);
@@ -360,6 +383,7 @@ CorrArgs corr_args(ps_problem* p, int mode, int n) {
   c.Gold = p->Gold.p + n * nt;
   c.inc = p->inc.p;
   c.nonfinite = p->flag.p;
+  c.slice_stats = p->sstats.p + 2 * (n + 1);
   return c;
 }
 
@@ -389,17 +413,21 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
     ++k;
     const int nlo = k - 1;
     PS_CUDA(cudaMemsetAsync(p->inc.p, 0, sizeof(unsigned long long), st));
+    PS_CUDA(cudaMemsetAsync(p->sstats.p, 0, sizeof(unsigned long long) * 2 * (N + 1), st));
     if (timing) PS_CUDA(cudaEventRecord(p->ev[1], st));
     run_F(p, nlo, N - nlo, p->U.p + nlo * nt, p->Fout.p + nlo * nt, st);
     if (timing) PS_CUDA(cudaEventRecord(p->ev[2], st));
     // slice k-1: U_k^k = F(U_{k-1}^{k-1}) exactly (its G bracket is zero)
-    copy_with_increment(nt, p->Fout.p + nlo * nt, p->U.p + k * nt, p->inc.p, p->flag.p, st);
+    copy_with_increment(nt, p->Fout.p + nlo * nt, p->U.p + k * nt, p->inc.p, p->flag.p, p->sstats.p + 2 * k, st);
     p->launches++;
     for (int n = k; n < N; ++n) run_G(p, n, p->U.p + n * nt, corr_args(p, 1, n), st);
     if (timing) PS_CUDA(cudaEventRecord(p->ev[3], st));
     PS_CUDA(cudaMemcpyAsync(p->h_inc, p->inc.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaMemcpyAsync(p->h_flag, p->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaMemcpyAsync(p->h_flag + 1, p->tmo.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (p->prm.tol_mode == 1)
+      PS_CUDA(cudaMemcpyAsync(p->h_sstats, p->sstats.p, sizeof(unsigned long long) * 2 * (N + 1),
+                              cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaStreamSynchronize(st));
     if (p->h_flag[1]) {
       p->iters = k;
@@ -417,6 +445,17 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
     double inc;
     unsigned long long bits = *p->h_inc;
     std::memcpy(&inc, &bits, sizeof inc);
+    if (p->prm.tol_mode == 1) {
+      // per-slice relative increments: max_n ||U_n^k - U_n^{k-1}|| / ||U_n^k||
+      inc = 0.0;
+      for (int j = 1; j <= N; ++j) {
+        double d, u;
+        std::memcpy(&d, &p->h_sstats[2 * j], sizeof d);
+        std::memcpy(&u, &p->h_sstats[2 * j + 1], sizeof u);
+        const double r = u > 0.0 ? d / u : (d > 0.0 ? HUGE_VAL : 0.0);
+        if (r > inc || r != r) inc = r;
+      }
+    }
     p->hist.push_back(inc);
     if (*p->h_flag) {
       p->iters = k;
@@ -430,6 +469,7 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
     PS_CUDA(cudaEventElapsedTime(&p->ms_total, p->ev[0], p->ev[1]));
   }
   p->iters = k;
+  if (!p->transposed) p->have_forward = true;
   if (iters_out) *iters_out = k;
 }
 
@@ -603,6 +643,9 @@ int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, doub
     p->gtmp.alloc((size_t)nt);
     p->inc.alloc(1);
     p->tmo.alloc(1);
+    p->sstats.alloc((size_t)2 * (N + 1));
+    PS_CUDA(cudaMallocHost(&p->h_sstats, sizeof(unsigned long long) * 2 * (N + 1)));
+    PS_REQUIRE(p->prm.tol_mode == 0 || p->prm.tol_mode == 1, "tol_mode must be 0 or 1");
     if (fine->kind == PS_SPLIT_DIM) {
       const int elem = mixed ? 4 : 8;
       const int TS = mixed ? 32 : 16;
@@ -762,6 +805,122 @@ int ps_problem_stats(const ps_problem* p, ps_stats* out) {
     out->ms_fine = p->ms_fine;
     out->ms_coarse = p->ms_coarse;
     out->kernel_launches = p->launches;
+  });
+}
+
+int ps_problem_update_coefficients(ps_problem* p, const double* a_nodal_dev, uintptr_t stream) {
+  return guarded([&] {
+    PS_REQUIRE(p && a_nodal_dev, "null argument");
+    ps_operator* op = const_cast<ps_operator*>(p->op);
+    PS_REQUIRE(op->a.p, "the operator was created with a = 1; create it with a nodal coefficient to update it");
+    cudaStream_t st = S(stream);
+    PS_CUDA(cudaMemcpyAsync(op->a.p, a_nodal_dev, sizeof(double) * op->a.n, cudaMemcpyDeviceToDevice, st));
+    const bool mixed = p->prm.precision == PS_PREC_MIXED;
+    Geom g3 = p->g;
+    if (g3.dim == 2) g3.n[2] = 1;
+    for (Prop* P : {&p->F, &p->G}) {
+      const bool fine = P == &p->F;
+      if (P->sp->kind == PS_SPLIT_DIM) {
+        for (int m = 0; m < p->g.dim; ++m) {
+          factor_dim(p->g, m, op->a.p, op->c / p->g.dim, P->tau, *P->dim[m], fine && mixed, st);
+          if (fine) factor_lines(g3, *P->dim[m], mixed, st);
+        }
+      } else {
+        dd_factor(p->g, P->sp->dd, op->a.p, op->c, P->tau, *P->dd, st);
+      }
+    }
+    p->have_forward = false;
+    PS_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+namespace {
+// Coefficient gradient: recompute every fine state of every slice from the checkpoints,
+// then sweep backwards with the transposed substeps, accumulating the edge products.
+void adjoint_coefficient_gradient(ps_problem* p, double* grad_a, cudaStream_t st) {
+  Prop& F = p->F;
+  const long long nt = p->g.nt;
+  const int N = p->N, s = F.steps, M = p->g.dim, S_pad = p->S_pad;
+  Geom g3 = p->g;
+  if (g3.dim == 2) g3.n[2] = 1;
+  const size_t wsz = (size_t)S_pad * nt;
+  if (!p->adj_ready) {
+    p->snap.alloc((size_t)s * M * wsz);
+    p->Lam.alloc(wsz);
+    PS_CUDA(cudaMemsetAsync(p->Lam.p, 0, wsz * sizeof(double), st));
+    for (int m = 0; m < M; ++m) {
+      p->gedge[m].alloc((size_t)edge_count(p->g, m));
+      tile_plan(g3, S_pad, 8, m, p->adj_tiles[m], p->Lam.p, p->prm.tile_positions,
+                p->prm.tile_pipeline == 1 ? 1 : 0, p->prm.tile_slots);
+    }
+    p->adj_ready = true;
+  }
+  // forward recomputation from U_0..U_{N-1}, every substep's result kept
+  to_interleaved<double>(p->g, p->Uchk.p, p->W64.p, S_pad, 0, N, st);
+  for (int q = 0; q < s; ++q)
+    for (int m = 0; m < M; ++m) {
+      SourceArgs sa = m == 0 ? source_for(p, F, q + 1, p->fs) : SourceArgs{};
+      tile_sweep<double>(g3, F.tiles[m], *F.dim[m], S_pad, 0, N, sa, p->srcrow64.p, p->tmo.p, st);
+      PS_CUDA(cudaMemcpyAsync(p->snap.p + ((size_t)q * M + m) * wsz, p->W64.p, wsz * sizeof(double),
+                              cudaMemcpyDeviceToDevice, st));
+    }
+  // slot n <- lambda_{n+1} = (adjoint state N-1-n of the reversed-time run held in U)
+  to_interleaved<double>(p->g, p->U.p, p->Lam.p, S_pad, 0, N, st, true);
+  for (int m = 0; m < M; ++m) PS_CUDA(cudaMemsetAsync(p->gedge[m].p, 0, p->gedge[m].n * sizeof(double), st));
+  for (int q = s - 1; q >= 0; --q)
+    for (int m = M - 1; m >= 0; --m) {
+      tile_sweep<double>(g3, p->adj_tiles[m], *F.dim[m], S_pad, 0, N, SourceArgs{}, nullptr, p->tmo.p, st);
+      const double h = 1.0 / (p->g.n[m] + 1);
+      grad_edges(g3, m, p->Lam.p, p->snap.p + ((size_t)q * M + m) * wsz, S_pad, N, F.tau / (h * h), p->gedge[m].p,
+                 st);
+    }
+  const double* ge[3] = {p->gedge[0].p, p->gedge[1].p, M == 3 ? p->gedge[2].p : nullptr};
+  combine_grad(g3, ge, grad_a, st);
+}
+}  // namespace
+
+int ps_adjoint_vjp(ps_problem* p, const double* gN_dev, double tol, int max_iter, double* grad_u0_dev,
+                   double* grad_a_dev, uintptr_t stream, int* iters_out) {
+  return guarded([&] {
+    PS_REQUIRE(p && gN_dev && grad_u0_dev, "null argument");
+    PS_REQUIRE(p->have_forward, "ps_adjoint_vjp needs a preceding ps_run_parareal on this problem");
+    if (grad_a_dev) {
+      if (p->F.sp->kind != PS_SPLIT_DIM || p->G.sp->kind != PS_SPLIT_DIM)
+        throw Error(PS_ERR_UNSUPPORTED, "the coefficient gradient is implemented for the dimensional splitting");
+      if (p->F.f32) throw Error(PS_ERR_UNSUPPORTED, "the coefficient gradient runs in FP64 (PS_PREC_FP64)");
+      PS_REQUIRE(p->op->a.p, "the coefficient gradient needs an operator created with a nodal coefficient");
+    }
+    cudaStream_t st = S(stream);
+    const long long nt = p->g.nt;
+    const size_t ubytes = sizeof(double) * (size_t)(p->N + 1) * nt;
+    if (!p->Uchk.p) p->Uchk.alloc((size_t)(p->N + 1) * nt);
+    PS_CUDA(cudaMemcpyAsync(p->Uchk.p, p->U.p, ubytes, cudaMemcpyDeviceToDevice, st));
+    const int saved_mode = p->prm.tol_mode;
+    const std::vector<double> saved_hist = p->hist;
+    const int saved_iters = p->iters;
+    p->transposed = true;
+    p->prm.tol_mode = 1;
+    try {
+      do_run(p, gN_dev, tol, max_iter, st, iters_out);
+    } catch (...) {
+      p->transposed = false;
+      p->prm.tol_mode = saved_mode;
+      throw;
+    }
+    p->transposed = false;
+    p->prm.tol_mode = saved_mode;
+    PS_CUDA(cudaMemcpyAsync(grad_u0_dev, p->U.p + (long long)p->N * nt, sizeof(double) * nt, cudaMemcpyDeviceToDevice,
+                            st));
+    if (grad_a_dev) adjoint_coefficient_gradient(p, grad_a_dev, st);
+    // the problem's states are the forward ones again
+    PS_CUDA(cudaMemcpyAsync(p->U.p, p->Uchk.p, ubytes, cudaMemcpyDeviceToDevice, st));
+    p->hist = saved_hist;
+    p->iters = saved_iters;
+    p->have_forward = true;
+    PS_CUDA(cudaStreamSynchronize(st));
+    int tmo = 0;
+    PS_CUDA(cudaMemcpy(&tmo, p->tmo.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (tmo) throw Error(PS_ERR_DEVICE_TIMEOUT, "a TMA tile load did not arrive within its wait limit");
   });
 }
 

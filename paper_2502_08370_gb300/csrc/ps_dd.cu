@@ -265,13 +265,14 @@ __global__ void dd_rhs_kernel(const double* in, double* out, long long total, lo
 }
 
 __global__ void dd_correct_kernel(long long nt, const double* __restrict__ g, CorrArgs ca) {
-  double my = 0.0;
+  double my = 0.0, nrm = 0.0;
   bool bad = false;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nt; i += (long long)gridDim.x * blockDim.x) {
     const double gi = g[i];
     if (ca.mode == 1) {
       const double unew = ca.Fout[i] + (gi - ca.Gold[i]);
       my = fmax(my, fabs(unew - ca.U_next[i]));
+      nrm = fmax(nrm, fabs(unew));
       if (!isfinite(unew)) bad = true;
       ca.Gold[i] = gi;
       ca.U_next[i] = unew;
@@ -281,8 +282,15 @@ __global__ void dd_correct_kernel(long long nt, const double* __restrict__ g, Co
       ca.U_next[i] = gi;
     }
   }
-  for (int o = 16; o > 0; o >>= 1) my = fmax(my, __shfl_xor_sync(0xffffffffu, my, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    my = fmax(my, __shfl_xor_sync(0xffffffffu, my, o));
+    nrm = fmax(nrm, __shfl_xor_sync(0xffffffffu, nrm, o));
+  }
   if ((threadIdx.x & 31) == 0 && my > 0.0) atomicMax(ca.inc, (unsigned long long)__double_as_longlong(my));
+  if ((threadIdx.x & 31) == 0 && ca.slice_stats) {
+    if (my > 0.0) atomicMax(ca.slice_stats, (unsigned long long)__double_as_longlong(my));
+    if (nrm > 0.0) atomicMax(ca.slice_stats + 1, (unsigned long long)__double_as_longlong(nrm));
+  }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(ca.nonfinite, 1);
 }
 

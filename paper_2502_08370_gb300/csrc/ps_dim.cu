@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kThreads) sweep_strided_kernel(const Tin* in, 
                                                                 const Tc* __restrict__ fl, const Tc* __restrict__ fr,
                                                                 SourceArgs sa, CorrArgs ca) {
   const long long L = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double my_inc = 0.0;
+  double my_inc = 0.0, my_norm = 0.0;
   bool bad = false;
   if (L < lines) {
     const long long outer = L / S;
@@ -250,6 +250,7 @@ __global__ void __launch_bounds__(kThreads) sweep_strided_kernel(const Tin* in, 
               const double d = fabs(unew - uo[u]);
               if (!isfinite(unew)) bad = true;
               my_inc = fmax(my_inc, d);
+              my_norm = fmax(my_norm, fabs(unew));
               ca.Gold[si] = g;
               ca.U_next[si] = unew;
             } else {
@@ -263,8 +264,15 @@ __global__ void __launch_bounds__(kThreads) sweep_strided_kernel(const Tin* in, 
     }
   }
   if (EPI == 1) {
-    for (int o = 16; o > 0; o >>= 1) my_inc = fmax(my_inc, __shfl_xor_sync(0xffffffffu, my_inc, o));
+    for (int o = 16; o > 0; o >>= 1) {
+      my_inc = fmax(my_inc, __shfl_xor_sync(0xffffffffu, my_inc, o));
+      my_norm = fmax(my_norm, __shfl_xor_sync(0xffffffffu, my_norm, o));
+    }
     if ((threadIdx.x & 31) == 0 && my_inc > 0.0) atomic_max_nonneg(ca.inc, my_inc);
+    if ((threadIdx.x & 31) == 0 && ca.slice_stats) {
+      if (my_inc > 0.0) atomic_max_nonneg(ca.slice_stats, my_inc);
+      if (my_norm > 0.0) atomic_max_nonneg(ca.slice_stats + 1, my_norm);
+    }
   }
   if (EPI != 0) {
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(ca.nonfinite, 1);
@@ -272,18 +280,26 @@ __global__ void __launch_bounds__(kThreads) sweep_strided_kernel(const Tin* in, 
 }
 
 __global__ void copy_inc_kernel(long long n, const double* __restrict__ src, double* __restrict__ dst,
-                                unsigned long long* inc, int* nonfinite) {
+                                unsigned long long* inc, int* nonfinite, unsigned long long* slice_stats) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double my = 0.0;
+  double my = 0.0, nrm = 0.0;
   bool bad = false;
   for (; i < n; i += (long long)gridDim.x * blockDim.x) {
     double v = src[i];
     my = fmax(my, fabs(v - dst[i]));
+    nrm = fmax(nrm, fabs(v));
     if (!isfinite(v)) bad = true;
     dst[i] = v;
   }
-  for (int o = 16; o > 0; o >>= 1) my = fmax(my, __shfl_xor_sync(0xffffffffu, my, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    my = fmax(my, __shfl_xor_sync(0xffffffffu, my, o));
+    nrm = fmax(nrm, __shfl_xor_sync(0xffffffffu, nrm, o));
+  }
   if ((threadIdx.x & 31) == 0 && my > 0.0) atomic_max_nonneg(inc, my);
+  if ((threadIdx.x & 31) == 0 && slice_stats) {
+    if (my > 0.0) atomic_max_nonneg(slice_stats, my);
+    if (nrm > 0.0) atomic_max_nonneg(slice_stats + 1, nrm);
+  }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(nonfinite, 1);
 }
 
@@ -410,9 +426,9 @@ template void sweep_dim<float, double>(const Geom&, int, const LineFactors&, boo
                                        const SourceArgs&, const CorrArgs&, double*, cudaStream_t);
 
 void copy_with_increment(long long nt, const double* src, double* dst, unsigned long long* inc, int* nonfinite,
-                         cudaStream_t st) {
+                         unsigned long long* slice_stats, cudaStream_t st) {
   long long blocks = std::min<long long>((nt + 255) / 256, 152 * 8);
-  copy_inc_kernel<<<(unsigned)blocks, 256, 0, st>>>(nt, src, dst, inc, nonfinite);
+  copy_inc_kernel<<<(unsigned)blocks, 256, 0, st>>>(nt, src, dst, inc, nonfinite, slice_stats);
   PS_CUDA(cudaGetLastError());
 }
 

@@ -108,6 +108,7 @@ struct CorrArgs {
   double* Gold = nullptr;            // G(U_n^{k-1}) in, G(U_n^k) out
   unsigned long long* inc = nullptr; // running max |U^k - U^{k-1}| as bits of a nonnegative double
   int* nonfinite = nullptr;          // set to 1 when a non-finite value appears
+  unsigned long long* slice_stats = nullptr;  // optional {max |U^k - U^{k-1}|, max |U^k|} of this slice
 };
 
 // Launchers (ps_dim.cu).  `in` and `out` may alias (in-place sweeps).  nslices states of
@@ -119,6 +120,6 @@ template <typename Tin, typename Tout>
 void sweep_dim(const Geom& g, int nslices, const LineFactors& f, bool fp32, const Tin* in, Tout* out,
                const SourceArgs& srcargs, const CorrArgs& corr, double* tmp, cudaStream_t st);
 void copy_with_increment(long long nt, const double* src, double* dst, unsigned long long* inc, int* nonfinite,
-                         cudaStream_t st);
+                         unsigned long long* slice_stats, cudaStream_t st);
 
 }  // namespace ps

@@ -471,14 +471,15 @@ __global__ void tile_sweep_pipe_kernel(const __grid_constant__ CUtensorMap map, 
 // U (slice-major, FP64, slices [s_first, s_first+nsl)) <-> W (interleaved, S_pad slots).
 template <typename T>
 __global__ void to_interleaved_kernel(const double* __restrict__ U, T* __restrict__ W, long long nt, int S_pad,
-                                      int s_first, int nsl) {
+                                      int s_first, int nsl, int rev) {
   __shared__ double tile[32][33];
   const long long pos0 = (long long)blockIdx.x * 32;
   const int sl0 = blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int sl = sl0 + r;
     const long long pos = pos0 + threadIdx.x;
-    tile[r][threadIdx.x] = (sl < nsl && pos < nt) ? U[(long long)sl * nt + pos] : 0.0;
+    const long long src = rev ? (long long)(nsl - 1 - sl) : (long long)sl;  // slot s_first + sl <- state src
+    tile[r][threadIdx.x] = (sl < nsl && pos < nt) ? U[src * nt + pos] : 0.0;
   }
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -726,9 +727,9 @@ void source_rows(const Geom& g, const double* src, void* out, int elem, cudaStre
 }
 
 template <typename T>
-void to_interleaved(const Geom& g, const double* U, T* W, int S_pad, int s_first, int nsl, cudaStream_t st) {
+void to_interleaved(const Geom& g, const double* U, T* W, int S_pad, int s_first, int nsl, cudaStream_t st, bool rev) {
   dim3 grid((unsigned)((g.nt + 31) / 32), (unsigned)((nsl + 31) / 32));
-  to_interleaved_kernel<T><<<grid, dim3(32, 8), 0, st>>>(U, W, g.nt, S_pad, s_first, nsl);
+  to_interleaved_kernel<T><<<grid, dim3(32, 8), 0, st>>>(U, W, g.nt, S_pad, s_first, nsl, rev ? 1 : 0);
   PS_CUDA(cudaGetLastError());
 }
 template <typename T>
@@ -737,8 +738,8 @@ void from_interleaved(const Geom& g, const T* W, double* U, int S_pad, int s_fir
   from_interleaved_kernel<T><<<grid, dim3(32, 8), 0, st>>>(W, U, g.nt, S_pad, s_first, nsl);
   PS_CUDA(cudaGetLastError());
 }
-template void to_interleaved<float>(const Geom&, const double*, float*, int, int, int, cudaStream_t);
-template void to_interleaved<double>(const Geom&, const double*, double*, int, int, int, cudaStream_t);
+template void to_interleaved<float>(const Geom&, const double*, float*, int, int, int, cudaStream_t, bool);
+template void to_interleaved<double>(const Geom&, const double*, double*, int, int, int, cudaStream_t, bool);
 template void from_interleaved<float>(const Geom&, const float*, double*, int, int, int, cudaStream_t);
 template void from_interleaved<double>(const Geom&, const double*, double*, int, int, int, cudaStream_t);
 

@@ -30,8 +30,11 @@ void tile_sweep(const Geom& g, const TilePlan& tp, const LineFactors& f, int S_p
 void factor_lines(const Geom& g, LineFactors& f, bool fp32, cudaStream_t st);
 // Source rows along x, line-major [z*ny + y][Lp], in precision elem (4 or 8 bytes).
 void source_rows(const Geom& g, const double* src, void* out, int elem, cudaStream_t st);
+// Pack states U[0..nsl) into slots [s_first, s_first + nsl); rev = true takes them in reverse
+// order (slot s_first + j <- U[nsl - 1 - j]).
 template <typename T>
-void to_interleaved(const Geom& g, const double* U, T* W, int S_pad, int s_first, int nsl, cudaStream_t st);
+void to_interleaved(const Geom& g, const double* U, T* W, int S_pad, int s_first, int nsl, cudaStream_t st,
+                    bool rev = false);
 template <typename T>
 void from_interleaved(const Geom& g, const T* W, double* U, int S_pad, int s_first, int nsl, cudaStream_t st);
 

@@ -1,0 +1,123 @@
+"""GPU adjoint (vector-Jacobian product) against the oracle's discrete adjoint and against
+central finite differences of the GPU forward solve.
+
+J = 1/2 ||U_N - target||^2 with U_N the sequential fine solution (the parareal run is
+taken to a tight per-slice relative tolerance so that its U_N equals the fine solution to
+~1e-13).  Bars: oracle adjoint 1e-9 relative max-norm (parareal, not sequential, on the
+GPU side); finite differences 1e-6 relative.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as orc
+from paper_2502_08370_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ps():
+    from paper_2502_08370_gb300 import build
+    build.build()
+    import paper_2502_08370_gb300 as ps
+    return ps
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def relmax(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def build(ps, n, a, c=0.0, src=None, src_t=None, T=0.2, N=4, s=6, g=1):
+    grid = ps.Grid(n)
+    op = ps.Operator(grid, a=dev(a), c=c, src=None if src is None else dev(src), src_t=src_t)
+    sp = ps.Splitting(op)
+    prob = ps.Problem(sp, T, N, g, s, tol_mode=1)
+    prob._keep = (grid, op, sp)
+    return prob
+
+
+@pytest.mark.parametrize("n,N,s,g", [((13, 11), 4, 6, 1), ((9, 7, 6), 3, 4, 2), ((40, 33), 6, 8, 1)])
+def test_adjoint_matches_oracle(ps, n, N, s, g):
+    rng = np.random.default_rng(41)
+    shape_a = tuple(v + 2 for v in reversed(n))
+    a = np.exp(0.3 * rng.standard_normal(shape_a))
+    src = rng.standard_normal(n[::-1])
+    T = 0.2
+    src_t = 1.0 + 0.5 * np.sin(np.arange(N * s + 1) * 0.7)
+    u0 = rng.standard_normal(n[::-1])
+    tgt = rng.standard_normal(n[::-1])
+    prob = build(ps, n, a, c=0.3, src=src, src_t=src_t, T=T, N=N, s=s, g=g)
+    prob.run(dev(u0), 1e-14)
+    UN = prob.state(N)
+    gN = UN - dev(tgt)
+    gu, ga = prob.vjp(gN, 1e-14)
+    orp = orc.Problem(n, a=a, c=0.3, src=src, src_t=src_t)
+    J, gu_ref, ga_ref = orc.adjoint(orp, T, N, s, u0, tgt)
+    assert abs(0.5 * float((gN ** 2).sum()) - J) <= 1e-10 * abs(J)
+    assert relmax(gu.cpu().numpy(), gu_ref) < 1e-9
+    assert relmax(ga.cpu().numpy(), ga_ref) < 1e-9
+    # the problem's states are the forward states again
+    assert torch.equal(prob.state(N), UN)
+
+
+def test_adjoint_finite_differences_adjoint2d(ps):
+    """The adjoint workload's recipe at reduced size: 20 seeded unit directions for a,
+    5 for u0; central differences of J from the GPU forward solve."""
+    cfg = wl.adjoint2d_511(n=63, N=8, s=16)
+    n = cfg["n"]
+    prob = build(ps, n, cfg["a"], T=cfg["T"], N=cfg["N"], s=cfg["s"])
+    u0 = dev(cfg["u0"])
+    # target: the fine solution of the perturbed coefficient
+    prob.update_coefficients(dev(cfg["a_target"]))
+    prob.run(u0, 1e-14)
+    tgt = prob.state(cfg["N"]).clone()
+    a = dev(cfg["a"])
+
+    def J_of(aa, uu):
+        prob.update_coefficients(aa)
+        prob.run(uu, 1e-14)
+        d = prob.state(cfg["N"]) - tgt
+        return 0.5 * float((d * d).sum())
+
+    J0 = J_of(a, u0)
+    gN = prob.state(cfg["N"]) - tgt
+    gu, ga = prob.vjp(gN, 1e-14)
+    assert J0 > 0
+    for d in wl.random_directions(tuple(a.shape), 20, cfg["dirs_seed"]):
+        dd = dev(d)
+        eps = 1e-4
+        fd = (J_of(a + eps * dd, u0) - J_of(a - eps * dd, u0)) / (2 * eps)
+        an = float((ga * dd).sum())
+        assert abs(an - fd) <= 1e-6 * abs(fd) + 1e-30, (an, fd)
+    for d in wl.random_directions(tuple(u0.shape), 5, cfg["dirs_seed"] + 1):
+        dd = dev(d)
+        eps = 1e-3
+        fd = (J_of(a, u0 + eps * dd) - J_of(a, u0 - eps * dd)) / (2 * eps)
+        an = float((gu * dd).sum())
+        assert abs(an - fd) <= 1e-6 * abs(fd) + 1e-30, (an, fd)
+
+
+def test_autograd_function(ps):
+    rng = np.random.default_rng(43)
+    n, N, s = (21, 17), 4, 8
+    shape_a = tuple(v + 2 for v in reversed(n))
+    a0 = np.exp(0.2 * rng.standard_normal(shape_a))
+    prob = build(ps, n, a0, T=0.1, N=N, s=s)
+    u0 = dev(rng.standard_normal(n[::-1])).requires_grad_(True)
+    a = dev(a0).requires_grad_(True)
+    tgt = dev(rng.standard_normal(n[::-1]))
+    UN = ps.parareal_solve(prob, u0, a, 1e-14)
+    loss = 0.5 * ((UN - tgt) ** 2).sum()
+    loss.backward()
+    orp = orc.Problem(n, a=a0)
+    J, gu_ref, ga_ref = orc.adjoint(orp, 0.1, N, s, u0.detach().cpu().numpy(), tgt.cpu().numpy())
+    assert abs(float(loss.detach()) - J) <= 1e-10 * J
+    assert relmax(u0.grad.cpu().numpy(), gu_ref) < 1e-9
+    assert relmax(a.grad.cpu().numpy(), ga_ref) < 1e-9
