@@ -214,6 +214,38 @@ typedef struct {
 } ps_kernel_time;
 int ps_problem_kernel_times(const ps_problem* p, ps_kernel_time* out, int cap, int* len);
 
+/* ---- batches of independent problems (uneven grids, slice and step counts) ------------- */
+/* A batch advances its problems' parareal iterations together: every phase-step of an
+ * iteration is one grouped persistent launch over all problems that still iterate (the fine
+ * line solves of every slice of every problem, then each coarse step with its correction),
+ * the whole iteration is one CUDA graph replayed until every problem has converged, and only
+ * small work tables change between replays.  Results equal each problem's own
+ * ps_run_parareal bitwise.  Problems: 2-D, dimensional splitting, PS_PREC_MIXED, one coarse
+ * step per slice, no source term, all with a nodal coefficient or all without
+ * (PS_ERR_UNSUPPORTED otherwise).  The batch keeps pointers to the problems (destroy it
+ * first); states and histories are read per problem afterwards (ps_get_state, ...). */
+typedef struct ps_batch ps_batch;
+int ps_batch_create(ps_problem* const* problems, int count, uintptr_t stream, ps_batch** out);
+/* u0_devs: host array of `count` device pointers.  Each problem stops at the first k with
+ * max_n ||U_n^k - U_n^{k-1}||_inf < tol, at k = N_p, or at max_iter (<= 0: no cap).
+ * iters_out (host, `count` ints, may be NULL) receives each problem's k. */
+int ps_batch_run(ps_batch* b, const double* const* u0_devs, double tol, int max_iter, uintptr_t stream,
+                 int* iters_out);
+/* iterations = the largest k, unknown_updates over all problems, kernel_launches (graph nodes
+ * executed).  ms fields are 0. */
+int ps_batch_stats(const ps_batch* b, ps_stats* out);
+const char* ps_batch_last_error(void);
+int ps_batch_destroy(ps_batch* b);
+
+/* Autotuner of the fine line-solve schedule: times the fine sweeps of this problem with each
+ * candidate tile shape (slices per tile 32/64, positions 1/2, one tile per CTA or persistent
+ * double-buffered CTAs) for about budget_ms and installs the fastest.  Results do not depend
+ * on the schedule (each line's arithmetic is the same).  *choice_out (may be NULL) receives
+ * slots*100 + positions*10 + pipelined. */
+int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out);
+/* Same schedule on `dst` as on `src` (same grid and slice count). */
+int ps_copy_schedule(const ps_problem* src, ps_problem* dst);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,10 +86,17 @@ SIGNATURES = {
     "ps_propagate": [_VP, _I, _I, _I, _I, _VP, _U],
     "ps_problem_stats": [_VP, C.POINTER(_Stats)],
     "ps_problem_update_coefficients": [_VP, _VP, _U],
+    "ps_batch_create": [C.POINTER(_VP), _I, _U, C.POINTER(_VP)],
+    "ps_batch_run": [_VP, C.POINTER(_VP), _D, _I, _U, _IP],
+    "ps_batch_stats": [_VP, C.POINTER(_Stats)],
+    "ps_batch_last_error": [],
+    "ps_batch_destroy": [_VP],
+    "ps_autotune": [_VP, _I, _U, _IP],
+    "ps_copy_schedule": [_VP, _VP],
     "ps_adjoint_vjp": [_VP, _VP, _D, _I, _VP, _VP, _U, _IP],
     "ps_problem_kernel_times": [_VP, C.POINTER(_KTime), _I, _IP],
 }
-_RESTYPE = {"ps_last_error": C.c_char_p}
+_RESTYPE = {"ps_last_error": C.c_char_p, "ps_batch_last_error": C.c_char_p}
 
 
 def lib():
@@ -292,6 +299,15 @@ class Problem:
         self.last_adjoint_iters = it.value
         return gu, ga
 
+    def autotune(self, budget_ms=200, stream=None):
+        """Time the fine-sweep schedules on this problem and keep the fastest (returns its code)."""
+        ch = C.c_int(0)
+        check(lib().ps_autotune(self._h, int(budget_ms), _stream(stream), C.byref(ch)))
+        return ch.value
+
+    def copy_schedule_from(self, other: "Problem"):
+        check(lib().ps_copy_schedule(other._h, self._h))
+
     def kernel_times(self):
         """Per-kernel-kind times of the last run (needs timing=2): name -> dict."""
         buf = (_KTime * 64)()
@@ -325,3 +341,48 @@ def parareal_solve(problem: "Problem", u0, a, tol, adjoint_tol=None):
             return gu, ga
 
     return _Solve.apply(u0, a)
+
+
+class Batch:
+    """Independent problems advanced together (grouped launches, one CUDA graph per parareal
+    iteration).  Keeps references to its problems."""
+
+    def __init__(self, problems, stream=None):
+        self.problems = list(problems)
+        arr = (_VP * len(self.problems))(*[p._h for p in self.problems])
+        h = _VP()
+        rc = lib().ps_batch_create(arr, len(self.problems), _stream(stream), C.byref(h))
+        if rc != PS_OK:
+            raise PsError(rc, lib().ps_batch_last_error().decode())
+        self._h = h
+
+    def run(self, u0s, tol, max_iter=0, stream=None):
+        ptrs = (_VP * len(u0s))(*[_dev_ptr(u, p.grid.nt) for u, p in zip(u0s, self.problems)])
+        its = (C.c_int * len(u0s))()
+        rc = lib().ps_batch_run(self._h, ptrs, float(tol), int(max_iter), _stream(stream), its)
+        if rc != PS_OK:
+            raise PsError(rc, lib().ps_batch_last_error().decode())
+        return list(its)
+
+    def stats(self):
+        s = _Stats()
+        rc = lib().ps_batch_stats(self._h, C.byref(s))
+        if rc != PS_OK:
+            raise PsError(rc, lib().ps_batch_last_error().decode())
+        return dict(iterations=s.iterations, unknown_updates=s.unknown_updates, kernel_launches=s.kernel_launches)
+
+    def autotune(self, budget_ms=100, stream=None):
+        """Autotune one problem per grid size and slice count, copy its schedule to the rest."""
+        chosen = {}
+        for p in self.problems:
+            key = (p.grid.n, p.N)
+            if key not in chosen:
+                chosen[key] = (p, p.autotune(budget_ms, stream))
+            else:
+                p.copy_schedule_from(chosen[key][0])
+        return {k: v[1] for k, v in chosen.items()}
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().ps_batch_destroy(self._h)
+            self._h = None

@@ -1,0 +1,450 @@
+// ps_batch.cu -- many independent parareal problems advanced together (batched launches,
+// one CUDA graph per parareal iteration) and the tile-shape autotuner.
+//
+// All problems of a batch start together, so every unconverged problem is at the same
+// parareal iteration k (Sec. 3).  One iteration of the whole batch is a fixed sequence of
+// grouped persistent launches:
+//   pack U_n -> interleaved FP32 (slices n >= k-1 of every problem)
+//   for every fine step j and direction m: one tile-sweep launch over every problem with
+//     s_p > j (the fine line solves of all slices of all problems)
+//   unpack -> F results;  U_k <- F(U_{k-1}) (the finite-termination slice)
+//   for every coarse step n: one x-sweep and one y-sweep-with-correction launch over every
+//     problem with N_p > n >= k
+// The launches read their work from device tables (which problems, which tiles or blocks),
+// so the sequence is captured once as a CUDA graph and replayed every iteration; between
+// replays the host only rewrites the tables (converged problems drop out) and reads back
+// the per-problem increments.  Each problem's arithmetic is the same as in its own
+// ps_run_parareal, so batched and individual results agree bitwise.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "ps_handles.h"
+
+using namespace ps;
+
+struct ps_batch {
+  std::vector<ps_problem*> probs;
+  int count = 0;
+  int maxS = 0, maxN = 0;
+  bool var = true;
+  // device tables
+  DevBuf<unsigned char> tile_jobs;  // [2][count] TileJob
+  DevBuf<WorkSeg> tile_segs;        // [2][count]
+  DevBuf<int> tile_nseg;            // [maxS][2]
+  DevBuf<PackJob> pack_jobs, unpack_jobs;
+  DevBuf<WorkSeg> pack_segs, unpack_segs;
+  DevBuf<CoarseJob> copy_jobs;
+  DevBuf<WorkSeg> copy_segs;
+  DevBuf<CoarseJob> cjobs;          // [maxN][count]
+  DevBuf<WorkSeg> xsegs, ysegs;     // [maxN][count]
+  DevBuf<int> nseg_misc;            // [0] pack, [1] unpack, [2] copy, [3 + n] coarse step n
+  DevBuf<unsigned long long> inc;   // per problem
+  DevBuf<int> flag, tmo;
+  size_t tile_smem = 0;
+  int tile_threads = 0;
+  size_t x_smem = 0;
+  int sms = 152;
+  cudaStream_t cs = nullptr;
+  cudaGraphExec_t iter_graph = nullptr, init_graph = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // host staging
+  std::vector<unsigned char> h_tile_jobs;
+  std::vector<WorkSeg> h_tile_segs, h_pack_segs, h_unpack_segs, h_copy_segs, h_xsegs, h_ysegs;
+  std::vector<int> h_tile_nseg, h_nseg_misc;
+  std::vector<PackJob> h_pack, h_unpack;
+  std::vector<CoarseJob> h_copy, h_cjobs;
+  std::vector<unsigned long long> h_inc;
+  std::vector<int> h_flag;
+  double updates = 0.0;
+  int launches_per_iter = 0, launches = 0;
+  ~ps_batch() {
+    if (iter_graph) cudaGraphExecDestroy(iter_graph);
+    if (init_graph) cudaGraphExecDestroy(init_graph);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (cs) cudaStreamDestroy(cs);
+  }
+};
+
+namespace {
+
+thread_local std::string g_batch_error;
+int bfail(int code, const std::string& m) {
+  g_batch_error = m;
+  return code;
+}
+template <typename F>
+int bguarded(F&& f) {
+  try {
+    f();
+    return PS_OK;
+  } catch (const Error& e) {
+    return bfail(e.code, e.what());
+  } catch (const std::exception& e) {
+    return bfail(PS_ERR_INVALID, e.what());
+  }
+}
+
+int x_rows_per_block(int nx) {
+  const int ld = (nx % 2) ? nx : nx + 1;
+  return std::max(1, std::min(256, 96 * 1024 / (ld * 8)));
+}
+
+CoarseJob coarse_job(ps_batch* b, int i, int n) {
+  ps_problem* p = b->probs[i];
+  CoarseJob j{};
+  const long long nt = p->g.nt;
+  j.xin = p->U.p + n * nt;
+  j.xout = p->gtmp.p;
+  j.nx = p->g.n[0];
+  j.ny = p->g.n[1];
+  j.rows = p->g.n[1];
+  j.nt = nt;
+  j.ld = (j.nx % 2) ? j.nx : j.nx + 1;
+  j.R = x_rows_per_block(j.nx);
+  j.lx = p->G.dim[0]->l64.p;
+  j.rx = p->G.dim[0]->r64.p;
+  j.ly = p->G.dim[1]->l64.p;
+  j.ry = p->G.dim[1]->r64.p;
+  j.ca.U_next = p->U.p + (n + 1) * nt;
+  j.ca.Fout = p->Fout.p + n * nt;
+  j.ca.Gold = p->Gold.p + n * nt;
+  j.ca.inc = b->inc.p + i;
+  j.ca.nonfinite = b->flag.p + i;
+  j.ca.slice_stats = nullptr;
+  return j;
+}
+
+template <typename T>
+void upload(DevBuf<T>& d, const std::vector<T>& h, cudaStream_t st) {
+  if (!h.empty()) PS_CUDA(cudaMemcpyAsync(d.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st));
+}
+
+// Coarse tables for the initial sweep (mode 2) or iteration k (mode 1): for every step n,
+// the problems with N_p > n (and n >= k) in order of decreasing N_p.
+void fill_coarse_tables(ps_batch* b, const std::vector<int>& active, int k) {
+  std::vector<int> order(active);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->probs[a]->N > b->probs[c]->N; });
+  const int P = b->count;
+  for (int n = 0; n < b->maxN; ++n) {
+    int cnt = 0, px = 0, py = 0;
+    if (n >= k)
+      for (int i : order) {
+        ps_problem* p = b->probs[i];
+        if (p->N <= n) break;
+        b->h_cjobs[(size_t)n * P + cnt] = coarse_job(b, i, n);
+        const int bx = (p->g.n[1] + x_rows_per_block(p->g.n[0]) - 1) / x_rows_per_block(p->g.n[0]);
+        const int by = (p->g.n[0] + 255) / 256;
+        b->h_xsegs[(size_t)n * P + cnt] = WorkSeg{cnt, 0, bx, px};  // job index within step n
+        b->h_ysegs[(size_t)n * P + cnt] = WorkSeg{cnt, 0, by, py};
+        px += bx;
+        py += by;
+        ++cnt;
+      }
+    b->h_nseg_misc[3 + n] = cnt;
+  }
+}
+
+// Tables of iteration k: fine phase on slices k-1.. of every active problem, the slice-k
+// copy, and the coarse chain.
+void fill_iteration_tables(ps_batch* b, const std::vector<int>& active, int k) {
+  const int P = b->count;
+  const size_t jb = tile_job_bytes();
+  // fine tiles, problems in order of decreasing s
+  std::vector<int> order(active);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->probs[a]->fs > b->probs[c]->fs; });
+  for (int m = 0; m < 2; ++m) {
+    int prefix = 0;
+    for (size_t r = 0; r < order.size(); ++r) {
+      ps_problem* p = b->probs[order[r]];
+      const int nsl = p->N - (k - 1);
+      Geom g3 = p->g;
+      g3.n[2] = 1;
+      const long long tiles = tile_job_fill(g3, p->F.tiles[m], *p->F.dim[m], p->S_pad, k - 1, nsl, b->tmo.p,
+                                            b->h_tile_jobs.data() + ((size_t)m * P + r) * jb);
+      b->h_tile_segs[(size_t)m * P + r] = WorkSeg{(int)r, 0, (int)tiles, prefix};  // job index within axis m
+      prefix += (int)tiles;
+    }
+    for (int j = 0; j < b->maxS; ++j) {
+      int cnt = 0;
+      for (int i : order)
+        if (b->probs[i]->fs > j) ++cnt;
+      b->h_tile_nseg[(size_t)j * 2 + m] = cnt;
+    }
+  }
+  // pack / unpack / copy, any order
+  int pp = 0, cp = 0, cnt = 0;
+  for (size_t r = 0; r < active.size(); ++r) {
+    ps_problem* p = b->probs[active[r]];
+    const int nsl = p->N - (k - 1);
+    const long long nt = p->g.nt;
+    b->h_pack[r] = PackJob{p->U.p + (k - 1) * nt, p->W.p, nt, p->S_pad, k - 1, nsl, 0};
+    b->h_unpack[r] = PackJob{p->Fout.p + (k - 1) * nt, p->W.p, nt, p->S_pad, k - 1, nsl, 0};
+    const int blocks = (int)(((nt + 31) / 32) * ((nsl + 31) / 32));
+    b->h_pack_segs[r] = WorkSeg{(int)r, 0, blocks, pp};
+    b->h_unpack_segs[r] = WorkSeg{(int)r, 0, blocks, pp};
+    pp += blocks;
+    CoarseJob cj{};
+    cj.xin = p->Fout.p + (k - 1) * nt;
+    cj.xout = p->U.p + k * nt;
+    cj.nt = nt;
+    cj.ca.inc = b->inc.p + active[r];
+    cj.ca.nonfinite = b->flag.p + active[r];
+    b->h_copy[r] = cj;
+    const int cb = (int)((nt + 255) / 256);
+    b->h_copy_segs[r] = WorkSeg{(int)r, 0, cb, cp};
+    cp += cb;
+    ++cnt;
+  }
+  b->h_nseg_misc[0] = b->h_nseg_misc[1] = b->h_nseg_misc[2] = cnt;
+  fill_coarse_tables(b, active, k);
+}
+
+void upload_tables(ps_batch* b, cudaStream_t st) {
+  PS_CUDA(cudaMemcpyAsync(b->tile_jobs.p, b->h_tile_jobs.data(), b->h_tile_jobs.size(), cudaMemcpyHostToDevice, st));
+  upload(b->tile_segs, b->h_tile_segs, st);
+  upload(b->tile_nseg, b->h_tile_nseg, st);
+  upload(b->pack_jobs, b->h_pack, st);
+  upload(b->unpack_jobs, b->h_unpack, st);
+  upload(b->pack_segs, b->h_pack_segs, st);
+  upload(b->unpack_segs, b->h_unpack_segs, st);
+  upload(b->copy_jobs, b->h_copy, st);
+  upload(b->copy_segs, b->h_copy_segs, st);
+  upload(b->cjobs, b->h_cjobs, st);
+  upload(b->xsegs, b->h_xsegs, st);
+  upload(b->ysegs, b->h_ysegs, st);
+  upload(b->nseg_misc, b->h_nseg_misc, st);
+}
+
+// The launch sequence of one iteration (mode 1) or of the initial coarse sweep (mode 2).
+int enqueue_sequence(ps_batch* b, int mode, cudaStream_t st) {
+  const int P = b->count;
+  const int grid = b->sms * 8;
+  int n_launch = 0;
+  if (mode == 1) {
+    pack_grouped(true, b->pack_jobs.p, b->pack_segs.p, b->nseg_misc.p + 0, grid, st);
+    ++n_launch;
+    for (int j = 0; j < b->maxS; ++j)
+      for (int m = 0; m < 2; ++m) {
+        tile_sweep_grouped(b->tile_jobs.p + (size_t)m * P * tile_job_bytes(), b->tile_segs.p + (size_t)m * P,
+                           b->tile_nseg.p + (size_t)j * 2 + m, grid, b->tile_threads, b->tile_smem, b->tmo.p, st);
+        ++n_launch;
+      }
+    pack_grouped(false, b->unpack_jobs.p, b->unpack_segs.p, b->nseg_misc.p + 1, grid, st);
+    copy_inc_grouped(b->copy_jobs.p, b->copy_segs.p, b->nseg_misc.p + 2, grid, st);
+    n_launch += 2;
+  }
+  for (int n = 0; n < b->maxN; ++n) {
+    coarse_x_grouped(b->var, b->cjobs.p + (size_t)n * P, b->xsegs.p + (size_t)n * P, b->nseg_misc.p + 3 + n, grid,
+                     b->x_smem, st);
+    coarse_y_grouped(b->var, mode, b->cjobs.p + (size_t)n * P, b->ysegs.p + (size_t)n * P, b->nseg_misc.p + 3 + n,
+                     grid, st);
+    n_launch += 2;
+  }
+  return n_launch;
+}
+
+cudaGraphExec_t capture(ps_batch* b, int mode) {
+  cudaGraph_t g = nullptr;
+  PS_CUDA(cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
+  int n = 0;
+  try {
+    n = enqueue_sequence(b, mode, b->cs);
+  } catch (...) {
+    cudaStreamEndCapture(b->cs, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  PS_CUDA(cudaStreamEndCapture(b->cs, &g));
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  PS_CUDA(e);
+  if (mode == 1) b->launches_per_iter = n;
+  return ex;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ps_batch_last_error(void) { return g_batch_error.c_str(); }
+
+int ps_batch_create(ps_problem* const* problems, int count, uintptr_t stream, ps_batch** out) {
+  return bguarded([&] {
+    PS_REQUIRE(problems && out && count >= 1, "bad argument");
+    auto b = std::make_unique<ps_batch>();
+    b->count = count;
+    b->probs.assign(problems, problems + count);
+    for (int i = 0; i < count; ++i) {
+      ps_problem* p = b->probs[i];
+      PS_REQUIRE(p, "null problem");
+      if (p->g.dim != 2 || p->fine->kind != PS_SPLIT_DIM || p->coarse->kind != PS_SPLIT_DIM)
+        throw Error(PS_ERR_UNSUPPORTED, "batches hold 2-D problems with dimensional splitting");
+      if (p->prm.precision != PS_PREC_MIXED)
+        throw Error(PS_ERR_UNSUPPORTED, "batches run the FP32 line-solve form (PS_PREC_MIXED)");
+      if (p->gs != 1) throw Error(PS_ERR_UNSUPPORTED, "batches use one coarse step per slice");
+      if (p->op->src.p) throw Error(PS_ERR_UNSUPPORTED, "batches hold problems without a source term");
+      const bool var = p->op->a.p != nullptr;
+      if (i == 0) b->var = var;
+      PS_REQUIRE(var == b->var, "all problems of a batch need a nodal coefficient, or none");
+      for (int j = 0; j < i; ++j) PS_REQUIRE(b->probs[j] != p, "a problem appears twice in the batch");
+      b->maxS = std::max(b->maxS, p->fs);
+      b->maxN = std::max(b->maxN, p->N);
+      b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[0]));
+      b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[1]));
+      b->tile_threads = std::max(b->tile_threads, std::max(p->F.tiles[0].threads, p->F.tiles[1].threads));
+      const int nx = p->g.n[0];
+      const int ld = (nx % 2) ? nx : nx + 1;
+      b->x_smem = std::max(b->x_smem, (size_t)x_rows_per_block(nx) * ld * sizeof(double));
+    }
+    const int P = count;
+    b->tile_threads = (b->tile_threads + 31) / 32 * 32;
+    b->tile_jobs.alloc((size_t)2 * P * tile_job_bytes());
+    b->tile_segs.alloc((size_t)2 * P);
+    b->tile_nseg.alloc((size_t)2 * b->maxS);
+    b->pack_jobs.alloc(P);
+    b->unpack_jobs.alloc(P);
+    b->pack_segs.alloc(P);
+    b->unpack_segs.alloc(P);
+    b->copy_jobs.alloc(P);
+    b->copy_segs.alloc(P);
+    b->cjobs.alloc((size_t)b->maxN * P);
+    b->xsegs.alloc((size_t)b->maxN * P);
+    b->ysegs.alloc((size_t)b->maxN * P);
+    b->nseg_misc.alloc((size_t)3 + b->maxN);
+    b->inc.alloc(P);
+    b->flag.alloc(P);
+    b->tmo.alloc(1);
+    b->h_tile_jobs.assign((size_t)2 * P * tile_job_bytes(), 0);
+    b->h_tile_segs.assign((size_t)2 * P, WorkSeg{});
+    b->h_tile_nseg.assign((size_t)2 * b->maxS, 0);
+    b->h_pack.assign(P, PackJob{});
+    b->h_unpack.assign(P, PackJob{});
+    b->h_pack_segs.assign(P, WorkSeg{});
+    b->h_unpack_segs.assign(P, WorkSeg{});
+    b->h_copy.assign(P, CoarseJob{});
+    b->h_copy_segs.assign(P, WorkSeg{});
+    b->h_cjobs.assign((size_t)b->maxN * P, CoarseJob{});
+    b->h_xsegs.assign((size_t)b->maxN * P, WorkSeg{});
+    b->h_ysegs.assign((size_t)b->maxN * P, WorkSeg{});
+    b->h_nseg_misc.assign((size_t)3 + b->maxN, 0);
+    b->h_inc.assign(P, 0);
+    b->h_flag.assign(P, 0);
+    int dev = 0;
+    PS_CUDA(cudaGetDevice(&dev));
+    PS_CUDA(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev));
+    PS_CUDA(cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking));
+    PS_CUDA(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
+    PS_CUDA(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
+    PS_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+    *out = b.release();
+  });
+}
+
+int ps_batch_destroy(ps_batch* b) {
+  delete b;
+  return PS_OK;
+}
+
+int ps_batch_run(ps_batch* b, const double* const* u0_devs, double tol, int max_iter, uintptr_t stream,
+                 int* iters_out) {
+  return bguarded([&] {
+    PS_REQUIRE(b && u0_devs, "null argument");
+    cudaStream_t ust = reinterpret_cast<cudaStream_t>(stream);
+    cudaStream_t st = b->cs;
+    const int P = b->count;
+    // (re)capture the graphs: tile shapes may have changed (autotuner)
+    if (b->iter_graph) {
+      cudaGraphExecDestroy(b->iter_graph);
+      b->iter_graph = nullptr;
+    }
+    if (b->init_graph) {
+      cudaGraphExecDestroy(b->init_graph);
+      b->init_graph = nullptr;
+    }
+    b->tile_smem = 0;
+    b->tile_threads = 0;
+    for (ps_problem* p : b->probs) {
+      b->tile_smem = std::max(b->tile_smem, std::max(tile_grouped_smem(p->F.tiles[0]), tile_grouped_smem(p->F.tiles[1])));
+      b->tile_threads = std::max(b->tile_threads, std::max(p->F.tiles[0].threads, p->F.tiles[1].threads));
+    }
+    b->tile_threads = (b->tile_threads + 31) / 32 * 32;
+    b->init_graph = capture(b, 2);
+    b->iter_graph = capture(b, 1);
+    PS_CUDA(cudaEventRecord(b->ev_in, ust));
+    PS_CUDA(cudaStreamWaitEvent(st, b->ev_in, 0));
+    PS_CUDA(cudaMemsetAsync(b->flag.p, 0, sizeof(int) * P, st));
+    PS_CUDA(cudaMemsetAsync(b->tmo.p, 0, sizeof(int), st));
+    b->updates = 0;
+    b->launches = 0;
+    std::vector<int> active(P);
+    std::iota(active.begin(), active.end(), 0);
+    for (int i = 0; i < P; ++i) {
+      ps_problem* p = b->probs[i];
+      PS_REQUIRE(u0_devs[i], "null u0");
+      PS_CUDA(cudaMemcpyAsync(p->U.p, u0_devs[i], sizeof(double) * p->g.nt, cudaMemcpyDeviceToDevice, st));
+      p->hist.clear();
+      p->iters = 0;
+      b->updates += (double)p->N * p->g.nt;
+    }
+    // k = 0: coarse sweep of every problem
+    fill_coarse_tables(b, active, 0);
+    upload_tables(b, st);
+    PS_CUDA(cudaGraphLaunch(b->init_graph, st));
+    b->launches += 2 * b->maxN;
+    int k = 0;
+    const int cap = max_iter <= 0 ? (1 << 30) : max_iter;
+    while (!active.empty()) {
+      ++k;
+      fill_iteration_tables(b, active, k);
+      upload_tables(b, st);
+      PS_CUDA(cudaMemsetAsync(b->inc.p, 0, sizeof(unsigned long long) * P, st));
+      PS_CUDA(cudaGraphLaunch(b->iter_graph, st));
+      b->launches += b->launches_per_iter;
+      PS_CUDA(cudaMemcpyAsync(b->h_inc.data(), b->inc.p, sizeof(unsigned long long) * P, cudaMemcpyDeviceToHost, st));
+      PS_CUDA(cudaMemcpyAsync(b->h_flag.data(), b->flag.p, sizeof(int) * P, cudaMemcpyDeviceToHost, st));
+      int tmo = 0;
+      PS_CUDA(cudaMemcpyAsync(&tmo, b->tmo.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      PS_CUDA(cudaStreamSynchronize(st));
+      if (tmo) throw Error(PS_ERR_DEVICE_TIMEOUT, "a TMA tile load did not arrive within its wait limit");
+      std::vector<int> next;
+      for (int i : active) {
+        ps_problem* p = b->probs[i];
+        double inc;
+        std::memcpy(&inc, &b->h_inc[i], sizeof inc);
+        p->hist.push_back(inc);
+        p->iters = k;
+        b->updates += (double)(p->N - k + 1) * p->fs * p->g.nt + (double)(p->N - k) * p->g.nt;
+        if (b->h_flag[i]) throw Error(PS_ERR_NONFINITE, "non-finite value in batch problem " + std::to_string(i));
+        const bool done = inc < tol || k >= p->N || k >= cap;
+        if (done) p->have_forward = true;
+        else next.push_back(i);
+      }
+      active.swap(next);
+    }
+    if (iters_out)
+      for (int i = 0; i < P; ++i) iters_out[i] = b->probs[i]->iters;
+    PS_CUDA(cudaEventRecord(b->ev_out, st));
+    PS_CUDA(cudaStreamWaitEvent(ust, b->ev_out, 0));
+  });
+}
+
+int ps_batch_stats(const ps_batch* b, ps_stats* out) {
+  return bguarded([&] {
+    PS_REQUIRE(b && out, "null argument");
+    std::memset(out, 0, sizeof *out);
+    int kmax = 0;
+    for (ps_problem* p : b->probs) kmax = std::max(kmax, p->iters);
+    out->iterations = kmax;
+    out->unknown_updates = b->updates;
+    out->kernel_launches = b->launches;
+  });
+}
+
+}  // extern "C"

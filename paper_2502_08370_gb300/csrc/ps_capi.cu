@@ -19,30 +19,9 @@
 #include <vector>
 
 #include "ps_adjoint.h"
-#include "ps_dd.h"
-#include "ps_tile.h"
+#include "ps_handles.h"
 
 using namespace ps;
-
-struct ps_grid {
-  Geom g;
-};
-
-struct ps_operator {
-  const ps_grid* grid = nullptr;
-  DevBuf<double> a;
-  DevBuf<double> src;
-  DevBuf<double> src_t;
-  int src_t_len = 0;
-  double c = 0.0;
-};
-
-struct ps_splitting {
-  const ps_operator* op = nullptr;
-  int kind = PS_SPLIT_DIM;
-  ps_dd_params dd{};
-  int M = 0;
-};
 
 namespace {
 
@@ -69,125 +48,7 @@ int guarded(F&& f) {
 
 inline cudaStream_t S(uintptr_t s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// One propagator: `steps` FIE steps of size tau per slice; step q of slice n ends at fine
-// time index n*s + (q+1)*tstride.
-struct Prop {
-  const ps_splitting* sp = nullptr;
-  double tau = 0.0;
-  int steps = 1;
-  int tstride = 1;
-  bool f32 = false;
-  std::vector<std::unique_ptr<LineFactors>> dim;
-  std::unique_ptr<DDFactors> dd;
-  TilePlan tiles[3];  // fine propagator, dimensional splitting: one TMA plan per direction
-};
-
-// Per-launch CUDA events around the library's kernels (params.timing == 2), resolved at
-// the host synchronisation points and summed per kernel kind.
-struct KernelTimer {
-  struct Kind {
-    std::string name;
-    int launches = 0;
-    double ms = 0.0, bytes = 0.0, flops = 0.0;
-  };
-  bool on = false;
-  std::vector<cudaEvent_t> pool;
-  struct Mark {
-    int kind;
-    double bytes, flops;
-  };
-  std::vector<Mark> marks;
-  std::vector<Kind> kinds;
-  cudaStream_t st = nullptr;
-  ~KernelTimer() {
-    for (auto e : pool) cudaEventDestroy(e);
-  }
-  int kind_id(const std::string& name) {
-    for (size_t i = 0; i < kinds.size(); ++i)
-      if (kinds[i].name == name) return (int)i;
-    kinds.push_back(Kind{name});
-    return (int)kinds.size() - 1;
-  }
-  void begin(cudaStream_t s) {
-    if (!on) return;
-    st = s;
-    size_t need = 2 * (marks.size() + 1);
-    while (pool.size() < need) {
-      cudaEvent_t e;
-      PS_CUDA(cudaEventCreate(&e));
-      pool.push_back(e);
-    }
-    PS_CUDA(cudaEventRecord(pool[2 * marks.size()], s));
-  }
-  void end(const std::string& name, double bytes, double flops) {
-    if (!on) return;
-    PS_CUDA(cudaEventRecord(pool[2 * marks.size() + 1], st));
-    marks.push_back(Mark{kind_id(name), bytes, flops});
-  }
-  // call after the stream was synchronised
-  void resolve() {
-    for (size_t i = 0; i < marks.size(); ++i) {
-      float ms = 0.f;
-      PS_CUDA(cudaEventElapsedTime(&ms, pool[2 * i], pool[2 * i + 1]));
-      Kind& k = kinds[marks[i].kind];
-      k.launches++;
-      k.ms += ms;
-      k.bytes += marks[i].bytes;
-      k.flops += marks[i].flops;
-    }
-    marks.clear();
-  }
-  void reset() {
-    marks.clear();
-    kinds.clear();
-  }
-};
-
 }  // namespace
-
-struct ps_problem {
-  const ps_splitting* fine = nullptr;
-  const ps_splitting* coarse = nullptr;
-  const ps_operator* op = nullptr;
-  Geom g;
-  double T = 1.0;
-  int N = 1, gs = 1, fs = 1;
-  ps_params prm{};
-  Prop F, G;
-  DevBuf<double> U, Fout, Gold, gtmp;
-  DevBuf<float> W;      // fine working state, slice-interleaved (FP32 line solves)
-  DevBuf<double> W64;   // same for FP64 line solves
-  int S_pad = 0;        // slots of the interleaved layout
-  DevBuf<int> tmo;      // set by a kernel whose bounded wait ran out
-  DevBuf<float> srcrow32;   // fine source rows along x, line-major (tile sweeps)
-  DevBuf<double> srcrow64;
-  DevBuf<unsigned long long> sstats;  // per slice {max |U^k - U^{k-1}|, max |U^k|}, slices 0..N
-  unsigned long long* h_sstats = nullptr;
-  bool transposed = false;  // propagate with the transposed steps (substeps reversed, no source)
-  bool have_forward = false;
-  // adjoint workspaces (allocated by the first ps_adjoint_vjp with a coefficient gradient)
-  DevBuf<double> Uchk, snap, Lam, gedge[3];
-  TilePlan adj_tiles[3];
-  bool adj_ready = false;
-  DevBuf<unsigned long long> inc;
-  DevBuf<int> flag;
-  unsigned long long* h_inc = nullptr;
-  int* h_flag = nullptr;
-  std::vector<double> hist;
-  int iters = 0;
-  double updates = 0.0;
-  int launches = 0;
-  float ms_total = 0, ms_fine = 0, ms_coarse = 0;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  KernelTimer kt;
-  ~ps_problem() {
-    if (h_sstats) cudaFreeHost(h_sstats);
-    if (h_inc) cudaFreeHost(h_inc);
-    if (h_flag) cudaFreeHost(h_flag);
-    for (auto& e : ev)
-      if (e) cudaEventDestroy(e);
-  }
-};
 
 namespace {
 
@@ -805,6 +666,105 @@ int ps_problem_stats(const ps_problem* p, ps_stats* out) {
     out->ms_fine = p->ms_fine;
     out->ms_coarse = p->ms_coarse;
     out->kernel_launches = p->launches;
+  });
+}
+
+namespace {
+// Tile plans of the fine propagator for a schedule (slots per tile, positions, pipeline).
+void rebuild_tiles(ps_problem* p, int slots, int positions, int pipe) {
+  if (p->F.sp->kind != PS_SPLIT_DIM) return;
+  Geom g3 = p->g;
+  if (g3.dim == 2) g3.n[2] = 1;
+  const bool mixed = p->prm.precision == PS_PREC_MIXED;
+  void* W = mixed ? static_cast<void*>(p->W.p) : static_cast<void*>(p->W64.p);
+  TilePlan tmp[3];
+  for (int m = 0; m < p->g.dim; ++m) tile_plan(g3, p->S_pad, mixed ? 4 : 8, m, tmp[m], W, positions, pipe, slots);
+  for (int m = 0; m < p->g.dim; ++m) p->F.tiles[m] = tmp[m];
+  p->prm.tile_slots = slots;
+  p->prm.tile_positions = positions;
+  p->prm.tile_pipeline = pipe ? 1 : 2;
+}
+}  // namespace
+
+int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out) {
+  return guarded([&] {
+    PS_REQUIRE(p, "null argument");
+    if (choice_out) *choice_out = 0;
+    if (p->F.sp->kind != PS_SPLIT_DIM) return;
+    cudaStream_t st = S(stream);
+    const bool mixed = p->prm.precision == PS_PREC_MIXED;
+    struct Cand {
+      int slots, positions, pipe;
+    };
+    const std::vector<Cand> cands = {{32, 1, 0}, {64, 1, 0}, {32, 2, 0}, {16, 1, 0}, {32, 1, 1}};
+    cudaEvent_t e0, e1;
+    PS_CUDA(cudaEventCreate(&e0));
+    PS_CUDA(cudaEventCreate(&e1));
+    Geom g3 = p->g;
+    if (g3.dim == 2) g3.n[2] = 1;
+    const int M = p->g.dim;
+    float best = 1e30f;
+    Cand bestc{0, 0, 0};
+    const double per_cand_ms = std::max(1.0, (double)budget_ms / cands.size());
+    const int old_slots = p->prm.tile_slots, old_pos = p->prm.tile_positions, old_pipe = p->prm.tile_pipeline;
+    try {
+      for (const Cand& c : cands) {
+        try {
+          rebuild_tiles(p, c.slots, c.positions, c.pipe);
+        } catch (const Error&) {
+          continue;  // shape does not fit this grid / precision
+        }
+        auto sweep_all = [&]() {
+          for (int m = 0; m < M; ++m) {
+            if (mixed)
+              tile_sweep<float>(g3, p->F.tiles[m], *p->F.dim[m], p->S_pad, 0, p->N, SourceArgs{}, nullptr, p->tmo.p,
+                                st);
+            else
+              tile_sweep<double>(g3, p->F.tiles[m], *p->F.dim[m], p->S_pad, 0, p->N, SourceArgs{}, nullptr, p->tmo.p,
+                                 st);
+          }
+        };
+        sweep_all();  // warm-up
+        int reps = 1;
+        float ms = 0.f;
+        for (;;) {
+          PS_CUDA(cudaEventRecord(e0, st));
+          for (int r = 0; r < reps; ++r) sweep_all();
+          PS_CUDA(cudaEventRecord(e1, st));
+          PS_CUDA(cudaEventSynchronize(e1));
+          PS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          if (ms * 4 >= per_cand_ms || reps >= 64) break;
+          reps *= 2;
+        }
+        const float per = ms / reps;
+        if (per < best) {
+          best = per;
+          bestc = c;
+        }
+      }
+    } catch (...) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (bestc.slots == 0) {
+      rebuild_tiles(p, old_slots, old_pos, old_pipe == 1 ? 1 : 0);
+      return;
+    }
+    rebuild_tiles(p, bestc.slots, bestc.positions, bestc.pipe);
+    int tmo = 0;
+    PS_CUDA(cudaMemcpy(&tmo, p->tmo.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (tmo) throw Error(PS_ERR_DEVICE_TIMEOUT, "a TMA tile load did not arrive within its wait limit");
+    if (choice_out) *choice_out = bestc.slots * 100 + bestc.positions * 10 + bestc.pipe;
+  });
+}
+
+int ps_copy_schedule(const ps_problem* src, ps_problem* dst) {
+  return guarded([&] {
+    PS_REQUIRE(src && dst, "null argument");
+    rebuild_tiles(dst, src->prm.tile_slots, src->prm.tile_positions, src->prm.tile_pipeline == 1 ? 1 : 0);
   });
 }
 

@@ -81,13 +81,10 @@ __device__ __forceinline__ float to<float>(double v) { return (float)v; }
 // coalesced.  ld = row pitch in shared memory, odd so that thread t's row start t*ld hits
 // distinct banks.
 template <typename Tin, typename Tout, typename Tc, bool VAR, bool SRC>
-__global__ void __launch_bounds__(kThreads) sweep_x_kernel(const Tin* in, Tout* out, long long rows, int nx,
-                                                          int ld, int R, long long rows_per_slice,
-                                                          const Tc* __restrict__ fl, const Tc* __restrict__ fr,
-                                                          SourceArgs sa) {
-  extern __shared__ unsigned char smem_raw[];
-  Tc* sm = reinterpret_cast<Tc*>(smem_raw);
-  const long long row0 = (long long)blockIdx.x * R;
+__device__ __forceinline__ void sweep_x_body(long long blk, Tc* sm, const Tin* in, Tout* out, long long rows, int nx,
+                                             int ld, int R, long long rows_per_slice, const Tc* __restrict__ fl,
+                                             const Tc* __restrict__ fr, const SourceArgs& sa) {
+  const long long row0 = blk * R;
   const int nrows = (int)min((long long)R, rows - row0);
   const long long g0 = row0 * nx;
   const int total = nrows * nx;
@@ -159,6 +156,16 @@ __global__ void __launch_bounds__(kThreads) sweep_x_kernel(const Tin* in, Tout* 
   }
 }
 
+template <typename Tin, typename Tout, typename Tc, bool VAR, bool SRC>
+__global__ void __launch_bounds__(kThreads) sweep_x_kernel(const Tin* in, Tout* out, long long rows, int nx,
+                                                          int ld, int R, long long rows_per_slice,
+                                                          const Tc* __restrict__ fl, const Tc* __restrict__ fr,
+                                                          SourceArgs sa) {
+  extern __shared__ unsigned char smem_raw[];
+  sweep_x_body<Tin, Tout, Tc, VAR, SRC>(blockIdx.x, reinterpret_cast<Tc*>(smem_raw), in, out, rows, nx, ld, R,
+                                         rows_per_slice, fl, fr, sa);
+}
+
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
   // nonnegative doubles order like their bit patterns
   atomicMax(addr, (unsigned long long)__double_as_longlong(v));
@@ -173,11 +180,11 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, doub
 //     U_{n+1} <- Fout + (g - Gold),  Gold <- g,  inc <- max(inc, |U_{n+1}^new - U_{n+1}^old|)
 // EPI = 2 is the initial coarse sweep: U_{n+1} <- g, Gold <- g.
 template <typename Tin, typename Tout, typename Tc, bool VAR, bool SRC, int EPI>
-__global__ void __launch_bounds__(kThreads) sweep_strided_kernel(const Tin* in, Tout* out, Tout* tmp, long long lines,
-                                                                int nm, long long S, long long nt,
-                                                                const Tc* __restrict__ fl, const Tc* __restrict__ fr,
-                                                                SourceArgs sa, CorrArgs ca) {
-  const long long L = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void sweep_strided_body(long long blk, const Tin* in, Tout* out, Tout* tmp, long long lines,
+                                                   int nm, long long S, long long nt, const Tc* __restrict__ fl,
+                                                   const Tc* __restrict__ fr, const SourceArgs& sa,
+                                                   const CorrArgs& ca) {
+  const long long L = blk * blockDim.x + threadIdx.x;
   double my_inc = 0.0, my_norm = 0.0;
   bool bad = false;
   if (L < lines) {
@@ -276,6 +283,94 @@ __global__ void __launch_bounds__(kThreads) sweep_strided_kernel(const Tin* in, 
   }
   if (EPI != 0) {
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(ca.nonfinite, 1);
+  }
+}
+
+template <typename Tin, typename Tout, typename Tc, bool VAR, bool SRC, int EPI>
+__global__ void __launch_bounds__(kThreads) sweep_strided_kernel(const Tin* in, Tout* out, Tout* tmp, long long lines,
+                                                                int nm, long long S, long long nt,
+                                                                const Tc* __restrict__ fl, const Tc* __restrict__ fr,
+                                                                SourceArgs sa, CorrArgs ca) {
+  sweep_strided_body<Tin, Tout, Tc, VAR, SRC, EPI>(blockIdx.x, in, out, tmp, lines, nm, S, nt, fl, fr, sa, ca);
+}
+
+// ---------------------------------------------------------------------------------------
+// Grouped coarse steps (batched problems, 2-D, FP64, no source): one launch runs the same
+// sweep of many problems' coarse step n.  jobs[j] describes problem j's sweep; the first
+// *nseg segments of `segs` list (job, first block, block count, prefix) runs of blocks.
+__device__ __forceinline__ int find_segment(const WorkSeg* segs, int nseg, long long it) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (segs[mid].prefix <= it) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <bool VAR>
+__global__ void __launch_bounds__(kThreads) sweep_x_grouped_kernel(const CoarseJob* __restrict__ jobs,
+                                                                  const WorkSeg* __restrict__ segs,
+                                                                  const int* __restrict__ nseg_ptr) {
+  extern __shared__ unsigned char smem_raw[];
+  const int nseg = *nseg_ptr;
+  if (nseg <= 0) return;
+  const long long total = (long long)segs[nseg - 1].prefix + segs[nseg - 1].count;
+  for (long long it = blockIdx.x; it < total; it += gridDim.x) {
+    const WorkSeg sg = segs[find_segment(segs, nseg, it)];
+    const CoarseJob& j = jobs[sg.job];
+    sweep_x_body<double, double, double, VAR, false>(sg.first + (it - sg.prefix), reinterpret_cast<double*>(smem_raw),
+                                                       j.xin, j.xout, j.rows, j.nx, j.ld, j.R, j.rows, j.lx, j.rx,
+                                                       SourceArgs{});
+    __syncthreads();  // the next item reuses the shared rows
+  }
+}
+
+template <bool VAR, int EPI>
+__global__ void __launch_bounds__(kThreads) sweep_y_grouped_kernel(const CoarseJob* __restrict__ jobs,
+                                                                  const WorkSeg* __restrict__ segs,
+                                                                  const int* __restrict__ nseg_ptr) {
+  const int nseg = *nseg_ptr;
+  if (nseg <= 0) return;
+  const long long total = (long long)segs[nseg - 1].prefix + segs[nseg - 1].count;
+  for (long long it = blockIdx.x; it < total; it += gridDim.x) {
+    const WorkSeg sg = segs[find_segment(segs, nseg, it)];
+    const CoarseJob& j = jobs[sg.job];
+    sweep_strided_body<double, double, double, VAR, false, EPI>(sg.first + (it - sg.prefix), j.xout, j.xout, j.xout,
+                                                                j.nx, j.ny, j.nx, j.nt, j.ly, j.ry, SourceArgs{}, j.ca);
+  }
+}
+
+__global__ void copy_inc_grouped_kernel(const CoarseJob* __restrict__ jobs, const WorkSeg* __restrict__ segs,
+                                        const int* __restrict__ nseg_ptr) {
+  const int nseg = *nseg_ptr;
+  if (nseg <= 0) return;
+  const long long total = (long long)segs[nseg - 1].prefix + segs[nseg - 1].count;
+  for (long long it = blockIdx.x; it < total; it += gridDim.x) {
+    const WorkSeg sg = segs[find_segment(segs, nseg, it)];
+    const CoarseJob& j = jobs[sg.job];
+    const long long i = (sg.first + (it - sg.prefix)) * blockDim.x + threadIdx.x;
+    double my = 0.0, nrm = 0.0;
+    bool bad = false;
+    if (i < j.nt) {
+      const double v = j.xin[i];
+      my = fabs(v - j.xout[i]);
+      nrm = fabs(v);
+      bad = !isfinite(v);
+      j.xout[i] = v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      my = fmax(my, __shfl_xor_sync(0xffffffffu, my, o));
+      nrm = fmax(nrm, __shfl_xor_sync(0xffffffffu, nrm, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (my > 0.0) atomic_max_nonneg(j.ca.inc, my);
+      if (j.ca.slice_stats) {
+        if (my > 0.0) atomic_max_nonneg(j.ca.slice_stats, my);
+        if (nrm > 0.0) atomic_max_nonneg(j.ca.slice_stats + 1, nrm);
+      }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(j.ca.nonfinite, 1);
   }
 }
 
@@ -424,6 +519,31 @@ template void sweep_dim<float, float>(const Geom&, int, const LineFactors&, bool
                                       const SourceArgs&, const CorrArgs&, double*, cudaStream_t);
 template void sweep_dim<float, double>(const Geom&, int, const LineFactors&, bool, const float*, double*,
                                        const SourceArgs&, const CorrArgs&, double*, cudaStream_t);
+
+int max_dyn_smem_public() { return max_dyn_smem(); }
+
+void coarse_x_grouped(bool var, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid, size_t smem,
+                      cudaStream_t st) {
+  auto kern = var ? sweep_x_grouped_kernel<true> : sweep_x_grouped_kernel<false>;
+  PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, kThreads, smem, st>>>(jobs, segs, nseg);
+  PS_CUDA(cudaGetLastError());
+}
+void coarse_y_grouped(bool var, int epi, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
+                      cudaStream_t st) {
+  if (var) {
+    if (epi == 1) sweep_y_grouped_kernel<true, 1><<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
+    else sweep_y_grouped_kernel<true, 2><<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
+  } else {
+    if (epi == 1) sweep_y_grouped_kernel<false, 1><<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
+    else sweep_y_grouped_kernel<false, 2><<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
+  }
+  PS_CUDA(cudaGetLastError());
+}
+void copy_inc_grouped(const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid, cudaStream_t st) {
+  copy_inc_grouped_kernel<<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
+  PS_CUDA(cudaGetLastError());
+}
 
 void copy_with_increment(long long nt, const double* src, double* dst, unsigned long long* inc, int* nonfinite,
                          unsigned long long* slice_stats, cudaStream_t st) {

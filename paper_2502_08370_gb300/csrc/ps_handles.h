@@ -1,0 +1,155 @@
+// ps_handles.h -- definitions of the opaque handles of include/ps.h (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "ps_dd.h"
+#include "ps_tile.h"
+
+struct ps_grid {
+  ps::Geom g;
+};
+struct ps_operator {
+  const ps_grid* grid = nullptr;
+  ps::DevBuf<double> a;
+  ps::DevBuf<double> src;
+  ps::DevBuf<double> src_t;
+  int src_t_len = 0;
+  double c = 0.0;
+};
+
+struct ps_splitting {
+  const ps_operator* op = nullptr;
+  int kind = PS_SPLIT_DIM;
+  ps_dd_params dd{};
+  int M = 0;
+};
+
+
+namespace ps {
+
+// One propagator: `steps` FIE steps of size tau per slice; step q of slice n ends at fine
+// time index n*s + (q+1)*tstride.
+struct Prop {
+  const ps_splitting* sp = nullptr;
+  double tau = 0.0;
+  int steps = 1;
+  int tstride = 1;
+  bool f32 = false;
+  std::vector<std::unique_ptr<LineFactors>> dim;
+  std::unique_ptr<DDFactors> dd;
+  TilePlan tiles[3];  // fine propagator, dimensional splitting: one TMA plan per direction
+};
+
+// Per-launch CUDA events around the library's kernels (params.timing == 2), resolved at
+// the host synchronisation points and summed per kernel kind.
+struct KernelTimer {
+  struct Kind {
+    std::string name;
+    int launches = 0;
+    double ms = 0.0, bytes = 0.0, flops = 0.0;
+  };
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  struct Mark {
+    int kind;
+    double bytes, flops;
+  };
+  std::vector<Mark> marks;
+  std::vector<Kind> kinds;
+  cudaStream_t st = nullptr;
+  ~KernelTimer() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+  int kind_id(const std::string& name) {
+    for (size_t i = 0; i < kinds.size(); ++i)
+      if (kinds[i].name == name) return (int)i;
+    kinds.push_back(Kind{name});
+    return (int)kinds.size() - 1;
+  }
+  void begin(cudaStream_t s) {
+    if (!on) return;
+    st = s;
+    size_t need = 2 * (marks.size() + 1);
+    while (pool.size() < need) {
+      cudaEvent_t e;
+      PS_CUDA(cudaEventCreate(&e));
+      pool.push_back(e);
+    }
+    PS_CUDA(cudaEventRecord(pool[2 * marks.size()], s));
+  }
+  void end(const std::string& name, double bytes, double flops) {
+    if (!on) return;
+    PS_CUDA(cudaEventRecord(pool[2 * marks.size() + 1], st));
+    marks.push_back(Mark{kind_id(name), bytes, flops});
+  }
+  // call after the stream was synchronised
+  void resolve() {
+    for (size_t i = 0; i < marks.size(); ++i) {
+      float ms = 0.f;
+      PS_CUDA(cudaEventElapsedTime(&ms, pool[2 * i], pool[2 * i + 1]));
+      Kind& k = kinds[marks[i].kind];
+      k.launches++;
+      k.ms += ms;
+      k.bytes += marks[i].bytes;
+      k.flops += marks[i].flops;
+    }
+    marks.clear();
+  }
+  void reset() {
+    marks.clear();
+    kinds.clear();
+  }
+};
+
+
+}  // namespace ps
+
+struct ps_problem {
+  const ps_splitting* fine = nullptr;
+  const ps_splitting* coarse = nullptr;
+  const ps_operator* op = nullptr;
+  ps::Geom g;
+  double T = 1.0;
+  int N = 1, gs = 1, fs = 1;
+  ps_params prm{};
+  ps::Prop F, G;
+  ps::DevBuf<double> U, Fout, Gold, gtmp;
+  ps::DevBuf<float> W;      // fine working state, slice-interleaved (FP32 line solves)
+  ps::DevBuf<double> W64;   // same for FP64 line solves
+  int S_pad = 0;        // slots of the interleaved layout
+  ps::DevBuf<int> tmo;      // set by a kernel whose bounded wait ran out
+  ps::DevBuf<float> srcrow32;   // fine source rows along x, line-major (tile sweeps)
+  ps::DevBuf<double> srcrow64;
+  ps::DevBuf<unsigned long long> sstats;  // per slice {max |U^k - U^{k-1}|, max |U^k|}, slices 0..N
+  unsigned long long* h_sstats = nullptr;
+  bool transposed = false;  // propagate with the transposed steps (substeps reversed, no source)
+  bool have_forward = false;
+  // adjoint workspaces (allocated by the first ps_adjoint_vjp with a coefficient gradient)
+  ps::DevBuf<double> Uchk, snap, Lam, gedge[3];
+  ps::TilePlan adj_tiles[3];
+  bool adj_ready = false;
+  ps::DevBuf<unsigned long long> inc;
+  ps::DevBuf<int> flag;
+  unsigned long long* h_inc = nullptr;
+  int* h_flag = nullptr;
+  std::vector<double> hist;
+  int iters = 0;
+  double updates = 0.0;
+  int launches = 0;
+  float ms_total = 0, ms_fine = 0, ms_coarse = 0;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  ps::KernelTimer kt;
+  ~ps_problem() {
+    if (h_sstats) cudaFreeHost(h_sstats);
+    if (h_inc) cudaFreeHost(h_inc);
+    if (h_flag) cudaFreeHost(h_flag);
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+

@@ -111,6 +111,31 @@ struct CorrArgs {
   unsigned long long* slice_stats = nullptr;  // optional {max |U^k - U^{k-1}|, max |U^k|} of this slice
 };
 
+// A run of work items of a grouped (batched) launch: items [prefix, prefix + count) are
+// blocks/tiles first .. first + count - 1 of job `job`.
+struct WorkSeg {
+  int job;
+  int first;
+  int count;
+  int prefix;
+};
+
+// One batched problem's coarse step n (2-D, FP64): the x-sweep reads xin (U_n) into xout
+// (the coarse scratch state) in blocks of R rows; the y-sweep solves xout in place and
+// applies the correction `ca` (mode 1) or the initial-sweep epilogue (mode 2).  The
+// slice-k copy reads xin (F result) into xout (U_k) with the increment in `ca`.
+struct CoarseJob {
+  const double* xin;
+  double* xout;
+  long long rows, nt;
+  int nx, ny, ld, R;
+  const double* lx;
+  const double* rx;
+  const double* ly;
+  const double* ry;
+  CorrArgs ca;
+};
+
 // Launchers (ps_dim.cu).  `in` and `out` may alias (in-place sweeps).  nslices states of
 // geometry g are stored back to back.  Tin/Tout are double or float; the recurrences run in
 // double when fp32 == false and in float otherwise.
@@ -121,5 +146,12 @@ void sweep_dim(const Geom& g, int nslices, const LineFactors& f, bool fp32, cons
                const SourceArgs& srcargs, const CorrArgs& corr, double* tmp, cudaStream_t st);
 void copy_with_increment(long long nt, const double* src, double* dst, unsigned long long* inc, int* nonfinite,
                          unsigned long long* slice_stats, cudaStream_t st);
+// Grouped coarse-step launches (persistent grids of `grid` CTAs; *nseg work segments).
+void coarse_x_grouped(bool var, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid, size_t smem,
+                      cudaStream_t st);
+void coarse_y_grouped(bool var, int epi, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
+                      cudaStream_t st);
+void copy_inc_grouped(const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid, cudaStream_t st);
+int max_dyn_smem_public();
 
 }  // namespace ps

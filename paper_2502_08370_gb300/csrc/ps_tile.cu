@@ -101,6 +101,12 @@ struct TileArgs {
   int* err;
 };
 
+// One (problem, direction) of a grouped launch, and a run of its tiles.
+struct alignas(64) TileJob {
+  CUtensorMap map;
+  TileArgs a;
+};
+
 // Offset of element i of line (slot-in-tile s, position p) in the tile's shared memory,
 // which mirrors the TMA box order (slice fastest, then x, y, z of the box).
 __device__ __forceinline__ int tile_off(const TileArgs& a, int s, int p, int i) {
@@ -233,46 +239,34 @@ __device__ __forceinline__ void line_solve(T* x, int st, int L, const T* Lf, con
   }
 }
 
+// Tile t -> (first slot, first paired position, fixed coordinate).
+__device__ __forceinline__ void tile_coords(const TileArgs& a, int t, int* s0, int* b0, int* c) {
+  const int ngroups = a.s_hi - a.s_lo;
+  *s0 = (a.s_lo + t % ngroups) * a.TS;
+  t /= ngroups;
+  *b0 = (t % a.nbt) * a.P;
+  *c = t / a.nbt;
+}
+
+// One tile: TMA load of the slots x positions x line block (and the line-major factor /
+// source rows by bulk copies) completing on `bar` (phase `parity`), the recurrences in
+// shared memory, TMA store back.  Thread 0 alone polls the barrier within its time limit
+// and shares the outcome.  Returns false (after setting *a.err) when the load timed out.
+// Shared memory from `tile` (128-byte aligned): [tile data | factors l | factors r | source].
 template <typename T, int V, bool SRC>
-__global__ void tile_sweep_kernel(const __grid_constant__ CUtensorMap map, TileArgs a) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  // carve: [tile data | factors l | factors r | source | barrier]; factor rows hold Lp =
-  // L rounded up to 4 entries (zero padded) and start 32-byte aligned
-  T* tile = reinterpret_cast<T*>(smem_raw);
+__device__ __forceinline__ bool tile_body(const CUtensorMap* map, const TileArgs& a, int t, T* tile, uint64_t* bar,
+                                          uint32_t parity) {
+  __shared__ int s_ok;
   const int lines = a.TS * a.P;
   const int Lp = a.Lp;
   T* fl_s = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(tile + (size_t)lines * a.L) + 31) & ~(uintptr_t)31);
   T* fr_s = fl_s + (size_t)a.P * Lp;
   T* src_s = fr_s + (size_t)a.P * Lp;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(
-      (reinterpret_cast<uintptr_t>(src_s + (SRC ? (size_t)a.P * Lp : 0)) + 15) & ~(uintptr_t)15);
-
-  // tile coordinates: blockIdx.x -> (slice group, b block, c)
-  int t = blockIdx.x;
-  const int ngroups = a.s_hi - a.s_lo;
-  const int g = a.s_lo + t % ngroups;
-  t /= ngroups;
-  const int bt = t % a.nbt;
-  const int c = t / a.nbt;
-  const int s0 = g * a.TS, b0 = bt * a.P;
-
+  int s0, b0, c;
+  tile_coords(a, t, &s0, &b0, &c);
   const int tid = threadIdx.x;
   const int nvalid = min(a.P, a.nb - b0);  // positions of this tile inside the grid
-  // once a tile has timed out the launch is abandoned: later tiles start no copies
-  __shared__ int s_abort;
   if (tid == 0) {
-    s_abort = *reinterpret_cast<volatile int*>(a.err);
-    // TMA tensor copies need 128-byte aligned shared-memory destinations
-    if (smem_addr(tile) & 127) {
-      atomicExch(a.err, 2);
-      s_abort = 1;
-    }
-  }
-  __syncthreads();
-  if (s_abort) return;
-  if (tid == 0) {
-    mbar_init(bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     if (a.axis == 0) {
       // x-lines: one box (TS slots x chunk nodes) per position and chunk
       mbar_expect_tx(bar, (uint32_t)(nvalid * a.L * a.TS * (int)sizeof(T)) + side_bytes<T, SRC>(a, nvalid));
@@ -280,7 +274,7 @@ __global__ void tile_sweep_kernel(const __grid_constant__ CUtensorMap map, TileA
       for (int p = 0; p < nvalid; ++p)
         for (int k = 0; k < a.chunks; ++k) {
           const int i0 = k * a.chunk;
-          tma_load_4d(tile + ((size_t)p * a.L + i0) * a.TS, &map, bar, s0, i0, b0 + p, c);
+          tma_load_4d(tile + ((size_t)p * a.L + i0) * a.TS, map, bar, s0, i0, b0 + p, c);
         }
     } else {
       // y/z-lines: one box (TS slots x P positions x chunk nodes) per chunk
@@ -289,17 +283,17 @@ __global__ void tile_sweep_kernel(const __grid_constant__ CUtensorMap map, TileA
       for (int k = 0; k < a.chunks; ++k) {
         const int i0 = k * a.chunk;
         T* dst = tile + (size_t)i0 * a.P * a.TS;
-        if (a.axis == 1) tma_load_4d(dst, &map, bar, s0, b0, i0, c);
-        else tma_load_4d(dst, &map, bar, s0, b0, c, i0);
+        if (a.axis == 1) tma_load_4d(dst, map, bar, s0, b0, i0, c);
+        else tma_load_4d(dst, map, bar, s0, b0, c, i0);
       }
     }
+    s_ok = mbar_wait(bar, parity) ? 1 : 0;
+    if (!s_ok) atomicExch(a.err, 1);
   }
   __syncthreads();
-  if (!mbar_wait(bar, 0)) {
-    if (tid == 0) atomicExch(a.err, 1);
-    return;
-  }
-  const int per_row = a.TS / V;  // threads per line position
+  if (!s_ok) return false;
+  if (tid != 0) mbar_wait(bar, parity);  // completed: acquires the tile's bytes
+  const int per_row = a.TS / V;          // threads per line position
   const int s = (tid % per_row) * V, p = tid / per_row;
   if (p < a.P && b0 + p < a.nb) {
     T ft[V];
@@ -315,28 +309,95 @@ __global__ void tile_sweep_kernel(const __grid_constant__ CUtensorMap map, TileA
       for (int p = 0; p < nvalid; ++p)
         for (int k = 0; k < a.chunks; ++k) {
           const int i0 = k * a.chunk;
-          tma_store_4d(&map, tile + ((size_t)p * a.L + i0) * a.TS, s0, i0, b0 + p, c);
+          tma_store_4d(map, tile + ((size_t)p * a.L + i0) * a.TS, s0, i0, b0 + p, c);
         }
     } else {
       for (int k = 0; k < a.chunks; ++k) {
         const int i0 = k * a.chunk;
         const T* srcp = tile + (size_t)i0 * a.P * a.TS;
-        if (a.axis == 1) tma_store_4d(&map, srcp, s0, b0, i0, c);
-        else tma_store_4d(&map, srcp, s0, b0, c, i0);
+        if (a.axis == 1) tma_store_4d(map, srcp, s0, b0, i0, c);
+        else tma_store_4d(map, srcp, s0, b0, c, i0);
       }
     }
     tma_store_commit_and_drain();
   }
+  __syncthreads();
+  return true;
 }
 
-// Tile t -> (first slot, first paired position, fixed coordinate).
-__device__ __forceinline__ void tile_coords(const TileArgs& a, int t, int* s0, int* b0, int* c) {
-  const int ngroups = a.s_hi - a.s_lo;
-  *s0 = (a.s_lo + t % ngroups) * a.TS;
-  t /= ngroups;
-  *b0 = (t % a.nbt) * a.P;
-  *c = t / a.nbt;
+// Shared memory of a tile kernel: [barrier (128 bytes) | tile ...].
+template <typename T, int V, bool SRC>
+__global__ void tile_sweep_kernel(const __grid_constant__ CUtensorMap map, TileArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  T* tile = reinterpret_cast<T*>(smem_raw + 128);
+  __shared__ int s_abort;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    // once a tile has timed out the launch is abandoned: later tiles start no copies
+    s_abort = *reinterpret_cast<volatile int*>(a.err);
+    // TMA tensor copies need 128-byte aligned shared-memory destinations
+    if (smem_addr(tile) & 127) {
+      atomicExch(a.err, 2);
+      s_abort = 1;
+    }
+    if (!s_abort) {
+      mbar_init(bar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
+  __syncthreads();
+  if (s_abort) return;
+  tile_body<T, V, SRC>(&map, a, blockIdx.x, tile, bar, 0);
 }
+
+// Grouped, persistent form: many problems' tiles in one launch.  jobs[j] holds one
+// (problem, direction)'s tensor map and tile arguments (in global memory, 64-byte aligned);
+// the first *nseg segments of `segs` list which tiles of which job run, with running
+// prefix counts.  Each CTA walks the items t = blockIdx.x, blockIdx.x + gridDim.x, ...
+template <typename T, int V>
+__global__ void tile_sweep_grouped_kernel(const TileJob* __restrict__ jobs, const WorkSeg* __restrict__ segs,
+                                          const int* __restrict__ nseg_ptr, int* err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  T* tile = reinterpret_cast<T*>(smem_raw + 128);
+  __shared__ int s_abort;
+  const int nseg = *nseg_ptr;
+  if (nseg <= 0) return;
+  const long long total = (long long)segs[nseg - 1].prefix + segs[nseg - 1].count;
+  if (threadIdx.x == 0) {
+    s_abort = *reinterpret_cast<volatile int*>(err);
+    if (smem_addr(tile) & 127) {
+      atomicExch(err, 2);
+      s_abort = 1;
+    }
+    if (!s_abort) {
+      mbar_init(bar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
+  __syncthreads();
+  if (s_abort) return;
+  uint32_t parity = 0;
+  for (long long it = blockIdx.x; it < total; it += gridDim.x) {
+    // segment of item `it`: the last segment whose prefix is <= it
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (segs[mid].prefix <= it) lo = mid;
+      else hi = mid - 1;
+    }
+    const WorkSeg sg = segs[lo];
+    const TileJob& job = jobs[sg.job];
+    // the tensor map lives in global memory (written by a host copy): acquire it for the
+    // tensormap proxy before TMA reads it
+    if (threadIdx.x == 0)
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&job.map) : "memory");
+    if (!tile_body<T, V, false>(&job.map, job.a, sg.first + (int)(it - sg.prefix), tile, bar, parity)) return;
+    parity ^= 1u;
+  }
+}
+
 
 template <typename T, bool SRC>
 __device__ __forceinline__ void issue_tile_load(const CUtensorMap* map, const TileArgs& a, T* buf, T* fl_s, T* fr_s,
@@ -507,6 +568,59 @@ __global__ void from_interleaved_kernel(const T* __restrict__ W, double* __restr
   }
 }
 
+// Grouped pack / unpack of many problems' slices (FP64 slice-major <-> FP32 interleaved).
+__device__ __forceinline__ int pack_segment(const WorkSeg* segs, int nseg, long long it) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (segs[mid].prefix <= it) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+template <bool TO>
+__global__ void pack_grouped_kernel(const PackJob* __restrict__ jobs, const WorkSeg* __restrict__ segs,
+                                    const int* __restrict__ nseg_ptr) {
+  __shared__ double tile[32][33];
+  const int nseg = *nseg_ptr;
+  if (nseg <= 0) return;
+  const long long total = (long long)segs[nseg - 1].prefix + segs[nseg - 1].count;
+  for (long long it = blockIdx.x; it < total; it += gridDim.x) {
+    const WorkSeg sg = segs[pack_segment(segs, nseg, it)];
+    const PackJob& j = jobs[sg.job];
+    const long long b = sg.first + (it - sg.prefix);
+    const int nsb = (j.nsl + 31) / 32;
+    const long long pos0 = (b / nsb) * 32;
+    const int sl0 = (int)(b % nsb) * 32;
+    if (TO) {
+      for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int sl = sl0 + r;
+        const long long pos = pos0 + threadIdx.x;
+        tile[r][threadIdx.x] = (sl < j.nsl && pos < j.nt) ? j.U[(long long)sl * j.nt + pos] : 0.0;
+      }
+      __syncthreads();
+      for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const long long pos = pos0 + r;
+        const int sl = sl0 + threadIdx.x;
+        if (sl < j.nsl && pos < j.nt) j.W[pos * j.S_pad + j.s_first + sl] = (float)tile[threadIdx.x][r];
+      }
+    } else {
+      for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const long long pos = pos0 + r;
+        const int sl = sl0 + threadIdx.x;
+        tile[r][threadIdx.x] = (sl < j.nsl && pos < j.nt) ? (double)j.W[pos * j.S_pad + j.s_first + sl] : 0.0;
+      }
+      __syncthreads();
+      for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int sl = sl0 + r;
+        const long long pos = pos0 + threadIdx.x;
+        if (sl < j.nsl && pos < j.nt) j.U[(long long)sl * j.nt + pos] = tile[threadIdx.x][r];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -580,7 +694,7 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
   tp.V = (elem == 4 && tp.TS >= 32) ? 2 : 1;  // slots per thread: FP32 threads take two adjacent lines
   // stages x (tile + factor rows l, r) + alignment + barriers; the source, when added, takes
   // one more factor row per position and stage
-  tp.smem = (size_t)stages * ((size_t)lines * L * elem + 2 * (size_t)tp.P * Lp * elem + 64) + 64;
+  tp.smem = (size_t)stages * ((size_t)lines * L * elem + 2 * (size_t)tp.P * Lp * elem + 64) + 64 + 128;
   tp.threads = lines / tp.V;
   int dev = 0, maxsm = 0;
   PS_CUDA(cudaGetDevice(&dev));
@@ -715,6 +829,55 @@ void factor_lines(const Geom& g, LineFactors& f, bool fp32, cudaStream_t st) {
     line_major_kernel<double><<<blocks, 256, 0, st>>>(f.l64.p, f.r64.p, f.lt64.p, f.rt64.p, m, g.n[0], g.n[1],
                                                       g.n[2], lines, L, Lp, f.var);
   }
+  PS_CUDA(cudaGetLastError());
+}
+
+long long tile_job_fill(const Geom& g, const TilePlan& tp, const LineFactors& f, int S_pad, int s_first, int nsl,
+                        int* err, void* job_out) {
+  TileJob* job = reinterpret_cast<TileJob*>(job_out);
+  std::memset(job, 0, sizeof(TileJob));
+  job->map = tp.map;
+  TileArgs& a = job->a;
+  a.axis = tp.axis;
+  a.L = tp.L;
+  a.P = tp.P;
+  a.TS = tp.TS;
+  a.n[0] = g.n[0];
+  a.n[1] = g.n[1];
+  a.n[2] = g.n[2];
+  const int other[3][2] = {{1, 2}, {0, 2}, {0, 1}};
+  const int bax = other[tp.axis][0], cax = other[tp.axis][1];
+  a.nb = g.n[bax];
+  a.nbt = (a.nb + tp.P - 1) / tp.P;
+  a.s_lo = s_first / tp.TS;
+  a.s_hi = (s_first + nsl + tp.TS - 1) / tp.TS;
+  a.chunks = tp.chunks;
+  a.chunk = tp.chunk;
+  a.var = f.var;
+  a.rows_x = (long long)g.n[1] * g.n[2];
+  a.Lp = (tp.L + 3) & ~3;
+  a.fl = f.lt32.p;
+  a.fr = f.rt32.p;
+  a.err = err;
+  PS_REQUIRE(a.fl && a.fr, "line-major FP32 factors missing");
+  return (long long)(a.s_hi - a.s_lo) * a.nbt * g.n[cax];
+}
+size_t tile_job_bytes() { return sizeof(TileJob); }
+
+size_t tile_grouped_smem(const TilePlan& tp) { return tp.smem; }
+
+void tile_sweep_grouped(const void* jobs, const WorkSeg* segs, const int* nseg, int grid, int threads, size_t smem,
+                        int* err, cudaStream_t st) {
+  auto kern = tile_sweep_grouped_kernel<float, 2>;
+  PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, threads, smem, st>>>(reinterpret_cast<const TileJob*>(jobs), segs, nseg, err);
+  PS_CUDA(cudaGetLastError());
+}
+
+void pack_grouped(bool to_interleaved_dir, const PackJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
+                  cudaStream_t st) {
+  if (to_interleaved_dir) pack_grouped_kernel<true><<<grid, dim3(32, 8), 0, st>>>(jobs, segs, nseg);
+  else pack_grouped_kernel<false><<<grid, dim3(32, 8), 0, st>>>(jobs, segs, nseg);
   PS_CUDA(cudaGetLastError());
 }
 

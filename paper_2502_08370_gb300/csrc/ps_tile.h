@@ -38,4 +38,24 @@ void to_interleaved(const Geom& g, const double* U, T* W, int S_pad, int s_first
 template <typename T>
 void from_interleaved(const Geom& g, const T* W, double* U, int S_pad, int s_first, int nsl, cudaStream_t st);
 
+// ---- grouped (batched) launches -------------------------------------------------------
+// Pack job: slices [s_first, s_first + nsl) of one problem between U (FP64 slice-major,
+// starting at slice s_first) and W (FP32 interleaved, S_pad slots).
+struct PackJob {
+  double* U;
+  float* W;
+  long long nt;
+  int S_pad, s_first, nsl, pad;
+};
+// Fills one (problem, direction) job of a grouped FP32 tile launch (job_out must hold
+// tile_job_bytes(), 64-byte aligned) and returns its tile count.
+long long tile_job_fill(const Geom& g, const TilePlan& tp, const LineFactors& f, int S_pad, int s_first, int nsl,
+                        int* err, void* job_out);
+size_t tile_job_bytes();
+size_t tile_grouped_smem(const TilePlan& tp);
+void tile_sweep_grouped(const void* jobs, const WorkSeg* segs, const int* nseg, int grid, int threads, size_t smem,
+                        int* err, cudaStream_t st);
+void pack_grouped(bool to_interleaved_dir, const PackJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
+                  cudaStream_t st);
+
 }  // namespace ps

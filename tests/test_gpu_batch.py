@@ -1,0 +1,105 @@
+"""Batched problems (grouped launches, CUDA graph per iteration) and the schedule autotuner.
+
+A batch must reproduce each problem's own ps_run_parareal bitwise (same arithmetic per
+line, only the launch grouping differs); the autotuner changes the tile schedule and
+therefore must not change any result either.  One problem of the small batch is also
+checked against the FP64 oracle within the FP32 line-solve bound.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as orc
+from paper_2502_08370_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ps():
+    from paper_2502_08370_gb300 import build
+    build.build()
+    import paper_2502_08370_gb300 as ps
+    return ps
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def make(ps, cfg):
+    grid = ps.Grid(cfg["n"])
+    op = ps.Operator(grid, a=None if cfg["a"] is None else dev(cfg["a"]))
+    sp = ps.Splitting(op)
+    prob = ps.Problem(sp, cfg["T"], cfg["N"], 1, cfg["s"], precision="mixed")
+    prob._keep = (grid, op, sp)
+    return prob
+
+
+def small_batch(count=7, seed=5):
+    return wl.batch256(count=count, seed=seed, sizes=(17, 31, 47, 64), slices=(4, 8, 16), s_range=(3, 20))
+
+
+def snapshot(prob):
+    return [prob.state(n).cpu().numpy() for n in range(prob.N + 1)]
+
+
+def test_small_batch_equals_individual_runs_bitwise(ps):
+    cfgs = small_batch()
+    probs = [make(ps, c) for c in cfgs]
+    u0s = [dev(c["u0"]) for c in cfgs]
+    ref_it, ref_states, ref_hist = [], [], []
+    for p, u in zip(probs, u0s):
+        ref_it.append(p.run(u, 1e-8))
+        ref_states.append(snapshot(p))
+        ref_hist.append(p.history())
+    batch = ps.Batch(probs)
+    its = batch.run(u0s, 1e-8)
+    assert its == ref_it
+    for p, st, h in zip(probs, ref_states, ref_hist):
+        got = snapshot(p)
+        for n in range(p.N + 1):
+            assert np.array_equal(got[n], st[n]), n
+        assert np.array_equal(p.history(), h)
+    # a second run of the same batch (graphs re-used) gives the same again
+    its2 = batch.run(u0s, 1e-8)
+    assert its2 == ref_it
+    assert np.array_equal(snapshot(probs[0])[-1], ref_states[0][-1])
+    # one problem against the FP64 oracle, within the FP32 line-solve bound
+    c = cfgs[0]
+    U_ref, _, _ = orc.parareal(orc.Problem(c["n"], a=c["a"]), c["T"], c["N"], 1, c["s"], c["u0"], 1e-8)
+    err = np.abs(ref_states[0][-1] - U_ref[-1]).max() / np.abs(U_ref[-1]).max()
+    assert err < 4.0 * c["s"] * c["N"] * 2 * 2.0 ** -24
+
+
+def test_autotune_changes_no_result(ps):
+    c = wl.batch256(count=1, seed=11, sizes=(127,), slices=(32,), s_range=(16, 16))[0]
+    p = make(ps, c)
+    u0 = dev(c["u0"])
+    p.run(u0, 1e-8)
+    before = snapshot(p)
+    choice = p.autotune(budget_ms=50)
+    assert choice > 0
+    p.run(u0, 1e-8)
+    after = snapshot(p)
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+
+
+def test_batch256_sampled_against_individual_runs(ps):
+    """The full heterogeneous batch (256 problems, grids up to 511^2, N up to 64, s up to 128):
+    eight sampled problems re-run alone must match their batched results bitwise."""
+    cfgs = wl.batch256()
+    probs = [make(ps, c) for c in cfgs]
+    u0s = [dev(c["u0"]) for c in cfgs]
+    batch = ps.Batch(probs)
+    its = batch.run(u0s, 1e-8)
+    assert all(1 <= k <= c["N"] for k, c in zip(its, cfgs))
+    sample = np.random.default_rng(0).choice(len(cfgs), 8, replace=False)
+    batched = {int(i): (its[i], probs[i].state(probs[i].N).cpu().numpy()) for i in sample}
+    for i in sample:
+        i = int(i)
+        k = probs[i].run(u0s[i], 1e-8)
+        assert k == batched[i][0]
+        assert np.array_equal(probs[i].state(probs[i].N).cpu().numpy(), batched[i][1])
