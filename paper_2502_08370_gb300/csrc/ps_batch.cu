@@ -321,6 +321,7 @@ int ps_batch_create(ps_problem* const* problems, int count, uintptr_t stream, ps
     b->inc.alloc(P);
     b->flag.alloc(P);
     b->tmo.alloc(1);
+    PS_CUDA(cudaMemset(b->tmo.p, 0, sizeof(int)));
     b->h_tile_jobs.assign((size_t)2 * P * tile_job_bytes(), 0);
     b->h_tile_segs.assign((size_t)2 * P, WorkSeg{});
     b->h_tile_nseg.assign((size_t)2 * b->maxS, 0);

@@ -248,6 +248,23 @@ CorrArgs corr_args(ps_problem* p, int mode, int n) {
   return c;
 }
 
+// The tile kernels abandon their work once the flag `tmo` holds an error (1: a bounded TMA wait
+// ran out, 2: a misaligned shared-memory destination), so every entry point that launches them
+// zeroes it first and reads it back after its last launch.
+void tile_flag_reset(ps_problem* p, cudaStream_t st) { PS_CUDA(cudaMemsetAsync(p->tmo.p, 0, sizeof(int), st)); }
+
+void tile_flag_throw(int v) {
+  if (v == 2) throw Error(PS_ERR_CUDA, "a tile's shared-memory buffer was not 128-byte aligned");
+  if (v) throw Error(PS_ERR_DEVICE_TIMEOUT, "a TMA tile load did not arrive within its wait limit");
+}
+
+void tile_flag_check(ps_problem* p, cudaStream_t st) {
+  int v = 0;
+  PS_CUDA(cudaMemcpyAsync(&v, p->tmo.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PS_CUDA(cudaStreamSynchronize(st));
+  tile_flag_throw(v);
+}
+
 void check_state_len(const ps_problem* p, int slice) {
   PS_REQUIRE(slice >= 0 && slice <= p->N, "slice out of range");
 }
@@ -266,7 +283,7 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
   if (timing) PS_CUDA(cudaEventRecord(p->ev[0], st));
   PS_CUDA(cudaMemcpyAsync(p->U.p, u0, sizeof(double) * nt, cudaMemcpyDeviceToDevice, st));
   PS_CUDA(cudaMemsetAsync(p->flag.p, 0, sizeof(int), st));
-  PS_CUDA(cudaMemsetAsync(p->tmo.p, 0, sizeof(int), st));
+  tile_flag_reset(p, st);
   // k = 0: sequential coarse sweep, U_{n+1}^0 = G(U_n^0), Gold_n = G(U_n^0)
   for (int n = 0; n < N; ++n) run_G(p, n, p->U.p + n * nt, corr_args(p, 2, n), st);
   int k = 0;
@@ -292,8 +309,7 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
     PS_CUDA(cudaStreamSynchronize(st));
     if (p->h_flag[1]) {
       p->iters = k;
-      if (p->h_flag[1] == 2) throw Error(PS_ERR_CUDA, "a tile's shared-memory buffer was not 128-byte aligned");
-      throw Error(PS_ERR_DEVICE_TIMEOUT, "a TMA tile load did not arrive within its wait limit");
+      tile_flag_throw(p->h_flag[1]);
     }
     p->kt.resolve();
     if (timing) {
@@ -504,6 +520,7 @@ int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, doub
     p->gtmp.alloc((size_t)nt);
     p->inc.alloc(1);
     p->tmo.alloc(1);
+    PS_CUDA(cudaMemset(p->tmo.p, 0, sizeof(int)));
     p->sstats.alloc((size_t)2 * (N + 1));
     PS_CUDA(cudaMallocHost(&p->h_sstats, sizeof(unsigned long long) * 2 * (N + 1)));
     PS_REQUIRE(p->prm.tol_mode == 0 || p->prm.tol_mode == 1, "tol_mode must be 0 or 1");
@@ -601,9 +618,10 @@ int ps_run_fine_sequential(ps_problem* p, const double* u0_dev, double* U_out_de
     const long long nt = p->g.nt;
     p->updates = 0;
     p->launches = 0;
+    tile_flag_reset(p, st);
     PS_CUDA(cudaMemcpyAsync(U_out_dev, u0_dev, sizeof(double) * nt, cudaMemcpyDeviceToDevice, st));
     for (int n = 0; n < p->N; ++n) run_F(p, n, 1, U_out_dev + n * nt, U_out_dev + (n + 1) * nt, st);
-    PS_CUDA(cudaStreamSynchronize(st));
+    tile_flag_check(p, st);
   });
 }
 
@@ -697,6 +715,7 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
       int slots, positions, pipe;
     };
     const std::vector<Cand> cands = {{32, 1, 0}, {64, 1, 0}, {32, 2, 0}, {16, 1, 0}, {32, 1, 1}};
+    tile_flag_reset(p, st);
     cudaEvent_t e0, e1;
     PS_CUDA(cudaEventCreate(&e0));
     PS_CUDA(cudaEventCreate(&e1));
@@ -754,9 +773,7 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
       return;
     }
     rebuild_tiles(p, bestc.slots, bestc.positions, bestc.pipe);
-    int tmo = 0;
-    PS_CUDA(cudaMemcpy(&tmo, p->tmo.p, sizeof(int), cudaMemcpyDeviceToHost));
-    if (tmo) throw Error(PS_ERR_DEVICE_TIMEOUT, "a TMA tile load did not arrive within its wait limit");
+    tile_flag_check(p, st);
     if (choice_out) *choice_out = bestc.slots * 100 + bestc.positions * 10 + bestc.pipe;
   });
 }
@@ -877,10 +894,7 @@ int ps_adjoint_vjp(ps_problem* p, const double* gN_dev, double tol, int max_iter
     p->hist = saved_hist;
     p->iters = saved_iters;
     p->have_forward = true;
-    PS_CUDA(cudaStreamSynchronize(st));
-    int tmo = 0;
-    PS_CUDA(cudaMemcpy(&tmo, p->tmo.p, sizeof(int), cudaMemcpyDeviceToHost));
-    if (tmo) throw Error(PS_ERR_DEVICE_TIMEOUT, "a TMA tile load did not arrive within its wait limit");
+    tile_flag_check(p, st);
   });
 }
 

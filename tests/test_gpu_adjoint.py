@@ -104,6 +104,63 @@ def test_adjoint_finite_differences_adjoint2d(ps):
         assert abs(an - fd) <= 1e-6 * abs(fd) + 1e-30, (an, fd)
 
 
+def test_adjoint_full_size_directional_derivatives(ps):
+    """511^2, N = 32, s = 64, parareal to 1e-10: <grad, d> against fourth-order central
+    differences of J on seeded unit directions, J evaluated on the discrete forward map the
+    adjoint differentiates (N*s fine steps from u0).  U_N's ~1e-15 relative rounding, divided
+    by e, sets the step: e = 0.1 (each node moves by ~2e-4), where the stencil's truncation
+    error stays near 1e-8 of the derivative."""
+    cfg = wl.adjoint2d_511()
+    n, N = cfg["n"], cfg["N"]
+    prob = build(ps, n, cfg["a"], T=cfg["T"], N=N, s=cfg["s"])
+    u0 = dev(cfg["u0"])
+    prob.update_coefficients(dev(cfg["a_target"]))
+    tgt = prob.fine_sequential(u0)[N].clone()
+    a = dev(cfg["a"])
+    prob.update_coefficients(a)
+    prob.run(u0, cfg["tol"])
+    gN = prob.state(N) - tgt
+    gu, ga = prob.vjp(gN, cfg["tol"])
+
+    def J_of(aa, uu):
+        prob.update_coefficients(aa)
+        x = uu.clone()
+        prob.propagate(0, N * cfg["s"], x)
+        r = x - tgt
+        return 0.5 * float((r * r).sum())
+
+    def fd4(f, eps):
+        return (8.0 * (f(eps) - f(-eps)) - (f(2 * eps) - f(-2 * eps))) / (12.0 * eps)
+
+    eps = 0.1
+    for d in wl.random_directions(tuple(a.shape), 4, cfg["dirs_seed"]):
+        dd = dev(d)
+        fd = fd4(lambda e: J_of(a + e * dd, u0), eps)
+        an = float((ga * dd).sum())
+        assert abs(an - fd) <= 1e-6 * abs(fd), (an, fd)
+    for d in wl.random_directions(tuple(u0.shape), 2, cfg["dirs_seed"] + 1):
+        dd = dev(d)
+        fd = fd4(lambda e: J_of(a, u0 + e * dd), eps)
+        an = float((gu * dd).sum())
+        assert abs(an - fd) <= 1e-6 * abs(fd), (an, fd)
+
+
+def test_adjoint_full_size_matches_oracle(ps):
+    """511^2, N = 32, s = 64: the GPU gradient (parareal forward and adjoint to 1e-10 per-slice
+    relative) against the oracle's sequential discrete adjoint, for J = 1/2 ||U_N||^2."""
+    cfg = wl.adjoint2d_511()
+    n, N = cfg["n"], cfg["N"]
+    prob = build(ps, n, cfg["a"], T=cfg["T"], N=N, s=cfg["s"])
+    prob.run(dev(cfg["u0"]), cfg["tol"])
+    UN = prob.state(N)
+    gu, ga = prob.vjp(UN, cfg["tol"])
+    J, gu_ref, ga_ref = orc.adjoint(orc.Problem(n, a=cfg["a"]), cfg["T"], N, cfg["s"], cfg["u0"],
+                                    np.zeros(n[::-1]))
+    assert abs(0.5 * float((UN * UN).sum()) - J) <= 1e-10 * J
+    assert relmax(gu.cpu().numpy(), gu_ref) < 1e-9
+    assert relmax(ga.cpu().numpy(), ga_ref) < 1e-9
+
+
 def test_autograd_function(ps):
     rng = np.random.default_rng(43)
     n, N, s = (21, 17), 4, 8
@@ -121,3 +178,20 @@ def test_autograd_function(ps):
     assert abs(float(loss.detach()) - J) <= 1e-10 * J
     assert relmax(u0.grad.cpu().numpy(), gu_ref) < 1e-9
     assert relmax(a.grad.cpu().numpy(), ga_ref) < 1e-9
+
+
+@pytest.mark.parametrize("n", [(300, 11), (9, 280)])
+def test_adjoint_long_lines_matches_oracle(ps, n):
+    rng = np.random.default_rng(44)
+    shape_a = tuple(v + 2 for v in reversed(n))
+    a = np.exp(0.3 * rng.standard_normal(shape_a))
+    N, s, T = 2, 3, 0.01
+    u0 = rng.standard_normal(n[::-1])
+    tgt = rng.standard_normal(n[::-1])
+    prob = build(ps, n, a, T=T, N=N, s=s)
+    prob.run(dev(u0), 1e-14)
+    gN = prob.state(N) - dev(tgt)
+    gu, ga = prob.vjp(gN, 1e-14)
+    J, gu_ref, ga_ref = orc.adjoint(orc.Problem(n, a=a), T, N, s, u0, tgt)
+    assert relmax(gu.cpu().numpy(), gu_ref) < 1e-9
+    assert relmax(ga.cpu().numpy(), ga_ref) < 1e-9

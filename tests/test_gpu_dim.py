@@ -194,3 +194,40 @@ def test_nonfinite_input_is_reported(ps):
     with pytest.raises(ps.PsError) as e:
         prob.run(dev(u0), 1e-8)
     assert e.value.code == 4
+
+
+@pytest.mark.parametrize("n", [(511, 9), (7, 300), (6, 5, 300), (300, 4, 3)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fine_sequential_long_lines_chunked_tiles(ps, n, precision):
+    """Lines longer than one TMA box (256 nodes) are moved in several chunks."""
+    rng = np.random.default_rng(17)
+    a = np.exp(0.3 * rng.standard_normal([v + 2 for v in reversed(n)]))
+    src = rng.standard_normal(n[::-1])
+    N, s = 3, 2
+    src_t = 1.0 + np.cos(np.arange(N * s + 1))
+    prob, orp = make(ps, n, a=a, c=0.2, src=src, src_t=src_t, T=0.01, N=N, g=1, s=s, precision=precision)
+    u0 = rng.standard_normal(n[::-1])
+    got = prob.fine_sequential(dev(u0)).cpu().numpy()
+    ref = orc.fine_sequential(orp, 0.01, N, s, u0)
+    bound = RTOL64 if precision == "fp64" else mixed_bound(s, N, len(n))
+    for j in range(N + 1):
+        assert relmax(got[j], ref[j]) < bound, j
+
+
+def test_fine_sequential_on_recycled_device_memory(ps):
+    """Device buffers handed back by the driver keep their old contents: fill memory with
+    all-ones words, release it, then create a problem (its status flags are carved from the
+    same pool) and check that the fine propagator still runs every sweep."""
+    junk = torch.full((1 << 26,), -1, dtype=torch.int32, device="cuda")
+    del junk
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(19)
+    n, N, s = (7, 300), 3, 2
+    a = np.exp(0.3 * rng.standard_normal([v + 2 for v in reversed(n)]))
+    prob, orp = make(ps, n, a=a, T=0.01, N=N, g=1, s=s)
+    u0 = rng.standard_normal(n[::-1])
+    got = prob.fine_sequential(dev(u0)).cpu().numpy()
+    ref = orc.fine_sequential(orp, 0.01, N, s, u0)
+    for j in range(N + 1):
+        assert relmax(got[j], ref[j]) < RTOL64, j
