@@ -51,6 +51,19 @@ def load_peaks():
 FP64_PEAK_TFLOPS = 1.19
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per node-slice of the fine tile
+# sweeps, from one ncu capture of the kernel built from the tile source with this hash prefix
+# (127^3 x 64 slices, scaled to any launch by the node-slices it processes).  A kernel whose
+# source changed since is reported with traffic null.
+TRAFFIC = {"F.z.f32": {"bytes_per_node_slice": 1003.901184e6 / (127 ** 3 * 64), "tile_src_sha": "fc38e8fad410ea13"}}
+
+
+def tile_src_sha():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2502_08370_gb300", "csrc", "ps_tile.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
 def workload(name):
     from paper_2502_08370_gb300 import workloads as wl
     if name == "heat3d_255":
@@ -132,13 +145,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def make_problem(ps, torch, cfg, precision, timing):
+def make_problem(ps, torch, cfg, precision, timing, coarse_mode="fp64"):
     grid = ps.Grid(cfg["n"])
     a = None if cfg["a"] is None else torch.as_tensor(cfg["a"]).cuda()
     src = None if cfg["src"] is None else torch.as_tensor(cfg["src"]).cuda()
     op = ps.Operator(grid, a=a, c=cfg["c"], src=src, src_t=cfg["src_t"])
     sp = ps.Splitting(op, cfg["split"], cfg.get("boxes", (1, 1)), cfg.get("overlap", 0.0))
-    prob = ps.Problem(sp, cfg["T"], cfg["N"], cfg["g"], cfg["s"], precision=precision, timing=timing)
+    prob = ps.Problem(sp, cfg["T"], cfg["N"], cfg["g"], cfg["s"], precision=precision, timing=timing,
+                      coarse_mode=coarse_mode)
     prob._keep = (grid, op, sp, a, src)
     return prob
 
@@ -210,7 +224,7 @@ def config_of(args, cfg):
     gb = nt * (3 * cfg["N"] + 1) * 8 / 1e9
     out = {"workload": args.workload, "grid": grid, "splitting": cfg["split"], "N_slices": cfg["N"],
            "coarse_steps": cfg["g"], "fine_steps": cfg["s"], "T": cfg["T"], "tol": cfg["tol"],
-           "precision": args.precision,
+           "precision": args.precision, "coarse": getattr(args, "coarse", "fp64"),
            "l2": (f"inputs larger than L2 ({gb:.1f} GB of slice states streamed per step)" if gb > 0.2 else
                   f"working set {gb * 1e3:.0f} MB fits in L2: latency-bound case, no roofline claim")}
     if cfg["split"] == "dd":
@@ -318,25 +332,35 @@ def run_adjoint(args, cfg, ps, torch, rank, ws):
     prob.update_coefficients(a)
     stream = torch.cuda.current_stream()
 
+    M = len(n)
+
     def gradient():
         prob.run(u0, tol)
-        fwd = prob.stats()["unknown_updates"]
+        fwd = prob.stats()
         gN = prob.state(cfg["N"]) - tgt
         gu, ga = prob.vjp(gN, tol)
-        adj = prob.stats()["unknown_updates"]  # the adjoint parareal's own count
-        return gu, ga, fwd + adj + 2.0 * cfg["N"] * cfg["s"] * nt  # + recomputation + backward sweeps
+        adj = prob.stats()  # the adjoint parareal's own counts
+        # + recomputation and backward sweeps of every slice: 2 packs, s*M sweeps, s*M transposed
+        # sweeps and s*M edge-product kernels, one combine
+        nl = fwd["kernel_launches"] + adj["kernel_launches"] + 3 + 3 * cfg["s"] * M
+        return gu, ga, fwd["unknown_updates"] + adj["unknown_updates"] + 2.0 * cfg["N"] * cfg["s"] * nt, nl
 
     for _ in range(args.warmup):
         gradient()
     torch.cuda.synchronize()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) if rank == 0 else None
+    if sampler:
+        sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    upd = 0.0
+    upd, launches = 0.0, 0
     e0.record(stream)
     for _ in range(args.steps):
-        gu, ga, u = gradient()
+        gu, ga, u, nl = gradient()
         upd += u
+        launches += nl
     e1.record(stream)
     torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
     ms = e0.elapsed_time(e1)
     # Central differences of J on seeded unit directions, fourth order,
     #   dJ ~ [8 (J(+e) - J(-e)) - (J(+2e) - J(-2e))] / (12 e),
@@ -379,7 +403,7 @@ def run_adjoint(args, cfg, ps, torch, rank, ws):
                           "fd_directions_u0": len(errs_u),
                           "fd_max_rel_err_u0": max(errs_u),
                           "adjoint_parareal_iters": getattr(prob, "last_adjoint_iters", None)}}
-    finish_line(args, cfg, upd / (ms / 1e3), ms / args.steps, None, extra, rank, ws)
+    finish_line(args, cfg, upd / (ms / 1e3), ms / args.steps, launches, extra, rank, ws, clocks=clocks)
 
 
 def main():
@@ -390,13 +414,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="heat3d_255")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--coarse", default="delta32", choices=["delta32", "fp64"],
+                    help="coarse propagator of the mixed form: FP32 increment form or FP64 (dimensional splitting)")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 time-to-tolerance run")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--fd-dirs", type=int, default=20, help="finite-difference directions (adjoint workload)")
+    ap.add_argument("--slices", type=int, default=0,
+                    help="override the workload's slice count N (small-footprint profiling runs; named in config)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     cfg = workload(args.workload)
+    if args.slices > 0 and "batch" not in cfg:
+        cfg["N"] = args.slices
 
     if args.impl == "reference":
         rank, ws = dist_setup("gloo")
@@ -420,12 +450,14 @@ def main():
     if args.workload in ("heat2d_63", "dd2d_1023", "adjoint2d_511"):
         args.precision = "fp64"  # these workloads are specified in FP64
         args.no_compare = True
+    if args.precision == "fp64" or cfg.get("split") == "dd":
+        args.coarse = "fp64"
     if args.workload == "batch256":
         return run_batch(args, cfg, ps, torch, rank, ws)
     if args.workload == "adjoint2d_511":
         return run_adjoint(args, cfg, ps, torch, rank, ws)
 
-    prob = make_problem(ps, torch, cfg, args.precision, timing=2)
+    prob = make_problem(ps, torch, cfg, args.precision, timing=2, coarse_mode=args.coarse)
     max_iter = cfg.get("max_iter", 0)
     u0 = torch.as_tensor(cfg["u0"]).cuda()
     stream = torch.cuda.current_stream()
@@ -490,6 +522,12 @@ def main():
         achieved = dom["bytes"] / dom["launches"] / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": None}
+        tr = TRAFFIC.get(dom_name)
+        if tr and tr["tile_src_sha"] == tile_src_sha():
+            # fine sweep bytes = node-slices x (4 in + 4 out) + the line factors l, r (FP32, per node)
+            nt = float(np.prod(cfg["n"]))
+            node_slices = (dom["bytes"] / dom["launches"] - 8.0 * nt) / 8.0
+            roof["traffic"] = tr["bytes_per_node_slice"] * node_slices
     roof.update({"kernel": dom_name, "launches_timed": dom["launches"], "ms_per_launch": per_launch_ms,
                  "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
                  "share_of_step": dom["ms"] / ms, "peak_source": pk_kind})
@@ -534,24 +572,37 @@ def main():
     if not args.no_compare and args.precision != "fp64":
         del prob
         torch.cuda.empty_cache()
-        p64 = make_problem(ps, torch, cfg, "fp64", timing=1)
-        p64.run(u0, cfg["tol"])
-        torch.cuda.synchronize()
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 2
-        c0.record(stream)
-        for _ in range(reps):
-            it64 = p64.run(u0, cfg["tol"])
-        c1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = c0.elapsed_time(c1) / reps
-        uN64 = p64.state(cfg["N"]).cpu().numpy()
-        err = float(np.abs(uN_mixed - uN64).max() / max(np.abs(uN64).max(), 1e-300))
-        compare = {"fp64_ms_to_tol": ms64, "fp64_iters": it64, "ms_to_tol": ms / args.steps,
-                   "iters": iters[-1], "speedup_vs_fp64": ms64 / (ms / args.steps),
-                   "rel_maxnorm_diff_UN_vs_fp64": err,
-                   "fp64_unknown_updates_per_s": p64.stats()["unknown_updates"] / (ms64 / 1000.0)}
-        del p64
+
+        def time_to_tol(precision, coarse_mode):
+            q = make_problem(ps, torch, cfg, precision, timing=1, coarse_mode=coarse_mode)
+            q.run(u0, cfg["tol"])
+            torch.cuda.synchronize()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 2
+            c0.record(stream)
+            for _ in range(reps):
+                it = q.run(u0, cfg["tol"])
+            c1.record(stream)
+            torch.cuda.synchronize()
+            t = c0.elapsed_time(c1) / reps
+            out = (t, it, q.state(cfg["N"]).cpu().numpy(), q.stats()["unknown_updates"] / (t / 1000.0))
+            del q
+            torch.cuda.empty_cache()
+            return out
+
+        ms64, it64, uN64, ups64 = time_to_tol("fp64", "fp64")
+
+        def rel(a, b):
+            return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+        compare = {"plain_fp64_ms_to_tol": ms64, "plain_fp64_iters": it64, "ms_to_tol": ms / args.steps,
+                   "iters": iters[-1], "speedup_vs_plain_fp64": ms64 / (ms / args.steps),
+                   "rel_maxnorm_diff_UN_vs_plain_fp64": rel(uN_mixed, uN64),
+                   "plain_fp64_unknown_updates_per_s": ups64}
+        if args.coarse != "fp64":
+            msm, itm, uNm, _ = time_to_tol("mixed", "fp64")
+            compare.update({"mixed_fp64_coarse_ms_to_tol": msm, "mixed_fp64_coarse_iters": itm,
+                            "mixed_fp64_coarse_rel_maxnorm_diff_UN_vs_plain_fp64": rel(uNm, uN64)})
 
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_seconds > 0:

@@ -56,6 +56,18 @@ extern "C" {
 #define PS_PREC_MIXED 1 /* fine-propagator line solves in FP32; coarse propagator, the
                            parareal correction, the increments and the test in FP64 */
 
+/* Coarse propagator arithmetic (ps_params.coarse).  G is affine (Sec. 2.2, eq. FIE_method:
+ * G(u) = B u + c with c from the source), so the bracket G(U_n^k) - G(U_n^{k-1}) of the
+ * parareal correction equals B (U_n^k - U_n^{k-1}).  PS_COARSE_DELTA32 evaluates it in that
+ * form with FP32 line solves on the FP32-rounded increment: the rounding is relative to the
+ * increment, not to U, so the FP64 increment test still reaches small tolerances.  The
+ * correction U_{n+1}^k = F(U_n^{k-1}) + B d_n, the increments and the test stay FP64; the
+ * initial coarse sweep U_{n+1}^0 = G(U_n^0) runs with FP32 line solves on the state.
+ * Finite termination stays bitwise (d_n = 0 gives B d_n = 0).  Dimensional splitting only;
+ * not in batches or adjoints.  ps_run_coarse_sequential keeps the FP64 coarse steps. */
+#define PS_COARSE_FP64 0    /* G in FP64, correction written as F + (G_new - G_old) (Sec. 3) */
+#define PS_COARSE_DELTA32 1 /* G's linear part in FP32 on the increment, see above */
+
 #define PS_SCHED_AUTO 0   /* library default for dimensional line solves */
 #define PS_SCHED_THOMAS 1 /* one thread per line, Thomas/LDL^T recurrences */
 #define PS_SCHED_PCR 2    /* one warp per line, parallel cyclic reduction */
@@ -101,13 +113,16 @@ typedef struct {
   int schedule;  /* PS_SCHED_* for the fine line solves */
   int timing;    /* 1: per-phase CUDA events (ps_problem_stats); 2: also per-kernel
                     events (ps_problem_kernel_times) */
-  int dd_slices_per_block; /* DD subdomain solves: slices (one warp each) per CTA, 1..8; 0 = 2 */
+  int dd_slices_per_block; /* DD subdomain solves: time slices per CTA (1, 2 or 4); 0 = 2 */
   int tile_positions;      /* fine line solves: line positions per TMA tile (1, 2, 4); 0 = auto */
   int tile_pipeline;       /* fine line solves: 1 persistent double-buffered CTAs, 2 one tile per
                               CTA, 0 = auto */
   int tile_slots;          /* fine line solves: time slices per TMA tile (16, 32, 64); 0 = auto */
   int tol_mode;            /* stopping test: 0 = max_n ||U_n^k - U_n^{k-1}||_inf < tol (absolute);
                               1 = max_n ||U_n^k - U_n^{k-1}||_inf / ||U_n^k||_inf < tol (per slice) */
+  int coarse;              /* PS_COARSE_FP64 (0) or PS_COARSE_DELTA32 */
+  int tile_lines_per_thread; /* fine line solves (FP32 tiles of 32+ slots): lines a thread solves
+                                side by side, 1 or 2; 0 = auto (2) */
 } ps_params;
 
 /* fine, coarse: splittings of the same operator used by F and G (coarse = NULL: use

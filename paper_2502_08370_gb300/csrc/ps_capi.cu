@@ -125,10 +125,11 @@ void fie_step_dd(ps_problem* p, Prop& P, int nsl, const double* in, double* out,
   for (int q = 0; q < M; ++q) {
     const int c = p->transposed ? M - 1 - q : q;
     p->kt.begin(st);
-    dd_solve(p->g, nsl, *P.dd, c, out, spb, st);
+    dd_solve(p->g, nsl, *P.dd, c, out, spb, p->tmo.p, st);
     if (p->kt.on) {
       const auto& pl = P.dd->plan;
-      const double w = pl.nodes[c] > 0 ? pl.fac_entries[c] / (2.0 * pl.nodes[c]) - 1.0 : 0.0;
+      // per box node and slice: w FMAs forward and w backward (w = line length of the box)
+      const double w = pl.nodes[c] > 0 ? pl.fac_entries[c] / (2.0 * pl.nodes[c]) - 0.5 : 0.0;
       p->kt.end(std::string(phase) + ".dd" + std::to_string(c) + ".f64", nsl * pl.nodes[c] * 16.0 + pl.fac_entries[c] * 8.0,
                 nsl * pl.nodes[c] * 4.0 * w);
     }
@@ -235,6 +236,47 @@ void run_G(ps_problem* p, int n, const double* in, const CorrArgs& corr, cudaStr
   p->updates += (double)P.steps * (double)p->g.nt;
 }
 
+// G's one FIE step in FP32 line solves for the coarse increment form (PS_COARSE_DELTA32):
+// init = true:  U_{n+1}^0 = G(U_n^0) on the state, source included (x-sweep reads FP64 U_n);
+// init = false: U_{n+1}^k = Fout_n + B d_n with d_n = U_n^k - U_n^{k-1} (FP32, in d32), no
+// source (it cancels); the last sweep's epilogue writes the new increment d_{n+1} to d32.
+void run_G32(ps_problem* p, int n, bool init, cudaStream_t st) {
+  Prop& P = p->G;
+  const int M = P.sp->M;
+  const long long nt = p->g.nt;
+  const double dnt = (double)nt;
+  PS_REQUIRE(P.steps == 1, "the FP32 coarse increment form takes one coarse step per slice");
+  CorrArgs c;
+  c.mode = init ? 2 : 3;
+  c.U_next = p->U.p + (n + 1) * nt;
+  c.nonfinite = p->flag.p;
+  if (!init) {
+    c.Fout = p->Fout.p + n * nt;
+    c.inc = p->inc.p;
+    c.slice_stats = p->sstats.p + 2 * (n + 1);
+    c.dnext = p->d32.p;
+  }
+  for (int m = 0; m < M; ++m) {
+    const bool last = m == M - 1;
+    SourceArgs sa = (init && m == 0) ? source_for(p, P, n * p->fs + P.tstride, 0) : SourceArgs{};
+    p->kt.begin(st);
+    double bytes = 0;
+    if (m == 0 && init) {
+      sweep_dim<double, float>(p->g, 1, *P.dim[m], true, p->U.p + n * nt, p->g32.p, sa, CorrArgs{}, nullptr, st);
+      bytes = dnt * (8 + 4 + 8 + (sa.src ? 8 : 0));
+    } else {
+      const float* in = m == 0 ? p->d32.p : p->g32.p;
+      sweep_dim<float, float>(p->g, 1, *P.dim[m], true, in, p->g32.p, SourceArgs{}, last ? c : CorrArgs{}, nullptr, st);
+      bytes = dnt * (4 + 4 + 8) + (last ? dnt * (init ? 8.0 : 28.0) : 0.0);
+    }
+    if (p->kt.on)
+      p->kt.end(std::string("G.") + kAxis[m] + ".f32" + (last ? (init ? "+init" : "+dcorr") : ""), bytes,
+                dnt * 5.0);
+    p->launches++;
+  }
+  p->updates += dnt;
+}
+
 CorrArgs corr_args(ps_problem* p, int mode, int n) {
   CorrArgs c;
   c.mode = mode;
@@ -255,7 +297,7 @@ void tile_flag_reset(ps_problem* p, cudaStream_t st) { PS_CUDA(cudaMemsetAsync(p
 
 void tile_flag_throw(int v) {
   if (v == 2) throw Error(PS_ERR_CUDA, "a tile's shared-memory buffer was not 128-byte aligned");
-  if (v) throw Error(PS_ERR_DEVICE_TIMEOUT, "a TMA tile load did not arrive within its wait limit");
+  if (v) throw Error(PS_ERR_DEVICE_TIMEOUT, "an asynchronous copy into shared memory did not arrive within its wait limit");
 }
 
 void tile_flag_check(ps_problem* p, cudaStream_t st) {
@@ -285,7 +327,10 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
   PS_CUDA(cudaMemsetAsync(p->flag.p, 0, sizeof(int), st));
   tile_flag_reset(p, st);
   // k = 0: sequential coarse sweep, U_{n+1}^0 = G(U_n^0), Gold_n = G(U_n^0)
-  for (int n = 0; n < N; ++n) run_G(p, n, p->U.p + n * nt, corr_args(p, 2, n), st);
+  for (int n = 0; n < N; ++n) {
+    if (p->delta32) run_G32(p, n, true, st);
+    else run_G(p, n, p->U.p + n * nt, corr_args(p, 2, n), st);
+  }
   int k = 0;
   while (k < max_iter) {
     ++k;
@@ -296,9 +341,13 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
     run_F(p, nlo, N - nlo, p->U.p + nlo * nt, p->Fout.p + nlo * nt, st);
     if (timing) PS_CUDA(cudaEventRecord(p->ev[2], st));
     // slice k-1: U_k^k = F(U_{k-1}^{k-1}) exactly (its G bracket is zero)
-    copy_with_increment(nt, p->Fout.p + nlo * nt, p->U.p + k * nt, p->inc.p, p->flag.p, p->sstats.p + 2 * k, st);
+    copy_with_increment(nt, p->Fout.p + nlo * nt, p->U.p + k * nt, p->inc.p, p->flag.p, p->sstats.p + 2 * k,
+                        p->delta32 ? p->d32.p : nullptr, st);
     p->launches++;
-    for (int n = k; n < N; ++n) run_G(p, n, p->U.p + n * nt, corr_args(p, 1, n), st);
+    for (int n = k; n < N; ++n) {
+      if (p->delta32) run_G32(p, n, false, st);
+      else run_G(p, n, p->U.p + n * nt, corr_args(p, 1, n), st);
+    }
     if (timing) PS_CUDA(cudaEventRecord(p->ev[3], st));
     PS_CUDA(cudaMemcpyAsync(p->h_inc, p->inc.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaMemcpyAsync(p->h_flag, p->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -386,7 +435,7 @@ void coarse_step_into(ps_problem* p, int n, int q, const double* in, double* wor
     SourceArgs sa = source_for(p, P, t_end, 0);
     dd_rhs(p->g, 1, in, work, sa, st);
     const int spb = p->prm.dd_slices_per_block > 0 ? p->prm.dd_slices_per_block : 2;
-    for (int c = 0; c < M; ++c) dd_solve(p->g, 1, *P.dd, c, work, spb, st);
+    for (int c = 0; c < M; ++c) dd_solve(p->g, 1, *P.dd, c, work, spb, p->tmo.p, st);
     return;
   }
   for (int m = 0; m < M; ++m) {
@@ -399,7 +448,7 @@ void coarse_step_into(ps_problem* p, int n, int q, const double* in, double* wor
 extern "C" {
 
 const char* ps_last_error(void) { return g_last_error.c_str(); }
-int ps_version(void) { return 100; }
+int ps_version(void) { return 101; }
 
 int ps_grid_create(int dim, const int n[3], ps_grid** out) {
   return guarded([&] {
@@ -511,12 +560,21 @@ int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, doub
       PS_REQUIRE(p->op->src_t_len >= N * f_steps + 1, "src_t must cover the fine times 0..N*f_steps");
     cudaStream_t st = S(stream);
     const bool mixed = p->prm.precision == PS_PREC_MIXED;
+    PS_REQUIRE(p->prm.coarse == PS_COARSE_FP64 || p->prm.coarse == PS_COARSE_DELTA32, "unknown coarse mode");
+    p->delta32 = p->prm.coarse == PS_COARSE_DELTA32;
+    if (p->delta32 && (fine->kind != PS_SPLIT_DIM || coarse->kind != PS_SPLIT_DIM))
+      throw Error(PS_ERR_UNSUPPORTED, "the FP32 coarse increment form needs the dimensional splitting");
     build_prop(p.get(), p->F, fine, T / N / f_steps, f_steps, 1, mixed, st);
-    build_prop(p.get(), p->G, coarse, T / N / g_steps, g_steps, f_steps / g_steps, false, st);
+    build_prop(p.get(), p->G, coarse, T / N / g_steps, g_steps, f_steps / g_steps, p->delta32, st);
     const long long nt = p->g.nt;
     p->U.alloc((size_t)(N + 1) * nt);
     p->Fout.alloc((size_t)N * nt);
-    p->Gold.alloc((size_t)N * nt);
+    if (p->delta32) {
+      p->d32.alloc((size_t)nt);
+      p->g32.alloc((size_t)nt);
+    } else {
+      p->Gold.alloc((size_t)N * nt);
+    }
     p->gtmp.alloc((size_t)nt);
     p->inc.alloc(1);
     p->tmo.alloc(1);
@@ -541,7 +599,7 @@ int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, doub
       if (g3.dim == 2) g3.n[2] = 1;
       for (int m = 0; m < p->g.dim; ++m) {
         tile_plan(g3, p->S_pad, elem, m, p->F.tiles[m], W, p->prm.tile_positions,
-                  p->prm.tile_pipeline == 0 ? 0 : (p->prm.tile_pipeline == 1 ? 1 : 0), p->prm.tile_slots);
+                  p->prm.tile_pipeline == 0 ? 0 : (p->prm.tile_pipeline == 1 ? 1 : 0), p->prm.tile_slots, p->prm.tile_lines_per_thread);
         factor_lines(g3, *p->F.dim[m], mixed, st);
       }
       if (p->op->src.p) {
@@ -630,12 +688,13 @@ int ps_run_coarse_sequential(ps_problem* p, const double* u0_dev, double* U_out_
     PS_REQUIRE(p && u0_dev && U_out_dev, "null argument");
     cudaStream_t st = S(stream);
     const long long nt = p->g.nt;
+    tile_flag_reset(p, st);
     PS_CUDA(cudaMemcpyAsync(U_out_dev, u0_dev, sizeof(double) * nt, cudaMemcpyDeviceToDevice, st));
     for (int n = 0; n < p->N; ++n) {
       run_G(p, n, U_out_dev + n * nt, CorrArgs{}, st);
       PS_CUDA(cudaMemcpyAsync(U_out_dev + (n + 1) * nt, p->gtmp.p, sizeof(double) * nt, cudaMemcpyDeviceToDevice, st));
     }
-    PS_CUDA(cudaStreamSynchronize(st));
+    tile_flag_check(p, st);
   });
 }
 
@@ -646,7 +705,9 @@ int ps_substep_solve(ps_problem* p, int which, int m, double* x_dev, uintptr_t s
     Prop& P = which == 0 ? p->F : p->G;
     PS_REQUIRE(m >= 0 && m < P.sp->M, "substep out of range");
     if (P.sp->kind == PS_SPLIT_DD) {
-      dd_solve(p->g, 1, *P.dd, m, x_dev, 1, S(stream));
+      tile_flag_reset(p, S(stream));
+      dd_solve(p->g, 1, *P.dd, m, x_dev, 1, p->tmo.p, S(stream));
+      tile_flag_check(p, S(stream));
       return;
     }
     sweep_dim<double, double>(p->g, 1, *P.dim[m], P.f32, x_dev, x_dev, SourceArgs{}, CorrArgs{}, nullptr, S(stream));
@@ -661,6 +722,7 @@ int ps_propagate(ps_problem* p, int which, int nsteps, int t0, int tstride, doub
     if (p->op->src_t.p)
       PS_REQUIRE(t0 >= 0 && t0 + (long long)nsteps * tstride < p->op->src_t_len, "time index outside src_t");
     cudaStream_t st = S(stream);
+    tile_flag_reset(p, st);
     for (int q = 0; q < nsteps; ++q) {
       const int te = t0 + (q + 1) * tstride;
       if (!P.f32) {
@@ -672,6 +734,7 @@ int ps_propagate(ps_problem* p, int which, int nsteps, int t0, int tstride, doub
         }
       }
     }
+    tile_flag_check(p, st);
   });
 }
 
@@ -689,18 +752,20 @@ int ps_problem_stats(const ps_problem* p, ps_stats* out) {
 
 namespace {
 // Tile plans of the fine propagator for a schedule (slots per tile, positions, pipeline).
-void rebuild_tiles(ps_problem* p, int slots, int positions, int pipe) {
+void rebuild_tiles(ps_problem* p, int slots, int positions, int pipe, int vec) {
   if (p->F.sp->kind != PS_SPLIT_DIM) return;
   Geom g3 = p->g;
   if (g3.dim == 2) g3.n[2] = 1;
   const bool mixed = p->prm.precision == PS_PREC_MIXED;
   void* W = mixed ? static_cast<void*>(p->W.p) : static_cast<void*>(p->W64.p);
   TilePlan tmp[3];
-  for (int m = 0; m < p->g.dim; ++m) tile_plan(g3, p->S_pad, mixed ? 4 : 8, m, tmp[m], W, positions, pipe, slots);
+  for (int m = 0; m < p->g.dim; ++m)
+    tile_plan(g3, p->S_pad, mixed ? 4 : 8, m, tmp[m], W, positions, pipe, slots, vec);
   for (int m = 0; m < p->g.dim; ++m) p->F.tiles[m] = tmp[m];
   p->prm.tile_slots = slots;
   p->prm.tile_positions = positions;
   p->prm.tile_pipeline = pipe ? 1 : 2;
+  p->prm.tile_lines_per_thread = vec;
 }
 }  // namespace
 
@@ -712,9 +777,11 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
     cudaStream_t st = S(stream);
     const bool mixed = p->prm.precision == PS_PREC_MIXED;
     struct Cand {
-      int slots, positions, pipe;
+      int slots, positions, pipe, vec;
     };
-    const std::vector<Cand> cands = {{32, 1, 0}, {64, 1, 0}, {32, 2, 0}, {16, 1, 0}, {32, 1, 1}};
+    // slots per tile, line positions per tile, persistent double-buffered CTAs, lines per thread
+    const std::vector<Cand> cands = {{32, 2, 0, 2}, {32, 1, 0, 2}, {32, 1, 0, 1}, {32, 2, 0, 1}, {64, 1, 0, 2},
+                                     {16, 1, 0, 1}, {32, 1, 1, 2}, {32, 1, 1, 1}};
     tile_flag_reset(p, st);
     cudaEvent_t e0, e1;
     PS_CUDA(cudaEventCreate(&e0));
@@ -723,13 +790,14 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
     if (g3.dim == 2) g3.n[2] = 1;
     const int M = p->g.dim;
     float best = 1e30f;
-    Cand bestc{0, 0, 0};
+    Cand bestc{0, 0, 0, 0};
     const double per_cand_ms = std::max(1.0, (double)budget_ms / cands.size());
-    const int old_slots = p->prm.tile_slots, old_pos = p->prm.tile_positions, old_pipe = p->prm.tile_pipeline;
+    const int old_slots = p->prm.tile_slots, old_pos = p->prm.tile_positions, old_pipe = p->prm.tile_pipeline,
+              old_vec = p->prm.tile_lines_per_thread;
     try {
       for (const Cand& c : cands) {
         try {
-          rebuild_tiles(p, c.slots, c.positions, c.pipe);
+          rebuild_tiles(p, c.slots, c.positions, c.pipe, c.vec);
         } catch (const Error&) {
           continue;  // shape does not fit this grid / precision
         }
@@ -769,19 +837,21 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (bestc.slots == 0) {
-      rebuild_tiles(p, old_slots, old_pos, old_pipe == 1 ? 1 : 0);
+      rebuild_tiles(p, old_slots, old_pos, old_pipe == 1 ? 1 : 0, old_vec);
       return;
     }
-    rebuild_tiles(p, bestc.slots, bestc.positions, bestc.pipe);
+    rebuild_tiles(p, bestc.slots, bestc.positions, bestc.pipe, bestc.vec);
     tile_flag_check(p, st);
-    if (choice_out) *choice_out = bestc.slots * 100 + bestc.positions * 10 + bestc.pipe;
+    // choice code: lines per thread, slots, positions, pipeline as decimal digits vSSpq
+    if (choice_out) *choice_out = bestc.vec * 10000 + bestc.slots * 100 + bestc.positions * 10 + bestc.pipe;
   });
 }
 
 int ps_copy_schedule(const ps_problem* src, ps_problem* dst) {
   return guarded([&] {
     PS_REQUIRE(src && dst, "null argument");
-    rebuild_tiles(dst, src->prm.tile_slots, src->prm.tile_positions, src->prm.tile_pipeline == 1 ? 1 : 0);
+    rebuild_tiles(dst, src->prm.tile_slots, src->prm.tile_positions, src->prm.tile_pipeline == 1 ? 1 : 0,
+                  src->prm.tile_lines_per_thread);
   });
 }
 
@@ -799,7 +869,7 @@ int ps_problem_update_coefficients(ps_problem* p, const double* a_nodal_dev, uin
       const bool fine = P == &p->F;
       if (P->sp->kind == PS_SPLIT_DIM) {
         for (int m = 0; m < p->g.dim; ++m) {
-          factor_dim(p->g, m, op->a.p, op->c / p->g.dim, P->tau, *P->dim[m], fine && mixed, st);
+          factor_dim(p->g, m, op->a.p, op->c / p->g.dim, P->tau, *P->dim[m], fine ? mixed : p->delta32, st);
           if (fine) factor_lines(g3, *P->dim[m], mixed, st);
         }
       } else {
@@ -861,6 +931,7 @@ int ps_adjoint_vjp(ps_problem* p, const double* gN_dev, double tol, int max_iter
   return guarded([&] {
     PS_REQUIRE(p && gN_dev && grad_u0_dev, "null argument");
     PS_REQUIRE(p->have_forward, "ps_adjoint_vjp needs a preceding ps_run_parareal on this problem");
+    if (p->delta32) throw Error(PS_ERR_UNSUPPORTED, "the adjoint runs with the FP64 coarse propagator");
     if (grad_a_dev) {
       if (p->F.sp->kind != PS_SPLIT_DIM || p->G.sp->kind != PS_SPLIT_DIM)
         throw Error(PS_ERR_UNSUPPORTED, "the coefficient gradient is implemented for the dimensional splitting");
@@ -907,12 +978,13 @@ int ps_run_coarse_sequential_noalloc(ps_problem* p, const double* u0_dev, double
                                       std::to_string(PS_NOALLOC_MAX_UNKNOWNS));
     cudaStream_t st = S(stream);
     double* work = noalloc_work_ptr();
+    tile_flag_reset(p, st);
     PS_CUDA(cudaMemcpyAsync(U_out_dev, u0_dev, sizeof(double) * nt, cudaMemcpyDeviceToDevice, st));
     for (int n = 0; n < p->N; ++n) {
       for (int q = 0; q < p->G.steps; ++q) coarse_step_into(p, n, q, q == 0 ? U_out_dev + n * nt : work, work, st);
       PS_CUDA(cudaMemcpyAsync(U_out_dev + (n + 1) * nt, work, sizeof(double) * nt, cudaMemcpyDeviceToDevice, st));
     }
-    PS_CUDA(cudaStreamSynchronize(st));
+    tile_flag_check(p, st);
   });
 }
 

@@ -1,24 +1,29 @@
 // ps_dd.cu -- domain-decomposition splitting (Sec. 2.1): partition of unity over
-// overlapping boxes, banded subdomain factorisation and batched subdomain solves.
+// overlapping boxes, blocked subdomain factorisation and batched subdomain solves.
 //
 // Colour j's suboperator is L_j u = div(rho_j a grad u) - rho_j c u (Sec. 2.1).  With
 // rho_j evaluated at edge midpoints, (I - tau A_j) is the identity outside the boxes of
-// colour j and block diagonal over its boxes (Sec. 2.2: "q independent subsystems, one
-// for each connected component").  Every box block is SPD and banded (half-bandwidth =
-// the box's lead extent in its local ordering); it is factored once per step size as
-// L L^T and the substeps solve  L y = b,  L^T x = y  for all time slices of a launch.
+// colour j and block diagonal over its boxes (Sec. 2.2: one independent subsystem per
+// connected component).  Ordered line by line (the box's shorter extent w fastest, m lines),
+// a box block is SPD block tridiagonal: tridiagonal w x w blocks T_k on the diagonal and
+// diagonal couplings C_k = diag(c_k) between lines k-1 and k.  It is solved by block
+// elimination with explicit inverses of the Schur complements,
+//     S_0 = T_0,  S_k = T_k - C_k S_{k-1}^{-1} C_k,
+//     y_k = S_k^{-1} (b_k - C_k y_{k-1}),   x_k = y_k - S_k^{-1} C_{k+1} x_{k+1},
+// which is the same LU factorisation as the banded Cholesky of the oracle, grouped by lines:
+// the dependent chain of a solve is m block steps instead of m*w scalar ones, and each step
+// is a dense (w x w)(w x slices) product spread over a CTA.
 //
-// Both triangular solves run column by column: when the pivot row's value p_j is final,
-// the w rows below it receive  acc_r -= (L_{rj} / L_jj) p_j.  One warp owns one
-// (box, slice) system; its 32 lanes share the w updates of each column and the running
-// sums of the w+1 rows in flight live in a shared-memory ring.  The factors are stored
-// pre-divided by the pivot (column-major for L, row-major for L^T), so no multiply sits
-// on the critical path between two pivots.
+// Factors per box and line k, contiguous: S_k^{-1} (w x w, column-major; symmetric),
+// F_k = S_k^{-1} C_{k+1} (w x w, column-major), c_k (w); each padded to 16 bytes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <string>
+#include <vector>
 
+#include "ps_async.h"
 #include "ps_dd.h"
 
 namespace ps {
@@ -38,20 +43,6 @@ __host__ __device__ inline double phi1d(int b, int B, double w, double x) {
   const double left = (b == 0) ? 1.0 : 1.0 - ramp_down(x, (double)b / B, w);
   const double right = (b == B - 1) ? 1.0 : ramp_down(x, (double)(b + 1) / B, w);
   return left * right;
-}
-
-// Node (1-based interior indices) of box-local row r.
-__device__ __forceinline__ long long box_node(const DDBox& bx, int nx, int r) {
-  int slow = r / bx.lead, fast = r - slow * bx.lead;
-  int gx, gy;
-  if (bx.xfast) {
-    gx = bx.x0 + fast;
-    gy = bx.y0 + slow;
-  } else {
-    gx = bx.x0 + slow;
-    gy = bx.y0 + fast;
-  }
-  return (long long)(gy - 1) * nx + (gx - 1);
 }
 
 // Assembled band row r of (I - tau A_j) restricted to the box, entries (r, r - d),
@@ -103,151 +94,271 @@ __device__ __forceinline__ void store_row(double* row, const RowEntries& e, int 
   }
 }
 
+// Entries of the box block: line k, position i (0-based, w positions per line).
+__device__ __forceinline__ int box_row(const DDBox& bx, int k, int i) { return k * bx.lead + i; }
+
+// Node (0-based index into a slice) of line k, position i.
+__device__ __forceinline__ long long line_node(const DDBox& bx, int nx, int k, int i) {
+  const int gx = bx.xfast ? bx.x0 + i : bx.x0 + k;
+  const int gy = bx.xfast ? bx.y0 + k : bx.y0 + i;
+  return (long long)(gy - 1) * nx + (gx - 1);
+}
+
+__host__ __device__ inline long long dd_sq(int w) { return ((long long)w * w + 1) & ~1LL; }
+__host__ __device__ inline long long dd_vec(int w) { return (w + 1) & ~1; }
+__host__ __device__ inline long long dd_line_stride(int w) { return 2 * dd_sq(w) + dd_vec(w); }
+
+// The factorisation holds one w x w Schur complement and five w-vectors in shared memory, and
+// the solve runs one thread per line position (at most 192).
+constexpr int kMaxLead = 160;
+
 // ---------------------------------------------------------------------------------------
-// a1 (DD): banded Cholesky of one box per CTA, right-looking, with the w+1 rows in flight
-// in a shared-memory ring win[slot][d] = A(r, r - d), slot = r mod (w+1).  Writes
-//   Lc[j*(w+1) + 0] = 1/L_jj,  Lc[j*(w+1) + d] = L_{j+d, j} / L_jj   (column j of L)
-//   Lr[i*(w+1) + 0] = 1/L_ii,  Lr[i*(w+1) + d] = L_{i, i-d} / L_ii   (row i of L)
-// Sets *status = 1 if a pivot is not positive (the matrix is SPD, so only on bad input).
-__global__ void dd_factor_kernel(const DDBox* __restrict__ boxes, DDGeomArgs ga, double* __restrict__ fac,
-                                 int* status) {
+// a1 (DD): one CTA per box.  The Schur complement of the current line lives in shared
+// memory; it is inverted in place by Gauss-Jordan elimination without pivoting (SPD), its
+// inverse stored, and the next line's complement formed from it.  *status = 1 on a
+// non-positive pivot (the blocks are SPD, so only on bad input).
+// Shared memory: A (w x w, row-major), then the vectors rs, cp, cprev, dg, ld (w each).
+__global__ void __launch_bounds__(512) dd_factor_kernel(const DDBox* __restrict__ boxes, DDGeomArgs ga,
+                                                        double* __restrict__ fac, int* status) {
   const DDBox bx = boxes[blockIdx.x];
-  const int w = bx.lead, W = w + 1, n = bx.n;
-  extern __shared__ double win[];  // W*W ring + W column values
-  double* col = win + (size_t)W * W;
-  double* Lc = fac + bx.offset;
-  double* Lr = Lc + (size_t)n * W;
-  const int tid = threadIdx.x + threadIdx.y * blockDim.x, nthr = blockDim.x * blockDim.y;
-  // load rows 0..min(w, n-1)
-  for (int e = tid; e < W * W; e += nthr) win[e] = 0.0;
-  __syncthreads();
-  for (int r = tid; r < min(W, n); r += nthr) store_row(win + (size_t)(r % W) * W, assemble_row(bx, ga, r), w);
-  __syncthreads();
-  __shared__ double s_rinv;
-  for (int k = 0; k < n; ++k) {
-    double* rowk = win + (size_t)(k % W) * W;
-    if (tid == 0) {
-      const double piv = rowk[0];
-      if (!(piv > 0.0)) atomicExch(status, 1);
-      const double lkk = sqrt(piv > 0.0 ? piv : 1.0);
-      s_rinv = 1.0 / lkk;
-      rowk[0] = lkk;
+  const int w = bx.lead, m = bx.n / w;
+  extern __shared__ double sm[];
+  double* A = sm;
+  double* rs = A + w * w;  // pivot row / pivot
+  double* cp = rs + w;     // pivot column
+  double* cprev = cp + w;  // c_k: coupling of line k to line k - 1
+  double* dg = cprev + w;  // diagonal of T_k
+  double* ld = dg + w;     // sub-diagonal of T_k (entry (i, i-1))
+  __shared__ double s_inv;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ty * blockDim.x, nthr = blockDim.x * blockDim.y;
+  double* base = fac + bx.offset;
+  const long long ls = dd_line_stride(w), sq = dd_sq(w);
+  for (int e = tid; e < w; e += nthr) cprev[e] = 0.0;
+  for (int k = 0; k < m; ++k) {
+    double* Sinv = base + k * ls;
+    double* Fk = Sinv + sq;
+    double* ck = Sinv + 2 * sq;
+    for (int e = tid; e < w; e += nthr) {
+      const RowEntries re = assemble_row(bx, ga, box_row(bx, k, e));
+      dg[e] = re.diag;
+      ld[e] = re.lead;
+      ck[e] = cprev[e];
     }
     __syncthreads();
-    const double rinv = s_rinv;
-    const int tmax = min(w, n - 1 - k);
-    // column k: L_{k+t, k} = A(k+t, k) / L_kk
-    for (int t = 1 + tid; t <= tmax; t += nthr) {
-      double* rowi = win + (size_t)((k + t) % W) * W;
-      const double lik = rowi[t] * rinv;
-      rowi[t] = lik;
-      col[t] = lik;
-      Lc[(size_t)k * W + t] = lik * rinv;
-    }
-    if (tid == 0) Lc[(size_t)k * W] = rinv;
-    for (int t = tmax + 1 + tid; t <= w; t += nthr) Lc[(size_t)k * W + t] = 0.0;
+    // S_k = T_k - C_k S_{k-1}^{-1} C_k   (A holds S_{k-1}^{-1}; cprev = c_k)
+    for (int i = ty; i < w; i += blockDim.y)
+      for (int j = tx; j < w; j += blockDim.x) {
+        double t = (i == j) ? dg[i] : (j == i - 1 ? ld[i] : (i == j - 1 ? ld[j] : 0.0));
+        if (k > 0) t -= cprev[i] * A[i * w + j] * cprev[j];
+        A[i * w + j] = t;
+      }
     __syncthreads();
-    // trailing update of the rows in flight: A(i, j) -= L_ik L_jk, k < j <= i <= k + w
-    for (int ti = 1 + threadIdx.y; ti <= tmax; ti += blockDim.y) {
-      double* rowi = win + (size_t)((k + ti) % W) * W;
-      const double lik = col[ti];
-      for (int tj = 1 + threadIdx.x; tj <= ti; tj += blockDim.x) rowi[ti - tj] -= lik * col[tj];
-    }
-    __syncthreads();
-    // row k is final: L_{k, k-d} for d = 1..w, and the pivot
-    for (int d = tid; d <= w; d += nthr) {
-      if (d == 0) Lr[(size_t)k * W] = rinv;
-      else Lr[(size_t)k * W + d] = (k - d >= 0) ? rowk[d] * rinv : 0.0;
-    }
-    __syncthreads();
-    // the slot of row k takes row k + W
-    const int rn = k + W;
-    if (rn < n) {
-      for (int d = tid; d <= w; d += nthr) rowk[d] = 0.0;
+    for (int p = 0; p < w; ++p) {
+      for (int e = tid; e < w; e += nthr) {
+        rs[e] = A[p * w + e];
+        cp[e] = A[e * w + p];
+      }
       __syncthreads();
-      if (tid == 0) store_row(rowk, assemble_row(bx, ga, rn), w);
+      if (tid == 0) {
+        const double piv = rs[p];
+        if (!(piv > 0.0)) atomicExch(status, 1);
+        s_inv = 1.0 / (piv > 0.0 ? piv : 1.0);
+      }
+      __syncthreads();
+      const double inv = s_inv;
+      for (int e = tid; e < w; e += nthr) rs[e] *= inv;
+      __syncthreads();
+      for (int i = ty; i < w; i += blockDim.y) {
+        const double ci = cp[i];
+        for (int j = tx; j < w; j += blockDim.x) {
+          double v;
+          if (i == p) v = (j == p) ? inv : rs[j];
+          else if (j == p) v = -ci * inv;
+          else v = fma(-ci, rs[j], A[i * w + j]);
+          A[i * w + j] = v;
+        }
+      }
+      __syncthreads();
     }
+    // S_k^{-1}, column-major
+    for (int i = ty; i < w; i += blockDim.y)
+      for (int j = tx; j < w; j += blockDim.x) Sinv[(long long)j * w + i] = A[i * w + j];
+    // c_{k+1} and F_k = S_k^{-1} C_{k+1}, column-major
+    for (int e = tid; e < w; e += nthr) cprev[e] = (k + 1 < m) ? assemble_row(bx, ga, box_row(bx, k + 1, e)).other : 0.0;
+    __syncthreads();
+    for (int i = ty; i < w; i += blockDim.y)
+      for (int j = tx; j < w; j += blockDim.x) Fk[(long long)j * w + i] = A[i * w + j] * cprev[j];
     __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------------------
-// a3 (DD): one warp solves one (box, slice) system in place in the state array:
-// forward L y = b with the column-major factor, then backward L^T x = y with the
-// row-major one.  The right-hand sides and factor columns are fetched kPre rows ahead.
-constexpr int kRing = 256;  // running-sum ring, a power of two > w
-constexpr int kPre = 4;     // prefetch distance in rows
-constexpr int kPerLane = 8; // factor entries per lane per row: w + 1 <= 32 * kPerLane
+// a3 (DD): block forward and backward substitution of one box for S slices, in place in the
+// state array.  One thread per position of a line (w <= blockDim.x); each thread keeps two
+// partial sums per slice (2S independent FMA chains).  The m matrices S_k^{-1} of the forward
+// pass and the m - 1 matrices F_k of the backward pass stream through shared memory in
+// chunks of kChunk columns: two buffers, bulk copies completing on one mbarrier each, the
+// copy of chunk g + 2 issued as soon as chunk g has been consumed, so the stream runs ahead
+// across block steps.  Waits are bounded: on a timeout the CTA sets *err = 1, waits (again
+// bounded) for its copies in flight and returns.
+constexpr int kChunk = 32;
 
-template <bool BACKWARD>
-__device__ __forceinline__ void dd_triangular(const DDBox& bx, int nx, const double* __restrict__ F,
-                                              double* __restrict__ x, double* ring, int lane) {
-  const int w = bx.lead, W = w + 1, n = bx.n;
-  for (int e = lane; e < kRing; e += 32) ring[e] = 0.0;
-  __syncwarp();
-  double cf[kPre][kPerLane];
-  double rhs[kPre];
-#pragma unroll
-  for (int u = 0; u < kPre; ++u) {
-    const int j = BACKWARD ? n - 1 - u : u;
-    const bool ok = BACKWARD ? j >= 0 : j < n;
-    rhs[u] = ok ? x[box_node(bx, nx, j)] : 0.0;
-#pragma unroll
-    for (int t = 0; t < kPerLane; ++t) {
-      const int d = lane + 32 * t;
-      cf[u][t] = (ok && d <= w) ? F[(size_t)j * W + d] : 0.0;
-    }
-  }
-  for (int j0 = 0; j0 < n; j0 += kPre) {
-#pragma unroll
-    for (int u = 0; u < kPre; ++u) {
-      const int step = j0 + u;
-      if (step < n) {
-        const int j = BACKWARD ? n - 1 - step : step;
-        const int slot = j & (kRing - 1);
-        const double p = ring[slot] + rhs[u];  // final value of row j
-        __syncwarp();
-        if (lane == 0) {
-          ring[slot] = 0.0;
-          x[box_node(bx, nx, j)] = p * cf[u][0];
-        }
-#pragma unroll
-        for (int t = 0; t < kPerLane; ++t) {
-          const int d = lane + 32 * t;
-          if (d >= 1 && d <= w) {
-            const int r = BACKWARD ? j - d : j + d;
-            if (BACKWARD ? r >= 0 : r < n) ring[r & (kRing - 1)] -= cf[u][t] * p;
-          }
-        }
-        // prefetch row j -/+ kPre
-        const int sn = step + kPre;
-        const int jn = BACKWARD ? n - 1 - sn : sn;
-        const bool ok = sn < n;
-        rhs[u] = ok ? x[box_node(bx, nx, jn)] : 0.0;
-#pragma unroll
-        for (int t = 0; t < kPerLane; ++t) {
-          const int d = lane + 32 * t;
-          cf[u][t] = (ok && d <= w) ? F[(size_t)jn * W + d] : 0.0;
-        }
-        __syncwarp();
+struct DDChunk {
+  const double* src;
+  int j0, cols;  // first column, columns used
+  uint32_t bytes;
+};
+
+// Chunk g of the stream: forward matrices k = 0..m-1, then backward ones k = m-2..0.
+__device__ __forceinline__ DDChunk dd_chunk(const double* base, long long ls, long long sq, int w, int m, int nch,
+                                            long long g) {
+  const long long mat = g / nch;
+  const int c = (int)(g - mat * nch);
+  const double* M = mat < m ? base + mat * ls : base + (long long)(2 * m - 2 - mat) * ls + sq;
+  DDChunk ch;
+  ch.j0 = c * kChunk;
+  ch.cols = min(kChunk, w - ch.j0);
+  // an even column count keeps the size a multiple of 16 bytes when w is odd; the extra column
+  // lies inside the line's record (padding, F_k or c_k) and is not used
+  const int cols_even = (ch.cols + 1) & ~1;
+  ch.src = M + (long long)ch.j0 * w;
+  ch.bytes = (uint32_t)((long long)cols_even * w * sizeof(double));
+  return ch;
+}
+
+template <int S>
+__global__ void __launch_bounds__(192) dd_solve_kernel(const DDBox* __restrict__ boxes, int nx, long long nt,
+                                                       const double* __restrict__ fac, double* state, int nslices,
+                                                       int ld_buf, int* err) {
+  const DDBox bx = boxes[blockIdx.x];
+  const int w = bx.lead, m = bx.n / w;
+  const int s0 = blockIdx.y * S;
+  const int ns = min(S, nslices - s0);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // two barriers, 128 bytes reserved
+  double* buf0 = reinterpret_cast<double*>(smem_raw + 128);
+  double* bufs[2] = {buf0, buf0 + (size_t)kChunk * ld_buf};
+  double* t = buf0 + 2 * (size_t)kChunk * ld_buf;  // S x w
+  double* v = t + S * w;                           // S x w
+  __shared__ int s_ok;
+  const int r = threadIdx.x;
+  const bool act = r < w;
+  const double* base = fac + bx.offset;
+  const long long ls = dd_line_stride(w), sq = dd_sq(w);
+  const int nch = (w + kChunk - 1) / kChunk;
+  const long long total = (long long)(2 * m - 1) * nch;
+  if (r == 0) {
+    s_ok = *reinterpret_cast<volatile int*>(err) ? 0 : 1;
+    if (s_ok) {
+      mbar_init(&bar[0], 1);
+      mbar_init(&bar[1], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      for (long long g = 0; g < 2 && g < total; ++g) {
+        const DDChunk ch = dd_chunk(base, ls, sq, w, m, nch, g);
+        mbar_expect_tx(&bar[g], ch.bytes);
+        bulk_load(bufs[g], ch.src, ch.bytes, &bar[g]);
       }
     }
   }
-  __syncwarp();
-}
-
-__global__ void dd_solve_kernel(const DDBox* __restrict__ boxes, int nx, long long nt, const double* __restrict__ fac,
-                                double* state, int nslices, int slices_per_block) {
-  __shared__ double rings[8][kRing];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const DDBox bx = boxes[blockIdx.x];
-  const int sl = blockIdx.y * slices_per_block + warp;
-  if (warp >= slices_per_block || sl >= nslices) return;
-  double* x = state + (long long)sl * nt;
-  const double* Lc = fac + bx.offset;
-  const double* Lr = Lc + (size_t)bx.n * (bx.lead + 1);
-  dd_triangular<false>(bx, nx, Lc, x, rings[warp], lane);
-  dd_triangular<true>(bx, nx, Lr, x, rings[warp], lane);
+  __syncthreads();
+  if (!s_ok) return;
+  double* st[S];
+#pragma unroll
+  for (int q = 0; q < S; ++q) st[q] = state + (long long)(s0 + (q < ns ? q : 0)) * nt;
+  long long g = 0;  // next chunk of the stream
+  // consumes the nch chunks of one matrix: acc += M t (sign +1) or acc -= M t (sign -1);
+  // returns false (uniformly) when a copy did not arrive in time
+  auto matvec = [&](const double* vec, double sign, double* a0, double* a1) -> bool {
+    for (int c = 0; c < nch; ++c, ++g) {
+      const int b = (int)(g & 1);
+      if (r == 0) s_ok = mbar_wait(&bar[b], (uint32_t)((g >> 1) & 1)) ? 1 : 0;
+      __syncthreads();
+      if (!s_ok) return false;
+      const double* M = bufs[b];
+      const int j0 = c * kChunk, cols = min(kChunk, w - j0);
+      if (act) {
+        int jj = 0;
+#pragma unroll 4
+        for (; jj + 1 < cols; jj += 2) {
+          const double d0 = sign * M[(size_t)jj * w + r], d1 = sign * M[(size_t)(jj + 1) * w + r];
+#pragma unroll
+          for (int q = 0; q < S; ++q) {
+            a0[q] = fma(d0, vec[q * w + j0 + jj], a0[q]);
+            a1[q] = fma(d1, vec[q * w + j0 + jj + 1], a1[q]);
+          }
+        }
+        if (jj < cols) {
+          const double d0 = sign * M[(size_t)jj * w + r];
+#pragma unroll
+          for (int q = 0; q < S; ++q) a0[q] = fma(d0, vec[q * w + j0 + jj], a0[q]);
+        }
+      }
+      __syncthreads();  // buffer b consumed
+      if (r == 0 && g + 2 < total) {
+        fence_async_smem();
+        const DDChunk ch = dd_chunk(base, ls, sq, w, m, nch, g + 2);
+        mbar_expect_tx(&bar[b], ch.bytes);
+        bulk_load(bufs[b], ch.src, ch.bytes, &bar[b]);
+      }
+    }
+    return true;
+  };
+  bool ok = true;
+  // forward: y_k = S_k^{-1} (b_k - C_k y_{k-1})
+  for (int k = 0; k < m && ok; ++k) {
+    const long long node = act ? line_node(bx, nx, k, r) : 0;
+    if (act) {
+      const double c = base[k * ls + 2 * sq + r];
+#pragma unroll
+      for (int q = 0; q < S; ++q)
+        if (q < ns) {
+          // explicit FMA: the same rounding in every instance of the kernel (any S), so the
+          // solve of a slice does not depend on how many slices share its CTA
+          const double b = st[q][node];
+          t[q * w + r] = k > 0 ? fma(-c, v[q * w + r], b) : b;
+        }
+    }
+    double a0[S], a1[S];
+#pragma unroll
+    for (int q = 0; q < S; ++q) a0[q] = a1[q] = 0.0;
+    ok = matvec(t, 1.0, a0, a1);  // starts with a barrier: t is complete
+    if (ok && act) {
+      // v[., r] is read only by this thread in the next right-hand side
+#pragma unroll
+      for (int q = 0; q < S; ++q)
+        if (q < ns) {
+          const double y = a0[q] + a1[q];
+          v[q * w + r] = y;
+          st[q][node] = y;
+        }
+    }
+  }
+  // backward: x_{m-1} = y_{m-1} (in v and in the state); x_k = y_k - F_k x_{k+1}
+  for (int k = m - 2; k >= 0 && ok; --k) {
+    const long long node = act ? line_node(bx, nx, k, r) : 0;
+    double a0[S], a1[S];
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      a0[q] = (act && q < ns) ? st[q][node] : 0.0;
+      a1[q] = 0.0;
+    }
+    __syncthreads();  // v holds x_{k+1} of every position
+    ok = matvec(v, -1.0, a0, a1);
+    if (ok && act) {
+#pragma unroll
+      for (int q = 0; q < S; ++q)
+        if (q < ns) {
+          const double x = a0[q] + a1[q];
+          v[q * w + r] = x;
+          st[q][node] = x;
+        }
+    }
+  }
+  if (!ok && r == 0) {
+    atomicExch(err, 1);
+    // the copies still in flight land in this CTA's shared memory: wait for them (bounded)
+    for (long long h = g; h < g + 2 && h < total; ++h) mbar_wait(&bar[h & 1], (uint32_t)((h >> 1) & 1));
+  }
 }
 
 // out = in + tau * src * src_t (all nodes, nslices states); out may alias in.
@@ -340,9 +451,11 @@ void dd_plan(const Geom& g, const ps_dd_params& dd, DDPlan& plan) {
       b.xfast = wx <= wy ? 1 : 0;
       b.lead = b.xfast ? wx : wy;
       b.n = wx * wy;
-      PS_REQUIRE(b.lead + 1 <= 32 * 8, "DD box too wide (lead extent must be < 256)");
+      if (b.lead > kMaxLead)
+        throw Error(PS_ERR_UNSUPPORTED, "DD box too wide: its shorter extent must be at most " +
+                                            std::to_string(kMaxLead) + " nodes (use more boxes)");
       b.offset = off;
-      off += 2LL * b.n * (b.lead + 1);
+      off += (long long)(b.n / b.lead) * dd_line_stride(b.lead);
       plan.colours[(bxi % 2) + ncx * (by % 2)].push_back(b);
     }
   plan.fac_len = off;
@@ -353,7 +466,7 @@ void dd_plan(const Geom& g, const ps_dd_params& dd, DDPlan& plan) {
     for (auto& b : plan.colours[c]) {
       plan.max_lead = std::max(plan.max_lead, b.lead);
       plan.nodes[c] += b.n;
-      plan.fac_entries[c] += 2.0 * b.n * (b.lead + 1);
+      plan.fac_entries[c] += (double)(b.n / b.lead) * (2.0 * b.lead * b.lead + b.lead);
     }
 }
 
@@ -374,22 +487,27 @@ void dd_factor(const Geom& g, const ps_dd_params& dd, const double* a_nodal, dou
   ga.Bx = dd.boxes[0];
   ga.By = dd.boxes[1];
   ga.overlap = dd.overlap;
-  const int W = f.plan.max_lead + 1;
-  const size_t smem = ((size_t)W * W + W) * sizeof(double);
+  const int w = f.plan.max_lead;
+  const size_t smem = ((size_t)w * w + 5 * (size_t)w) * sizeof(double);
   int dev = 0, maxsm = 0;
   PS_CUDA(cudaGetDevice(&dev));
   PS_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  // the kernel also holds one static double
   if ((int)smem + 64 > maxsm) throw Error(PS_ERR_UNSUPPORTED, "DD box too wide for the shared-memory factorisation");
   PS_CUDA(cudaFuncSetAttribute(dd_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  std::vector<DDBox> all;
   for (int c = 0; c < f.plan.M; ++c) {
     auto& boxes = f.plan.colours[c];
     f.dev_boxes[c].alloc(boxes.size());
     if (boxes.empty()) continue;
     PS_CUDA(cudaMemcpyAsync(f.dev_boxes[c].p, boxes.data(), sizeof(DDBox) * boxes.size(), cudaMemcpyHostToDevice,
                             st));
-    dd_factor_kernel<<<(unsigned)boxes.size(), dim3(32, 16), smem, st>>>(f.dev_boxes[c].p, ga, f.fac.p,
-                                                                          f.status.p);
+    all.insert(all.end(), boxes.begin(), boxes.end());
+  }
+  if (!all.empty()) {
+    // every box of every colour in one launch: each CTA runs its box's m dense inversions
+    f.dev_all.alloc(all.size());
+    PS_CUDA(cudaMemcpyAsync(f.dev_all.p, all.data(), sizeof(DDBox) * all.size(), cudaMemcpyHostToDevice, st));
+    dd_factor_kernel<<<(unsigned)all.size(), dim3(32, 16), smem, st>>>(f.dev_all.p, ga, f.fac.p, f.status.p);
     PS_CUDA(cudaGetLastError());
   }
   int h = 0;
@@ -399,13 +517,22 @@ void dd_factor(const Geom& g, const ps_dd_params& dd, const double* a_nodal, dou
 }
 
 void dd_solve(const Geom& g, int nslices, const DDFactors& f, int colour, double* state, int slices_per_block,
-              cudaStream_t st) {
+              int* err, cudaStream_t st) {
   const auto& boxes = f.plan.colours[colour];
   if (boxes.empty()) return;
-  slices_per_block = std::max(1, std::min(8, slices_per_block));
-  dim3 grid((unsigned)boxes.size(), (unsigned)((nslices + slices_per_block - 1) / slices_per_block));
-  dd_solve_kernel<<<grid, 32 * slices_per_block, 0, st>>>(f.dev_boxes[colour].p, g.n[0], g.nt, f.fac.p, state,
-                                                         nslices, slices_per_block);
+  // slices per CTA: each streamed factor entry serves S slices; fewer CTAs as S grows
+  const int S = nslices == 1 ? 1 : (slices_per_block >= 4 ? 4 : (slices_per_block == 1 ? 1 : 2));
+  const int ld = f.plan.max_lead;
+  const int threads = (ld + 31) / 32 * 32;
+  const size_t smem = 128 + (2 * (size_t)kChunk * ld + 2 * (size_t)S * ld) * sizeof(double);
+  dim3 grid((unsigned)boxes.size(), (unsigned)((nslices + S - 1) / S));
+  auto launch = [&](auto kern) {
+    PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, threads, smem, st>>>(f.dev_boxes[colour].p, g.n[0], g.nt, f.fac.p, state, nslices, ld, err);
+  };
+  if (S == 1) launch(dd_solve_kernel<1>);
+  else if (S == 2) launch(dd_solve_kernel<2>);
+  else launch(dd_solve_kernel<4>);
   PS_CUDA(cudaGetLastError());
 }
 

@@ -16,7 +16,7 @@ struct DDBox {
   int lead;           // half-bandwidth
   int n;              // nodes in the box
   int pad;
-  long long offset;   // of the box's factors in DDFactors::fac (2 * n * (lead + 1) doubles)
+  long long offset;   // of the box's factors in DDFactors::fac (per line: S^{-1}, F, c; see ps_dd.cu)
 };
 
 struct DDGeomArgs {
@@ -38,7 +38,8 @@ struct DDFactors {
   double tau = 0.0;
   DevBuf<double> fac;
   DevBuf<int> status;
-  std::vector<DevBuf<DDBox>> dev_boxes;
+  std::vector<DevBuf<DDBox>> dev_boxes;  // per colour
+  DevBuf<DDBox> dev_all;                 // every box (factorisation launch)
   DDFactors() = default;
   DDFactors(const DDFactors&) = delete;
 };
@@ -46,8 +47,11 @@ struct DDFactors {
 void dd_plan(const Geom& g, const ps_dd_params& dd, DDPlan& plan);
 void dd_factor(const Geom& g, const ps_dd_params& dd, const double* a_nodal, double c, double tau, DDFactors& f,
                cudaStream_t st);
+// Colour `colour`'s substep on nslices consecutive states, in place.  err: device flag set to
+// 1 when a bounded wait for a streamed factor chunk ran out (the launch is then abandoned);
+// a launch does nothing while the flag is set.
 void dd_solve(const Geom& g, int nslices, const DDFactors& f, int colour, double* state, int slices_per_block,
-              cudaStream_t st);
+              int* err, cudaStream_t st);
 void dd_rhs(const Geom& g, int nslices, const double* in, double* out, const SourceArgs& sa, cudaStream_t st);
 void dd_correct(const Geom& g, const double* gstate, const CorrArgs& ca, cudaStream_t st);
 

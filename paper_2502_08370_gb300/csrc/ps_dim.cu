@@ -86,20 +86,20 @@ __device__ __forceinline__ void sweep_x_body(long long blk, Tc* sm, const Tin* i
                                              const Tc* __restrict__ fr, const SourceArgs& sa) {
   const long long row0 = blk * R;
   const int nrows = (int)min((long long)R, rows - row0);
-  const long long g0 = row0 * nx;
-  const int total = nrows * nx;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    int rr = e / nx;
-    int cc = e - rr * nx;
-    Tc v = (Tc)in[g0 + e];
+  // one warp per row, lanes along the row: coalesced, and no per-element index division
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int rr = warp; rr < nrows; rr += nwarps) {
+    const long long row = row0 + rr;
+    const Tin* grow = in + row * nx;
+    Tc* srow = sm + rr * ld;
     if (SRC) {
-      long long row = row0 + rr;
-      long long sl = row / rows_per_slice;
-      long long ris = row - sl * rows_per_slice;
-      double ft = sa.src_t ? sa.src_t[sa.t0 + sl * sa.tstride] : 1.0;
-      v = v + to<Tc>(sa.tau * sa.src[ris * nx + cc] * ft);
+      const long long sl = row / rows_per_slice;
+      const double* s = sa.src + (row - sl * rows_per_slice) * nx;
+      const double c = sa.tau * (sa.src_t ? sa.src_t[sa.t0 + sl * sa.tstride] : 1.0);
+      for (int cc = lane; cc < nx; cc += 32) srow[cc] = (Tc)grow[cc] + to<Tc>(c * s[cc]);
+    } else {
+      for (int cc = lane; cc < nx; cc += 32) srow[cc] = (Tc)grow[cc];
     }
-    sm[rr * ld + cc] = v;
   }
   __syncthreads();
   if (threadIdx.x < nrows) {
@@ -109,8 +109,11 @@ __device__ __forceinline__ void sweep_x_body(long long blk, Tc* sm, const Tin* i
     const Tc* L = fl + (VAR ? ris : 0);
     const Tc* Rr = fr + (VAR ? ris : 0);
     const long long fs = VAR ? rows_per_slice : 1;
-    // chunks of K elements: the shared-memory and factor loads of a chunk issue together
+    // chunks of K elements: the shared-memory and factor loads of a chunk issue together, so
+    // one factor-load latency is paid per chunk (the arithmetic order does not depend on K;
+    // 16-node chunks measured slower here: they cost occupancy)
     constexpr int K = 8;
+    constexpr int KB = 8;
     Tc y = x[0];
     for (int i0 = 1; i0 < nx; i0 += K) {
       Tc b[K], l[K];
@@ -129,17 +132,17 @@ __device__ __forceinline__ void sweep_x_body(long long blk, Tc* sm, const Tin* i
       }
     }
     Tc xn = y;
-    for (int i0 = nx - 1; i0 >= 0; i0 -= K) {
-      Tc yy[K], r[K], l[K];
+    for (int i0 = nx - 1; i0 >= 0; i0 -= KB) {
+      Tc yy[KB], r[KB], l[KB];
 #pragma unroll
-      for (int u = 0; u < K; ++u) {
+      for (int u = 0; u < KB; ++u) {
         const int i = i0 - u;
         yy[u] = i >= 0 ? x[i] : Tc(0);
         r[u] = i >= 0 ? Rr[i * fs] : Tc(0);
         l[u] = (i >= 0 && i + 1 < nx) ? L[(i + 1) * fs] : Tc(0);
       }
 #pragma unroll
-      for (int u = 0; u < K; ++u) {
+      for (int u = 0; u < KB; ++u) {
         const int i = i0 - u;
         if (i >= 0) {
           xn = (i == nx - 1) ? r[u] * yy[u] : r[u] * yy[u] - l[u] * xn;
@@ -149,10 +152,10 @@ __device__ __forceinline__ void sweep_x_body(long long blk, Tc* sm, const Tin* i
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    int rr = e / nx;
-    int cc = e - rr * nx;
-    out[g0 + e] = (Tout)sm[rr * ld + cc];
+  for (int rr = warp; rr < nrows; rr += nwarps) {
+    Tout* grow = out + (row0 + rr) * nx;
+    const Tc* srow = sm + rr * ld;
+    for (int cc = lane; cc < nx; cc += 32) grow[cc] = (Tout)srow[cc];
   }
 }
 
@@ -171,6 +174,14 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, doub
   atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }
 
+// |v| as the bit pattern of a nonnegative double.  Maxima of such patterns are taken with
+// 64-bit integer instructions: they order like the values, and GB300's FP64 pipe, which
+// the line recurrences already saturate, is left to the recurrences.
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;  // |v| bits >= this: inf or NaN
+
 // ---------------------------------------------------------------------------------------
 // a3/a4: y- or z-direction substep, one thread per line; consecutive threads take
 // consecutive x so every access of a warp is one coalesced row segment.  The forward
@@ -185,7 +196,7 @@ __device__ __forceinline__ void sweep_strided_body(long long blk, const Tin* in,
                                                    const Tc* __restrict__ fr, const SourceArgs& sa,
                                                    const CorrArgs& ca) {
   const long long L = blk * blockDim.x + threadIdx.x;
-  double my_inc = 0.0, my_norm = 0.0;
+  unsigned long long my_inc = 0, my_norm = 0;  // bit patterns of nonnegative doubles
   bool bad = false;
   if (L < lines) {
     const long long outer = L / S;
@@ -197,7 +208,9 @@ __device__ __forceinline__ void sweep_strided_body(long long blk, const Tin* in,
     const long long fs = VAR ? S : 1;
     double ft = 0.0;
     if (SRC) ft = sa.tau * (sa.src_t ? sa.src_t[sa.t0 + sl * sa.tstride] : 1.0);
-    // forward recurrence; the loads of each chunk of K elements are issued together
+    // forward recurrence; the loads of each chunk of K elements are issued together (one
+    // memory latency per chunk; the arithmetic order does not depend on K).  Wider chunks
+    // cost registers here: every element carries its own 64-bit address.
     constexpr int K = 8;
     Tc y = (Tc)in[base];
     if (SRC) y = y + to<Tc>(ft * sa.src[pos]);
@@ -232,13 +245,11 @@ __device__ __forceinline__ void sweep_strided_body(long long blk, const Tin* in,
         yy[u] = ok ? (Tc)tmp[base + i * S] : Tc(0);
         r[u] = ok ? Rf[i * fs] : Tc(0);
         l[u] = (ok && i + 1 < nm) ? Lf[(i + 1) * fs] : Tc(0);
-        if (EPI != 0) {
+        if (EPI == 1 || EPI == 3) {
           const long long si = pos + (long long)(ok ? i : 0) * S;
-          go[u] = ok ? ca.Gold[si] : 0.0;
-          if (EPI == 1) {
-            fo[u] = ok ? ca.Fout[si] : 0.0;
-            uo[u] = ok ? ca.U_next[si] : 0.0;
-          }
+          if (EPI == 1) go[u] = ok ? ca.Gold[si] : 0.0;
+          fo[u] = ok ? ca.Fout[si] : 0.0;
+          uo[u] = ok ? ca.U_next[si] : 0.0;
         }
       }
 #pragma unroll
@@ -254,15 +265,25 @@ __device__ __forceinline__ void sweep_strided_body(long long blk, const Tin* in,
             const double g = (double)xn;
             if (EPI == 1) {
               const double unew = fo[u] + (g - go[u]);
-              const double d = fabs(unew - uo[u]);
-              if (!isfinite(unew)) bad = true;
-              my_inc = fmax(my_inc, d);
-              my_norm = fmax(my_norm, fabs(unew));
+              const unsigned long long an = abs_bits(unew);
+              bad |= an >= kInfBits;
+              my_inc = max(my_inc, abs_bits(unew - uo[u]));
+              my_norm = max(my_norm, an);
               ca.Gold[si] = g;
               ca.U_next[si] = unew;
+            } else if (EPI == 3) {
+              // G is affine, so G(U^k) - G(U^{k-1}) is its linear part applied to the increment
+              const double unew = fo[u] + g;
+              const double d = unew - uo[u];
+              const unsigned long long an = abs_bits(unew);
+              bad |= an >= kInfBits;
+              my_inc = max(my_inc, abs_bits(d));
+              my_norm = max(my_norm, an);
+              ca.U_next[si] = unew;
+              ca.dnext[si] = (float)d;
             } else {
-              if (!isfinite(g)) bad = true;
-              ca.Gold[si] = g;
+              bad |= abs_bits(g) >= kInfBits;
+              if (ca.Gold) ca.Gold[si] = g;
               ca.U_next[si] = g;
             }
           }
@@ -270,15 +291,15 @@ __device__ __forceinline__ void sweep_strided_body(long long blk, const Tin* in,
       }
     }
   }
-  if (EPI == 1) {
+  if (EPI == 1 || EPI == 3) {
     for (int o = 16; o > 0; o >>= 1) {
-      my_inc = fmax(my_inc, __shfl_xor_sync(0xffffffffu, my_inc, o));
-      my_norm = fmax(my_norm, __shfl_xor_sync(0xffffffffu, my_norm, o));
+      my_inc = max(my_inc, __shfl_xor_sync(0xffffffffu, my_inc, o));
+      my_norm = max(my_norm, __shfl_xor_sync(0xffffffffu, my_norm, o));
     }
-    if ((threadIdx.x & 31) == 0 && my_inc > 0.0) atomic_max_nonneg(ca.inc, my_inc);
+    if ((threadIdx.x & 31) == 0 && my_inc > 0) atomicMax(ca.inc, my_inc);
     if ((threadIdx.x & 31) == 0 && ca.slice_stats) {
-      if (my_inc > 0.0) atomic_max_nonneg(ca.slice_stats, my_inc);
-      if (my_norm > 0.0) atomic_max_nonneg(ca.slice_stats + 1, my_norm);
+      if (my_inc > 0) atomicMax(ca.slice_stats, my_inc);
+      if (my_norm > 0) atomicMax(ca.slice_stats + 1, my_norm);
     }
   }
   if (EPI != 0) {
@@ -375,16 +396,19 @@ __global__ void copy_inc_grouped_kernel(const CoarseJob* __restrict__ jobs, cons
 }
 
 __global__ void copy_inc_kernel(long long n, const double* __restrict__ src, double* __restrict__ dst,
-                                unsigned long long* inc, int* nonfinite, unsigned long long* slice_stats) {
+                                unsigned long long* inc, int* nonfinite, unsigned long long* slice_stats,
+                                float* __restrict__ dout) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double my = 0.0, nrm = 0.0;
   bool bad = false;
   for (; i < n; i += (long long)gridDim.x * blockDim.x) {
     double v = src[i];
-    my = fmax(my, fabs(v - dst[i]));
+    const double d = v - dst[i];
+    my = fmax(my, fabs(d));
     nrm = fmax(nrm, fabs(v));
     if (!isfinite(v)) bad = true;
     dst[i] = v;
+    if (dout) dout[i] = (float)d;
   }
   for (int o = 16; o > 0; o >>= 1) {
     my = fmax(my, __shfl_xor_sync(0xffffffffu, my, o));
@@ -464,8 +488,19 @@ void dispatch(const Geom& g, int nslices, const LineFactors& f, const Tc* fl, co
     if (var) { if (src) PS_STRIDED(true, true, 0); else PS_STRIDED(true, false, 0); }
     else { if (src) PS_STRIDED(false, true, 0); else PS_STRIDED(false, false, 0); }
   } else if (ca.mode == 1) {
-    if (var) { if (src) PS_STRIDED(true, true, 1); else PS_STRIDED(true, false, 1); }
-    else { if (src) PS_STRIDED(false, true, 1); else PS_STRIDED(false, false, 1); }
+    if constexpr (sizeof(Tc) == 8) {
+      if (var) { if (src) PS_STRIDED(true, true, 1); else PS_STRIDED(true, false, 1); }
+      else { if (src) PS_STRIDED(false, true, 1); else PS_STRIDED(false, false, 1); }
+    } else {
+      throw Error(PS_ERR_INVALID, "the standard correction runs with FP64 recurrences");
+    }
+  } else if (ca.mode == 3) {
+    if constexpr (sizeof(Tc) == 4 && sizeof(Tout) == 4) {
+      PS_REQUIRE(ca.dnext && ca.Fout && ca.U_next, "increment-form correction needs Fout, U_next and dnext");
+      if (var) PS_STRIDED(true, false, 3); else PS_STRIDED(false, false, 3);
+    } else {
+      throw Error(PS_ERR_INVALID, "the increment-form correction runs with FP32 recurrences");
+    }
   } else {
     if (var) { if (src) PS_STRIDED(true, true, 2); else PS_STRIDED(true, false, 2); }
     else { if (src) PS_STRIDED(false, true, 2); else PS_STRIDED(false, false, 2); }
@@ -500,7 +535,7 @@ void sweep_dim(const Geom& g, int nslices, const LineFactors& f, bool fp32, cons
                const SourceArgs& sa, const CorrArgs& ca, double* tmp, cudaStream_t st) {
   if (fp32) {
     PS_REQUIRE(f.l32.p != nullptr, "FP32 factors missing");
-    PS_REQUIRE(ca.mode == 0 && tmp == nullptr, "the FP32 sweeps carry no correction");
+    PS_REQUIRE(tmp == nullptr && ca.mode != 1, "FP32 sweeps carry only the initial or increment-form epilogue");
     dispatch<Tin, Tout, float>(g, nslices, f, f.l32.p, f.r32.p, in, out, sa, ca, nullptr, st);
   } else {
     if constexpr (sizeof(Tout) == 8) {
@@ -546,9 +581,9 @@ void copy_inc_grouped(const CoarseJob* jobs, const WorkSeg* segs, const int* nse
 }
 
 void copy_with_increment(long long nt, const double* src, double* dst, unsigned long long* inc, int* nonfinite,
-                         unsigned long long* slice_stats, cudaStream_t st) {
+                         unsigned long long* slice_stats, float* dout, cudaStream_t st) {
   long long blocks = std::min<long long>((nt + 255) / 256, 152 * 8);
-  copy_inc_kernel<<<(unsigned)blocks, 256, 0, st>>>(nt, src, dst, inc, nonfinite, slice_stats);
+  copy_inc_kernel<<<(unsigned)blocks, 256, 0, st>>>(nt, src, dst, inc, nonfinite, slice_stats, dout);
   PS_CUDA(cudaGetLastError());
 }
 

@@ -119,6 +119,8 @@ struct ps_problem {
   ps_params prm{};
   ps::Prop F, G;
   ps::DevBuf<double> U, Fout, Gold, gtmp;
+  bool delta32 = false;       // coarse increment form in FP32 (PS_COARSE_DELTA32); no Gold then
+  ps::DevBuf<float> d32, g32; // its increment U_n^k - U_n^{k-1} and coarse working state
   ps::DevBuf<float> W;      // fine working state, slice-interleaved (FP32 line solves)
   ps::DevBuf<double> W64;   // same for FP64 line solves
   int S_pad = 0;        // slots of the interleaved layout

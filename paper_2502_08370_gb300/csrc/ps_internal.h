@@ -102,13 +102,17 @@ struct SourceArgs {
 
 // Epilogue of the last sweep of a coarse step (the parareal correction, Sec. 3).
 struct CorrArgs {
-  int mode = 0;                      // 0 none, 1 correction, 2 initial sweep (U = Gold = g)
+  // 0 none; 1 correction U_{n+1} = Fout + (g - Gold), Gold <- g; 2 initial sweep U_{n+1} = g
+  // (and Gold = g when Gold is set); 3 increment form U_{n+1} = Fout + g with g = G applied
+  // to the increment of U_n, writing the new increment of U_{n+1} to dnext
+  int mode = 0;
   double* U_next = nullptr;          // U_{n+1}: old value in, new value out
   const double* Fout = nullptr;      // F(U_n^{k-1})
   double* Gold = nullptr;            // G(U_n^{k-1}) in, G(U_n^k) out
   unsigned long long* inc = nullptr; // running max |U^k - U^{k-1}| as bits of a nonnegative double
   int* nonfinite = nullptr;          // set to 1 when a non-finite value appears
   unsigned long long* slice_stats = nullptr;  // optional {max |U^k - U^{k-1}|, max |U^k|} of this slice
+  float* dnext = nullptr;            // mode 3: U_{n+1}^k - U_{n+1}^{k-1}, rounded to FP32
 };
 
 // A run of work items of a grouped (batched) launch: items [prefix, prefix + count) are
@@ -144,8 +148,10 @@ void factor_dim(const Geom& g, int m, const double* a_nodal, double c_over_M, do
 template <typename Tin, typename Tout>
 void sweep_dim(const Geom& g, int nslices, const LineFactors& f, bool fp32, const Tin* in, Tout* out,
                const SourceArgs& srcargs, const CorrArgs& corr, double* tmp, cudaStream_t st);
+// dst <- src with the increment max |src - dst| (and per-slice stats); when dout is set it
+// also receives src - dst rounded to FP32 (the increment the coarse increment form propagates).
 void copy_with_increment(long long nt, const double* src, double* dst, unsigned long long* inc, int* nonfinite,
-                         unsigned long long* slice_stats, cudaStream_t st);
+                         unsigned long long* slice_stats, float* dout, cudaStream_t st);
 // Grouped coarse-step launches (persistent grids of `grid` CTAs; *nseg work segments).
 void coarse_x_grouped(bool var, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid, size_t smem,
                       cudaStream_t st);

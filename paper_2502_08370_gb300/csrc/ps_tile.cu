@@ -21,41 +21,12 @@
 #include <algorithm>
 #include <cstring>
 
+#include "ps_async.h"
 #include "ps_tile.h"
 
 namespace ps {
 namespace {
 
-constexpr unsigned long long kWaitNs = 500000000ULL;  // a tile gives up on its TMA load after 0.5 s
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-// Waits for phase `parity` of the barrier; returns false when kWaitNs have passed.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const unsigned long long t0 = global_ns();
-  for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
-  }
-}
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
                                             int c3) {
   asm volatile(
@@ -74,7 +45,6 @@ __device__ __forceinline__ void tma_store_commit_and_drain() {
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
   asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Tile geometry shared by host and device.
 struct TileArgs {
@@ -113,13 +83,6 @@ __device__ __forceinline__ int tile_off(const TileArgs& a, int s, int p, int i) 
   return a.axis == 0 ? (p * a.L + i) * a.TS + s : (i * a.P + p) * a.TS + s;
 }
 
-// 1-D bulk copy global -> shared, completing on `bar` (16-byte aligned, size a multiple of 16).
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_addr(dst)),
-               "l"(src), "r"(bytes), "r"(smem_addr(bar))
-               : "memory");
-}
 // Bytes the factor (and source) rows of a tile add to its barrier's transaction count.
 template <typename T, bool SRC>
 __device__ __forceinline__ uint32_t side_bytes(const TileArgs& a, int nvalid) {
@@ -637,7 +600,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // Chooses the tile shape of one direction and encodes its tensor map.
 void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void* W, int positions, int pipe,
-               int slots) {
+               int slots, int vec) {
   const int L = g.n[axis];
   tp.axis = axis;
   tp.L = L;
@@ -691,7 +654,9 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
   if (r != CUDA_SUCCESS) throw Error(PS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
   const int lines = tp.TS * tp.P;
   const int Lp = (L + 3) & ~3;
-  tp.V = (elem == 4 && tp.TS >= 32) ? 2 : 1;  // slots per thread: FP32 threads take two adjacent lines
+  // slots per thread: FP32 threads take two adjacent lines (paired 8-byte shared-memory
+  // accesses) unless one line per thread is asked for (twice the threads per tile)
+  tp.V = (elem == 4 && tp.TS >= 32 && vec != 1) ? 2 : 1;
   // stages x (tile + factor rows l, r) + alignment + barriers; the source, when added, takes
   // one more factor row per position and stage
   tp.smem = (size_t)stages * ((size_t)lines * L * elem + 2 * (size_t)tp.P * Lp * elem + 64) + 64 + 128;

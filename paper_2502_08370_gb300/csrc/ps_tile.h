@@ -20,7 +20,7 @@ struct TilePlan {
 // positions: 1, 2 or 4 line positions per tile (0 = largest that fits); pipe: 1 persistent
 // double-buffered, 0 one tile per CTA, -1 auto.
 void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void* W, int positions = 0, int pipe = -1,
-               int slots = 0);
+               int slots = 0, int vec = 0);
 // One substep along tp.axis on slots [s_first, s_first + nsl) (whole TS-slot groups are
 // processed).  `err` is set when a tile's TMA load does not arrive within the wait limit.
 template <typename T>

@@ -231,3 +231,74 @@ def test_fine_sequential_on_recycled_device_memory(ps):
     ref = orc.fine_sequential(orp, 0.01, N, s, u0)
     for j in range(N + 1):
         assert relmax(got[j], ref[j]) < RTOL64, j
+
+
+def make_delta(ps, n, a=None, src=None, T=1.0, N=4, s=4):
+    grid = ps.Grid(n)
+    op = ps.Operator(grid, a=None if a is None else dev(a), src=None if src is None else dev(src))
+    sp = ps.Splitting(op)
+    prob = ps.Problem(sp, T, N, 1, s, precision="mixed", coarse_mode="delta32")
+    prob._keep = (grid, op, sp)
+    return prob, orc.Problem(n, a=a, src=src)
+
+
+@pytest.mark.parametrize("n,N,s,variable", [((33, 31), 8, 16, True), ((15, 14, 13), 6, 8, True), ((63, 63), 16, 64, False),
+                                             ((300, 11), 5, 4, True)])
+def test_coarse_increment_form_fp32(ps, n, N, s, variable):
+    """Coarse increment form (FP32 line solves on U_n^k - U_n^{k-1}, FP64 correction and test) with
+    FP32 fine solves: U_N within the FP32 bound of the FP64 oracle, iteration count within one of
+    the oracle's, finite termination bitwise, and k = N reproduces the FP32 fine solution."""
+    rng = np.random.default_rng(23)
+    a = np.exp(0.3 * rng.standard_normal([v + 2 for v in reversed(n)])) if variable else None
+    src = rng.standard_normal(n[::-1])
+    prob, orp = make_delta(ps, n, a=a, src=src, T=1.0, N=N, s=s)
+    u0 = rng.standard_normal(n[::-1])
+    tol = 1e-8
+    it = prob.run(dev(u0), tol)
+    U_ref, _, it_ref = orc.parareal(orp, 1.0, N, 1, s, u0, tol)
+    assert abs(it - it_ref) <= 1, (it, it_ref)
+    err = relmax(prob.state(N).cpu().numpy(), U_ref[N])
+    assert err < mixed_bound(s, N, len(n)), err
+    u0d = dev(u0)
+    fine = prob.fine_sequential(u0d).cpu().numpy()
+    for k in (1, 2, N):
+        assert prob.run(u0d, 0.0, max_iter=k) == k
+        for j in range(k + 1):
+            assert np.array_equal(prob.state(j).cpu().numpy(), fine[j]), (k, j)
+
+
+def test_coarse_increment_form_is_rejected_where_unsupported(ps):
+    prob, _ = make_delta(ps, (17, 15), a=np.ones((17, 19)), N=4, s=4)
+    u0 = dev(np.ones((15, 17)))
+    prob.run(u0, 1e-8)
+    with pytest.raises(ps.PsError) as e:
+        prob.vjp(prob.state(4), 1e-8)
+    assert e.value.code == 6
+    with pytest.raises(ps.PsError) as e:
+        ps.Batch([prob])
+    assert e.value.code == 6
+    # the sequential coarse solution keeps the FP64 coarse steps
+    ref = orc.coarse_sequential(orc.Problem((17, 15), a=np.ones((17, 19))), 1.0, 4, 1, 4, np.ones((15, 17)))
+    assert relmax(prob.coarse_sequential(u0).cpu().numpy(), ref) < RTOL64
+
+
+@pytest.mark.parametrize("n,positions", [((40, 37, 33), 1), ((64, 17), 2), ((300, 11), 1)])
+def test_fp32_tiles_one_line_per_thread(ps, n, positions):
+    """FP32 tiles solved with one line per thread (twice the threads per tile) give the same
+    states as two lines per thread, bitwise: each line's recurrence is the same arithmetic."""
+    rng = np.random.default_rng(29)
+    a = np.exp(0.3 * rng.standard_normal([v + 2 for v in reversed(n)]))
+    src = rng.standard_normal(n[::-1])
+    u0 = dev(rng.standard_normal(n[::-1]))
+    out = []
+    for vec in (2, 1):
+        grid = ps.Grid(n)
+        op = ps.Operator(grid, a=dev(a), src=dev(src))
+        sp = ps.Splitting(op)
+        prob = ps.Problem(sp, 0.5, 6, 1, 5, precision="mixed", tile_positions=positions, tile_lines_per_thread=vec)
+        prob.run(u0, 1e-8)
+        out.append([prob.state(j).cpu().numpy() for j in range(7)])
+    for j in range(7):
+        assert np.array_equal(out[0][j], out[1][j]), j
+    U_ref, _, _ = orc.parareal(orc.Problem(n, a=a, src=src), 0.5, 6, 1, 5, u0.cpu().numpy(), 1e-8)
+    assert relmax(out[1][6], U_ref[6]) < mixed_bound(5, 6, len(n))
