@@ -77,6 +77,13 @@ typedef struct ps_operator ps_operator;
 typedef struct ps_splitting ps_splitting;
 typedef struct ps_problem ps_problem;
 
+/* Self-test of the device-side wait limit (no counterpart in the paper): launches a kernel
+ * that waits, with the bounded wait every tile and DD kernel uses, on a shared-memory
+ * barrier that nothing arrives at, for limit_us microseconds (1..1e6).  Returns
+ * PS_ERR_DEVICE_TIMEOUT when the wait ran out and the kernel reported it, which is the
+ * expected outcome; the CUDA context stays usable.  PS_ERR_INVALID for a bad limit. */
+int ps_selftest_wait_timeout(int limit_us, uintptr_t stream);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char* ps_last_error(void);
 /* ABI version (major*100 + minor). */
@@ -114,7 +121,8 @@ typedef struct {
   int timing;    /* 1: per-phase CUDA events (ps_problem_stats); 2: also per-kernel
                     events (ps_problem_kernel_times) */
   int dd_slices_per_block; /* DD subdomain solves: time slices per CTA (1, 2 or 4); 0 = 2 */
-  int tile_positions;      /* fine line solves: line positions per TMA tile (1, 2, 4); 0 = auto */
+  int tile_positions;      /* fine line solves: line positions per TMA tile (1, 2, 4); 0 = auto
+                              (FP32: 1; FP64: as many as fit 96 KB, up to 4) */
   int tile_pipeline;       /* fine line solves: 1 persistent double-buffered CTAs, 2 one tile per
                               CTA, 0 = auto */
   int tile_slots;          /* fine line solves: time slices per TMA tile (16, 32, 64); 0 = auto */
@@ -122,7 +130,7 @@ typedef struct {
                               1 = max_n ||U_n^k - U_n^{k-1}||_inf / ||U_n^k||_inf < tol (per slice) */
   int coarse;              /* PS_COARSE_FP64 (0) or PS_COARSE_DELTA32 */
   int tile_lines_per_thread; /* fine line solves (FP32 tiles of 32+ slots): lines a thread solves
-                                side by side, 1 or 2; 0 = auto (2) */
+                                side by side, 1 or 2; 0 = auto (1) */
 } ps_params;
 
 /* fine, coarse: splittings of the same operator used by F and G (coarse = NULL: use
@@ -235,10 +243,12 @@ int ps_problem_kernel_times(const ps_problem* p, ps_kernel_time* out, int cap, i
  * line solves of every slice of every problem, then each coarse step with its correction),
  * the whole iteration is one CUDA graph replayed until every problem has converged, and only
  * small work tables change between replays.  Results equal each problem's own
- * ps_run_parareal bitwise.  Problems: 2-D, dimensional splitting, PS_PREC_MIXED, one coarse
- * step per slice, no source term, all with a nodal coefficient or all without
- * (PS_ERR_UNSUPPORTED otherwise).  The batch keeps pointers to the problems (destroy it
- * first); states and histories are read per problem afterwards (ps_get_state, ...). */
+ * ps_run_parareal bitwise.  Problems: 2-D, dimensional splitting, PS_PREC_MIXED with
+ * PS_COARSE_FP64, one coarse step per slice, no source term, all with a nodal coefficient or
+ * all without (PS_ERR_UNSUPPORTED otherwise).  The batch keeps pointers to the problems
+ * (destroy it first); states and histories are read per problem afterwards (ps_get_state,
+ * ...).  While a problem belongs to a batch, ps_autotune only considers the tile shapes
+ * the batch's grouped kernels run (one tile per work item, two lines per thread). */
 typedef struct ps_batch ps_batch;
 int ps_batch_create(ps_problem* const* problems, int count, uintptr_t stream, ps_batch** out);
 /* u0_devs: host array of `count` device pointers.  Each problem stops at the first k with

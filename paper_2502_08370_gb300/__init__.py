@@ -96,6 +96,7 @@ SIGNATURES = {
     "ps_copy_schedule": [_VP, _VP],
     "ps_adjoint_vjp": [_VP, _VP, _D, _I, _VP, _VP, _U, _IP],
     "ps_problem_kernel_times": [_VP, C.POINTER(_KTime), _I, _IP],
+    "ps_selftest_wait_timeout": [_I, _U],
 }
 _RESTYPE = {"ps_last_error": C.c_char_p, "ps_batch_last_error": C.c_char_p}
 
@@ -137,6 +138,12 @@ def _stream(stream=None):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return int(s.cuda_stream)
+
+
+def selftest_wait_timeout(limit_us=20000, stream=None):
+    """Run the device-side bounded wait against a barrier nothing arrives at; returns the
+    status code (PS_ERR_DEVICE_TIMEOUT = 5 is the expected outcome)."""
+    return lib().ps_selftest_wait_timeout(int(limit_us), _stream(stream))
 
 
 class Grid:

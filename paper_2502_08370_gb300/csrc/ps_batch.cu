@@ -62,7 +62,10 @@ struct ps_batch {
   std::vector<int> h_flag;
   double updates = 0.0;
   int launches_per_iter = 0, launches = 0;
+  bool registered = false;  // counted in its problems' `batched`
   ~ps_batch() {
+    if (registered)
+      for (ps_problem* p : probs) --p->batched;
     if (iter_graph) cudaGraphExecDestroy(iter_graph);
     if (init_graph) cudaGraphExecDestroy(init_graph);
     if (ev_in) cudaEventDestroy(ev_in);
@@ -345,6 +348,8 @@ int ps_batch_create(ps_problem* const* problems, int count, uintptr_t stream, ps
     PS_CUDA(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
     PS_CUDA(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
     PS_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+    for (ps_problem* p : b->probs) ++p->batched;
+    b->registered = true;
     *out = b.release();
   });
 }

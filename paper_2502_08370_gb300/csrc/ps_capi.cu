@@ -18,7 +18,10 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ps_adjoint.h"
+#include "ps_async.h"
 #include "ps_handles.h"
 
 using namespace ps;
@@ -311,7 +314,16 @@ void check_state_len(const ps_problem* p, int slice) {
   PS_REQUIRE(slice >= 0 && slice <= p->N, "slice out of range");
 }
 
+// Host-side trace ranges (NVTX; free when no tool is attached), one per parareal phase.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+
 void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStream_t st, int* iters_out) {
+  TraceRange whole(p->transposed ? "ps.adjoint_parareal" : "ps.parareal");
   const long long nt = p->g.nt;
   const int N = p->N;
   if (max_iter <= 0 || max_iter > N) max_iter = N;
@@ -327,9 +339,12 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
   PS_CUDA(cudaMemsetAsync(p->flag.p, 0, sizeof(int), st));
   tile_flag_reset(p, st);
   // k = 0: sequential coarse sweep, U_{n+1}^0 = G(U_n^0), Gold_n = G(U_n^0)
-  for (int n = 0; n < N; ++n) {
-    if (p->delta32) run_G32(p, n, true, st);
-    else run_G(p, n, p->U.p + n * nt, corr_args(p, 2, n), st);
+  {
+    TraceRange r("ps.coarse_initial");
+    for (int n = 0; n < N; ++n) {
+      if (p->delta32) run_G32(p, n, true, st);
+      else run_G(p, n, p->U.p + n * nt, corr_args(p, 2, n), st);
+    }
   }
   int k = 0;
   while (k < max_iter) {
@@ -338,17 +353,24 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
     PS_CUDA(cudaMemsetAsync(p->inc.p, 0, sizeof(unsigned long long), st));
     PS_CUDA(cudaMemsetAsync(p->sstats.p, 0, sizeof(unsigned long long) * 2 * (N + 1), st));
     if (timing) PS_CUDA(cudaEventRecord(p->ev[1], st));
-    run_F(p, nlo, N - nlo, p->U.p + nlo * nt, p->Fout.p + nlo * nt, st);
+    {
+      TraceRange r("ps.fine_all_slices");
+      run_F(p, nlo, N - nlo, p->U.p + nlo * nt, p->Fout.p + nlo * nt, st);
+    }
     if (timing) PS_CUDA(cudaEventRecord(p->ev[2], st));
-    // slice k-1: U_k^k = F(U_{k-1}^{k-1}) exactly (its G bracket is zero)
-    copy_with_increment(nt, p->Fout.p + nlo * nt, p->U.p + k * nt, p->inc.p, p->flag.p, p->sstats.p + 2 * k,
-                        p->delta32 ? p->d32.p : nullptr, st);
-    p->launches++;
-    for (int n = k; n < N; ++n) {
-      if (p->delta32) run_G32(p, n, false, st);
-      else run_G(p, n, p->U.p + n * nt, corr_args(p, 1, n), st);
+    {
+      TraceRange r("ps.coarse_chain_correction");
+      // slice k-1: U_k^k = F(U_{k-1}^{k-1}) exactly (its G bracket is zero)
+      copy_with_increment(nt, p->Fout.p + nlo * nt, p->U.p + k * nt, p->inc.p, p->flag.p, p->sstats.p + 2 * k,
+                          p->delta32 ? p->d32.p : nullptr, st);
+      p->launches++;
+      for (int n = k; n < N; ++n) {
+        if (p->delta32) run_G32(p, n, false, st);
+        else run_G(p, n, p->U.p + n * nt, corr_args(p, 1, n), st);
+      }
     }
     if (timing) PS_CUDA(cudaEventRecord(p->ev[3], st));
+    TraceRange test("ps.increment_test");
     PS_CUDA(cudaMemcpyAsync(p->h_inc, p->inc.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaMemcpyAsync(p->h_flag, p->flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     PS_CUDA(cudaMemcpyAsync(p->h_flag + 1, p->tmo.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -443,9 +465,35 @@ void coarse_step_into(ps_problem* p, int n, int q, const double* in, double* wor
     sweep_dim<double, double>(p->g, 1, *P.dim[m], false, m == 0 ? in : work, work, sa, CorrArgs{}, nullptr, st);
   }
 }
+// The bounded wait of the tile and DD kernels, on a barrier that nothing arrives at: the wait
+// must run out after limit_ns, set the flag and return (ps_selftest_wait_timeout).
+__global__ void wait_selftest_kernel(int* err, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait_ns(&bar, 0, limit_ns)) atomicExch(err, 1);
+  }
+}
 }  // namespace
 
 extern "C" {
+
+int ps_selftest_wait_timeout(int limit_us, uintptr_t stream) {
+  return guarded([&] {
+    PS_REQUIRE(limit_us >= 1 && limit_us <= 1000000, "limit_us must be in [1, 1e6]");
+    cudaStream_t st = S(stream);
+    DevBuf<int> flag;
+    flag.alloc(1);
+    PS_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
+    wait_selftest_kernel<<<1, 32, 0, st>>>(flag.p, 1000ULL * (unsigned long long)limit_us);
+    PS_CUDA(cudaGetLastError());
+    int h = 0;
+    PS_CUDA(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    if (h) throw Error(PS_ERR_DEVICE_TIMEOUT, "self-test: the bounded wait ran out as designed");
+  });
+}
 
 const char* ps_last_error(void) { return g_last_error.c_str(); }
 int ps_version(void) { return 101; }
@@ -780,8 +828,11 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
       int slots, positions, pipe, vec;
     };
     // slots per tile, line positions per tile, persistent double-buffered CTAs, lines per thread
-    const std::vector<Cand> cands = {{32, 2, 0, 2}, {32, 1, 0, 2}, {32, 1, 0, 1}, {32, 2, 0, 1}, {64, 1, 0, 2},
-                                     {16, 1, 0, 1}, {32, 1, 1, 2}, {32, 1, 1, 1}};
+    std::vector<Cand> cands = {{32, 2, 0, 2}, {32, 1, 0, 2}, {32, 1, 0, 1}, {32, 2, 0, 1}, {64, 1, 0, 2},
+                               {16, 1, 0, 1}, {32, 1, 1, 2}, {32, 1, 1, 1}};
+    if (p->batched > 0)  // the grouped kernels of a batch run one tile per item, 2 lines per thread
+      cands.erase(std::remove_if(cands.begin(), cands.end(), [](const Cand& c) { return c.pipe || c.vec == 1; }),
+                  cands.end());
     tile_flag_reset(p, st);
     cudaEvent_t e0, e1;
     PS_CUDA(cudaEventCreate(&e0));

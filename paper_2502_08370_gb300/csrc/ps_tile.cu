@@ -27,6 +27,8 @@
 namespace ps {
 namespace {
 
+constexpr int kPipeStages = 3;  // shared-memory stages of the persistent tile kernel
+
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
                                             int c3) {
   asm volatile(
@@ -128,18 +130,35 @@ template <typename T, int V, bool SRC>
 __device__ __forceinline__ void line_solve(T* x, int st, int L, const T* Lf, const T* Rf, const T* S, const T* ft) {
   using VT = VecT<T, V>;
   using QT = Quad<T>;
+  // Each chunk of four nodes is loaded one chunk ahead, into registers, before the previous
+  // chunk is stored: the compiler cannot move those loads above the stores itself (it does
+  // not know that st > 0), and without them every chunk would wait a full shared-memory
+  // latency before its dependent FMAs.  The arithmetic is the same in every order.
   T y[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) y[v] = T(0);
   const int nq = L / 4;
+  QT l4n{}, s4n{};
+  VT bn[4];
+  if (nq > 0) {
+    l4n = *reinterpret_cast<const QT*>(Lf);
+    if (SRC) s4n = *reinterpret_cast<const QT*>(S);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) bn[u] = *reinterpret_cast<const VT*>(x + u * st);
+  }
   for (int c = 0; c < nq; ++c) {
     const int i0 = 4 * c;
-    const QT l4 = *reinterpret_cast<const QT*>(Lf + i0);
-    QT s4;
-    if (SRC) s4 = *reinterpret_cast<const QT*>(S + i0);
+    const QT l4 = l4n;
+    const QT s4 = s4n;
     VT b[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) b[u] = *reinterpret_cast<const VT*>(x + (i0 + u) * st);
+    for (int u = 0; u < 4; ++u) b[u] = bn[u];
+    if (c + 1 < nq) {
+      l4n = *reinterpret_cast<const QT*>(Lf + i0 + 4);
+      if (SRC) s4n = *reinterpret_cast<const QT*>(S + i0 + 4);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) bn[u] = *reinterpret_cast<const VT*>(x + (i0 + 4 + u) * st);
+    }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
 #pragma unroll
@@ -180,13 +199,28 @@ __device__ __forceinline__ void line_solve(T* x, int st, int L, const T* Lf, con
     *reinterpret_cast<VT*>(x + i * st) = yy;
     lnext = Lf[i];
   }
+  QT r4n{};
+  VT yyn[4];
+  if (nq > 0) {
+    const int i0 = 4 * (nq - 1);
+    r4n = *reinterpret_cast<const QT*>(Rf + i0);
+    l4n = *reinterpret_cast<const QT*>(Lf + i0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) yyn[u] = *reinterpret_cast<const VT*>(x + (i0 + u) * st);
+  }
   for (int c = nq - 1; c >= 0; --c) {
     const int i0 = 4 * c;
-    const QT r4 = *reinterpret_cast<const QT*>(Rf + i0);
-    const QT l4 = *reinterpret_cast<const QT*>(Lf + i0);
+    const QT r4 = r4n;
+    const QT l4 = l4n;
     VT yy[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) yy[u] = *reinterpret_cast<const VT*>(x + (i0 + u) * st);
+    for (int u = 0; u < 4; ++u) yy[u] = yyn[u];
+    if (c > 0) {
+      r4n = *reinterpret_cast<const QT*>(Rf + i0 - 4);
+      l4n = *reinterpret_cast<const QT*>(Lf + i0 - 4);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) yyn[u] = *reinterpret_cast<const VT*>(x + (i0 - 4 + u) * st);
+    }
 #pragma unroll
     for (int u = 3; u >= 0; --u) {
       const T l1 = u == 3 ? lnext : l4.q[u + 1];
@@ -410,49 +444,52 @@ __device__ __forceinline__ void issue_tile_store(const CUtensorMap* map, const T
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
-// Persistent form: each CTA walks tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... with two
-// shared-memory stages, so the TMA load of tile k+1 (and the store of tile k-1) run while
-// tile k is solved.  Thread 0 alone polls a stage's barrier (bounded by kWaitNs) and
-// shares the outcome; on a timeout the CTA records the error, drains the other stage's
-// load (bounded) and returns.
+// Persistent form: each CTA walks tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... through a
+// ring of kPipeStages shared-memory stages.  While tile k is solved, the loads of tiles
+// k+1 .. k+kPipeStages-2 are in flight and the store of tile k-1 drains; the stage of tile
+// k-1 is refilled once its store has been read out (wait_group.read 1 leaves only tile k's
+// store pending), so no thread waits on a store it has just issued.  Thread 0 alone polls a
+// stage's barrier (bounded by kWaitNs) and shares the outcome; on a timeout the CTA records
+// the error, drains the loads it has in flight (bounded) and returns.
 template <typename T, int V, bool SRC>
 __global__ void tile_sweep_pipe_kernel(const __grid_constant__ CUtensorMap map, TileArgs a, int ntiles) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr int R = kPipeStages;
   const int lines = a.TS * a.P;
   const int Lp = a.Lp;
   const size_t tile_elems = (size_t)lines * a.L;
   const size_t side = (size_t)a.P * Lp;
   T* buf0 = reinterpret_cast<T*>(smem_raw);
   // per stage: l, r (and source) of the tile's positions, rows of Lp entries, 32-byte aligned
-  T* fac0 = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(buf0 + 2 * tile_elems) + 31) & ~(uintptr_t)31);
+  T* fac0 = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(buf0 + R * tile_elems) + 31) & ~(uintptr_t)31);
   const size_t fac_stride = SRC ? 3 * side : 2 * side;
   uint64_t* bars = reinterpret_cast<uint64_t*>(
-      (reinterpret_cast<uintptr_t>(fac0 + 2 * fac_stride) + 15) & ~(uintptr_t)15);
+      (reinterpret_cast<uintptr_t>(fac0 + R * fac_stride) + 15) & ~(uintptr_t)15);
   __shared__ int s_ok;
   const int tid = threadIdx.x;
+  auto stage_load = [&](int stage, int t) {
+    T* fl = fac0 + stage * fac_stride;
+    issue_tile_load<T, SRC>(&map, a, buf0 + stage * tile_elems, fl, fl + side, fl + 2 * side, &bars[stage], t);
+  };
   if (tid == 0) {
     s_ok = *reinterpret_cast<volatile int*>(a.err) ? 0 : 1;
     if (smem_addr(buf0) & 127) {  // TMA tensor destinations must be 128-byte aligned
       atomicExch(a.err, 2);
       s_ok = 0;
     }
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (s_ok) {
+      for (int q = 0; q < R; ++q) mbar_init(&bars[q], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      for (int q = 0; q < R - 1; ++q)
+        if (blockIdx.x + q * (int)gridDim.x < ntiles) stage_load(q, blockIdx.x + q * gridDim.x);
+    }
   }
   __syncthreads();
   if (!s_ok) return;
-  if (tid == 0) {
-    if (blockIdx.x < ntiles)
-      issue_tile_load<T, SRC>(&map, a, buf0, fac0, fac0 + side, fac0 + 2 * side, &bars[0], blockIdx.x);
-    if (blockIdx.x + gridDim.x < ntiles)
-      issue_tile_load<T, SRC>(&map, a, buf0 + tile_elems, fac0 + fac_stride, fac0 + fac_stride + side,
-                              fac0 + fac_stride + 2 * side, &bars[1], blockIdx.x + gridDim.x);
-  }
   int k = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
-    const int stage = k & 1;
-    const uint32_t parity = (k >> 1) & 1;
+    const int stage = k % R;
+    const uint32_t parity = (uint32_t)((k / R) & 1);
     T* buf = buf0 + stage * tile_elems;
     T* fl_s = fac0 + stage * fac_stride;
     T* fr_s = fl_s + side;
@@ -464,7 +501,11 @@ __global__ void tile_sweep_pipe_kernel(const __grid_constant__ CUtensorMap map, 
     if (!s_ok) {
       if (tid == 0) {
         atomicExch(a.err, 1);
-        if (t + (int)gridDim.x < ntiles) mbar_wait(&bars[stage ^ 1], (k + 1) >> 1 & 1);
+        // this tile's load and those issued for the next tiles land in this CTA's shared
+        // memory: wait for them (bounded)
+        for (int q = 0; q < R - 1; ++q)
+          if (t + q * (int)gridDim.x < ntiles) mbar_wait(&bars[(k + q) % R], (uint32_t)(((k + q) / R) & 1));
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
       }
       return;
     }
@@ -481,11 +522,12 @@ __global__ void tile_sweep_pipe_kernel(const __grid_constant__ CUtensorMap map, 
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
-      issue_tile_store(&map, a, buf, t);
-      const int t2 = t + 2 * (int)gridDim.x;
-      if (t2 < ntiles) {
-        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // the stage may be refilled
-        issue_tile_load<T, SRC>(&map, a, buf, fl_s, fr_s, src_s, &bars[stage], t2);
+      issue_tile_store(&map, a, buf, t);  // commits one bulk group
+      const int tn = t + (R - 1) * (int)gridDim.x;
+      if (tn < ntiles) {
+        // the refilled stage held tile k-1 (or is unused yet): its store group must be read out
+        asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        stage_load((k + R - 1) % R, tn);
       }
     }
   }
@@ -618,13 +660,18 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
   }
   PS_REQUIRE((tp.TS * elem) % 128 == 0, "tile rows must be a multiple of 128 bytes");
   tp.pipe = pipe < 0 ? 1 : pipe;
-  const int stages = tp.pipe ? 2 : 1;
-  const size_t budget = tp.pipe ? 72 * 1024 : 96 * 1024;  // per CTA, so that 2-3 CTAs share an SM
+  const int stages = tp.pipe ? kPipeStages : 1;
+  // per CTA, so that 2 (ring of stages) or 2-3 (one tile) CTAs share an SM
+  const size_t budget = tp.pipe ? 110 * 1024 : 96 * 1024;
   const int nb = g.n[axis == 0 ? 1 : 0];  // the paired axis: y for x-lines, x otherwise
   if (positions > 0) {
     tp.P = positions >= 4 ? 4 : (positions >= 2 ? 2 : 1);
     // fewer positions when the paired axis is short or the stages would not fit in shared memory
     while (tp.P > 1 && (tp.P > nb || (size_t)stages * tp.TS * tp.P * L * elem > 200 * 1024)) tp.P /= 2;
+  } else if (elem == 4) {
+    // FP32: one position per tile (34 KB at 255-node lines), so that six tiles share an SM and
+    // their loads, solves and stores overlap (measured best at 127^3 and 255^3, 64 slices)
+    tp.P = 1;
   } else {
     tp.P = 1;
     while (tp.P < 4 && tp.P * 2 <= nb && (size_t)stages * tp.TS * (tp.P * 2) * L * elem <= budget) tp.P *= 2;
@@ -654,9 +701,9 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
   if (r != CUDA_SUCCESS) throw Error(PS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
   const int lines = tp.TS * tp.P;
   const int Lp = (L + 3) & ~3;
-  // slots per thread: FP32 threads take two adjacent lines (paired 8-byte shared-memory
-  // accesses) unless one line per thread is asked for (twice the threads per tile)
-  tp.V = (elem == 4 && tp.TS >= 32 && vec != 1) ? 2 : 1;
+  // lines per thread: one by default (more threads per tile); FP32 threads can take two
+  // adjacent lines (paired 8-byte shared-memory accesses) when asked for
+  tp.V = (elem == 4 && tp.TS >= 32 && vec == 2) ? 2 : 1;
   // stages x (tile + factor rows l, r) + alignment + barriers; the source, when added, takes
   // one more factor row per position and stage
   tp.smem = (size_t)stages * ((size_t)lines * L * elem + 2 * (size_t)tp.P * Lp * elem + 64) + 64 + 128;
@@ -711,7 +758,7 @@ void tile_sweep(const Geom& g, const TilePlan& tp, const LineFactors& f, int S_p
   const long long tiles = (long long)(a.s_hi - a.s_lo) * a.nbt * g.n[cax];
   const bool src = sa.src != nullptr;
   PS_REQUIRE(!src || tp.axis == 0, "the source enters with the x-substep");
-  const int stages = tp.pipe ? 2 : 1;
+  const int stages = tp.pipe ? kPipeStages : 1;
   const int Lp = (tp.L + 3) & ~3;
   const size_t smem = tp.smem + (src ? (size_t)stages * tp.P * Lp * sizeof(T) : 0);
   if (!tp.pipe) {

@@ -56,3 +56,6 @@ def test_host_side_validation_without_gpu(libps):
     arr = (ctypes.c_int * 3)(5, 6, 7)
     assert lib.ps_grid_create(3, ctypes.byref(arr), ctypes.byref(h)) == 0
     assert lib.ps_grid_destroy(h) == 0
+    # the wait-limit self-test validates its limit before touching the device
+    assert lib.ps_selftest_wait_timeout(0, 0) == 1
+    assert b"limit_us" in lib.ps_last_error()
