@@ -55,7 +55,10 @@ FP64_PEAK_TFLOPS = 1.19
 # sweeps, from one ncu capture of the kernel built from the tile source with this hash prefix
 # (127^3 x 64 slices, scaled to any launch by the node-slices it processes).  A kernel whose
 # source changed since is reported with traffic null.
-TRAFFIC = {"F.z.f32": {"bytes_per_node_slice": 1003.901184e6 / (127 ** 3 * 64), "tile_src_sha": "fc38e8fad410ea13"}}
+_UNITS_127 = 127 ** 3 * 64
+TRAFFIC = {"F.x.f32": {"bytes_per_node_slice": (549.195264e6 + 462.892032e6) / _UNITS_127, "tile_src_sha": "174c7381bce44bab"},
+           "F.y.f32": {"bytes_per_node_slice": (540.956160e6 + 463.310592e6) / _UNITS_127, "tile_src_sha": "174c7381bce44bab"},
+           "F.z.f32": {"bytes_per_node_slice": (540.969472e6 + 463.245824e6) / _UNITS_127, "tile_src_sha": "174c7381bce44bab"}}
 
 
 def tile_src_sha():
@@ -525,8 +528,10 @@ def main():
         tr = TRAFFIC.get(dom_name)
         if tr and tr["tile_src_sha"] == tile_src_sha():
             # fine sweep bytes = node-slices x (4 in + 4 out) + the line factors l, r (FP32, per node)
+            # (+ the source row, 8 B per node, on the x sweep that adds it)
             nt = float(np.prod(cfg["n"]))
-            node_slices = (dom["bytes"] / dom["launches"] - 8.0 * nt) / 8.0
+            src_b = 8.0 * nt if (dom_name.startswith("F.x") and cfg.get("src") is not None) else 0.0
+            node_slices = (dom["bytes"] / dom["launches"] - 8.0 * nt - src_b) / 8.0
             roof["traffic"] = tr["bytes_per_node_slice"] * node_slices
     roof.update({"kernel": dom_name, "launches_timed": dom["launches"], "ms_per_launch": per_launch_ms,
                  "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],

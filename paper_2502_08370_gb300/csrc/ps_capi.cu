@@ -264,9 +264,11 @@ void run_G32(ps_problem* p, int n, bool init, cudaStream_t st) {
     SourceArgs sa = (init && m == 0) ? source_for(p, P, n * p->fs + P.tstride, 0) : SourceArgs{};
     p->kt.begin(st);
     double bytes = 0;
-    if (m == 0 && init) {
-      sweep_dim<double, float>(p->g, 1, *P.dim[m], true, p->U.p + n * nt, p->g32.p, sa, CorrArgs{}, nullptr, st);
-      bytes = dnt * (8 + 4 + 8 + (sa.src ? 8 : 0));
+    if (m == 0) {
+      // x-lines are contiguous rows: one warp per row, segmented scans (sweep_x_warp)
+      if (init) sweep_x_warp<double>(p->g, *P.dim[0], p->U.p + n * nt, p->g32.p, sa, st);
+      else sweep_x_warp<float>(p->g, *P.dim[0], p->d32.p, p->g32.p, SourceArgs{}, st);
+      bytes = dnt * ((init ? 8 : 4) + 4 + 8 + (sa.src ? 8 : 0));
     } else {
       const float* in = m == 0 ? p->d32.p : p->g32.p;
       sweep_dim<float, float>(p->g, 1, *P.dim[m], true, in, p->g32.p, SourceArgs{}, last ? c : CorrArgs{}, nullptr, st);
@@ -614,6 +616,11 @@ int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, doub
       throw Error(PS_ERR_UNSUPPORTED, "the FP32 coarse increment form needs the dimensional splitting");
     build_prop(p.get(), p->F, fine, T / N / f_steps, f_steps, 1, mixed, st);
     build_prop(p.get(), p->G, coarse, T / N / g_steps, g_steps, f_steps / g_steps, p->delta32, st);
+    if (p->delta32) {
+      Geom g3 = p->g;
+      if (g3.dim == 2) g3.n[2] = 1;
+      factor_lines(g3, *p->G.dim[0], true, st);  // line-major x factors of the warp x-sweep
+    }
     const long long nt = p->g.nt;
     p->U.alloc((size_t)(N + 1) * nt);
     p->Fout.alloc((size_t)N * nt);
@@ -922,6 +929,7 @@ int ps_problem_update_coefficients(ps_problem* p, const double* a_nodal_dev, uin
         for (int m = 0; m < p->g.dim; ++m) {
           factor_dim(p->g, m, op->a.p, op->c / p->g.dim, P->tau, *P->dim[m], fine ? mixed : p->delta32, st);
           if (fine) factor_lines(g3, *P->dim[m], mixed, st);
+          else if (p->delta32 && m == 0) factor_lines(g3, *P->dim[m], true, st);
         }
       } else {
         dd_factor(p->g, P->sp->dd, op->a.p, op->c, P->tau, *P->dd, st);

@@ -169,6 +169,102 @@ __global__ void __launch_bounds__(kThreads) sweep_x_kernel(const Tin* in, Tout* 
                                          rows_per_slice, fl, fr, sa);
 }
 
+// ---------------------------------------------------------------------------------------
+// a3/a4 (coarse x-substep, FP32): one warp per row, the two recurrences of the L D L^T solve
+// as segmented scans.  Both are first-order affine,  y_i = -l_i y_{i-1} + b_i  and
+// x_i = -l_{i+1} x_{i+1} + r_i y_i,  so lane j composes the maps of its segment of m nodes
+// (A = product of the -l, B = the segment run from a zero input), a five-step shuffle scan
+// composes the segments, and each lane replays its segment from the exact incoming value.
+// The dependent chain is 3m + 10 operations per recurrence instead of L.  The row and its
+// factor rows are staged in shared memory with element i at i + i/m (m even), so the
+// segment reads of the 32 lanes fall in distinct banks.
+__device__ __forceinline__ void warp_line_solve_skewed(float* xb, const float* lb, const float* rb, int L, int m,
+                                                       int lane) {
+  const unsigned full = 0xffffffffu;
+  const int base = lane * (m + 1);
+  const int cnt = max(0, min(m, L - lane * m));
+  float A = 1.f, B = 0.f;
+  for (int u = 0; u < cnt; ++u) {
+    const float l = lb[base + u];
+    B = xb[base + u] - l * B;
+    A = -l * A;
+  }
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float Ap = __shfl_up_sync(full, A, d), Bp = __shfl_up_sync(full, B, d);
+    if (lane >= d) {
+      B = A * Bp + B;
+      A = A * Ap;
+    }
+  }
+  float y = __shfl_up_sync(full, B, 1);
+  if (lane == 0) y = 0.f;
+  for (int u = 0; u < cnt; ++u) {
+    y = xb[base + u] - lb[base + u] * y;
+    xb[base + u] = y;
+  }
+  __syncwarp();
+  // l_{i+1} past the segment's end: the next segment's first factor (0 past the line)
+  const float lnext = (lane * m + cnt < L) ? lb[base + m + 1] : 0.f;
+  A = 1.f;
+  B = 0.f;
+  for (int u = cnt - 1; u >= 0; --u) {
+    const float ln = (u + 1 < cnt) ? lb[base + u + 1] : lnext;
+    B = rb[base + u] * xb[base + u] - ln * B;
+    A = -ln * A;
+  }
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float An = __shfl_down_sync(full, A, d), Bn = __shfl_down_sync(full, B, d);
+    if (lane + d < 32) {
+      B = A * Bn + B;
+      A = A * An;
+    }
+  }
+  float xv = __shfl_down_sync(full, B, 1);
+  if (lane == 31) xv = 0.f;
+  for (int u = cnt - 1; u >= 0; --u) {
+    const float ln = (u + 1 < cnt) ? lb[base + u + 1] : lnext;
+    xv = rb[base + u] * xb[base + u] - ln * xv;
+    xb[base + u] = xv;
+  }
+  __syncwarp();
+}
+
+// One slice: rows of nx nodes, line-major factor rows lt/rt (pitch Lp).  SRC adds
+// tau * src * src_t[t0] to the right-hand side on the way in.
+template <typename Tin, bool SRC>
+__global__ void __launch_bounds__(256) sweep_x_warp_kernel(const Tin* __restrict__ in, float* __restrict__ out,
+                                                           long long rows, int nx, int m, int span,
+                                                           const float* __restrict__ lt, const float* __restrict__ rt,
+                                                           int Lp, SourceArgs sa) {
+  extern __shared__ float wsm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  float* xb = wsm + (size_t)warp * 3 * span;
+  float* lb = xb + span;
+  float* rb = lb + span;
+  const double c = SRC ? sa.tau * (sa.src_t ? sa.src_t[sa.t0] : 1.0) : 0.0;
+  for (long long row = (long long)blockIdx.x * nw + warp; row < rows; row += (long long)gridDim.x * nw) {
+    const Tin* gin = in + row * nx;
+    const float* gl = lt + row * Lp;
+    const float* gr = rt + row * Lp;
+    for (int i = lane; i < nx; i += 32) {
+      const int k = i + i / m;
+      float b = (float)gin[i];
+      if (SRC) b = b + (float)(c * sa.src[row * nx + i]);
+      xb[k] = b;
+      lb[k] = gl[i];
+      rb[k] = gr[i];
+    }
+    // one slot past the line: the backward step reads the next segment's first factor there
+    if (lane == 0) lb[nx + nx / m] = 0.f;
+    __syncwarp();
+    warp_line_solve_skewed(xb, lb, rb, nx, m, lane);
+    for (int i = lane; i < nx; i += 32) out[row * nx + i] = xb[i + i / m];
+    __syncwarp();
+  }
+}
+
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
   // nonnegative doubles order like their bit patterns
   atomicMax(addr, (unsigned long long)__double_as_longlong(v));
@@ -554,6 +650,36 @@ template void sweep_dim<float, float>(const Geom&, int, const LineFactors&, bool
                                       const SourceArgs&, const CorrArgs&, double*, cudaStream_t);
 template void sweep_dim<float, double>(const Geom&, int, const LineFactors&, bool, const float*, double*,
                                        const SourceArgs&, const CorrArgs&, double*, cudaStream_t);
+
+template <typename Tin>
+void sweep_x_warp(const Geom& g, const LineFactors& f, const Tin* in, float* out, const SourceArgs& sa,
+                  cudaStream_t st) {
+  PS_REQUIRE(f.m == 0 && f.lt32.p && f.rt32.p, "the warp x-sweep needs FP32 line-major x factors");
+  const int nx = g.n[0];
+  const long long rows = g.nt / nx;
+  const int m = ((nx + 31) / 32 + 1) & ~1;  // even: the skewed pitch m + 1 is odd
+  const int span = nx + nx / m + 2;
+  const int Lp = (nx + 3) & ~3;
+  const int threads = 256;
+  const size_t smem = (size_t)(threads / 32) * 3 * span * sizeof(float);
+  PS_REQUIRE(smem <= (size_t)max_dyn_smem(), "x-line too long for the warp x-sweep");
+  int dev = 0, sms = 0;
+  PS_CUDA(cudaGetDevice(&dev));
+  PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const long long want = (rows + threads / 32 - 1) / (threads / 32);
+  const unsigned grid = (unsigned)std::min<long long>(want, (long long)sms * 8);
+  auto launch = [&](auto kern) {
+    PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, threads, smem, st>>>(in, out, rows, nx, m, span, f.lt32.p, f.rt32.p, Lp, sa);
+  };
+  if (sa.src) launch(sweep_x_warp_kernel<Tin, true>);
+  else launch(sweep_x_warp_kernel<Tin, false>);
+  PS_CUDA(cudaGetLastError());
+}
+template void sweep_x_warp<float>(const Geom&, const LineFactors&, const float*, float*, const SourceArgs&,
+                                  cudaStream_t);
+template void sweep_x_warp<double>(const Geom&, const LineFactors&, const double*, float*, const SourceArgs&,
+                                   cudaStream_t);
 
 int max_dyn_smem_public() { return max_dyn_smem(); }
 

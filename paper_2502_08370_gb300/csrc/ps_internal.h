@@ -148,6 +148,11 @@ void factor_dim(const Geom& g, int m, const double* a_nodal, double c_over_M, do
 template <typename Tin, typename Tout>
 void sweep_dim(const Geom& g, int nslices, const LineFactors& f, bool fp32, const Tin* in, Tout* out,
                const SourceArgs& srcargs, const CorrArgs& corr, double* tmp, cudaStream_t st);
+// Coarse x-substep in FP32 on one slice, one warp per row (segmented scans of the two
+// recurrences); needs the line-major FP32 factors of direction x (factor_lines).
+template <typename Tin>
+void sweep_x_warp(const Geom& g, const LineFactors& f, const Tin* in, float* out, const SourceArgs& sa,
+                  cudaStream_t st);
 // dst <- src with the increment max |src - dst| (and per-slice stats); when dout is set it
 // also receives src - dst rounded to FP32 (the increment the coarse increment form propagates).
 void copy_with_increment(long long nt, const double* src, double* dst, unsigned long long* inc, int* nonfinite,
