@@ -248,7 +248,7 @@ int ps_problem_kernel_times(const ps_problem* p, ps_kernel_time* out, int cap, i
  * all without (PS_ERR_UNSUPPORTED otherwise).  The batch keeps pointers to the problems
  * (destroy it first); states and histories are read per problem afterwards (ps_get_state,
  * ...).  While a problem belongs to a batch, ps_autotune only considers the tile shapes
- * the batch's grouped kernels run (one tile per work item, two lines per thread). */
+ * the batch's grouped kernels run (one tile per work item, one line per thread). */
 typedef struct ps_batch ps_batch;
 int ps_batch_create(ps_problem* const* problems, int count, uintptr_t stream, ps_batch** out);
 /* u0_devs: host array of `count` device pointers.  Each problem stops at the first k with

@@ -302,7 +302,9 @@ int ps_batch_create(ps_problem* const* problems, int count, uintptr_t stream, ps
       b->maxN = std::max(b->maxN, p->N);
       b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[0]));
       b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[1]));
-      b->tile_threads = std::max(b->tile_threads, std::max(p->F.tiles[0].threads, p->F.tiles[1].threads));
+      // the grouped kernel runs one line per thread, whatever the plan's own split
+      b->tile_threads = std::max(b->tile_threads, std::max(p->F.tiles[0].TS * p->F.tiles[0].P,
+                                                           p->F.tiles[1].TS * p->F.tiles[1].P));
       const int nx = p->g.n[0];
       const int ld = (nx % 2) ? nx : nx + 1;
       b->x_smem = std::max(b->x_smem, (size_t)x_rows_per_block(nx) * ld * sizeof(double));
@@ -379,7 +381,9 @@ int ps_batch_run(ps_batch* b, const double* const* u0_devs, double tol, int max_
     b->tile_threads = 0;
     for (ps_problem* p : b->probs) {
       b->tile_smem = std::max(b->tile_smem, std::max(tile_grouped_smem(p->F.tiles[0]), tile_grouped_smem(p->F.tiles[1])));
-      b->tile_threads = std::max(b->tile_threads, std::max(p->F.tiles[0].threads, p->F.tiles[1].threads));
+      // the grouped kernel runs one line per thread, whatever the plan's own split
+      b->tile_threads = std::max(b->tile_threads, std::max(p->F.tiles[0].TS * p->F.tiles[0].P,
+                                                           p->F.tiles[1].TS * p->F.tiles[1].P));
     }
     b->tile_threads = (b->tile_threads + 31) / 32 * 32;
     b->init_graph = capture(b, 2);

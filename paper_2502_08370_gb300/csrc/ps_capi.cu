@@ -837,8 +837,8 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
     // slots per tile, line positions per tile, persistent double-buffered CTAs, lines per thread
     std::vector<Cand> cands = {{32, 2, 0, 2}, {32, 1, 0, 2}, {32, 1, 0, 1}, {32, 2, 0, 1}, {64, 1, 0, 2},
                                {16, 1, 0, 1}, {32, 1, 1, 2}, {32, 1, 1, 1}};
-    if (p->batched > 0)  // the grouped kernels of a batch run one tile per item, 2 lines per thread
-      cands.erase(std::remove_if(cands.begin(), cands.end(), [](const Cand& c) { return c.pipe || c.vec == 1; }),
+    if (p->batched > 0)  // the grouped kernels of a batch run one tile per item, one line per thread
+      cands.erase(std::remove_if(cands.begin(), cands.end(), [](const Cand& c) { return c.pipe || c.vec == 2; }),
                   cands.end());
     tile_flag_reset(p, st);
     cudaEvent_t e0, e1;

@@ -310,9 +310,9 @@ __device__ __forceinline__ void sweep_strided_body(long long blk, const Tin* in,
     constexpr int K = 8;
     Tc y = (Tc)in[base];
     if (SRC) y = y + to<Tc>(ft * sa.src[pos]);
-    tmp[base] = (Tout)y;
-    for (int i0 = 1; i0 < nm; i0 += K) {
-      Tc b[K], l[K];
+    // chunk loads one chunk ahead, issued before the previous chunk's stores (the compiler
+    // cannot hoist them itself: in and tmp may be the same array)
+    auto load_chunk = [&](int i0, Tc* b, Tc* l) {
 #pragma unroll
       for (int u = 0; u < K; ++u) {
         const int i = i0 + u;
@@ -320,6 +320,18 @@ __device__ __forceinline__ void sweep_strided_body(long long blk, const Tin* in,
         l[u] = i < nm ? Lf[i * fs] : Tc(0);
         if (SRC) b[u] = b[u] + (i < nm ? to<Tc>(ft * sa.src[pos + i * S]) : Tc(0));
       }
+    };
+    Tc bn[K], ln[K];
+    load_chunk(1, bn, ln);
+    tmp[base] = (Tout)y;
+    for (int i0 = 1; i0 < nm; i0 += K) {
+      Tc b[K], l[K];
+#pragma unroll
+      for (int u = 0; u < K; ++u) {
+        b[u] = bn[u];
+        l[u] = ln[u];
+      }
+      if (i0 + K < nm) load_chunk(i0 + K, bn, ln);
 #pragma unroll
       for (int u = 0; u < K; ++u) {
         if (i0 + u < nm) {

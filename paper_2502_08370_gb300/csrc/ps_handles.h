@@ -130,7 +130,7 @@ struct ps_problem {
   ps::DevBuf<unsigned long long> sstats;  // per slice {max |U^k - U^{k-1}|, max |U^k|}, slices 0..N
   unsigned long long* h_sstats = nullptr;
   bool transposed = false;  // propagate with the transposed steps (substeps reversed, no source)
-  int batched = 0;          // batches holding this problem (their grouped kernels run 2 lines per
+  int batched = 0;          // batches holding this problem (their grouped kernels run one line per
                             // thread, one tile per work item: the autotuner keeps to such shapes)
   bool have_forward = false;
   // adjoint workspaces (allocated by the first ps_adjoint_vjp with a coefficient gradient)

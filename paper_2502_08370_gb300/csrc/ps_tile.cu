@@ -880,7 +880,7 @@ size_t tile_grouped_smem(const TilePlan& tp) { return tp.smem; }
 
 void tile_sweep_grouped(const void* jobs, const WorkSeg* segs, const int* nseg, int grid, int threads, size_t smem,
                         int* err, cudaStream_t st) {
-  auto kern = tile_sweep_grouped_kernel<float, 2>;
+  auto kern = tile_sweep_grouped_kernel<float, 1>;  // one line per thread, as the default single-problem plan
   PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<grid, threads, smem, st>>>(reinterpret_cast<const TileJob*>(jobs), segs, nseg, err);
   PS_CUDA(cudaGetLastError());
