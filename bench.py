@@ -52,19 +52,25 @@ FP64_PEAK_TFLOPS = 1.19
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per node-slice of the fine tile
-# sweeps, from one ncu capture of the kernel built from the tile source with this hash prefix
+# sweeps, from one ncu capture of the kernel built from the kernel source with this hash prefix
 # (127^3 x 64 slices, scaled to any launch by the node-slices it processes).  A kernel whose
 # source changed since is reported with traffic null.
 _UNITS_127 = 127 ** 3 * 64
-TRAFFIC = {"F.x.f32": {"bytes_per_node_slice": (549.195264e6 + 462.892032e6) / _UNITS_127, "tile_src_sha": "174c7381bce44bab"},
-           "F.y.f32": {"bytes_per_node_slice": (540.956160e6 + 463.310592e6) / _UNITS_127, "tile_src_sha": "174c7381bce44bab"},
-           "F.z.f32": {"bytes_per_node_slice": (540.969472e6 + 463.245824e6) / _UNITS_127, "tile_src_sha": "174c7381bce44bab"}}
+TRAFFIC = {"F.x.f32": {"bytes_per_node_slice": (549.195264e6 + 462.892032e6) / _UNITS_127, "tile_src_sha": "6e9fdde89f1c3134"},
+           "F.y.f32": {"bytes_per_node_slice": (540.956160e6 + 463.310592e6) / _UNITS_127, "tile_src_sha": "6e9fdde89f1c3134"},
+           "F.z.f32": {"bytes_per_node_slice": (540.969472e6 + 463.245824e6) / _UNITS_127, "tile_src_sha": "6e9fdde89f1c3134"}}
 
 
 def tile_src_sha():
+    """Hash of the single-problem tile kernel's source: the async-copy helpers and ps_tile.cu up to
+    the persistent and grouped variants (the line solve, the tile body, tile_sweep_kernel)."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_2502_08370_gb300", "csrc", "ps_tile.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    csrc = os.path.join(ROOT, "paper_2502_08370_gb300", "csrc")
+    with open(os.path.join(csrc, "ps_async.h")) as f:
+        helpers = f.read()
+    with open(os.path.join(csrc, "ps_tile.cu")) as f:
+        tile = f.read()
+    return hashlib.sha256((helpers + tile[:tile.index("// Persistent form")]).encode()).hexdigest()[:16]
 
 
 def workload(name):
@@ -98,6 +104,22 @@ def dist_setup(backend):
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         dist.init_process_group(backend)
     return rank, ws
+
+
+def combine_ranks(ms, units, device):
+    """Whole-job figures of a replicas run: the slowest rank's time and the units of all ranks
+    (one rank: unchanged).  device: where the collective's tensor lives ("cuda" for NCCL,
+    "cpu" for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(units)
+    t = torch.tensor([float(ms), float(units)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
 
 
 class ClockSampler:
@@ -499,16 +521,7 @@ def main():
     barrier()
     clocks = sampler.stop() if sampler else None
     ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, updates], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_max, updates_all = float(mx[0]), float(sm[1])
-    else:
-        ms_max, updates_all = ms, updates
+    ms_max, updates_all = combine_ranks(ms, updates, "cuda")
     value = updates_all / (ms_max / 1000.0)
     uN_mixed = prob.state(cfg["N"]).cpu().numpy()
 
@@ -561,14 +574,7 @@ def main():
     e2e_ms = e0.elapsed_time(e1)
     e2e_wall = time.perf_counter() - t0
     barrier()
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms, e2e_upd], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        e2e_ms, e2e_upd = float(mx[0]), float(sm[1])
+    e2e_ms, e2e_upd = combine_ranks(e2e_ms, e2e_upd, "cuda")
     e2e = {"value": e2e_upd / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": 8 * nt,
            "d2h_bytes_per_step": 8 * nt, "wall_s": e2e_wall}
 

@@ -286,7 +286,7 @@ constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;  // |v| bits >= t
 // recurrence of the last sweep of a coarse step:
 //     U_{n+1} <- Fout + (g - Gold),  Gold <- g,  inc <- max(inc, |U_{n+1}^new - U_{n+1}^old|)
 // EPI = 2 is the initial coarse sweep: U_{n+1} <- g, Gold <- g.
-template <typename Tin, typename Tout, typename Tc, bool VAR, bool SRC, int EPI>
+template <typename Tin, typename Tout, typename Tc, bool VAR, bool SRC, int EPI, bool AHEAD>
 __device__ __forceinline__ void sweep_strided_body(long long blk, const Tin* in, Tout* out, Tout* tmp, long long lines,
                                                    int nm, long long S, long long nt, const Tc* __restrict__ fl,
                                                    const Tc* __restrict__ fr, const SourceArgs& sa,
@@ -310,33 +310,56 @@ __device__ __forceinline__ void sweep_strided_body(long long blk, const Tin* in,
     constexpr int K = 8;
     Tc y = (Tc)in[base];
     if (SRC) y = y + to<Tc>(ft * sa.src[pos]);
-    // chunk loads one chunk ahead, issued before the previous chunk's stores (the compiler
-    // cannot hoist them itself: in and tmp may be the same array)
-    auto load_chunk = [&](int i0, Tc* b, Tc* l) {
+    if constexpr (AHEAD) {
+      // chunk loads one chunk ahead, issued before the previous chunk's stores (the compiler
+      // cannot hoist them itself: in and tmp may be the same array).  Chosen at launch for
+      // short line strides (y-lines); long-stride sweeps (z-lines) keep the plain loop below,
+      // which measured faster there.
+      auto load_chunk = [&](int i0, Tc* b, Tc* l) {
 #pragma unroll
-      for (int u = 0; u < K; ++u) {
-        const int i = i0 + u;
-        b[u] = i < nm ? (Tc)in[base + i * S] : Tc(0);
-        l[u] = i < nm ? Lf[i * fs] : Tc(0);
-        if (SRC) b[u] = b[u] + (i < nm ? to<Tc>(ft * sa.src[pos + i * S]) : Tc(0));
+        for (int u = 0; u < K; ++u) {
+          const int i = i0 + u;
+          b[u] = i < nm ? (Tc)in[base + i * S] : Tc(0);
+          l[u] = i < nm ? Lf[i * fs] : Tc(0);
+          if (SRC) b[u] = b[u] + (i < nm ? to<Tc>(ft * sa.src[pos + i * S]) : Tc(0));
+        }
+      };
+      Tc bn[K], ln[K];
+      load_chunk(1, bn, ln);
+      tmp[base] = (Tout)y;
+      for (int i0 = 1; i0 < nm; i0 += K) {
+        Tc b[K], l[K];
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+          b[u] = bn[u];
+          l[u] = ln[u];
+        }
+        if (i0 + K < nm) load_chunk(i0 + K, bn, ln);
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+          if (i0 + u < nm) {
+            y = b[u] - l[u] * y;
+            tmp[base + (i0 + u) * S] = (Tout)y;
+          }
+        }
       }
-    };
-    Tc bn[K], ln[K];
-    load_chunk(1, bn, ln);
-    tmp[base] = (Tout)y;
-    for (int i0 = 1; i0 < nm; i0 += K) {
-      Tc b[K], l[K];
+    } else {
+      tmp[base] = (Tout)y;
+      for (int i0 = 1; i0 < nm; i0 += K) {
+        Tc b[K], l[K];
 #pragma unroll
-      for (int u = 0; u < K; ++u) {
-        b[u] = bn[u];
-        l[u] = ln[u];
-      }
-      if (i0 + K < nm) load_chunk(i0 + K, bn, ln);
+        for (int u = 0; u < K; ++u) {
+          const int i = i0 + u;
+          b[u] = i < nm ? (Tc)in[base + i * S] : Tc(0);
+          l[u] = i < nm ? Lf[i * fs] : Tc(0);
+          if (SRC) b[u] = b[u] + (i < nm ? to<Tc>(ft * sa.src[pos + i * S]) : Tc(0));
+        }
 #pragma unroll
-      for (int u = 0; u < K; ++u) {
-        if (i0 + u < nm) {
-          y = b[u] - l[u] * y;
-          tmp[base + (i0 + u) * S] = (Tout)y;
+        for (int u = 0; u < K; ++u) {
+          if (i0 + u < nm) {
+            y = b[u] - l[u] * y;
+            tmp[base + (i0 + u) * S] = (Tout)y;
+          }
         }
       }
     }
@@ -415,12 +438,12 @@ __device__ __forceinline__ void sweep_strided_body(long long blk, const Tin* in,
   }
 }
 
-template <typename Tin, typename Tout, typename Tc, bool VAR, bool SRC, int EPI>
+template <typename Tin, typename Tout, typename Tc, bool VAR, bool SRC, int EPI, bool AHEAD>
 __global__ void __launch_bounds__(kThreads) sweep_strided_kernel(const Tin* in, Tout* out, Tout* tmp, long long lines,
                                                                 int nm, long long S, long long nt,
                                                                 const Tc* __restrict__ fl, const Tc* __restrict__ fr,
                                                                 SourceArgs sa, CorrArgs ca) {
-  sweep_strided_body<Tin, Tout, Tc, VAR, SRC, EPI>(blockIdx.x, in, out, tmp, lines, nm, S, nt, fl, fr, sa, ca);
+  sweep_strided_body<Tin, Tout, Tc, VAR, SRC, EPI, AHEAD>(blockIdx.x, in, out, tmp, lines, nm, S, nt, fl, fr, sa, ca);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -465,7 +488,8 @@ __global__ void __launch_bounds__(kThreads) sweep_y_grouped_kernel(const CoarseJ
   for (long long it = blockIdx.x; it < total; it += gridDim.x) {
     const WorkSeg sg = segs[find_segment(segs, nseg, it)];
     const CoarseJob& j = jobs[sg.job];
-    sweep_strided_body<double, double, double, VAR, false, EPI>(sg.first + (it - sg.prefix), j.xout, j.xout, j.xout,
+    sweep_strided_body<double, double, double, VAR, false, EPI, true>(sg.first + (it - sg.prefix), j.xout, j.xout,
+                                                                      j.xout,
                                                                 j.nx, j.ny, j.nx, j.nt, j.ly, j.ry, SourceArgs{}, j.ca);
   }
 }
@@ -569,8 +593,12 @@ void launch_strided(const Geom& g, int m, int nslices, const Tc* fl, const Tc* f
   const long long S = g.stride(m);
   const long long lines = (g.nt / nm) * nslices;
   long long blocks = (lines + kThreads - 1) / kThreads;
-  sweep_strided_kernel<Tin, Tout, Tc, VAR, SRC, EPI>
-      <<<(unsigned)blocks, kThreads, 0, st>>>(in, out, tmp, lines, nm, S, g.nt, fl, fr, sa, ca);
+  if (S * (long long)sizeof(Tin) <= 8192)
+    sweep_strided_kernel<Tin, Tout, Tc, VAR, SRC, EPI, true>
+        <<<(unsigned)blocks, kThreads, 0, st>>>(in, out, tmp, lines, nm, S, g.nt, fl, fr, sa, ca);
+  else
+    sweep_strided_kernel<Tin, Tout, Tc, VAR, SRC, EPI, false>
+        <<<(unsigned)blocks, kThreads, 0, st>>>(in, out, tmp, lines, nm, S, g.nt, fl, fr, sa, ca);
   PS_CUDA(cudaGetLastError());
 }
 
