@@ -46,15 +46,16 @@ extern "C" {
 #define PS_ERR_CUDA 2           /* a CUDA runtime call failed (message has the CUDA error) */
 #define PS_ERR_OOM 3            /* device allocation failed */
 #define PS_ERR_NONFINITE 4      /* a NaN/Inf appeared in the parareal correction */
-#define PS_ERR_DEVICE_TIMEOUT 5 /* a device-side wait ran out of its iteration budget */
+#define PS_ERR_DEVICE_TIMEOUT 5 /* a device-side wait ran out of its time limit (0.5 s) */
 #define PS_ERR_UNSUPPORTED 6    /* combination not implemented (e.g. 3-D DD splitting) */
 
 #define PS_SPLIT_DIM 0 /* dimensional splitting, M = d substeps x, y(, z) (Sec. 2.1) */
 #define PS_SPLIT_DD 1  /* domain-decomposition splitting, 2-D, M = #colours (Sec. 2.1) */
 
 #define PS_PREC_FP64 0  /* every solve in FP64 */
-#define PS_PREC_MIXED 1 /* fine-propagator line solves in FP32; coarse propagator, the
-                           parareal correction, the increments and the test in FP64 */
+#define PS_PREC_MIXED 1 /* fine-propagator line solves in FP32; the coarse propagator (FP64
+                           unless PS_COARSE_DELTA32), the parareal correction, the increments
+                           and the test in FP64 */
 
 /* Coarse propagator arithmetic (ps_params.coarse).  G is affine (Sec. 2.2, eq. FIE_method:
  * G(u) = B u + c with c from the source), so the bracket G(U_n^k) - G(U_n^{k-1}) of the
@@ -123,8 +124,8 @@ typedef struct {
   int dd_slices_per_block; /* DD subdomain solves: time slices per CTA (1, 2 or 4); 0 = 2 */
   int tile_positions;      /* fine line solves: line positions per TMA tile (1, 2, 4); 0 = auto
                               (FP32: 1; FP64: as many as fit 96 KB, up to 4) */
-  int tile_pipeline;       /* fine line solves: 1 persistent double-buffered CTAs, 2 one tile per
-                              CTA, 0 = auto */
+  int tile_pipeline;       /* fine line solves: 1 persistent CTAs with a ring of three stages,
+                              2 one tile per CTA, 0 = auto (one tile per CTA) */
   int tile_slots;          /* fine line solves: time slices per TMA tile (16, 32, 64); 0 = auto */
   int tol_mode;            /* stopping test: 0 = max_n ||U_n^k - U_n^{k-1}||_inf < tol (absolute);
                               1 = max_n ||U_n^k - U_n^{k-1}||_inf / ||U_n^k||_inf < tol (per slice) */
@@ -137,7 +138,9 @@ typedef struct {
  * fine).  T > 0; N slices; G = g_steps FIE steps of DeltaT/g_steps; F = f_steps FIE
  * steps of dt = DeltaT/f_steps; f_steps % g_steps == 0.  Builds the substep factors
  * of (I - tau A_j) for both step sizes on the device (FP64) and allocates the slice
- * states: (N+1) U, N Gold, N F-results (+ N FP32 work states in PS_PREC_MIXED). */
+ * states: (N+1) U, N F-results, N Gold (PS_COARSE_FP64) or two FP32 single-slice states
+ * (PS_COARSE_DELTA32), and the slice-interleaved fine working state (FP32 in
+ * PS_PREC_MIXED). */
 int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, double T, int N, int g_steps,
                       int f_steps, const ps_params* params, uintptr_t stream, ps_problem** out);
 int ps_problem_destroy(ps_problem* p);
@@ -225,7 +228,7 @@ int ps_problem_stats(const ps_problem* p, ps_stats* out);
 /* Per-kernel-kind device times of the last run, recorded when params.timing >= 2 with a
  * CUDA event pair around every launch on the run's stream.  name: "<phase>.<axis>.<type>"
  * (phase F = fine, G = coarse; +corr / +init when the parareal correction / initial sweep
- * is fused in).  bytes / flops: algorithmic traffic and FP work summed over the launches
+ * is fused in, +dcorr for the correction of the FP32 coarse increment form).  bytes / flops: algorithmic traffic and FP work summed over the launches
  * (each sweep reads its right-hand side and writes its result once, reads the factors once
  * per launch; 5 flops per unknown per sweep, FMA = 2).  len = number of kinds (<= cap). */
 typedef struct {
@@ -263,10 +266,11 @@ const char* ps_batch_last_error(void);
 int ps_batch_destroy(ps_batch* b);
 
 /* Autotuner of the fine line-solve schedule: times the fine sweeps of this problem with each
- * candidate tile shape (slices per tile 32/64, positions 1/2, one tile per CTA or persistent
- * double-buffered CTAs) for about budget_ms and installs the fastest.  Results do not depend
- * on the schedule (each line's arithmetic is the same).  *choice_out (may be NULL) receives
- * slots*100 + positions*10 + pipelined. */
+ * candidate tile shape (time slices per tile 16/32/64, line positions 1/2, lines per thread
+ * 1/2, one tile per CTA or a persistent ring of three shared-memory stages) for about
+ * budget_ms and installs the fastest.  Results do not depend on the schedule (each line's
+ * arithmetic is the same).  *choice_out (may be NULL) receives
+ * lines_per_thread*10000 + slots*100 + positions*10 + pipelined. */
 int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out);
 /* Same schedule on `dst` as on `src` (same grid and slice count). */
 int ps_copy_schedule(const ps_problem* src, ps_problem* dst);

@@ -206,3 +206,25 @@ def test_dd_config_geometry():
     for b in range(1, 7):
         lo, hi = widths[b]
         assert (lo, hi) == (128 * b - 4, 128 * b + 132)
+
+
+@pytest.mark.parametrize("n", [(9, 8), (6, 5, 7)])
+def test_fie_steps_are_affine_increment_form(n):
+    """The FIE step is affine in the state (eq. FIE_method: the source enters as a fixed
+    right-hand-side term), so for any two states the difference of their propagations equals
+    the source-free propagation of their difference.  This is the identity the FP32 coarse
+    increment form uses: G(U^k) - G(U^{k-1}) = B (U^k - U^{k-1}).  A dropped or doubled source
+    term, or a source scaled by the state, breaks it."""
+    rng = np.random.default_rng(5)
+    a = np.exp(0.3 * rng.standard_normal([v + 2 for v in reversed(n)]))
+    src = rng.standard_normal(n[::-1])
+    src_t = 1.0 + np.sin(np.arange(20) * 0.4)
+    with_src = orc.Problem(n, a=a, c=0.3, src=src, src_t=src_t)
+    no_src = orc.Problem(n, a=a, c=0.3)
+    u, v = rng.standard_normal(n[::-1]), rng.standard_normal(n[::-1])
+    tau, steps = 0.07, 3
+    d = orc.propagate(with_src, tau, steps, u, t0=2) - orc.propagate(with_src, tau, steps, v, t0=2)
+    b = orc.propagate(no_src, tau, steps, u - v, t0=2)
+    assert np.abs(d - b).max() <= 1e-13 * np.abs(b).max()
+    # and the source does contribute: the propagations themselves differ from the source-free ones
+    assert np.abs(orc.propagate(with_src, tau, steps, u, t0=2) - orc.propagate(no_src, tau, steps, u, t0=2)).max() > 1e-3
