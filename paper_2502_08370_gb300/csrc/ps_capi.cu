@@ -1,4 +1,4 @@
-// ps_capi.cu -- handles, the parareal driver and the C ABI declared in include/ps.h.
+// ps_capi.cu -- handles, the parareal host loop and the C ABI declared in include/ps.h.
 //
 // Parareal (Sec. 3) with FIE propagators (Sec. 2.2, eq. FIE_method):
 //   U_0 = u0,  U_{n+1}^0 = G(U_n^0),
@@ -6,7 +6,7 @@
 // F of every slice runs in one batched launch per substep (all slices at once); the
 // coarse chain runs slice after slice with the correction fused into its last sweep.
 // Finite termination (Sec. 3): U_n^k = U_n^{k-1} for n <= k-1, so the correction of
-// slice k-1 has an exactly zero bracket and slices n < k-1 are unchanged; the driver
+// slice k-1 has an exactly zero bracket and slices n < k-1 are unchanged; the host loop
 // skips that work, which leaves every value bitwise as the full iteration computes it.
 #include <cuda_runtime.h>
 

@@ -15,7 +15,7 @@ def pytest_configure(config):
 
 def pytest_collection_modifyitems(config, items):
     # GPU tests need CUDA; on a machine without it they are skipped, not failed,
-    # only when the user explicitly deselected nothing. The driver selects with -m.
+    # only when the user explicitly deselected nothing. Runs select with -m.
     try:
         import torch
         has_cuda = torch.cuda.is_available()

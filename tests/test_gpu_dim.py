@@ -215,7 +215,7 @@ def test_fine_sequential_long_lines_chunked_tiles(ps, n, precision):
 
 
 def test_fine_sequential_on_recycled_device_memory(ps):
-    """Device buffers handed back by the driver keep their old contents: fill memory with
+    """Device memory that cudaMalloc hands back keeps its old contents: fill memory with
     all-ones words, release it, then create a problem (its status flags are carved from the
     same pool) and check that the fine propagator still runs every sweep."""
     junk = torch.full((1 << 26,), -1, dtype=torch.int32, device="cuda")
