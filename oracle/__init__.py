@@ -75,6 +75,11 @@ def _lib_handle():
                                           C.c_int, _D, _D, C.POINTER(C.c_int)]),
                 "or_parareal2": (C.c_int, [P, P, C.c_double, C.c_int, C.c_int, C.c_int, _D, C.c_double,
                                            C.c_int, _D, _D, C.POINTER(C.c_int)]),
+                "or_parareal_fine": (C.c_int, [P, P, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, _D,
+                                               C.c_double, C.c_int, _D, _D, C.POINTER(C.c_int)]),
+                "or_dr_step": (C.c_int, [P, C.c_double, C.c_int, _D]),
+                "or_propagate_dr": (C.c_int, [P, C.c_double, C.c_int, C.c_int, C.c_int, _D]),
+                "or_fine_sequential_dr": (C.c_int, [P, C.c_double, C.c_int, C.c_int, _D, _D]),
                 "or_adjoint": (C.c_int, [P, C.c_double, C.c_int, C.c_int, _D, _D, _D, _D, _D]),
                 "or_num_threads": (C.c_int, []),
                 "or_set_num_threads": (None, [C.c_int]),
@@ -212,11 +217,35 @@ def coarse_sequential(p: Problem, T, N, g, s, u0):
     return U.reshape((N + 1,) + p.shape)
 
 
-def parareal(p: Problem, T, N, g, s, u0, tol, max_iter=None, pG: Problem = None):
-    """Parareal/FIE-FIE (Sec. 3, Sec. 4).  Returns (U, history, iters):
+def dr_step(p: Problem, tau, u, t_end=0):
+    """One Douglas-Rachford step (eq. DR_method) with the source at fine time index t_end."""
+    x = p._state(u)
+    _check(_lib_handle().or_dr_step(C.byref(p._s), tau, t_end, _ptr(x)), "dr_step")
+    return x.reshape(p.shape)
+
+
+def propagate_dr(p: Problem, tau, nsteps, u, t0=0, tstride=1):
+    x = p._state(u)
+    _check(_lib_handle().or_propagate_dr(C.byref(p._s), tau, nsteps, t0, tstride, _ptr(x)), "propagate_dr")
+    return x.reshape(p.shape)
+
+
+def fine_sequential_dr(p: Problem, T, N, s, u0):
+    """Sequential solution by s DR steps per slice, at the coarse times T_n, n = 0..N."""
+    u0 = p._state(u0)
+    U = np.empty((N + 1) * p.size)
+    _check(_lib_handle().or_fine_sequential_dr(C.byref(p._s), T, N, s, _ptr(u0), _ptr(U)), "fine_sequential_dr")
+    return U.reshape((N + 1,) + p.shape)
+
+
+def parareal(p: Problem, T, N, g, s, u0, tol, max_iter=None, pG: Problem = None, fine="fie"):
+    """Parareal/FIE-FIE (Sec. 3, Sec. 4.1), or Parareal/FIE-DR with fine="dr" (Sec. 4.2: the
+    fine propagator takes s DR steps).  Returns (U, history, iters):
     U[n] = U_n^k at the final k, history[k-1] = max_n ||U_n^k - U_n^{k-1}||_inf.
     pG, when given, is the problem whose splitting the coarse propagator uses
     (Sec. 5.1 uses different DD decompositions for G and F)."""
+    if fine not in ("fie", "dr"):
+        raise ValueError("fine must be 'fie' or 'dr'")
     u0 = p._state(u0)
     if max_iter is None:
         max_iter = N
@@ -224,8 +253,8 @@ def parareal(p: Problem, T, N, g, s, u0, tol, max_iter=None, pG: Problem = None)
     hist = np.zeros(max(N, 1))
     it = C.c_int(0)
     pg = p if pG is None else pG
-    _check(_lib_handle().or_parareal2(C.byref(pg._s), C.byref(p._s), T, N, g, s, _ptr(u0), tol, max_iter,
-                                      _ptr(U), _ptr(hist), C.byref(it)), "parareal")
+    _check(_lib_handle().or_parareal_fine(C.byref(pg._s), C.byref(p._s), 0 if fine == "fie" else 1, T, N, g, s,
+                                          _ptr(u0), tol, max_iter, _ptr(U), _ptr(hist), C.byref(it)), "parareal")
     k = it.value
     return U.reshape((N + 1,) + p.shape), hist[:k].copy(), k
 

@@ -20,6 +20,8 @@
  *   - the fractional implicit Euler step (Sec. 2.2, eq. FIE_method);
  *   - the parareal iteration with G = FIE at step DeltaT and F = s FIE steps
  *     of step delta t (Sec. 3, the parareal recursion);
+ *   - the Douglas-Rachford step (Sec. 2.2, eq. DR_method) and the pairing
+ *     G = FIE, F = s DR steps (Parareal/FIE-DR, Sec. 4.2);
  *   - the discrete adjoint of the sequential fine solution (no counterpart in
  *     the paper; the transpose of the FIE steps above).
  *
@@ -393,8 +395,22 @@ int or_coarse_sequential(const or_problem* p, double T, int N, int g, int s, con
    pG and pF are the problems whose splittings the coarse and fine propagators
    use (the same problem, or two DD decompositions of it as in Sec. 5.1's
    scalability experiment).  Returns 0 and *iters = k, or a negative code. */
+/* fine propagator of slice n with method `fine`: 0 = FIE (eq. FIE_method), 1 = DR (eq. DR_method) */
+int or_propagate_dr(const or_problem* p, double tau, int nsteps, int t0, int tstride, double* u);
+static int prop_F_method(const or_problem* p, int fine, double T, int N, int s, int n, double* u) {
+  if (fine == 1) return or_propagate_dr(p, T / N / s, s, n * s, 1, u);
+  return prop_F(p, T, N, s, n, u);
+}
+int or_parareal_fine(const or_problem* pG, const or_problem* pF, int fine, double T, int N, int g, int s,
+                     const double* u0, double tol, int max_iter, double* U, double* hist, int* iters);
 int or_parareal2(const or_problem* pG, const or_problem* pF, double T, int N, int g, int s,
                  const double* u0, double tol, int max_iter, double* U, double* hist, int* iters) {
+  return or_parareal_fine(pG, pF, 0, T, N, g, s, u0, tol, max_iter, U, hist, iters);
+}
+/* Parareal with G = FIE on pG and F = `fine` (0 FIE, 1 DR) on pF. */
+int or_parareal_fine(const or_problem* pG, const or_problem* pF, int fine, double T, int N, int g, int s,
+                     const double* u0, double tol, int max_iter, double* U, double* hist, int* iters) {
+  if (fine != 0 && fine != 1) return -3;
   long nt = n_total(pF);
   if (g < 1 || s < 1 || N < 1 || s % g || n_total(pG) != nt) return -3;
   double* Fv = malloc(sizeof(double) * nt * N);
@@ -408,7 +424,7 @@ int or_parareal2(const or_problem* pG, const or_problem* pF, double T, int N, in
     ++k;
     for (int n = 0; n < N && !rc; ++n) {          /* F(U_n^{k-1}) and G(U_n^{k-1}) */
       memcpy(Fv + n * nt, U + n * nt, sizeof(double) * nt);
-      rc |= prop_F(pF, T, N, s, n, Fv + n * nt);
+      rc |= prop_F_method(pF, fine, T, N, s, n, Fv + n * nt);
       memcpy(Gold + n * nt, U + n * nt, sizeof(double) * nt);
       rc |= prop_G(pG, T, N, g, s, n, Gold + n * nt);
     }
@@ -435,6 +451,56 @@ int or_parareal2(const or_problem* pG, const or_problem* pF, double T, int N, in
 int or_parareal(const or_problem* p, double T, int N, int g, int s, const double* u0, double tol,
                 int max_iter, double* U, double* hist, int* iters) {
   return or_parareal2(p, p, T, N, g, s, u0, tol, max_iter, U, hist, iters);
+}
+
+/* ------------------------------------------------------------------ */
+/* Douglas-Rachford step (eq. DR_method) and Parareal/FIE-DR (Sec. 4.2) */
+/* ------------------------------------------------------------------ */
+/* u <- U_{n+1} of eq. DR_method from U_n = u, source at fine time index t_end:
+     U_{n,0} = (I + tau A) U_n + tau F_{n+1},   A = A_1 + ... + A_M,
+     (I - tau A_j) U_{n,j} = U_{n,j-1} - tau A_j U_n,   j = 1..M,
+     U_{n+1} = U_{n,M}. */
+int or_dr_step(const or_problem* p, double tau, int t_end, double* u) {
+  long nt = n_total(p);
+  int M = or_num_substeps(p);
+  double* AU = malloc(sizeof(double) * nt * M); /* A_j U_n, j = 1..M */
+  double* v = malloc(sizeof(double) * nt);
+  if (!AU || !v) { free(AU); free(v); return -4; }
+  for (int j = 0; j < M; ++j) or_apply_A(p, j, u, AU + j * nt);
+  double ft = p->src ? time_factor(p, t_end) : 0.0;
+  for (long i = 0; i < nt; ++i) {
+    double s = u[i];
+    for (int j = 0; j < M; ++j) s += tau * AU[j * nt + i];
+    if (p->src) s += tau * p->src[i] * ft;
+    v[i] = s;
+  }
+  int rc = 0;
+  for (int j = 0; j < M && !rc; ++j) {
+    for (long i = 0; i < nt; ++i) v[i] -= tau * AU[j * nt + i];
+    rc = or_substep_solve(p, j, tau, v);
+  }
+  if (!rc) memcpy(u, v, sizeof(double) * nt);
+  free(AU); free(v);
+  return rc;
+}
+/* nsteps DR steps of size tau; step q ends at fine time index t0 + (q+1)*tstride */
+int or_propagate_dr(const or_problem* p, double tau, int nsteps, int t0, int tstride, double* u) {
+  for (int q = 0; q < nsteps; ++q) {
+    int rc = or_dr_step(p, tau, t0 + (q + 1) * tstride, u);
+    if (rc) return rc;
+  }
+  return 0;
+}
+/* sequential fine solution with s DR steps per slice, at the coarse times */
+int or_fine_sequential_dr(const or_problem* p, double T, int N, int s, const double* u0, double* U) {
+  long nt = n_total(p);
+  memcpy(U, u0, sizeof(double) * nt);
+  for (int n = 0; n < N; ++n) {
+    memcpy(U + (n + 1) * nt, U + n * nt, sizeof(double) * nt);
+    int rc = or_propagate_dr(p, T / N / s, s, n * s, 1, U + (n + 1) * nt);
+    if (rc) return rc;
+  }
+  return 0;
 }
 
 /* ------------------------------------------------------------------ */
