@@ -69,6 +69,12 @@ extern "C" {
 #define PS_COARSE_FP64 0    /* G in FP64, correction written as F + (G_new - G_old) (Sec. 3) */
 #define PS_COARSE_DELTA32 1 /* G's linear part in FP32 on the increment, see above */
 
+/* Fine propagator (ps_params.fine_method).  PS_FINE_DR takes s Douglas-Rachford steps
+ * (Sec. 2.2, eq. DR_method) per slice: Parareal/FIE-DR of Sec. 4.2, G staying FIE.
+ * Dimensional splitting and PS_PREC_FP64 only; not in batches or adjoints. */
+#define PS_FINE_FIE 0 /* fractional implicit Euler (eq. FIE_method) */
+#define PS_FINE_DR 1  /* Douglas-Rachford (eq. DR_method) */
+
 #define PS_SCHED_AUTO 0   /* library default for dimensional line solves */
 #define PS_SCHED_THOMAS 1 /* one thread per line, Thomas/LDL^T recurrences */
 #define PS_SCHED_PCR 2    /* one warp per line, parallel cyclic reduction */
@@ -132,6 +138,7 @@ typedef struct {
   int coarse;              /* PS_COARSE_FP64 (0) or PS_COARSE_DELTA32 */
   int tile_lines_per_thread; /* fine line solves (FP32 tiles of 32+ slots): lines a thread solves
                                 side by side, 1 or 2; 0 = auto (1) */
+  int fine_method;         /* PS_FINE_FIE (0) or PS_FINE_DR */
 } ps_params;
 
 /* fine, coarse: splittings of the same operator used by F and G (coarse = NULL: use

@@ -26,6 +26,7 @@ PS_SPLIT_DIM, PS_SPLIT_DD = 0, 1
 PS_PREC_FP64, PS_PREC_MIXED = 0, 1
 PS_SCHED_AUTO, PS_SCHED_THOMAS, PS_SCHED_PCR = 0, 1, 2
 PS_COARSE_FP64, PS_COARSE_DELTA32 = 0, 1
+PS_FINE_FIE, PS_FINE_DR = 0, 1
 PS_NOALLOC_MAX_UNKNOWNS = 1 << 20
 
 _lock = threading.Lock()
@@ -45,7 +46,8 @@ class _DD(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("precision", C.c_int), ("schedule", C.c_int), ("timing", C.c_int), ("dd_slices_per_block", C.c_int),
                 ("tile_positions", C.c_int), ("tile_pipeline", C.c_int), ("tile_slots", C.c_int),
-                ("tol_mode", C.c_int), ("coarse", C.c_int), ("tile_lines_per_thread", C.c_int)]
+                ("tol_mode", C.c_int), ("coarse", C.c_int), ("tile_lines_per_thread", C.c_int),
+                ("fine_method", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -217,16 +219,19 @@ class Problem:
 
     def __init__(self, fine: Splitting, T, N, g, s, coarse: Splitting = None, precision="fp64",
                  schedule=PS_SCHED_AUTO, timing=False, dd_slices_per_block=0, tile_positions=0, tile_pipeline=0,
-                 tile_slots=0, tol_mode=0, coarse_mode="fp64", tile_lines_per_thread=0, stream=None):
+                 tile_slots=0, tol_mode=0, coarse_mode="fp64", tile_lines_per_thread=0, fine_method="fie",
+                 stream=None):
         self.fine, self.coarse = fine, coarse
         self.grid = fine.op.grid
         self.N = int(N)
         if coarse_mode not in ("fp64", "delta32"):
             raise ValueError("coarse_mode must be 'fp64' or 'delta32'")
+        if fine_method not in ("fie", "dr"):
+            raise ValueError("fine_method must be 'fie' or 'dr'")
         prm = _Params(PS_PREC_FP64 if precision == "fp64" else PS_PREC_MIXED, int(schedule), int(timing),
                       int(dd_slices_per_block), int(tile_positions), int(tile_pipeline), int(tile_slots),
                       int(tol_mode), PS_COARSE_FP64 if coarse_mode == "fp64" else PS_COARSE_DELTA32,
-                      int(tile_lines_per_thread))
+                      int(tile_lines_per_thread), PS_FINE_FIE if fine_method == "fie" else PS_FINE_DR)
         h = _VP()
         check(lib().ps_problem_create(fine._h, None if coarse is None else coarse._h, float(T), int(N), int(g),
                                       int(s), C.byref(prm), _stream(stream), C.byref(h)))

@@ -293,6 +293,7 @@ int ps_batch_create(ps_problem* const* problems, int count, uintptr_t stream, ps
         throw Error(PS_ERR_UNSUPPORTED, "batches run the FP32 line-solve form (PS_PREC_MIXED)");
       if (p->gs != 1) throw Error(PS_ERR_UNSUPPORTED, "batches use one coarse step per slice");
       if (p->delta32) throw Error(PS_ERR_UNSUPPORTED, "batches run the FP64 coarse propagator");
+      if (p->dr) throw Error(PS_ERR_UNSUPPORTED, "batches run the FIE fine propagator");
       if (p->op->src.p) throw Error(PS_ERR_UNSUPPORTED, "batches hold problems without a source term");
       const bool var = p->op->a.p != nullptr;
       if (i == 0) b->var = var;

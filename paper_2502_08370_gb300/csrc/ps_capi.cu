@@ -216,8 +216,50 @@ void run_F_tiles(ps_problem* p, int n_first, int nsl, const double* in, double* 
   p->launches++;
 }
 
+// F as s Douglas-Rachford steps (eq. DR_method) on nsl consecutive slices of the natural
+// layout: per step the products tau A_j U_n, the stage U_{n,0} = U_n + sum_j tau A_j U_n + tau f,
+// then for every j the right-hand side U_{n,j-1} - tau A_j U_n and the substep solve in place.
+void run_F_dr(ps_problem* p, int n_first, int nsl, const double* in, double* out, cudaStream_t st) {
+  Prop& P = p->F;
+  const int M = P.sp->M;
+  const long long total = (long long)nsl * p->g.nt;
+  const double dnt = (double)total;
+  const double c_over_M = p->op->c / p->g.dim;
+  for (int q = 0; q < P.steps; ++q) {
+    const double* u = q == 0 ? in : out;
+    for (int j = 0; j < M; ++j) {
+      p->kt.begin(st);
+      dr_apply_Aj(p->g, nsl, j, p->op->a.p, c_over_M, P.tau, u, p->dr_TA.p + j * total, st);
+      if (p->kt.on) p->kt.end(std::string("F.drA.") + kAxis[j] + ".f64", dnt * 16.0, dnt * 8.0);
+      p->launches++;
+    }
+    SourceArgs sa = source_for(p, P, n_first * p->fs + (q + 1) * P.tstride, p->fs);
+    p->kt.begin(st);
+    dr_stage0(p->g, nsl, u, p->dr_TA.p, M, sa, out, st);
+    if (p->kt.on) p->kt.end("F.dr0.f64", dnt * (16.0 + 8.0 * M), 0.0);
+    p->launches++;
+    for (int j = 0; j < M; ++j) {
+      p->kt.begin(st);
+      dr_subtract(p->g, nsl, out, p->dr_TA.p + j * total, st);
+      if (p->kt.on) p->kt.end("F.drrhs.f64", dnt * 24.0, 0.0);
+      p->launches++;
+      double bytes = 0, flops = 0;
+      if (p->kt.on) sweep_cost(p, *P.dim[j], nsl, 8, 8, 8, false, 0, &bytes, &flops);
+      p->kt.begin(st);
+      sweep_dim<double, double>(p->g, nsl, *P.dim[j], false, out, out, SourceArgs{}, CorrArgs{}, nullptr, st);
+      if (p->kt.on) p->kt.end(std::string("F.") + kAxis[j] + ".f64", bytes, flops);
+      p->launches++;
+    }
+  }
+  p->updates += (double)nsl * P.steps * (double)p->g.nt;
+}
+
 void run_F(ps_problem* p, int n_first, int nsl, const double* in, double* out, cudaStream_t st) {
   Prop& P = p->F;
+  if (p->dr) {
+    run_F_dr(p, n_first, nsl, in, out, st);
+    return;
+  }
   if (P.sp->kind == PS_SPLIT_DIM) {
     if (P.f32) run_F_tiles<float>(p, n_first, nsl, in, out, st);
     else run_F_tiles<double>(p, n_first, nsl, in, out, st);
@@ -611,6 +653,10 @@ int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, doub
     cudaStream_t st = S(stream);
     const bool mixed = p->prm.precision == PS_PREC_MIXED;
     PS_REQUIRE(p->prm.coarse == PS_COARSE_FP64 || p->prm.coarse == PS_COARSE_DELTA32, "unknown coarse mode");
+    PS_REQUIRE(p->prm.fine_method == PS_FINE_FIE || p->prm.fine_method == PS_FINE_DR, "unknown fine method");
+    p->dr = p->prm.fine_method == PS_FINE_DR;
+    if (p->dr && (fine->kind != PS_SPLIT_DIM || p->prm.precision != PS_PREC_FP64))
+      throw Error(PS_ERR_UNSUPPORTED, "the Douglas-Rachford fine propagator runs with the dimensional splitting in FP64");
     p->delta32 = p->prm.coarse == PS_COARSE_DELTA32;
     if (p->delta32 && (fine->kind != PS_SPLIT_DIM || coarse->kind != PS_SPLIT_DIM))
       throw Error(PS_ERR_UNSUPPORTED, "the FP32 coarse increment form needs the dimensional splitting");
@@ -631,6 +677,7 @@ int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, doub
       p->Gold.alloc((size_t)N * nt);
     }
     p->gtmp.alloc((size_t)nt);
+    if (p->dr) p->dr_TA.alloc((size_t)fine->M * N * nt);
     p->inc.alloc(1);
     p->tmo.alloc(1);
     PS_CUDA(cudaMemset(p->tmo.p, 0, sizeof(int)));
@@ -991,6 +1038,7 @@ int ps_adjoint_vjp(ps_problem* p, const double* gN_dev, double tol, int max_iter
     PS_REQUIRE(p && gN_dev && grad_u0_dev, "null argument");
     PS_REQUIRE(p->have_forward, "ps_adjoint_vjp needs a preceding ps_run_parareal on this problem");
     if (p->delta32) throw Error(PS_ERR_UNSUPPORTED, "the adjoint runs with the FP64 coarse propagator");
+    if (p->dr) throw Error(PS_ERR_UNSUPPORTED, "the adjoint differentiates the FIE fine propagator");
     if (grad_a_dev) {
       if (p->F.sp->kind != PS_SPLIT_DIM || p->G.sp->kind != PS_SPLIT_DIM)
         throw Error(PS_ERR_UNSUPPORTED, "the coefficient gradient is implemented for the dimensional splitting");
