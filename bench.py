@@ -7,7 +7,8 @@ over all slices, coarse chain with the fused correction, increment test) until
 the stopping rule fires.  Inputs are resident in HBM before the timed region.
 
 value    unknown-updates/s over the K timed solves (all ranks): interior unknowns
-         advanced by one FIE step, summed over the fine and coarse work executed.
+         advanced by one step (FIE; DR for the fine steps with --fine dr), summed over the
+         fine and coarse work executed.
 e2e      the same through ps_run_parareal_host with the initial state in pinned host
          memory and U_N copied back every step.
 roofline the dominant kernel's algorithmic bytes (or flops) per launch over its
@@ -170,20 +171,26 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def make_problem(ps, torch, cfg, precision, timing, coarse_mode="fp64"):
+def make_problem(ps, torch, cfg, precision, timing, coarse_mode="fp64", fine_method="fie"):
     grid = ps.Grid(cfg["n"])
     a = None if cfg["a"] is None else torch.as_tensor(cfg["a"]).cuda()
     src = None if cfg["src"] is None else torch.as_tensor(cfg["src"]).cuda()
     op = ps.Operator(grid, a=a, c=cfg["c"], src=src, src_t=cfg["src_t"])
     sp = ps.Splitting(op, cfg["split"], cfg.get("boxes", (1, 1)), cfg.get("overlap", 0.0))
     prob = ps.Problem(sp, cfg["T"], cfg["N"], cfg["g"], cfg["s"], precision=precision, timing=timing,
-                      coarse_mode=coarse_mode)
+                      coarse_mode=coarse_mode, fine_method=fine_method)
     prob._keep = (grid, op, sp, a, src)
     return prob
 
 
-def cpu_sample(cfg, seconds):
-    """The oracle, as it stands, on a bounded sample: whole fine FIE steps of one slice."""
+def fine_steps_fn(fine):
+    import oracle as orc
+    return (orc.propagate_dr, "DR") if fine == "dr" else (orc.propagate, "FIE")
+
+
+def cpu_sample(cfg, seconds, fine="fie"):
+    """The oracle, as it stands, on a bounded sample: whole fine steps (FIE, or DR for
+    Parareal/FIE-DR) of one slice."""
     import numpy as np
 
     import oracle as orc
@@ -192,21 +199,23 @@ def cpu_sample(cfg, seconds):
     tau = cfg["T"] / cfg["N"] / cfg["s"]
     u = np.ascontiguousarray(cfg["u0"], dtype=np.float64)
     t = time.perf_counter()
-    u = orc.propagate(orp, tau, 1, u, t0=0)
+    step_fn, kind = fine_steps_fn(fine)
+    u = step_fn(orp, tau, 1, u, t0=0)
     one = time.perf_counter() - t
     steps = max(1, int(seconds / max(one, 1e-6)))
     t = time.perf_counter()
-    orc.propagate(orp, tau, steps, u, t0=1)
+    step_fn(orp, tau, steps, u, t0=1)
     dt = time.perf_counter() - t
     nt = int(np.prod(cfg["n"]))
     grid = "x".join(str(v) for v in cfg["n"])
     return {"value": steps * nt / dt, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
-            "sample": f"{steps} fine FIE steps of one {grid} slice ({len(cfg['n'])} line-solve substeps each), "
+            "sample": f"{steps} fine {kind} steps of one {grid} slice ({len(cfg['n'])} line-solve substeps each), "
                       f"{dt:.1f} s"}
 
 
 def run_reference(args, cfg, rank, ws):
-    """The oracle as it stands: each step is one fine FIE step of one slice of the workload."""
+    """The oracle as it stands: each step is one fine step (FIE, or DR with --fine dr) of one
+    slice of the workload."""
     if rank != 0:
         return
     import numpy as np
@@ -217,11 +226,12 @@ def run_reference(args, cfg, rank, ws):
                       boxes=cfg.get("boxes", (1, 1)), overlap=cfg.get("overlap", 0.0))
     tau = cfg["T"] / cfg["N"] / cfg["s"]
     u = np.ascontiguousarray(cfg["u0"], dtype=np.float64)
+    step_fn, kind = fine_steps_fn(getattr(args, "fine", "fie"))
     for w in range(args.warmup):
-        u = orc.propagate(orp, tau, 1, u, t0=w)
+        u = step_fn(orp, tau, 1, u, t0=w)
     t = time.perf_counter()
     for k in range(args.steps):
-        u = orc.propagate(orp, tau, 1, u, t0=args.warmup + k)
+        u = step_fn(orp, tau, 1, u, t0=args.warmup + k)
     dt = time.perf_counter() - t
     nt = int(np.prod(cfg["n"]))
     value = args.steps * nt / dt
@@ -231,7 +241,7 @@ def run_reference(args, cfg, rank, ws):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(args, cfg),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
-                             "sample": f"each step: one fine FIE step ({len(cfg['n'])} line-solve substeps) of one "
+                             "sample": f"each step: one fine {kind} step ({len(cfg['n'])} line-solve substeps) of one "
                                        f"{grid} slice of the workload"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -250,6 +260,7 @@ def config_of(args, cfg):
     out = {"workload": args.workload, "grid": grid, "splitting": cfg["split"], "N_slices": cfg["N"],
            "coarse_steps": cfg["g"], "fine_steps": cfg["s"], "T": cfg["T"], "tol": cfg["tol"],
            "precision": args.precision, "coarse": getattr(args, "coarse", "fp64"),
+           "fine": "dr" if getattr(args, "fine", "fie") == "dr" else "fie",
            "l2": (f"inputs larger than L2 ({gb:.1f} GB of slice states streamed per step)" if gb > 0.2 else
                   f"working set {gb * 1e3:.0f} MB fits in L2: latency-bound case, no roofline claim")}
     if cfg["split"] == "dd":
@@ -444,6 +455,9 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 time-to-tolerance run")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--fd-dirs", type=int, default=20, help="finite-difference directions (adjoint workload)")
+    ap.add_argument("--fine", default="fie", choices=["fie", "dr"],
+                    help="fine propagator: FIE steps, or Douglas-Rachford steps (Parareal/FIE-DR, FP64, "
+                         "dimensional splitting)")
     ap.add_argument("--slices", type=int, default=0,
                     help="override the workload's slice count N (small-footprint profiling runs; named in config)")
     args = ap.parse_args()
@@ -452,6 +466,17 @@ def main():
     cfg = workload(args.workload)
     if args.slices > 0 and "batch" not in cfg:
         cfg["N"] = args.slices
+
+    if args.workload in ("heat2d_63", "dd2d_1023", "adjoint2d_511"):
+        args.precision = "fp64"  # these workloads are specified in FP64
+        args.no_compare = True
+    if args.fine == "dr":
+        if cfg.get("split") != "dim" or "batch" in cfg or args.workload == "adjoint2d_511":
+            raise SystemExit("--fine dr runs the single-problem dimensional-splitting workloads")
+        args.precision = "fp64"  # the DR fine propagator runs in FP64
+        args.no_compare = True
+    if args.precision == "fp64" or cfg.get("split") == "dd":
+        args.coarse = "fp64"
 
     if args.impl == "reference":
         rank, ws = dist_setup("gloo")
@@ -472,17 +497,12 @@ def main():
         import torch.distributed as dist
         dist.barrier()
     ps.lib()
-    if args.workload in ("heat2d_63", "dd2d_1023", "adjoint2d_511"):
-        args.precision = "fp64"  # these workloads are specified in FP64
-        args.no_compare = True
-    if args.precision == "fp64" or cfg.get("split") == "dd":
-        args.coarse = "fp64"
     if args.workload == "batch256":
         return run_batch(args, cfg, ps, torch, rank, ws)
     if args.workload == "adjoint2d_511":
         return run_adjoint(args, cfg, ps, torch, rank, ws)
 
-    prob = make_problem(ps, torch, cfg, args.precision, timing=2, coarse_mode=args.coarse)
+    prob = make_problem(ps, torch, cfg, args.precision, timing=2, coarse_mode=args.coarse, fine_method=args.fine)
     max_iter = cfg.get("max_iter", 0)
     u0 = torch.as_tensor(cfg["u0"]).cuda()
     stream = torch.cuda.current_stream()
@@ -529,7 +549,8 @@ def main():
     pk, pk_kind = load_peaks()
     dom_name, dom = max(kern.items(), key=lambda kv: kv[1]["ms"])
     per_launch_ms = dom["ms"] / dom["launches"]
-    is_f64 = dom_name.endswith("f64") or "f64+" in dom_name
+    # FP64 sweeps and the DR stencil are bound by the FP64 issue rate; the DR add pass by HBM
+    is_f64 = (dom_name.endswith("f64") or "f64+" in dom_name) and not dom_name.startswith("F.dradd")
     if is_f64:
         achieved = dom["flops"] / dom["launches"] / (per_launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -619,7 +640,7 @@ def main():
     if rank == 0 and ws == 1 and args.cpu_seconds > 0:
         import oracle as orc
         orc.build()
-        cpu = cpu_sample(cfg, args.cpu_seconds)
+        cpu = cpu_sample(cfg, args.cpu_seconds, args.fine)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -217,39 +217,36 @@ void run_F_tiles(ps_problem* p, int n_first, int nsl, const double* in, double* 
 }
 
 // F as s Douglas-Rachford steps (eq. DR_method) on nsl consecutive slices of the natural
-// layout: per step the products tau A_j U_n, the stage U_{n,0} = U_n + sum_j tau A_j U_n + tau f,
-// then for every j the right-hand side U_{n,j-1} - tau A_j U_n and the substep solve in place.
+// layout, in increment form: W_0 = tau (A U_n + f), the M substep solves (I - tau A_j) in
+// place on W (the printed right-hand sides U_{n,j-1} - tau A_j U_n minus (I - tau A_j) U_n),
+// then U_{n+1} = U_n + W_M.
 void run_F_dr(ps_problem* p, int n_first, int nsl, const double* in, double* out, cudaStream_t st) {
   Prop& P = p->F;
   const int M = P.sp->M;
-  const long long total = (long long)nsl * p->g.nt;
-  const double dnt = (double)total;
-  const double c_over_M = p->op->c / p->g.dim;
+  const double nt = (double)p->g.nt;
+  const double dnt = (double)nsl * nt;
+  double* W = p->dr_W.p;
   for (int q = 0; q < P.steps; ++q) {
     const double* u = q == 0 ? in : out;
-    for (int j = 0; j < M; ++j) {
-      p->kt.begin(st);
-      dr_apply_Aj(p->g, nsl, j, p->op->a.p, c_over_M, P.tau, u, p->dr_TA.p + j * total, st);
-      if (p->kt.on) p->kt.end(std::string("F.drA.") + kAxis[j] + ".f64", dnt * 16.0, dnt * 8.0);
-      p->launches++;
-    }
     SourceArgs sa = source_for(p, P, n_first * p->fs + (q + 1) * P.tstride, p->fs);
     p->kt.begin(st);
-    dr_stage0(p->g, nsl, u, p->dr_TA.p, M, sa, out, st);
-    if (p->kt.on) p->kt.end("F.dr0.f64", dnt * (16.0 + 8.0 * M), 0.0);
+    dr_increment(p->g, nsl, p->op->a.p, p->op->c, P.tau, u, W, sa, st);
+    if (p->kt.on)
+      p->kt.end("F.drW.f64", dnt * 16.0 + (p->op->a.p ? nt * 8.0 : 0.0) + (sa.src ? nt * 8.0 : 0.0),
+                dnt * (1.0 + 6.0 * M + (sa.src ? 3.0 : 0.0)));
     p->launches++;
     for (int j = 0; j < M; ++j) {
-      p->kt.begin(st);
-      dr_subtract(p->g, nsl, out, p->dr_TA.p + j * total, st);
-      if (p->kt.on) p->kt.end("F.drrhs.f64", dnt * 24.0, 0.0);
-      p->launches++;
       double bytes = 0, flops = 0;
       if (p->kt.on) sweep_cost(p, *P.dim[j], nsl, 8, 8, 8, false, 0, &bytes, &flops);
       p->kt.begin(st);
-      sweep_dim<double, double>(p->g, nsl, *P.dim[j], false, out, out, SourceArgs{}, CorrArgs{}, nullptr, st);
+      sweep_dim<double, double>(p->g, nsl, *P.dim[j], false, W, W, SourceArgs{}, CorrArgs{}, nullptr, st);
       if (p->kt.on) p->kt.end(std::string("F.") + kAxis[j] + ".f64", bytes, flops);
       p->launches++;
     }
+    p->kt.begin(st);
+    dr_add(p->g, nsl, u, W, out, st);
+    if (p->kt.on) p->kt.end("F.dradd.f64", dnt * 24.0, dnt);
+    p->launches++;
   }
   p->updates += (double)nsl * P.steps * (double)p->g.nt;
 }
@@ -677,7 +674,7 @@ int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, doub
       p->Gold.alloc((size_t)N * nt);
     }
     p->gtmp.alloc((size_t)nt);
-    if (p->dr) p->dr_TA.alloc((size_t)fine->M * N * nt);
+    if (p->dr) p->dr_W.alloc((size_t)N * nt);
     p->inc.alloc(1);
     p->tmo.alloc(1);
     PS_CUDA(cudaMemset(p->tmo.p, 0, sizeof(int)));

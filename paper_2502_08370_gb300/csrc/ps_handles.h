@@ -121,7 +121,7 @@ struct ps_problem {
   ps::DevBuf<double> U, Fout, Gold, gtmp;
   bool delta32 = false;       // coarse increment form in FP32 (PS_COARSE_DELTA32); no Gold then
   bool dr = false;            // fine propagator: Douglas-Rachford steps (PS_FINE_DR)
-  ps::DevBuf<double> dr_TA;   // its products tau A_j U_n, M x N states
+  ps::DevBuf<double> dr_W;    // its increments U_{n,j} - U_n, N states
   ps::DevBuf<float> d32, g32; // its increment U_n^k - U_n^{k-1} and coarse working state
   ps::DevBuf<float> W;      // fine working state, slice-interleaved (FP32 line solves)
   ps::DevBuf<double> W64;   // same for FP64 line solves

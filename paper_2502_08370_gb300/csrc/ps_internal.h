@@ -153,13 +153,12 @@ void sweep_dim(const Geom& g, int nslices, const LineFactors& f, bool fp32, cons
 template <typename Tin>
 void sweep_x_warp(const Geom& g, const LineFactors& f, const Tin* in, float* out, const SourceArgs& sa,
                   cudaStream_t st);
-// Douglas-Rachford fine step pieces (ps_dr.cu), nsl consecutive states of the natural layout:
-// out = tau A_j u; v = u + sum_j TA_j + tau f (TA_j at TA + j * nsl * nt); v -= TA.
-void dr_apply_Aj(const Geom& g, int nsl, int j, const double* a_nodal, double c_over_M, double tau, const double* u,
-                 double* out, cudaStream_t st);
-void dr_stage0(const Geom& g, int nsl, const double* u, const double* TA, int M, const SourceArgs& sa, double* v,
-               cudaStream_t st);
-void dr_subtract(const Geom& g, int nsl, double* v, const double* TA, cudaStream_t st);
+// Douglas-Rachford fine step in increment form (ps_dr.cu), nsl consecutive states of the
+// natural layout: w = tau (A u + f) (A with reaction c, f from sa at t0 + slice * tstride);
+// out = u + w (out may alias u).
+void dr_increment(const Geom& g, int nsl, const double* a_nodal, double c, double tau, const double* u, double* w,
+                  const SourceArgs& sa, cudaStream_t st);
+void dr_add(const Geom& g, int nsl, const double* u, const double* w, double* out, cudaStream_t st);
 // dst <- src with the increment max |src - dst| (and per-slice stats); when dout is set it
 // also receives src - dst rounded to FP32 (the increment the coarse increment form propagates).
 void copy_with_increment(long long nt, const double* src, double* dst, unsigned long long* inc, int* nonfinite,
