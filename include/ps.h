@@ -218,7 +218,8 @@ int ps_run_coarse_sequential_noalloc(ps_problem* p, const double* u0_dev, double
 /* Building blocks on one state x_dev (in place), for testing the kernels.
  * which = 0: fine propagator's step size and splitting, 1: coarse.
  * ps_substep_solve: x <- (I - tau A_m)^{-1} x (one internal stage of eq. FIE_method).
- * ps_propagate: nsteps FIE steps; step q ends at fine time index t0 + (q+1)*tstride. */
+ * ps_propagate: nsteps FIE steps (also when params.fine_method is PS_FINE_DR); step q ends at
+ * fine time index t0 + (q+1)*tstride. */
 int ps_substep_solve(ps_problem* p, int which, int m, double* x_dev, uintptr_t stream);
 int ps_propagate(ps_problem* p, int which, int nsteps, int t0, int tstride, double* x_dev, uintptr_t stream);
 
