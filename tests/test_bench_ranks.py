@@ -59,3 +59,22 @@ def test_reference_arm_under_torchrun_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_dr_times_douglas_rachford_steps():
+    """--fine dr: the reference arm times the oracle's DR steps, and the line's config says so
+    (FP64, fine = dr) before any GPU is touched."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "heat2d_63",
+           "--fine", "dr", "--steps", "2", "--warmup", "3"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    assert d["config"]["fine"] == "dr" and d["config"]["precision"] == "fp64"
+    assert "DR step" in d["cpu_baseline"]["sample"] and d["value"] > 0
+
+
+def test_fine_dr_refuses_workloads_without_the_dimensional_splitting():
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "dd2d_1023",
+           "--fine", "dr", "--steps", "1", "--warmup", "3"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode != 0 and "dimensional-splitting" in (r.stderr + r.stdout)
