@@ -75,9 +75,11 @@ extern "C" {
 #define PS_FINE_FIE 0 /* fractional implicit Euler (eq. FIE_method) */
 #define PS_FINE_DR 1  /* Douglas-Rachford (eq. DR_method) */
 
-#define PS_SCHED_AUTO 0   /* library default for dimensional line solves */
-#define PS_SCHED_THOMAS 1 /* one thread per line, Thomas/LDL^T recurrences */
-#define PS_SCHED_PCR 2    /* one warp per line, parallel cyclic reduction */
+#define PS_SCHED_AUTO 0   /* library default for dimensional line solves (= PS_SCHED_THOMAS) */
+#define PS_SCHED_THOMAS 1 /* Thomas/LDL^T recurrences: one thread per line (fine tiles, coarse
+                             y/z sweeps), segmented warp scans for the coarse FP32 x-sweep */
+#define PS_SCHED_PCR 2    /* parallel cyclic reduction: not built, ps_problem_create returns
+                             PS_ERR_UNSUPPORTED */
 
 typedef struct ps_grid ps_grid;
 typedef struct ps_operator ps_operator;
@@ -124,7 +126,8 @@ int ps_splitting_destroy(ps_splitting* sp);
 /* ---- parareal problem (Sec. 3) ----------------------------------------------------------- */
 typedef struct {
   int precision; /* PS_PREC_FP64 or PS_PREC_MIXED */
-  int schedule;  /* PS_SCHED_* for the fine line solves */
+  int schedule;  /* PS_SCHED_AUTO or PS_SCHED_THOMAS (PS_SCHED_PCR: PS_ERR_UNSUPPORTED; other
+                    values: PS_ERR_INVALID) */
   int timing;    /* 1: per-phase CUDA events (ps_problem_stats); 2: also per-kernel
                     events (ps_problem_kernel_times) */
   int dd_slices_per_block; /* DD subdomain solves: time slices per CTA (1, 2 or 4); 0 = 2 */

@@ -645,6 +645,10 @@ int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, doub
     p->fs = f_steps;
     if (params) p->prm = *params;
     PS_REQUIRE(p->prm.precision == PS_PREC_FP64 || p->prm.precision == PS_PREC_MIXED, "unknown precision");
+    PS_REQUIRE(p->prm.schedule >= PS_SCHED_AUTO && p->prm.schedule <= PS_SCHED_PCR, "unknown schedule");
+    if (p->prm.schedule == PS_SCHED_PCR)
+      throw Error(PS_ERR_UNSUPPORTED, "the parallel-cyclic-reduction schedule is not built; the line solves run "
+                                      "the Thomas/LDL^T recurrences (PS_SCHED_AUTO or PS_SCHED_THOMAS)");
     if (p->op->src_t.p)
       PS_REQUIRE(p->op->src_t_len >= N * f_steps + 1, "src_t must cover the fine times 0..N*f_steps");
     cudaStream_t st = S(stream);

@@ -180,6 +180,12 @@ def test_invalid_arguments_are_rejected(ps):
     assert e.value.code == 1
     with pytest.raises(ps.PsError):
         ps.Problem(sp, -1.0, 4, 1, 8)
+    with pytest.raises(ps.PsError) as e:
+        ps.Problem(sp, 1.0, 4, 1, 8, schedule=ps.PS_SCHED_PCR)  # not built
+    assert e.value.code == 6
+    with pytest.raises(ps.PsError) as e:
+        ps.Problem(sp, 1.0, 4, 1, 8, schedule=7)
+    assert e.value.code == 1
     prob = ps.Problem(sp, 1.0, 4, 1, 8)
     with pytest.raises(ps.PsError):
         prob.state(5)
