@@ -48,6 +48,8 @@ class _Problem(C.Structure):
         ("src", C.POINTER(C.c_double)), ("src_t", C.POINTER(C.c_double)),
         ("src_t_len", C.c_int), ("split", C.c_int),
         ("boxes_x", C.c_int), ("boxes_y", C.c_int), ("overlap", C.c_double),
+        ("d12", C.POINTER(C.c_double)), ("src2", C.POINTER(C.c_double)), ("src2_t", C.POINTER(C.c_double)),
+        ("src2_t_len", C.c_int),
     ]
 
 
@@ -101,7 +103,8 @@ def _f64(x):
 
 
 class Problem:
-    """Model problem of Sec. 2.1 with D = a(x) I, homogeneous Dirichlet data.
+    """Model problem of Sec. 2.1 with D = a(x) I, or in 2-D the full tensor
+    D = [[a, d12], [d12, a]] of Sec. 5.2; homogeneous Dirichlet data.
 
     n      : interior nodes per direction, (nx, ny) or (nx, ny, nz); h_i = 1/(n_i+1)
     a      : nodal diffusion on the (n+2)^d grid incl. boundary (x fastest), or None (a = 1)
@@ -110,9 +113,13 @@ class Problem:
     src_t  : time factor of the source at fine times t_j = j*dt (f = src(x) src_t(t)), or None
     split  : "dim" (x/y/z splitting) or "dd" (partition-of-unity splitting, 2-D)
     boxes  : DD boxes per direction (bx, by); overlap: DD overlap width beta
+    d12    : off-diagonal diffusion, nodal on the (n+2)^2 grid or a scalar; 2-D DD only
+             (dimensional splitting cannot take the mixed derivatives, Sec. 2.1)
+    src2, src2_t : a second separable source term, f = src src_t + src2 src2_t
     """
 
-    def __init__(self, n, a=None, c=0.0, src=None, src_t=None, split="dim", boxes=(1, 1), overlap=0.0):
+    def __init__(self, n, a=None, c=0.0, src=None, src_t=None, split="dim", boxes=(1, 1), overlap=0.0,
+                 d12=None, src2=None, src2_t=None):
         n = tuple(int(v) for v in n)
         assert len(n) in (2, 3)
         self.n = n
@@ -139,6 +146,17 @@ class Problem:
         s.split = 0 if split == "dim" else 1
         s.boxes_x, s.boxes_y = int(boxes[0]), int(boxes[1])
         s.overlap = self.overlap
+        if d12 is not None:
+            if self.dim != 2 or split != "dd":
+                raise ValueError("the off-diagonal diffusion d12 needs the 2-D DD splitting")
+            d12 = np.broadcast_to(np.asarray(d12, dtype=np.float64), (n[1] + 2, n[0] + 2))
+        self.d12 = _f64(d12)
+        self.src2 = _f64(src2)
+        self.src2_t = _f64(src2_t)
+        s.d12 = _ptr(self.d12)
+        s.src2 = _ptr(self.src2)
+        s.src2_t = _ptr(self.src2_t)
+        s.src2_t_len = 0 if self.src2_t is None else int(self.src2_t.size)
         self._s = s
 
     @property

@@ -10,7 +10,11 @@
  *
  * What it computes, in the paper's order and notation:
  *   - model problem u_t = div(D grad u) - c u + f, u = 0 on the boundary
- *     (Sec. 2.1, eq. cont_problem), D = a(x) I with a nodal scalar a;
+ *     (Sec. 2.1, eq. cont_problem), D = a(x) I with a nodal scalar a, or in 2-D
+ *     the full tensor D = [[a, d12], [d12, a]] of Sec. 5.2 (domain-decomposition
+ *     splitting only: the mixed derivatives give a 9-point stencil);
+ *   - f(x, t) = src(x) src_t(t) + src2(x) src2_t(t) (two separable terms, enough
+ *     for the manufactured solutions of Sec. 5);
  *   - method of lines with second-order finite differences on a uniform
  *     grid of interior nodes (Sec. 2.2, eq. semidisc_prob; Sec. 5);
  *   - dimensional splitting L_j u = (a u_{x_j})_{x_j} - c u / M (Sec. 2.1);
@@ -28,6 +32,13 @@
  * Readings where the paper is silent (each one is also listed in the design
  * notes of the repository):
  *   - edge coefficient a_{i+1/2} = (a_i + a_{i+1}) / 2 from the nodal a;
+ *   - full tensor: A_j is assembled from one quadratic form per grid cell, with D
+ *     (the mean of its four nodal values) and rho_j taken at the cell centre, the
+ *     x-differences of the cell's bottom and top edges, the y-differences of its
+ *     left and right edges, and cell-averaged gradients in the d12 term.  Each
+ *     cell's form is positive semidefinite when D is SPD, so every A_j is
+ *     symmetric negative semidefinite, sum_j A_j = A, and the stencil has 9
+ *     points (5 when d12 = 0);
  *   - DD weights rho_j evaluated at edge midpoints, so sum_j A_j = A;
  *   - the overlap ramp is cos^2 over an overlap of width beta centred on
  *     each core boundary (C^1, where the paper asks for C^infinity);
@@ -58,6 +69,10 @@ typedef struct {
   int split;           /* 0 = dimensional, 1 = domain decomposition (2-D) */
   int boxes_x, boxes_y;/* DD: boxes per direction */
   double overlap;      /* DD: overlap width beta (absolute, in [0,1] units) */
+  const double* d12;   /* 2-D nodal off-diagonal diffusion incl. boundary; NULL means 0 */
+  const double* src2;  /* second separable source term src2(x) src2_t(t); NULL means 0 */
+  const double* src2_t;
+  int src2_t_len;
 } or_problem;
 
 /* ------------------------------------------------------------------ */
@@ -77,6 +92,11 @@ static double a_node(const or_problem* p, int i, int j, int k) {
   long nx2 = p->nx + 2, ny2 = p->ny + 2;
   if (p->dim == 2) k = 0;
   return p->a[((long)k * ny2 + j) * nx2 + i];
+}
+
+/* nodal off-diagonal coefficient at (i,j) in 0..n+1 (2-D) */
+static double d12_node(const or_problem* p, int i, int j) {
+  return p->d12 ? p->d12[(long)j * (p->nx + 2) + i] : 0.0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -111,7 +131,9 @@ double or_rho(const or_problem* p, int colour, double x, double y) {
   return s;
 }
 /* node range [lo, hi] (1-based interior) of 1-D box b: nodes touching a point
-   (node or adjacent edge midpoint) where phi_b > 0 */
+   (node or adjacent edge midpoint) where phi_b > 0.  The adjacent midpoints are
+   also the centres of the cells around the node, which the full-tensor operator
+   weights, so the range serves both operators. */
 int or_box_range(const or_problem* p, int d, int b, int* lo, int* hi) {
   int n = nn(p, d), B = d == 0 ? p->boxes_x : p->boxes_y;
   double h = hh(p, d);
@@ -150,6 +172,46 @@ static double node_reaction_weight(const or_problem* p, int m, int i, int j) {
   if (p->split == 0) return 1.0 / p->dim;
   return or_rho(p, m, i * hh(p, 0), j * hh(p, 1));
 }
+/* Full tensor D = [[a, d12], [d12, a]] (2-D): the quadratic form of cell (ci, cj), the
+   cell with lower-left node (ci, cj), ci in 0..nx, cj in 0..ny, weighted by rho_m at its
+   centre.  Corners 0 = (ci, cj), 1 = (ci+1, cj), 2 = (ci, cj+1), 3 = (ci+1, cj+1).  With
+   the edge differences Dx_b = u1 - u0, Dx_t = u3 - u2, Dy_l = u2 - u0, Dy_r = u3 - u1 and
+   the cell gradient (gx, gy) = ((Dx_b + Dx_t)/(2hx), (Dy_l + Dy_r)/(2hy)):
+     Q(u, v) = d11 (Dx_b(u) Dx_b(v) + Dx_t(u) Dx_t(v)) / (2 hx^2)
+             + d22 (Dy_l(u) Dy_l(v) + Dy_r(u) Dy_r(v)) / (2 hy^2)
+             + d12 (gx(u) gy(v) + gx(v) gy(u)),
+   the one-cell approximation of the integral of grad v . D grad u divided by the cell
+   area.  K[p][q] = rho Q(e_q, e_p); (A_m u)_P = -sum over the cells at P of K[p][q] u_q. */
+static void cell_form(const or_problem* p, int m, int ci, int cj, double K[4][4]) {
+  double hx = hh(p, 0), hy = hh(p, 1);
+  double rho = p->split == 0 ? 1.0 : or_rho(p, m, (ci + 0.5) * hx, (cj + 0.5) * hy);
+  double d = 0.25 * (a_node(p, ci, cj, 0) + a_node(p, ci + 1, cj, 0) + a_node(p, ci, cj + 1, 0) +
+                     a_node(p, ci + 1, cj + 1, 0));
+  double b = 0.25 * (d12_node(p, ci, cj) + d12_node(p, ci + 1, cj) + d12_node(p, ci, cj + 1) +
+                     d12_node(p, ci + 1, cj + 1));
+  static const double ex_b[4] = {-1, 1, 0, 0}, ex_t[4] = {0, 0, -1, 1};
+  static const double ey_l[4] = {-1, 0, 1, 0}, ey_r[4] = {0, -1, 0, 1};
+  static const double gx[4] = {-0.5, 0.5, -0.5, 0.5}, gy[4] = {-0.5, -0.5, 0.5, 0.5};
+  for (int r = 0; r < 4; ++r)
+    for (int q = 0; q < 4; ++q) {
+      double v = d * (ex_b[r] * ex_b[q] + ex_t[r] * ex_t[q]) / (2.0 * hx * hx) +
+                 d * (ey_l[r] * ey_l[q] + ey_r[r] * ey_r[q]) / (2.0 * hy * hy) +
+                 b * (gx[q] * gy[r] + gx[r] * gy[q]) / (hx * hy);
+      K[r][q] = rho * v;
+    }
+}
+/* (A_m u)_P without the reaction, full-tensor form, P = (i, j) interior */
+static double tensor_apply(const or_problem* p, int m, const double* u, int i, int j) {
+  double s = 0.0, K[4][4];
+  for (int cj = j - 1; cj <= j; ++cj)
+    for (int ci = i - 1; ci <= i; ++ci) {
+      cell_form(p, m, ci, cj, K);
+      int pl = (i - ci) + 2 * (j - cj);
+      for (int q = 0; q < 4; ++q) s -= K[pl][q] * uval(p, u, ci + q % 2, cj + q / 2, 1);
+    }
+  return s;
+}
+
 /* out = A_m u (full grid) */
 void or_apply_A(const or_problem* p, int m, const double* u, double* out) {
   int nz = p->dim == 3 ? p->nz : 1;
@@ -159,6 +221,11 @@ void or_apply_A(const or_problem* p, int m, const double* u, double* out) {
       for (int i = 1; i <= p->nx; ++i) {
         int id[3] = {i, j, k};
         double uc = uval(p, u, i, j, k), s = 0.0;
+        if (p->d12) {
+          s = tensor_apply(p, m, u, i, j) - p->c * node_reaction_weight(p, m, i, j) * uc;
+          out[(long)(j - 1) * p->nx + (i - 1)] = s;
+          continue;
+        }
         for (int d = 0; d < p->dim; ++d) {
           double h2 = hh(p, d) * hh(p, d);
           int ip[3] = {id[0], id[1], id[2]}, im[3] = {id[0], id[1], id[2]};
@@ -272,7 +339,9 @@ static void band_cholesky_solve(long n, int w, const double* L, double* x) {
 
 /* DD substep for colour m: block-diagonal system, one block per box of the
    colour, identity rows elsewhere.  Each block is assembled from the edge
-   weights and solved by banded Cholesky in the box's x-fastest ordering. */
+   weights and solved by banded Cholesky in the box's x-fastest ordering
+   (half-bandwidth w, the box width; w + 1 for the full tensor, whose corner
+   couplings (i-1, j-1) and (i+1, j-1) sit at offsets w + 1 and w - 1). */
 static int solve_dd(const or_problem* p, int m, double tau, double* u) {
   double hx2 = hh(p, 0) * hh(p, 0), hy2 = hh(p, 1) * hh(p, 1);
   int nb = p->boxes_x * p->boxes_y;
@@ -284,31 +353,53 @@ static int solve_dd(const or_problem* p, int m, double tau, double* u) {
     int x0, x1, y0, y1;
     if (!or_box_range(p, 0, bx, &x0, &x1) || !or_box_range(p, 1, by, &y0, &y1)) continue;
     int w = x1 - x0 + 1, hgt = y1 - y0 + 1;
+    int bw = p->d12 ? w + 1 : w;
     long nloc = (long)w * hgt;
-    double* B = calloc((size_t)nloc * (w + 1), sizeof(double));
+    double* B = calloc((size_t)nloc * (bw + 1), sizeof(double));
     double* x = malloc(sizeof(double) * nloc);
     for (int j = y0; j <= y1; ++j)
       for (int i = x0; i <= x1; ++i) {
         long r = (long)(j - y0) * w + (i - x0);
+        x[r] = u[(long)(j - 1) * p->nx + (i - 1)];
+        if (p->d12) {
+          /* full tensor: row P = (i, j) of (I - tau A_m) from the forms of the four cells at P */
+          B[r * (bw + 1)] = 1.0 + tau * p->c * node_reaction_weight(p, m, i, j);
+          double K[4][4];
+          for (int cj = j - 1; cj <= j; ++cj)
+            for (int ci = i - 1; ci <= i; ++ci) {
+              cell_form(p, m, ci, cj, K);
+              int pl = (i - ci) + 2 * (j - cj);
+              for (int q = 0; q < 4; ++q) {
+                int qi = ci + q % 2, qj = cj + q / 2;
+                if (qi < 1 || qi > p->nx || qj < 1 || qj > p->ny) continue; /* boundary: u = 0 */
+                if (qi < x0 || qi > x1 || qj < y0 || qj > y1) {  /* couplings that leave the box */
+                  if (K[pl][q] != 0.0) err |= 1;
+                  continue;
+                }
+                long c = (long)(qj - y0) * w + (qi - x0);
+                if (c <= r) B[r * (bw + 1) + (r - c)] += tau * K[pl][q];
+              }
+            }
+          continue;
+        }
         double a0 = a_node(p, i, j, 0);
         /* four edges: +x, -x, +y, -y */
         double wxp = edge_weight(p, m, 0, i, j, 0) * 0.5 * (a0 + a_node(p, i + 1, j, 0)) / hx2;
         double wxm = edge_weight(p, m, 0, i - 1, j, 0) * 0.5 * (a0 + a_node(p, i - 1, j, 0)) / hx2;
         double wyp = edge_weight(p, m, 1, i, j, 0) * 0.5 * (a0 + a_node(p, i, j + 1, 0)) / hy2;
         double wym = edge_weight(p, m, 1, i, j - 1, 0) * 0.5 * (a0 + a_node(p, i, j - 1, 0)) / hy2;
-        B[r * (w + 1)] = 1.0 + tau * (wxp + wxm + wyp + wym) + tau * p->c * node_reaction_weight(p, m, i, j);
-        if (i > x0) B[r * (w + 1) + 1] = -tau * wxm;
-        if (j > y0) B[r * (w + 1) + w] = -tau * wym;
+        B[r * (bw + 1)] = 1.0 + tau * (wxp + wxm + wyp + wym) + tau * p->c * node_reaction_weight(p, m, i, j);
+        if (i > x0) B[r * (bw + 1) + 1] = -tau * wxm;
+        if (j > y0) B[r * (bw + 1) + w] = -tau * wym;
         /* couplings that leave the box must vanish (or point at the boundary) */
         if (i == x0 && i > 1 && wxm != 0.0) err |= 1;
         if (i == x1 && i < p->nx && wxp != 0.0) err |= 1;
         if (j == y0 && j > 1 && wym != 0.0) err |= 1;
         if (j == y1 && j < p->ny && wyp != 0.0) err |= 1;
-        x[r] = u[(long)(j - 1) * p->nx + (i - 1)];
       }
-    if (band_cholesky(nloc, w, B) != 0) err |= 2;
+    if (band_cholesky(nloc, bw, B) != 0) err |= 2;
     else {
-      band_cholesky_solve(nloc, w, B, x);
+      band_cholesky_solve(nloc, bw, B, x);
       for (int j = y0; j <= y1; ++j)
         for (int i = x0; i <= x1; ++i) u[(long)(j - 1) * p->nx + (i - 1)] = x[(long)(j - y0) * w + (i - x0)];
     }
@@ -318,6 +409,7 @@ static int solve_dd(const or_problem* p, int m, double tau, double* u) {
 }
 
 int or_substep_solve(const or_problem* p, int m, double tau, double* u) {
+  if (p->d12 && (p->split == 0 || p->dim != 2)) return -3; /* mixed terms: 2-D DD only */
   if (p->split == 0) { solve_dim(p, m, tau, u); return 0; }
   if (p->dim != 2) return -2;
   return solve_dd(p, m, tau, u);
@@ -326,20 +418,31 @@ int or_substep_solve(const or_problem* p, int m, double tau, double* u) {
 /* ------------------------------------------------------------------ */
 /* FIE step (eq. FIE_method) and propagators                           */
 /* ------------------------------------------------------------------ */
-static double time_factor(const or_problem* p, int t_index) {
-  if (!p->src_t) return 1.0;
-  if (t_index < 0 || t_index >= p->src_t_len) return NAN;
-  return p->src_t[t_index];
+static double time_factor_of(const double* tf, int len, int t_index) {
+  if (!tf) return 1.0;
+  if (t_index < 0 || t_index >= len) return NAN;
+  return tf[t_index];
 }
-/* u <- U_{n+1} of eq. FIE_method from U_n = u; source at fine time index t_end.
-   reversed != 0 applies the substeps in the order M..1 (the transpose of a
-   step, used by the adjoint). */
-int or_fie_step(const or_problem* p, double tau, int t_end, int reversed, double* u) {
+static double time_factor(const or_problem* p, int t_index) {
+  return time_factor_of(p->src_t, p->src_t_len, t_index);
+}
+/* u += tau f(t_end), f = src src_t + src2 src2_t */
+static void add_source(const or_problem* p, double tau, int t_end, double* u) {
   long nt = n_total(p);
   if (p->src) {
     double ft = time_factor(p, t_end);
     for (long i = 0; i < nt; ++i) u[i] += tau * p->src[i] * ft;
   }
+  if (p->src2) {
+    double ft = time_factor_of(p->src2_t, p->src2_t_len, t_end);
+    for (long i = 0; i < nt; ++i) u[i] += tau * p->src2[i] * ft;
+  }
+}
+/* u <- U_{n+1} of eq. FIE_method from U_n = u; source at fine time index t_end.
+   reversed != 0 applies the substeps in the order M..1 (the transpose of a
+   step, used by the adjoint). */
+int or_fie_step(const or_problem* p, double tau, int t_end, int reversed, double* u) {
+  add_source(p, tau, t_end, u);
   int M = or_num_substeps(p);
   for (int q = 0; q < M; ++q) {
     int m = reversed ? M - 1 - q : q;
@@ -467,13 +570,12 @@ int or_dr_step(const or_problem* p, double tau, int t_end, double* u) {
   double* v = malloc(sizeof(double) * nt);
   if (!AU || !v) { free(AU); free(v); return -4; }
   for (int j = 0; j < M; ++j) or_apply_A(p, j, u, AU + j * nt);
-  double ft = p->src ? time_factor(p, t_end) : 0.0;
   for (long i = 0; i < nt; ++i) {
     double s = u[i];
     for (int j = 0; j < M; ++j) s += tau * AU[j * nt + i];
-    if (p->src) s += tau * p->src[i] * ft;
     v[i] = s;
   }
+  add_source(p, tau, t_end, v);
   int rc = 0;
   for (int j = 0; j < M && !rc; ++j) {
     for (long i = 0; i < nt; ++i) v[i] -= tau * AU[j * nt + i];
@@ -525,10 +627,7 @@ int or_adjoint(const or_problem* p, double T, int N, int s, const double* u0, co
   for (long q = 0; q < nsteps; ++q) {
     double* w0 = W + (q * (M + 1)) * nt;
     memcpy(w0, cur, sizeof(double) * nt);
-    if (p->src) {
-      double ft = time_factor(p, (int)(q + 1));
-      for (long i = 0; i < nt; ++i) w0[i] += dt * p->src[i] * ft;
-    }
+    add_source(p, dt, (int)(q + 1), w0);
     for (int j = 1; j <= M; ++j) {
       double* wj = W + (q * (M + 1) + j) * nt;
       memcpy(wj, wj - nt, sizeof(double) * nt);

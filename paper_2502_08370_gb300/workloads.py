@@ -212,3 +212,44 @@ def manufactured(n, T, N, s):
         return np.sin(2 * np.pi * tt) * S
 
     return S, st, exact
+
+
+def full_tensor_coefficients(nx, ny):
+    """Diffusion tensor of Sec. 5.2 on the (ny+2, nx+2) nodal grid (boundary included):
+    d11 = d22 = 1 / (2 + cos(3 pi x) cos(2 pi y)), d12 = 1/4.  Returns (d11, d12)."""
+    x, y = _axis_with_boundary(nx), _axis_with_boundary(ny)
+    d = 1.0 / (2.0 + np.outer(np.cos(2 * np.pi * y), np.cos(3 * np.pi * x)))
+    return d, np.full_like(d, 0.25)
+
+
+def full_tensor_div_grad_S(x, y):
+    """div(D grad S) for S = sin(2 pi x) sin(2 pi y) and the tensor of Sec. 5.2, in closed form:
+    d (S_xx + S_yy) + d_x S_x + d_y S_y + 2 d12 S_xy, d = 1/g, g = 2 + cos(3 pi x) cos(2 pi y)."""
+    X, Y = np.meshgrid(x, y)
+    tp = 2 * np.pi
+    g = 2.0 + np.cos(3 * np.pi * X) * np.cos(tp * Y)
+    d = 1.0 / g
+    gx = -3 * np.pi * np.sin(3 * np.pi * X) * np.cos(tp * Y)
+    gy = -tp * np.cos(3 * np.pi * X) * np.sin(tp * Y)
+    S = np.sin(tp * X) * np.sin(tp * Y)
+    Sx = tp * np.cos(tp * X) * np.sin(tp * Y)
+    Sy = tp * np.sin(tp * X) * np.cos(tp * Y)
+    Sxy = tp * tp * np.cos(tp * X) * np.cos(tp * Y)
+    return d * (-2 * tp * tp * S) - gx / g ** 2 * Sx - gy / g ** 2 * Sy + 2 * 0.25 * Sxy
+
+
+def manufactured_full_tensor(n, T, N, s):
+    """Manufactured problem of Sec. 5.2: u = sin(2 pi t) sin(2 pi x) sin(2 pi y) with the full
+    tensor above, f = u_t - div(D grad u) = S 2 pi cos(2 pi t) - div(D grad S) sin(2 pi t): two
+    separable terms.  Returns dict(a, d12, src, src_t, src2, src2_t, exact)."""
+    nx, ny = n
+    x, y = _axis(nx), _axis(ny)
+    S = np.outer(np.sin(2 * np.pi * y), np.sin(2 * np.pi * x))
+    t = np.arange(N * s + 1) * (T / (N * s))
+    a, d12 = full_tensor_coefficients(nx, ny)
+
+    def exact(tt):
+        return np.sin(2 * np.pi * tt) * S
+
+    return dict(a=a, d12=d12, src=S, src_t=2 * np.pi * np.cos(2 * np.pi * t), src2=-full_tensor_div_grad_S(x, y),
+                src2_t=np.sin(2 * np.pi * t), exact=exact)
