@@ -95,7 +95,10 @@ int ps_selftest_wait_timeout(int limit_us, uintptr_t stream);
 
 /* Message of the calling thread's last failed call ("" if none). */
 const char* ps_last_error(void);
-/* ABI version (major*100 + minor). */
+/* ABI version of this header, major*100 + minor; raised whenever a struct layout or a
+ * signature changes.  ps_version() returns the value the library was built with, so a
+ * caller can refuse a library built from another header. */
+#define PS_VERSION 102
 int ps_version(void);
 
 /* ---- grid: unit box, n[d] interior nodes, h_d = 1/(n[d]+1) (Sec. 2.2) ---------------- */

@@ -24,6 +24,7 @@ ERRORS = {1: "PS_ERR_INVALID", 2: "PS_ERR_CUDA", 3: "PS_ERR_OOM", 4: "PS_ERR_NON
           5: "PS_ERR_DEVICE_TIMEOUT", 6: "PS_ERR_UNSUPPORTED"}
 PS_SPLIT_DIM, PS_SPLIT_DD = 0, 1
 PS_PREC_FP64, PS_PREC_MIXED = 0, 1
+PS_VERSION = 102  # the header's PS_VERSION this binding marshals for
 PS_SCHED_AUTO, PS_SCHED_THOMAS, PS_SCHED_PCR = 0, 1, 2
 PS_COARSE_FP64, PS_COARSE_DELTA32 = 0, 1
 PS_FINE_FIE, PS_FINE_DR = 0, 1
@@ -115,6 +116,9 @@ def lib():
                 f = getattr(h, name)
                 f.argtypes = args
                 f.restype = _RESTYPE.get(name, C.c_int)
+            if h.ps_version() != PS_VERSION:
+                raise RuntimeError(f"{LIB_PATH} has ABI version {h.ps_version()}, this binding expects "
+                                   f"{PS_VERSION}: rebuild it (paper_2502_08370_gb300.build.build())")
             _lib = h
     return _lib
 

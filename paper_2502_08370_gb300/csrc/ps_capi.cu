@@ -537,7 +537,7 @@ int ps_selftest_wait_timeout(int limit_us, uintptr_t stream) {
 }
 
 const char* ps_last_error(void) { return g_last_error.c_str(); }
-int ps_version(void) { return 101; }
+int ps_version(void) { return PS_VERSION; }
 
 int ps_grid_create(int dim, const int n[3], ps_grid** out) {
   return guarded([&] {

@@ -39,6 +39,13 @@ def test_every_declared_symbol_is_exported(libps):
     assert not missing, missing
 
 
+def test_abi_version_matches_header_and_binding(libps):
+    import paper_2502_08370_gb300 as ps
+    text = open(os.path.join(ROOT, "include", "ps.h")).read()
+    header = int(re.search(r"#define PS_VERSION (\d+)", text).group(1))
+    assert libps.ps_version() == header == ps.PS_VERSION
+
+
 def test_binding_covers_the_header():
     import paper_2502_08370_gb300 as ps
     assert set(declared_functions()) <= set(ps.SIGNATURES), set(declared_functions()) - set(ps.SIGNATURES)
