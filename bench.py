@@ -183,6 +183,22 @@ def make_problem(ps, torch, cfg, precision, timing, coarse_mode="fp64", fine_met
     return prob
 
 
+def time_fie_fie_to_tol(ps, torch, cfg, u0, stream, reps=2):
+    """Parareal/FIE-FIE in FP64 on the workload: mean device time of `reps` solves to the
+    workload's tolerance after one untimed solve; returns (ms, iterations, U_N on the host)."""
+    q = make_problem(ps, torch, cfg, "fp64", timing=0, fine_method="fie")
+    q.run(u0, cfg["tol"])
+    torch.cuda.synchronize()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for _ in range(reps):
+        it = q.run(u0, cfg["tol"])
+    c1.record(stream)
+    torch.cuda.synchronize()
+    uN = q.state(cfg["N"]).cpu().numpy()
+    return c0.elapsed_time(c1) / reps, it, uN
+
+
 def fine_steps_fn(fine):
     import oracle as orc
     return (orc.propagate_dr, "DR") if fine == "dr" else (orc.propagate, "FIE")
@@ -635,6 +651,15 @@ def main():
             msm, itm, uNm, _ = time_to_tol("mixed", "fp64")
             compare.update({"mixed_fp64_coarse_ms_to_tol": msm, "mixed_fp64_coarse_iters": itm,
                             "mixed_fp64_coarse_rel_maxnorm_diff_UN_vs_plain_fp64": rel(uNm, uN64)})
+
+    if args.fine == "dr":
+        # Parareal/FIE-DR beside Parareal/FIE-FIE on the same workload and GPU (Sec. 4 pairs both)
+        ms_fie, it_fie, uN_fie = time_fie_fie_to_tol(ps, torch, cfg, u0, stream)
+        uN_dr = prob.state(cfg["N"]).cpu().numpy()
+        compare = {"fie_dr_ms_to_tol": ms / args.steps, "fie_dr_iters": iters[-1],
+                   "fie_fie_ms_to_tol": ms_fie, "fie_fie_iters": it_fie,
+                   "rel_maxnorm_diff_UN_dr_vs_fie": float(np.abs(uN_dr - uN_fie).max() /
+                                                          max(np.abs(uN_fie).max(), 1e-300))}
 
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_seconds > 0:
