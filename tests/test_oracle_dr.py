@@ -47,15 +47,19 @@ def test_dr_step_amplification_factor(n, tau):
         np.testing.assert_allclose(orc.dr_step(p, tau, phi), R * phi, rtol=0, atol=1e-13 * max(1.0, abs(R)))
 
 
-@pytest.mark.parametrize("case", ["dim2", "dim3", "dd"])
+@pytest.mark.parametrize("case", ["dim2", "dim3", "dd", "dd_tensor"])
 def test_dr_step_matches_dense_definition(case):
     rng = np.random.default_rng(3)
     if case == "dim2":
         n, kw = (6, 5), {}
     elif case == "dim3":
         n, kw = (4, 3, 5), {}
-    else:
+    elif case == "dd":
         n, kw = (9, 8), dict(split="dd", boxes=(2, 2), overlap=2.0 / 10)
+    else:  # full tensor (Sec. 5.2) with a second separable source term
+        n = (9, 8)
+        kw = dict(split="dd", boxes=(2, 2), overlap=2.0 / 10, d12=0.2 + 0.05 * rng.standard_normal((10, 11)),
+                  src2=rng.standard_normal((8, 9)), src2_t=np.cos(np.arange(10) * 0.3))
     a = np.exp(0.4 * rng.standard_normal([v + 2 for v in reversed(n)]))
     src = rng.standard_normal(n[::-1])
     src_t = 1.0 + np.sin(np.arange(10) * 0.5)
@@ -66,6 +70,8 @@ def test_dr_step_matches_dense_definition(case):
     I = np.eye(u.size)
     uf = u.reshape(-1)
     v = uf + tau * sum(A @ uf for A in mats) + tau * src.reshape(-1) * src_t[t_end]
+    if "src2" in kw:
+        v = v + tau * kw["src2"].reshape(-1) * kw["src2_t"][t_end]
     for A in mats:
         v = np.linalg.solve(I - tau * A, v - tau * A @ uf)
     got = orc.dr_step(p, tau, u, t_end=t_end).reshape(-1)

@@ -187,3 +187,23 @@ def test_fig10_dependence_on_s():
     assert dr[2][1] / dr[2][0] > 0.6  # s = 2: no exponential decay
     assert all(dr[s][1] / dr[s][0] < 0.45 for s in (4, 10)), dr
     assert dr[4][1] / dr[10][1] < 10 and dr[10][1] / dr[4][1] < 10, dr
+
+
+def test_fie_step_with_two_source_terms_matches_dense_definition():
+    """eq. FIE_method with f = src src_t + src2 src2_t: V_0 = U + tau f(t_end), then the colour
+    solves in order, evaluated with dense matrices."""
+    n = (11, 9)
+    rng = np.random.default_rng(43)
+    src2, src2_t = rng.standard_normal(n[::-1]), np.cos(np.arange(12) * 0.4)
+    m = wl.manufactured_full_tensor(n, 1.0, 3, 3)
+    p = orc.Problem(n, a=m["a"], d12=m["d12"], c=0.3, src=m["src"], src_t=m["src_t"], src2=src2, src2_t=src2_t,
+                    split="dd", boxes=(2, 2), overlap=2.0 / 12)
+    mats = dense_ops(p, n)
+    I = np.eye(n[0] * n[1])
+    u = rng.standard_normal(n[::-1])
+    tau, t_end = 0.07, 5
+    v = (u + tau * m["src"] * m["src_t"][t_end] + tau * src2 * src2_t[t_end]).reshape(-1)
+    for Aj in mats:
+        v = np.linalg.solve(I - tau * Aj, v)
+    got = orc.fie_step(p, tau, u, t_end=t_end).reshape(-1)
+    assert np.abs(got - v).max() <= 1e-12 * np.abs(v).max()
