@@ -81,12 +81,17 @@ def workload(name):
     if name == "heat2d_63":
         return wl.heat2d_63()
     if name == "dd2d_1023":
-        # DD with this thin overlap does not contract monotonically (the oracle shows the same);
-        # like the paper's DD scalability runs, a fixed number of iterations is timed
-        cfg = wl.dd2d_1023()
-        cfg["max_iter"] = 5
-        cfg["tol"] = 0.0
-        return cfg
+        # run to its tolerance 1e-10 (or to k = N, where parareal is the sequential fine solution)
+        return wl.dd2d_1023()
+    if name.startswith("dd_scal99_q"):
+        # the scalability experiment of Sec. 5.1: 99^2, DeltaT = 1/32, delta t = 1/3200, F with q = 2
+        # strips (overlap 1/16), G with q strips (overlap 1/32), five iterations from u = 0
+        q = int(name[len("dd_scal99_q"):])
+        n, T, N, s = 99, 1.0, 32, 100
+        S, st, exact = wl.manufactured((n, n), T, N, s)
+        return dict(n=(n, n), a=None, c=0.0, src=S, src_t=st, u0=np.zeros((n, n)), T=T, N=N, g=1, s=s, tol=0.0,
+                    max_iter=5, split="dd", boxes=(4, 1), overlap=1 / 16, coarse_boxes=(2 * q, 1),
+                    coarse_overlap=1 / 32, exact=exact)
     if name == "adjoint2d_511":
         return wl.adjoint2d_511()
     if name == "batch256":
@@ -177,9 +182,11 @@ def make_problem(ps, torch, cfg, precision, timing, coarse_mode="fp64", fine_met
     src = None if cfg["src"] is None else torch.as_tensor(cfg["src"]).cuda()
     op = ps.Operator(grid, a=a, c=cfg["c"], src=src, src_t=cfg["src_t"])
     sp = ps.Splitting(op, cfg["split"], cfg.get("boxes", (1, 1)), cfg.get("overlap", 0.0))
-    prob = ps.Problem(sp, cfg["T"], cfg["N"], cfg["g"], cfg["s"], precision=precision, timing=timing,
+    spc = ps.Splitting(op, cfg["split"], cfg["coarse_boxes"], cfg["coarse_overlap"]) if "coarse_boxes" in cfg \
+        else None
+    prob = ps.Problem(sp, cfg["T"], cfg["N"], cfg["g"], cfg["s"], coarse=spc, precision=precision, timing=timing,
                       coarse_mode=coarse_mode, fine_method=fine_method)
-    prob._keep = (grid, op, sp, a, src)
+    prob._keep = (grid, op, sp, spc, a, src)
     return prob
 
 
@@ -282,6 +289,9 @@ def config_of(args, cfg):
     if cfg["split"] == "dd":
         out["boxes"] = list(cfg["boxes"])
         out["overlap"] = cfg["overlap"]
+        if "coarse_boxes" in cfg:
+            out["coarse_boxes"] = list(cfg["coarse_boxes"])
+            out["coarse_overlap"] = cfg["coarse_overlap"]
     if cfg.get("max_iter"):
         out["max_iter"] = cfg["max_iter"]
     return out
@@ -422,9 +432,16 @@ def run_adjoint(args, cfg, ps, torch, rank, ws):
     # moves by e / sqrt(#nodes) ~ 2e-4 and the stencil's truncation stays near 1e-8.
     from paper_2502_08370_gb300 import workloads as wl
 
+    # the gradient the finite differences check is the exact one of the forward map: forward and
+    # adjoint parareal run to k = N (finite termination, Sec. 3); the timed gradient at the
+    # workload's tolerance is compared with it
     prob.run(u0, tol)
+    gu_tol, ga_tol = prob.vjp(prob.state(cfg["N"]) - tgt, tol)
+    prob.run(u0, 0.0)
     gN = prob.state(cfg["N"]) - tgt
-    gu, ga = prob.vjp(gN, tol)
+    gu, ga = prob.vjp(gN, 0.0)
+    tol_gap = {"a": float((ga_tol - ga).abs().max() / ga.abs().max()),
+               "u0": float((gu_tol - gu).abs().max() / gu.abs().max())}
     nsteps = cfg["N"] * cfg["s"]
 
     def J_of(aa, uu):
@@ -454,6 +471,8 @@ def run_adjoint(args, cfg, ps, torch, rank, ws):
                           "fd_dirs_within_1e-6_a": int(sum(e <= 1e-6 for e in errs_a)),
                           "fd_directions_u0": len(errs_u),
                           "fd_max_rel_err_u0": max(errs_u),
+                          "fd_gradient": "exact (forward and adjoint parareal to k = N)",
+                          "rel_maxnorm_gap_gradient_at_tol_vs_exact": tol_gap,
                           "adjoint_parareal_iters": getattr(prob, "last_adjoint_iters", None)}}
     finish_line(args, cfg, upd / (ms / 1e3), ms / args.steps, launches, extra, rank, ws, clocks=clocks)
 
@@ -466,14 +485,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="heat3d_255")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--coarse", default="delta32", choices=["delta32", "fp64"],
-                    help="coarse propagator of the mixed form: FP32 increment form or FP64 (dimensional splitting)")
+    ap.add_argument("--coarse", default="fp64", choices=["delta32", "fp64"],
+                    help="coarse propagator of the mixed form: FP64 (default: the parareal defect, correction and "
+                         "test all in FP64), or the FP32 increment form (dimensional splitting)")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP64 time-to-tolerance run")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--fd-dirs", type=int, default=20, help="finite-difference directions (adjoint workload)")
     ap.add_argument("--fine", default="fie", choices=["fie", "dr"],
                     help="fine propagator: FIE steps, or Douglas-Rachford steps (Parareal/FIE-DR, FP64, "
-                         "dimensional splitting)")
+                         "dimensional or DD splitting)")
     ap.add_argument("--slices", type=int, default=0,
                     help="override the workload's slice count N (small-footprint profiling runs; named in config)")
     args = ap.parse_args()
@@ -483,12 +503,12 @@ def main():
     if args.slices > 0 and "batch" not in cfg:
         cfg["N"] = args.slices
 
-    if args.workload in ("heat2d_63", "dd2d_1023", "adjoint2d_511"):
+    if args.workload in ("heat2d_63", "dd2d_1023", "adjoint2d_511") or args.workload.startswith("dd_scal99"):
         args.precision = "fp64"  # these workloads are specified in FP64
         args.no_compare = True
     if args.fine == "dr":
-        if cfg.get("split") != "dim" or "batch" in cfg or args.workload == "adjoint2d_511":
-            raise SystemExit("--fine dr runs the single-problem dimensional-splitting workloads")
+        if "batch" in cfg or args.workload == "adjoint2d_511":
+            raise SystemExit("--fine dr runs the single-problem workloads (dimensional or DD splitting)")
         args.precision = "fp64"  # the DR fine propagator runs in FP64
         args.no_compare = True
     if args.precision == "fp64" or cfg.get("split") == "dd":
@@ -615,42 +635,73 @@ def main():
     e2e = {"value": e2e_upd / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": 8 * nt,
            "d2h_bytes_per_step": 8 * nt, "wall_s": e2e_wall}
 
-    # plain FP64 GPU method: time to tolerance at the same tolerance, and the accuracy gap
+    # plain FP64 GPU method: time to tolerance at the same tolerance; the other FP32 form; and the
+    # accuracy of every arm against one common reference
     compare = None
+    accuracy = None
     if not args.no_compare and args.precision != "fp64":
         del prob
         torch.cuda.empty_cache()
 
-        def time_to_tol(precision, coarse_mode):
-            q = make_problem(ps, torch, cfg, precision, timing=1, coarse_mode=coarse_mode)
-            q.run(u0, cfg["tol"])
+        def time_to_tol(precision, coarse_mode, s_fine=None, reps=2, timing=2):
+            c = dict(cfg) if s_fine is None else dict(cfg, s=s_fine)
+            q = make_problem(ps, torch, c, precision, timing=timing, coarse_mode=coarse_mode)
+            q.run(u0, c["tol"])
             torch.cuda.synchronize()
             c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = 2
             c0.record(stream)
             for _ in range(reps):
-                it = q.run(u0, cfg["tol"])
+                it = q.run(u0, c["tol"])
             c1.record(stream)
             torch.cuda.synchronize()
             t = c0.elapsed_time(c1) / reps
-            out = (t, it, q.state(cfg["N"]).cpu().numpy(), q.stats()["unknown_updates"] / (t / 1000.0))
+            out = {"ms": t, "iters": it, "uN": q.state(c["N"]).cpu().numpy(),
+                   "ups": q.stats()["unknown_updates"] / (t / 1000.0), "kern": q.kernel_times() if timing >= 2 else {}}
             del q
             torch.cuda.empty_cache()
             return out
 
-        ms64, it64, uN64, ups64 = time_to_tol("fp64", "fp64")
-
         def rel(a, b):
             return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
-        compare = {"plain_fp64_ms_to_tol": ms64, "plain_fp64_iters": it64, "ms_to_tol": ms / args.steps,
-                   "iters": iters[-1], "speedup_vs_plain_fp64": ms64 / (ms / args.steps),
-                   "rel_maxnorm_diff_UN_vs_plain_fp64": rel(uN_mixed, uN64),
-                   "plain_fp64_unknown_updates_per_s": ups64}
-        if args.coarse != "fp64":
-            msm, itm, uNm, _ = time_to_tol("mixed", "fp64")
-            compare.update({"mixed_fp64_coarse_ms_to_tol": msm, "mixed_fp64_coarse_iters": itm,
-                            "mixed_fp64_coarse_rel_maxnorm_diff_UN_vs_plain_fp64": rel(uNm, uN64)})
+        plain = time_to_tol("fp64", "fp64")
+        # the FP64 comparator against GB300's FP64 issue rate: its dominant kernel and the whole solve
+        pk_name, pk = max(plain["kern"].items(), key=lambda kv: kv[1]["ms"])
+        tot_flops = sum(k["flops"] for k in plain["kern"].values())
+        tot_ms = sum(k["ms"] for k in plain["kern"].values())
+        fp64_pipe = {"kernel": pk_name, "TFLOP/s": pk["flops"] / pk["ms"] / 1e9,
+                     "frac": pk["flops"] / pk["ms"] / 1e9 / FP64_PEAK_TFLOPS,
+                     "solve_TFLOP/s": tot_flops / tot_ms / 1e9, "solve_frac": tot_flops / tot_ms / 1e9 / FP64_PEAK_TFLOPS,
+                     "peak_TFLOP/s": FP64_PEAK_TFLOPS, "peak_source": "measured DFMA rate of this GPU pool"}
+        forms = {"fp64": "FP32 fine line solves; FP64 coarse propagator, parareal defect, correction and test",
+                 "delta32": "FP32 fine line solves; coarse increment form: FP32 line solves on the FP32-rounded "
+                            "increment, FP64 correction and test"}
+        other_mode = "delta32" if args.coarse == "fp64" else "fp64"
+        other = time_to_tol("mixed", other_mode, timing=0)
+        ms_this = ms / args.steps
+        compare = {"form": forms[args.coarse], "ms_to_tol": ms_this, "iters": iters[-1],
+                   "plain_fp64_ms_to_tol": plain["ms"], "plain_fp64_iters": plain["iters"],
+                   "speedup_vs_plain_fp64": plain["ms"] / ms_this,
+                   "rel_maxnorm_diff_UN_vs_plain_fp64": rel(uN_mixed, plain["uN"]),
+                   "plain_fp64_unknown_updates_per_s": plain["ups"], "plain_fp64_fp64_pipe": fp64_pipe,
+                   "variant": {"form": forms[other_mode], "coarse": other_mode, "ms_to_tol": other["ms"],
+                               "iters": other["iters"], "speedup_vs_plain_fp64": plain["ms"] / other["ms"],
+                               "rel_maxnorm_diff_UN_vs_plain_fp64": rel(other["uN"], plain["uN"])}}
+        if cfg.get("src_t") is None:
+            # common reference: the same parareal solve with half the fine step (s -> 2 s); the FIE
+            # steps are first order in delta t (Sec. 2.2), so 2 |U_N(dt) - U_N(dt/2)| estimates the
+            # temporal error of every arm at dt
+            ref = time_to_tol("mixed", "fp64", s_fine=2 * cfg["s"], reps=1, timing=0)
+            t_err = 2.0 * rel(plain["uN"], ref["uN"])
+            gap = rel(uN_mixed, plain["uN"])
+            accuracy = {"reference": f"parareal with FP32 fine line solves and s = {2 * cfg['s']} (half the fine "
+                                     f"step), tol {cfg['tol']}",
+                        "temporal_error_estimate_rel": t_err,
+                        "rel_err_vs_reference": {"plain_fp64": rel(plain["uN"], ref["uN"]),
+                                                 "this_form": rel(uN_mixed, ref["uN"]),
+                                                 "variant": rel(other["uN"], ref["uN"])},
+                        "fp32_gap_vs_plain_fp64_rel": gap,
+                        "fp32_gap_over_temporal_error": gap / t_err if t_err > 0 else None}
 
     if args.fine == "dr":
         # Parareal/FIE-DR beside Parareal/FIE-FIE on the same workload and GPU (Sec. 4 pairs both)
@@ -675,8 +726,15 @@ def main():
                 "dominant_kernel_note": ("FP64 sweeps are bound by the FP64 issue rate (1.19 TFLOP/s measured)"
                                          if args.precision == "fp64" else None),
                 "config": config_of(args, cfg), "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
-                "roofline": roof, "cpu_baseline": cpu, "time_to_tol": compare, "parareal_iterations": iters,
-                "kernels": kernels}
+                "roofline": roof, "cpu_baseline": cpu, "time_to_tol": compare, "accuracy": accuracy,
+                "parareal_iterations": iters, "kernels": kernels}
+        if "exact" in cfg:
+            # the scalability experiment: error of the final iterate against the manufactured solution,
+            # measured like Sec. 5 (max over the coarse times of the h-weighted 2-norm)
+            h = 1.0 / (cfg["n"][0] + 1)
+            err = max(float(np.sqrt(h * h * np.sum((prob.state(j).cpu().numpy() - cfg["exact"](j * cfg["T"] / cfg["N"]))
+                                                   ** 2))) for j in range(1, cfg["N"] + 1))
+            line["error_vs_exact_after_5_iterations"] = err
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

@@ -71,7 +71,7 @@ extern "C" {
 
 /* Fine propagator (ps_params.fine_method).  PS_FINE_DR takes s Douglas-Rachford steps
  * (Sec. 2.2, eq. DR_method) per slice: Parareal/FIE-DR of Sec. 4.2, G staying FIE.
- * Dimensional splitting and PS_PREC_FP64 only; not in batches or adjoints. */
+ * PS_PREC_FP64 only, with the dimensional or the DD splitting; not in batches or adjoints. */
 #define PS_FINE_FIE 0 /* fractional implicit Euler (eq. FIE_method) */
 #define PS_FINE_DR 1  /* Douglas-Rachford (eq. DR_method) */
 
@@ -98,7 +98,7 @@ const char* ps_last_error(void);
 /* ABI version of this header, major*100 + minor; raised whenever a struct layout or a
  * signature changes.  ps_version() returns the value the library was built with, so a
  * caller can refuse a library built from another header. */
-#define PS_VERSION 102
+#define PS_VERSION 103
 int ps_version(void);
 
 /* ---- grid: unit box, n[d] interior nodes, h_d = 1/(n[d]+1) (Sec. 2.2) ---------------- */
@@ -157,6 +157,15 @@ typedef struct {
 int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, double T, int N, int g_steps,
                       int f_steps, const ps_params* params, uintptr_t stream, ps_problem** out);
 int ps_problem_destroy(ps_problem* p);
+/* Change the slice count N and the propagators' step counts of an existing problem (Sec. 3:
+ * DeltaT = T/N, G = g_steps FIE steps of DeltaT/g_steps, F = f_steps FIE steps of
+ * DeltaT/f_steps; same rules as at creation).  Rebuilds the substep factors for the new step
+ * sizes and reallocates the slice states; the previous run's states, history and adjoint
+ * workspaces are dropped, the tile schedule (ps_autotune) is kept.  PS_ERR_INVALID for bad
+ * counts (nothing changed then) or while the problem belongs to a batch; PS_ERR_OOM when the
+ * new states do not fit, after which the problem has no slices and refuses every run until a
+ * later call succeeds. */
+int ps_problem_set_slices(ps_problem* p, int N, int g_steps, int f_steps, uintptr_t stream);
 
 /* Parareal from u0_dev: U_0 = u0, U^0 by a sequential coarse sweep, then
  * U_{n+1}^{k} = F(U_n^{k-1}) + (G(U_n^{k}) - G(U_n^{k-1})) for k = 1, 2, ...
@@ -200,6 +209,12 @@ int ps_problem_update_coefficients(ps_problem* p, const double* a_nodal_dev, uin
  * are the forward ones again on return; *iters_out = adjoint parareal iterations. */
 int ps_adjoint_vjp(ps_problem* p, const double* gN_dev, double tol, int max_iter, double* grad_u0_dev,
                    double* grad_a_dev, uintptr_t stream, int* iters_out);
+/* Gradient of the loss J = 1/2 ||U_N - u_target||^2 (sum over interior nodes) of the last
+ * parareal run: ps_adjoint_vjp with the upstream gradient g = U_N - u_target, formed on the
+ * device.  *J_out (host, may be NULL) receives J, summed in a fixed order (the same value on
+ * every call with the same data).  Same requirements and errors as ps_adjoint_vjp. */
+int ps_adjoint(ps_problem* p, const double* u_target_dev, double tol, int max_iter, double* grad_u0_dev,
+               double* grad_a_dev, uintptr_t stream, double* J_out, int* iters_out);
 
 /* Sequential coarse solution U_n = G^n(u0) without allocating any device memory.
  *
@@ -215,6 +230,8 @@ int ps_adjoint_vjp(ps_problem* p, const double* gN_dev, double tol, int max_iter
  *    PS_ERR_INVALID before any GPU work.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  *    with that device current; make that first call before any stream capture.
+ *  - Like the allocating version, the call waits for `stream` before it returns: it reads the
+ *    device-side error flag of its kernels back to the host.
  *  - All calls share the one array: calls that overlap on the GPU (other streams, other
  *    threads) race and produce wrong results.  Serialise them.
  *  - Nothing in the array needs to start at zero: each coarse step overwrites it fully. */
@@ -267,12 +284,18 @@ int ps_problem_kernel_times(const ps_problem* p, ps_kernel_time* out, int cap, i
  * ...).  While a problem belongs to a batch, ps_autotune only considers the tile shapes
  * the batch's grouped kernels run (one tile per work item, one line per thread). */
 typedef struct ps_batch ps_batch;
+/* count >= 0 problems (problems may be NULL when count = 0); more join with ps_batch_add. */
 int ps_batch_create(ps_problem* const* problems, int count, uintptr_t stream, ps_batch** out);
+/* Append problem p (same requirements as at creation; PS_ERR_UNSUPPORTED otherwise, the batch
+ * unchanged).  Its index is the number of problems the batch held before the call. */
+int ps_batch_add(ps_batch* b, ps_problem* p, uintptr_t stream);
+/* Copy state U_slice (0..N_p) of problem `index` of the last ps_batch_run to out_dev. */
+int ps_batch_get_state(const ps_batch* b, int index, int slice, double* out_dev, uintptr_t stream);
 /* u0_devs: host array of `count` device pointers.  Each problem stops at the first k with
  * max_n ||U_n^k - U_n^{k-1}||_inf < tol, at k = N_p, or at max_iter (<= 0: no cap).
  * iters_out (host, `count` ints, may be NULL) receives each problem's k. */
 int ps_batch_run(ps_batch* b, const double* const* u0_devs, double tol, int max_iter, uintptr_t stream,
-                 int* iters_out);
+                 int* iters_out);  /* PS_ERR_INVALID for an empty batch */
 /* iterations = the largest k, unknown_updates over all problems, kernel_launches (graph nodes
  * executed).  ms fields are 0. */
 int ps_batch_stats(const ps_batch* b, ps_stats* out);

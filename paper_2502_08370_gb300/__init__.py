@@ -24,7 +24,7 @@ ERRORS = {1: "PS_ERR_INVALID", 2: "PS_ERR_CUDA", 3: "PS_ERR_OOM", 4: "PS_ERR_NON
           5: "PS_ERR_DEVICE_TIMEOUT", 6: "PS_ERR_UNSUPPORTED"}
 PS_SPLIT_DIM, PS_SPLIT_DD = 0, 1
 PS_PREC_FP64, PS_PREC_MIXED = 0, 1
-PS_VERSION = 102  # the header's PS_VERSION this binding marshals for
+PS_VERSION = 103  # the header's PS_VERSION this binding marshals for
 PS_SCHED_AUTO, PS_SCHED_THOMAS, PS_SCHED_PCR = 0, 1, 2
 PS_COARSE_FP64, PS_COARSE_DELTA32 = 0, 1
 PS_FINE_FIE, PS_FINE_DR = 0, 1
@@ -98,6 +98,10 @@ SIGNATURES = {
     "ps_autotune": [_VP, _I, _U, _IP],
     "ps_copy_schedule": [_VP, _VP],
     "ps_adjoint_vjp": [_VP, _VP, _D, _I, _VP, _VP, _U, _IP],
+    "ps_adjoint": [_VP, _VP, _D, _I, _VP, _VP, _U, C.POINTER(C.c_double), _IP],
+    "ps_problem_set_slices": [_VP, _I, _I, _I, _U],
+    "ps_batch_add": [_VP, _VP, _U],
+    "ps_batch_get_state": [_VP, _I, _I, _VP, _U],
     "ps_problem_kernel_times": [_VP, C.POINTER(_KTime), _I, _IP],
     "ps_selftest_wait_timeout": [_I, _U],
 }
@@ -319,6 +323,24 @@ class Problem:
         self.last_adjoint_iters = it.value
         return gu, ga
 
+    def adjoint(self, u_target, tol, max_iter=0, want_a=True, stream=None):
+        """(J, dJ/du0, dJ/da) for J = 1/2 ||U_N - u_target||^2 of the last run."""
+        import torch
+        gu = torch.empty(self.grid.shape, dtype=torch.float64, device="cuda")
+        ga = torch.empty(tuple(v + 2 for v in reversed(self.grid.n)), dtype=torch.float64, device="cuda") \
+            if want_a else None
+        J = C.c_double(0.0)
+        it = C.c_int(0)
+        check(lib().ps_adjoint(self._h, _dev_ptr(u_target, self.grid.nt), float(tol), int(max_iter), _dev_ptr(gu),
+                               _dev_ptr(ga), _stream(stream), C.byref(J), C.byref(it)))
+        self.last_adjoint_iters = it.value
+        return J.value, gu, ga
+
+    def set_slices(self, N, g, s, stream=None):
+        """New slice count and propagator step counts (rebuilds factors and slice states)."""
+        check(lib().ps_problem_set_slices(self._h, int(N), int(g), int(s), _stream(stream)))
+        self.N = int(N)
+
     def autotune(self, budget_ms=200, stream=None):
         """Time the fine-sweep schedules on this problem and keep the fastest (returns its code)."""
         ch = C.c_int(0)
@@ -369,12 +391,30 @@ class Batch:
 
     def __init__(self, problems, stream=None):
         self.problems = list(problems)
-        arr = (_VP * len(self.problems))(*[p._h for p in self.problems])
+        arr = (_VP * max(len(self.problems), 1))(*[p._h for p in self.problems])
         h = _VP()
         rc = lib().ps_batch_create(arr, len(self.problems), _stream(stream), C.byref(h))
         if rc != PS_OK:
             raise PsError(rc, lib().ps_batch_last_error().decode())
         self._h = h
+
+    def add(self, problem, stream=None):
+        """Append a problem (its index is the previous problem count)."""
+        rc = lib().ps_batch_add(self._h, problem._h, _stream(stream))
+        if rc != PS_OK:
+            raise PsError(rc, lib().ps_batch_last_error().decode())
+        self.problems.append(problem)
+
+    def state(self, index, n, out=None, stream=None):
+        """U_n of problem `index` after the last run (through ps_batch_get_state)."""
+        import torch
+        p = self.problems[index]
+        if out is None:
+            out = torch.empty(p.grid.shape, dtype=torch.float64, device="cuda")
+        rc = lib().ps_batch_get_state(self._h, int(index), int(n), _dev_ptr(out, p.grid.nt), _stream(stream))
+        if rc != PS_OK:
+            raise PsError(rc, lib().ps_batch_last_error().decode())
+        return out
 
     def run(self, u0s, tol, max_iter=0, stream=None):
         ptrs = (_VP * len(u0s))(*[_dev_ptr(u, p.grid.nt) for u, p in zip(u0s, self.problems)])

@@ -125,6 +125,7 @@ CoarseJob coarse_job(ps_batch* b, int i, int n) {
 
 template <typename T>
 void upload(DevBuf<T>& d, const std::vector<T>& h, cudaStream_t st) {
+  PS_REQUIRE(h.size() <= d.n, "batch work table larger than its device buffer");
   if (!h.empty()) PS_CUDA(cudaMemcpyAsync(d.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st));
 }
 
@@ -209,6 +210,7 @@ void fill_iteration_tables(ps_batch* b, const std::vector<int>& active, int k) {
 }
 
 void upload_tables(ps_batch* b, cudaStream_t st) {
+  PS_REQUIRE(b->h_tile_jobs.size() <= b->tile_jobs.n, "batch tile table larger than its device buffer");
   PS_CUDA(cudaMemcpyAsync(b->tile_jobs.p, b->h_tile_jobs.data(), b->h_tile_jobs.size(), cudaMemcpyHostToDevice, st));
   upload(b->tile_segs, b->h_tile_segs, st);
   upload(b->tile_nseg, b->h_tile_nseg, st);
@@ -272,6 +274,88 @@ cudaGraphExec_t capture(ps_batch* b, int mode) {
   return ex;
 }
 
+// Problem i of a batch must run the batch's form (see include/ps.h, ps_batch_create).
+void batch_check(const ps_batch* b, const ps_problem* p) {
+  PS_REQUIRE(p, "null problem");
+  PS_REQUIRE(p->N >= 1, "the problem has no slices");
+  if (p->g.dim != 2 || p->fine->kind != PS_SPLIT_DIM || p->coarse->kind != PS_SPLIT_DIM)
+    throw Error(PS_ERR_UNSUPPORTED, "batches hold 2-D problems with dimensional splitting");
+  if (p->prm.precision != PS_PREC_MIXED)
+    throw Error(PS_ERR_UNSUPPORTED, "batches run the FP32 line-solve form (PS_PREC_MIXED)");
+  if (p->gs != 1) throw Error(PS_ERR_UNSUPPORTED, "batches use one coarse step per slice");
+  if (p->delta32) throw Error(PS_ERR_UNSUPPORTED, "batches run the FP64 coarse propagator");
+  if (p->dr) throw Error(PS_ERR_UNSUPPORTED, "batches run the FIE fine propagator");
+  if (p->op->src.p) throw Error(PS_ERR_UNSUPPORTED, "batches hold problems without a source term");
+  const bool var = p->op->a.p != nullptr;
+  if (!b->probs.empty())
+    PS_REQUIRE(var == (b->probs[0]->op->a.p != nullptr), "all problems of a batch need a nodal coefficient, or none");
+  for (const ps_problem* q : b->probs) PS_REQUIRE(q != p, "a problem appears twice in the batch");
+}
+
+// Sizes of the batch's tables from its problems, and the device tables and host staging.
+void batch_layout(ps_batch* b) {
+  const int P = (int)b->probs.size();
+  b->count = P;
+  b->maxS = b->maxN = 0;
+  b->tile_smem = b->x_smem = 0;
+  b->tile_threads = 0;
+  b->var = P > 0 ? b->probs[0]->op->a.p != nullptr : true;
+  for (ps_problem* p : b->probs) {
+    b->maxS = std::max(b->maxS, p->fs);
+    b->maxN = std::max(b->maxN, p->N);
+    b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[0]));
+    b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[1]));
+    // the grouped kernel runs one line per thread, whatever the plan's own split
+    b->tile_threads = std::max(b->tile_threads, std::max(p->F.tiles[0].TS * p->F.tiles[0].P,
+                                                         p->F.tiles[1].TS * p->F.tiles[1].P));
+    const int nx = p->g.n[0];
+    const int ld = (nx % 2) ? nx : nx + 1;
+    b->x_smem = std::max(b->x_smem, (size_t)x_rows_per_block(nx) * ld * sizeof(double));
+  }
+  b->tile_threads = (b->tile_threads + 31) / 32 * 32;
+  if (b->iter_graph) {
+    cudaGraphExecDestroy(b->iter_graph);
+    b->iter_graph = nullptr;
+  }
+  if (b->init_graph) {
+    cudaGraphExecDestroy(b->init_graph);
+    b->init_graph = nullptr;
+  }
+  const size_t Pz = (size_t)std::max(P, 1);
+  b->tile_jobs.alloc((size_t)2 * Pz * tile_job_bytes());
+  b->tile_segs.alloc((size_t)2 * Pz);
+  b->tile_nseg.alloc((size_t)2 * std::max(b->maxS, 1));
+  b->pack_jobs.alloc(Pz);
+  b->unpack_jobs.alloc(Pz);
+  b->pack_segs.alloc(Pz);
+  b->unpack_segs.alloc(Pz);
+  b->copy_jobs.alloc(Pz);
+  b->copy_segs.alloc(Pz);
+  b->cjobs.alloc((size_t)std::max(b->maxN, 1) * Pz);
+  b->xsegs.alloc((size_t)std::max(b->maxN, 1) * Pz);
+  b->ysegs.alloc((size_t)std::max(b->maxN, 1) * Pz);
+  b->nseg_misc.alloc((size_t)3 + b->maxN);
+  b->inc.alloc(Pz);
+  b->flag.alloc(Pz);
+  b->tmo.alloc(1);
+  PS_CUDA(cudaMemset(b->tmo.p, 0, sizeof(int)));
+  b->h_tile_jobs.assign((size_t)2 * P * tile_job_bytes(), 0);
+  b->h_tile_segs.assign((size_t)2 * P, WorkSeg{});
+  b->h_tile_nseg.assign((size_t)2 * b->maxS, 0);
+  b->h_pack.assign(P, PackJob{});
+  b->h_unpack.assign(P, PackJob{});
+  b->h_pack_segs.assign(P, WorkSeg{});
+  b->h_unpack_segs.assign(P, WorkSeg{});
+  b->h_copy.assign(P, CoarseJob{});
+  b->h_copy_segs.assign(P, WorkSeg{});
+  b->h_cjobs.assign((size_t)b->maxN * P, CoarseJob{});
+  b->h_xsegs.assign((size_t)b->maxN * P, WorkSeg{});
+  b->h_ysegs.assign((size_t)b->maxN * P, WorkSeg{});
+  b->h_nseg_misc.assign((size_t)3 + b->maxN, 0);
+  b->h_inc.assign(P, 0);
+  b->h_flag.assign(P, 0);
+}
+
 }  // namespace
 
 extern "C" {
@@ -280,80 +364,52 @@ const char* ps_batch_last_error(void) { return g_batch_error.c_str(); }
 
 int ps_batch_create(ps_problem* const* problems, int count, uintptr_t stream, ps_batch** out) {
   return bguarded([&] {
-    PS_REQUIRE(problems && out && count >= 1, "bad argument");
+    PS_REQUIRE(out && count >= 0 && (problems || count == 0), "bad argument");
     auto b = std::make_unique<ps_batch>();
-    b->count = count;
-    b->probs.assign(problems, problems + count);
-    for (int i = 0; i < count; ++i) {
-      ps_problem* p = b->probs[i];
-      PS_REQUIRE(p, "null problem");
-      if (p->g.dim != 2 || p->fine->kind != PS_SPLIT_DIM || p->coarse->kind != PS_SPLIT_DIM)
-        throw Error(PS_ERR_UNSUPPORTED, "batches hold 2-D problems with dimensional splitting");
-      if (p->prm.precision != PS_PREC_MIXED)
-        throw Error(PS_ERR_UNSUPPORTED, "batches run the FP32 line-solve form (PS_PREC_MIXED)");
-      if (p->gs != 1) throw Error(PS_ERR_UNSUPPORTED, "batches use one coarse step per slice");
-      if (p->delta32) throw Error(PS_ERR_UNSUPPORTED, "batches run the FP64 coarse propagator");
-      if (p->dr) throw Error(PS_ERR_UNSUPPORTED, "batches run the FIE fine propagator");
-      if (p->op->src.p) throw Error(PS_ERR_UNSUPPORTED, "batches hold problems without a source term");
-      const bool var = p->op->a.p != nullptr;
-      if (i == 0) b->var = var;
-      PS_REQUIRE(var == b->var, "all problems of a batch need a nodal coefficient, or none");
-      for (int j = 0; j < i; ++j) PS_REQUIRE(b->probs[j] != p, "a problem appears twice in the batch");
-      b->maxS = std::max(b->maxS, p->fs);
-      b->maxN = std::max(b->maxN, p->N);
-      b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[0]));
-      b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[1]));
-      // the grouped kernel runs one line per thread, whatever the plan's own split
-      b->tile_threads = std::max(b->tile_threads, std::max(p->F.tiles[0].TS * p->F.tiles[0].P,
-                                                           p->F.tiles[1].TS * p->F.tiles[1].P));
-      const int nx = p->g.n[0];
-      const int ld = (nx % 2) ? nx : nx + 1;
-      b->x_smem = std::max(b->x_smem, (size_t)x_rows_per_block(nx) * ld * sizeof(double));
-    }
-    const int P = count;
-    b->tile_threads = (b->tile_threads + 31) / 32 * 32;
-    b->tile_jobs.alloc((size_t)2 * P * tile_job_bytes());
-    b->tile_segs.alloc((size_t)2 * P);
-    b->tile_nseg.alloc((size_t)2 * b->maxS);
-    b->pack_jobs.alloc(P);
-    b->unpack_jobs.alloc(P);
-    b->pack_segs.alloc(P);
-    b->unpack_segs.alloc(P);
-    b->copy_jobs.alloc(P);
-    b->copy_segs.alloc(P);
-    b->cjobs.alloc((size_t)b->maxN * P);
-    b->xsegs.alloc((size_t)b->maxN * P);
-    b->ysegs.alloc((size_t)b->maxN * P);
-    b->nseg_misc.alloc((size_t)3 + b->maxN);
-    b->inc.alloc(P);
-    b->flag.alloc(P);
-    b->tmo.alloc(1);
-    PS_CUDA(cudaMemset(b->tmo.p, 0, sizeof(int)));
-    b->h_tile_jobs.assign((size_t)2 * P * tile_job_bytes(), 0);
-    b->h_tile_segs.assign((size_t)2 * P, WorkSeg{});
-    b->h_tile_nseg.assign((size_t)2 * b->maxS, 0);
-    b->h_pack.assign(P, PackJob{});
-    b->h_unpack.assign(P, PackJob{});
-    b->h_pack_segs.assign(P, WorkSeg{});
-    b->h_unpack_segs.assign(P, WorkSeg{});
-    b->h_copy.assign(P, CoarseJob{});
-    b->h_copy_segs.assign(P, WorkSeg{});
-    b->h_cjobs.assign((size_t)b->maxN * P, CoarseJob{});
-    b->h_xsegs.assign((size_t)b->maxN * P, WorkSeg{});
-    b->h_ysegs.assign((size_t)b->maxN * P, WorkSeg{});
-    b->h_nseg_misc.assign((size_t)3 + b->maxN, 0);
-    b->h_inc.assign(P, 0);
-    b->h_flag.assign(P, 0);
     int dev = 0;
     PS_CUDA(cudaGetDevice(&dev));
     PS_CUDA(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev));
     PS_CUDA(cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking));
     PS_CUDA(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
     PS_CUDA(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
+    for (int i = 0; i < count; ++i) {
+      batch_check(b.get(), problems[i]);
+      b->probs.push_back(problems[i]);
+    }
+    batch_layout(b.get());
     PS_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
     for (ps_problem* p : b->probs) ++p->batched;
     b->registered = true;
     *out = b.release();
+  });
+}
+
+int ps_batch_add(ps_batch* b, ps_problem* p, uintptr_t stream) {
+  return bguarded([&] {
+    PS_REQUIRE(b && p, "null argument");
+    batch_check(b, p);
+    b->probs.push_back(p);
+    try {
+      batch_layout(b);
+    } catch (...) {
+      b->probs.pop_back();
+      batch_layout(b);
+      throw;
+    }
+    ++p->batched;
+    PS_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+  });
+}
+
+int ps_batch_get_state(const ps_batch* b, int index, int slice, double* out_dev, uintptr_t stream) {
+  return bguarded([&] {
+    PS_REQUIRE(b && out_dev, "null argument");
+    PS_REQUIRE(index >= 0 && index < b->count, "problem index out of range");
+    const ps_problem* p = b->probs[index];
+    PS_REQUIRE(slice >= 0 && slice <= p->N, "slice out of range");
+    const long long nt = p->g.nt;
+    PS_CUDA(cudaMemcpyAsync(out_dev, p->U.p + slice * nt, sizeof(double) * nt, cudaMemcpyDeviceToDevice,
+                            reinterpret_cast<cudaStream_t>(stream)));
   });
 }
 
@@ -366,6 +422,7 @@ int ps_batch_run(ps_batch* b, const double* const* u0_devs, double tol, int max_
                  int* iters_out) {
   return bguarded([&] {
     PS_REQUIRE(b && u0_devs, "null argument");
+    PS_REQUIRE(b->count > 0, "the batch holds no problem");
     cudaStream_t ust = reinterpret_cast<cudaStream_t>(stream);
     cudaStream_t st = b->cs;
     const int P = b->count;

@@ -219,7 +219,9 @@ void run_F_tiles(ps_problem* p, int n_first, int nsl, const double* in, double* 
 // F as s Douglas-Rachford steps (eq. DR_method) on nsl consecutive slices of the natural
 // layout, in increment form: W_0 = tau (A U_n + f), the M substep solves (I - tau A_j) in
 // place on W (the printed right-hand sides U_{n,j-1} - tau A_j U_n minus (I - tau A_j) U_n),
-// then U_{n+1} = U_n + W_M.
+// then U_{n+1} = U_n + W_M.  The stencil pass is the same for both splittings: the DD
+// suboperators sum to A exactly (rho_j sums to 1 at every edge midpoint and node), so only
+// the substep solves differ (line sweeps, or colour j's box solves).
 void run_F_dr(ps_problem* p, int n_first, int nsl, const double* in, double* out, cudaStream_t st) {
   Prop& P = p->F;
   const int M = P.sp->M;
@@ -236,6 +238,20 @@ void run_F_dr(ps_problem* p, int n_first, int nsl, const double* in, double* out
                 dnt * (1.0 + 6.0 * M + (sa.src ? 3.0 : 0.0)));
     p->launches++;
     for (int j = 0; j < M; ++j) {
+      if (P.sp->kind == PS_SPLIT_DD) {
+        // colour j's box solves on W (identity outside its boxes, like the FIE substep)
+        const int spb = p->prm.dd_slices_per_block > 0 ? p->prm.dd_slices_per_block : 2;
+        p->kt.begin(st);
+        dd_solve(p->g, nsl, *P.dd, j, W, spb, p->tmo.p, st);
+        if (p->kt.on) {
+          const auto& pl = P.dd->plan;
+          const double w = pl.nodes[j] > 0 ? pl.fac_entries[j] / (2.0 * pl.nodes[j]) - 0.5 : 0.0;
+          p->kt.end("F.dd" + std::to_string(j) + ".f64", nsl * pl.nodes[j] * 16.0 + pl.fac_entries[j] * 8.0,
+                    nsl * pl.nodes[j] * 4.0 * w);
+        }
+        p->launches++;
+        continue;
+      }
       double bytes = 0, flops = 0;
       if (p->kt.on) sweep_cost(p, *P.dim[j], nsl, 8, 8, 8, false, 0, &bytes, &flops);
       p->kt.begin(st);
@@ -351,7 +367,12 @@ void tile_flag_check(ps_problem* p, cudaStream_t st) {
   tile_flag_throw(v);
 }
 
+void require_slices(const ps_problem* p) {
+  PS_REQUIRE(p->N >= 1, "the problem has no slices (its last ps_problem_set_slices failed)");
+}
+
 void check_state_len(const ps_problem* p, int slice) {
+  require_slices(p);
   PS_REQUIRE(slice >= 0 && slice <= p->N, "slice out of range");
 }
 
@@ -365,6 +386,7 @@ struct TraceRange {
 
 void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStream_t st, int* iters_out) {
   TraceRange whole(p->transposed ? "ps.adjoint_parareal" : "ps.parareal");
+  require_slices(p);
   const long long nt = p->g.nt;
   const int N = p->N;
   if (max_iter <= 0 || max_iter > N) max_iter = N;
@@ -464,6 +486,102 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
 
 }  // namespace
 
+namespace {
+// Slice count N, coarse steps g and fine steps f per slice (Sec. 3: G = g FIE steps of
+// DeltaT/g, F = f FIE steps of DeltaT/f, DeltaT = T/N).  Builds the substep factors of both
+// propagators for their step sizes and (re)allocates every per-slice buffer; the previous
+// run's states, history and adjoint workspaces are dropped.  The arguments are checked
+// before anything is released; if an allocation fails afterwards the problem is left with
+// no slices (N = 0) and every run refuses it until a later call succeeds.
+void configure_slices(ps_problem* p, int N, int g_steps, int f_steps, cudaStream_t st) {
+  PS_REQUIRE(N >= 1 && g_steps >= 1 && f_steps >= 1, "N, g_steps, f_steps must be >= 1");
+  PS_REQUIRE(f_steps % g_steps == 0, "f_steps must be a multiple of g_steps");
+  if (p->op->src_t.p)
+    PS_REQUIRE(p->op->src_t_len >= (long long)N * f_steps + 1, "src_t must cover the fine times 0..N*f_steps");
+  PS_REQUIRE((long long)(N + 1) * p->g.nt * 8 < (1LL << 46), "slice states too large");
+  const ps_splitting* fine = p->fine;
+  const ps_splitting* coarse = p->coarse;
+  // drop everything that depends on N or on the step sizes
+  p->N = 0;
+  p->iters = 0;
+  p->hist.clear();
+  p->have_forward = false;
+  p->adj_ready = false;
+  for (auto* b : {&p->U, &p->Fout, &p->Gold, &p->gtmp, &p->dr_W, &p->W64, &p->srcrow64, &p->Uchk, &p->snap, &p->Lam})
+    b->reset();
+  for (auto& b : p->gedge) b.reset();
+  for (auto* b : {&p->d32, &p->g32, &p->W, &p->srcrow32}) b->reset();
+  p->sstats.reset();
+  if (p->h_sstats) {
+    cudaFreeHost(p->h_sstats);
+    p->h_sstats = nullptr;
+  }
+  p->F = Prop{};
+  p->G = Prop{};
+  const bool mixed = p->prm.precision == PS_PREC_MIXED;
+  const double T = p->T;
+  build_prop(p, p->F, fine, T / N / f_steps, f_steps, 1, mixed, st);
+  build_prop(p, p->G, coarse, T / N / g_steps, g_steps, f_steps / g_steps, p->delta32, st);
+  if (p->delta32) {
+    Geom g3 = p->g;
+    if (g3.dim == 2) g3.n[2] = 1;
+    factor_lines(g3, *p->G.dim[0], true, st);  // line-major x factors of the warp x-sweep
+  }
+  const long long nt = p->g.nt;
+  p->U.alloc((size_t)(N + 1) * nt);
+  p->Fout.alloc((size_t)N * nt);
+  if (p->delta32) {
+    p->d32.alloc((size_t)nt);
+    p->g32.alloc((size_t)nt);
+  } else {
+    p->Gold.alloc((size_t)N * nt);
+  }
+  p->gtmp.alloc((size_t)nt);
+  if (p->dr) p->dr_W.alloc((size_t)N * nt);
+  p->sstats.alloc((size_t)2 * (N + 1));
+  PS_CUDA(cudaMallocHost(&p->h_sstats, sizeof(unsigned long long) * 2 * (N + 1)));
+  p->S_pad = 0;
+  if (fine->kind == PS_SPLIT_DIM) {
+    const int elem = mixed ? 4 : 8;
+    const int TS = mixed ? 32 : 16;
+    p->S_pad = (N + TS - 1) / TS * TS;
+    void* W = nullptr;
+    if (mixed) {
+      p->W.alloc((size_t)p->S_pad * nt);
+      W = p->W.p;
+    } else {
+      p->W64.alloc((size_t)p->S_pad * nt);
+      W = p->W64.p;
+    }
+    PS_CUDA(cudaMemsetAsync(W, 0, (size_t)p->S_pad * nt * elem, st));
+    Geom g3 = p->g;
+    if (g3.dim == 2) g3.n[2] = 1;
+    for (int m = 0; m < p->g.dim; ++m) {
+      tile_plan(g3, p->S_pad, elem, m, p->F.tiles[m], W, p->prm.tile_positions,
+                p->prm.tile_pipeline == 0 ? 0 : (p->prm.tile_pipeline == 1 ? 1 : 0), p->prm.tile_slots,
+                p->prm.tile_lines_per_thread);
+      factor_lines(g3, *p->F.dim[m], mixed, st);
+    }
+    if (p->op->src.p) {
+      const size_t rows = (size_t)(nt / g3.n[0]) * ((g3.n[0] + 3) & ~3);
+      void* out;
+      if (mixed) {
+        p->srcrow32.alloc(rows);
+        out = p->srcrow32.p;
+      } else {
+        p->srcrow64.alloc(rows);
+        out = p->srcrow64.p;
+      }
+      source_rows(g3, p->op->src.p, out, elem, st);
+    }
+  }
+  PS_CUDA(cudaStreamSynchronize(st));
+  p->N = N;
+  p->gs = g_steps;
+  p->fs = f_steps;
+}
+}  // namespace
+
 // ---------------------------------------------------------------------------------------
 // Coarse sequential solution without device allocation (ps_run_coarse_sequential_noalloc).
 // The working state of each coarse step lives in this file-scope array instead of the
@@ -516,6 +634,43 @@ __global__ void wait_selftest_kernel(int* err, unsigned long long limit_ns) {
     if (!mbar_wait_ns(&bar, 0, limit_ns)) atomicExch(err, 1);
   }
 }
+}  // namespace
+
+namespace {
+// Deterministic loss of ps_adjoint: g = U_N - target and per-block sums of g^2 (fixed grid),
+// then one block adds the partial sums in a fixed order; out[0] = J = 1/2 sum g^2.
+constexpr int kLossBlocks = 512;
+__global__ void __launch_bounds__(256) loss_residual_kernel(const double* __restrict__ uN,
+                                                          const double* __restrict__ tgt, double* __restrict__ g,
+                                                          long long n, double* __restrict__ part) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double d = uN[i] - tgt[i];
+    g[i] = d;
+    acc = fma(d, d, acc);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+__global__ void __launch_bounds__(256) loss_sum_kernel(const double* __restrict__ part, int nb, double* out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += part[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = 0.5 * red[0];
+}
+
 }  // namespace
 
 extern "C" {
@@ -632,98 +787,46 @@ int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, doub
     if (!coarse) coarse = fine;
     PS_REQUIRE(coarse->op == fine->op, "coarse and fine splittings must share the operator");
     PS_REQUIRE(T > 0 && std::isfinite(T), "T must be positive");
-    PS_REQUIRE(N >= 1 && g_steps >= 1 && f_steps >= 1, "N, g_steps, f_steps must be >= 1");
-    PS_REQUIRE(f_steps % g_steps == 0, "f_steps must be a multiple of g_steps");
     auto p = std::make_unique<ps_problem>();
     p->fine = fine;
     p->coarse = coarse;
     p->op = fine->op;
     p->g = fine->op->grid->g;
     p->T = T;
-    p->N = N;
-    p->gs = g_steps;
-    p->fs = f_steps;
     if (params) p->prm = *params;
     PS_REQUIRE(p->prm.precision == PS_PREC_FP64 || p->prm.precision == PS_PREC_MIXED, "unknown precision");
     PS_REQUIRE(p->prm.schedule >= PS_SCHED_AUTO && p->prm.schedule <= PS_SCHED_PCR, "unknown schedule");
     if (p->prm.schedule == PS_SCHED_PCR)
       throw Error(PS_ERR_UNSUPPORTED, "the parallel-cyclic-reduction schedule is not built; the line solves run "
                                       "the Thomas/LDL^T recurrences (PS_SCHED_AUTO or PS_SCHED_THOMAS)");
-    if (p->op->src_t.p)
-      PS_REQUIRE(p->op->src_t_len >= N * f_steps + 1, "src_t must cover the fine times 0..N*f_steps");
-    cudaStream_t st = S(stream);
-    const bool mixed = p->prm.precision == PS_PREC_MIXED;
     PS_REQUIRE(p->prm.coarse == PS_COARSE_FP64 || p->prm.coarse == PS_COARSE_DELTA32, "unknown coarse mode");
     PS_REQUIRE(p->prm.fine_method == PS_FINE_FIE || p->prm.fine_method == PS_FINE_DR, "unknown fine method");
+    PS_REQUIRE(p->prm.tol_mode == 0 || p->prm.tol_mode == 1, "tol_mode must be 0 or 1");
     p->dr = p->prm.fine_method == PS_FINE_DR;
-    if (p->dr && (fine->kind != PS_SPLIT_DIM || p->prm.precision != PS_PREC_FP64))
-      throw Error(PS_ERR_UNSUPPORTED, "the Douglas-Rachford fine propagator runs with the dimensional splitting in FP64");
+    if (p->dr && p->prm.precision != PS_PREC_FP64)
+      throw Error(PS_ERR_UNSUPPORTED, "the Douglas-Rachford fine propagator runs in FP64");
     p->delta32 = p->prm.coarse == PS_COARSE_DELTA32;
     if (p->delta32 && (fine->kind != PS_SPLIT_DIM || coarse->kind != PS_SPLIT_DIM))
       throw Error(PS_ERR_UNSUPPORTED, "the FP32 coarse increment form needs the dimensional splitting");
-    build_prop(p.get(), p->F, fine, T / N / f_steps, f_steps, 1, mixed, st);
-    build_prop(p.get(), p->G, coarse, T / N / g_steps, g_steps, f_steps / g_steps, p->delta32, st);
-    if (p->delta32) {
-      Geom g3 = p->g;
-      if (g3.dim == 2) g3.n[2] = 1;
-      factor_lines(g3, *p->G.dim[0], true, st);  // line-major x factors of the warp x-sweep
-    }
-    const long long nt = p->g.nt;
-    p->U.alloc((size_t)(N + 1) * nt);
-    p->Fout.alloc((size_t)N * nt);
-    if (p->delta32) {
-      p->d32.alloc((size_t)nt);
-      p->g32.alloc((size_t)nt);
-    } else {
-      p->Gold.alloc((size_t)N * nt);
-    }
-    p->gtmp.alloc((size_t)nt);
-    if (p->dr) p->dr_W.alloc((size_t)N * nt);
-    p->inc.alloc(1);
-    p->tmo.alloc(1);
-    PS_CUDA(cudaMemset(p->tmo.p, 0, sizeof(int)));
-    p->sstats.alloc((size_t)2 * (N + 1));
-    PS_CUDA(cudaMallocHost(&p->h_sstats, sizeof(unsigned long long) * 2 * (N + 1)));
-    PS_REQUIRE(p->prm.tol_mode == 0 || p->prm.tol_mode == 1, "tol_mode must be 0 or 1");
-    if (fine->kind == PS_SPLIT_DIM) {
-      const int elem = mixed ? 4 : 8;
-      const int TS = mixed ? 32 : 16;
-      p->S_pad = (N + TS - 1) / TS * TS;
-      void* W = nullptr;
-      if (mixed) {
-        p->W.alloc((size_t)p->S_pad * nt);
-        W = p->W.p;
-      } else {
-        p->W64.alloc((size_t)p->S_pad * nt);
-        W = p->W64.p;
-      }
-      PS_CUDA(cudaMemsetAsync(W, 0, (size_t)p->S_pad * nt * elem, st));
-      Geom g3 = p->g;
-      if (g3.dim == 2) g3.n[2] = 1;
-      for (int m = 0; m < p->g.dim; ++m) {
-        tile_plan(g3, p->S_pad, elem, m, p->F.tiles[m], W, p->prm.tile_positions,
-                  p->prm.tile_pipeline == 0 ? 0 : (p->prm.tile_pipeline == 1 ? 1 : 0), p->prm.tile_slots, p->prm.tile_lines_per_thread);
-        factor_lines(g3, *p->F.dim[m], mixed, st);
-      }
-      if (p->op->src.p) {
-        const size_t rows = (size_t)(nt / g3.n[0]) * ((g3.n[0] + 3) & ~3);
-        void* out;
-        if (mixed) {
-          p->srcrow32.alloc(rows);
-          out = p->srcrow32.p;
-        } else {
-          p->srcrow64.alloc(rows);
-          out = p->srcrow64.p;
-        }
-        source_rows(g3, p->op->src.p, out, elem, st);
-      }
-    }
-    p->flag.alloc(1);
+    cudaStream_t st = S(stream);
     PS_CUDA(cudaMallocHost(&p->h_inc, sizeof(unsigned long long)));
     PS_CUDA(cudaMallocHost(&p->h_flag, 2 * sizeof(int)));
     for (auto& e : p->ev) PS_CUDA(cudaEventCreate(&e));
-    PS_CUDA(cudaStreamSynchronize(st));
+    p->inc.alloc(1);
+    p->tmo.alloc(1);
+    p->flag.alloc(1);
+    p->jpart.alloc(kLossBlocks + 1);
+    PS_CUDA(cudaMemset(p->tmo.p, 0, sizeof(int)));
+    configure_slices(p.get(), N, g_steps, f_steps, st);
     *out = p.release();
+  });
+}
+
+int ps_problem_set_slices(ps_problem* p, int N, int g_steps, int f_steps, uintptr_t stream) {
+  return guarded([&] {
+    PS_REQUIRE(p, "null argument");
+    PS_REQUIRE(p->batched == 0, "the problem belongs to a batch: destroy the batch before changing its slices");
+    configure_slices(p, N, g_steps, f_steps, S(stream));
   });
 }
 
@@ -744,6 +847,7 @@ int ps_run_parareal_host(ps_problem* p, const double* u0_host, double* uN_host, 
                          uintptr_t stream, int* iters_out) {
   return guarded([&] {
     PS_REQUIRE(p && u0_host && uN_host, "null argument");
+    require_slices(p);
     cudaStream_t st = S(stream);
     const long long nt = p->g.nt;
     // u0 is staged in the coarse scratch state, which the run copies to U_0 before using it
@@ -775,6 +879,7 @@ int ps_get_history(const ps_problem* p, double* inc_host, int cap, int* len) {
 int ps_run_fine_sequential(ps_problem* p, const double* u0_dev, double* U_out_dev, uintptr_t stream) {
   return guarded([&] {
     PS_REQUIRE(p && u0_dev && U_out_dev, "null argument");
+    require_slices(p);
     cudaStream_t st = S(stream);
     const long long nt = p->g.nt;
     p->updates = 0;
@@ -789,6 +894,7 @@ int ps_run_fine_sequential(ps_problem* p, const double* u0_dev, double* U_out_de
 int ps_run_coarse_sequential(ps_problem* p, const double* u0_dev, double* U_out_dev, uintptr_t stream) {
   return guarded([&] {
     PS_REQUIRE(p && u0_dev && U_out_dev, "null argument");
+    require_slices(p);
     cudaStream_t st = S(stream);
     const long long nt = p->g.nt;
     tile_flag_reset(p, st);
@@ -804,6 +910,7 @@ int ps_run_coarse_sequential(ps_problem* p, const double* u0_dev, double* U_out_
 int ps_substep_solve(ps_problem* p, int which, int m, double* x_dev, uintptr_t stream) {
   return guarded([&] {
     PS_REQUIRE(p && x_dev, "null argument");
+    require_slices(p);
     PS_REQUIRE(which == 0 || which == 1, "which must be 0 (fine) or 1 (coarse)");
     Prop& P = which == 0 ? p->F : p->G;
     PS_REQUIRE(m >= 0 && m < P.sp->M, "substep out of range");
@@ -820,6 +927,7 @@ int ps_substep_solve(ps_problem* p, int which, int m, double* x_dev, uintptr_t s
 int ps_propagate(ps_problem* p, int which, int nsteps, int t0, int tstride, double* x_dev, uintptr_t stream) {
   return guarded([&] {
     PS_REQUIRE(p && x_dev && nsteps >= 0, "bad argument");
+    require_slices(p);
     PS_REQUIRE(which == 0 || which == 1, "which must be 0 (fine) or 1 (coarse)");
     Prop& P = which == 0 ? p->F : p->G;
     if (p->op->src_t.p)
@@ -875,6 +983,7 @@ void rebuild_tiles(ps_problem* p, int slots, int positions, int pipe, int vec) {
 int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out) {
   return guarded([&] {
     PS_REQUIRE(p, "null argument");
+    require_slices(p);
     if (choice_out) *choice_out = 0;
     if (p->F.sp->kind != PS_SPLIT_DIM) return;
     cudaStream_t st = S(stream);
@@ -964,6 +1073,7 @@ int ps_copy_schedule(const ps_problem* src, ps_problem* dst) {
 int ps_problem_update_coefficients(ps_problem* p, const double* a_nodal_dev, uintptr_t stream) {
   return guarded([&] {
     PS_REQUIRE(p && a_nodal_dev, "null argument");
+    require_slices(p);
     ps_operator* op = const_cast<ps_operator*>(p->op);
     PS_REQUIRE(op->a.p, "the operator was created with a = 1; create it with a nodal coefficient to update it");
     cudaStream_t st = S(stream);
@@ -1031,55 +1141,84 @@ void adjoint_coefficient_gradient(ps_problem* p, double* grad_a, cudaStream_t st
   const double* ge[3] = {p->gedge[0].p, p->gedge[1].p, M == 3 ? p->gedge[2].p : nullptr};
   combine_grad(g3, ge, grad_a, st);
 }
+
+// Body of ps_adjoint_vjp (see include/ps.h).
+void adjoint_vjp(ps_problem* p, const double* gN_dev, double tol, int max_iter, double* grad_u0_dev,
+                 double* grad_a_dev, cudaStream_t st, int* iters_out) {
+  PS_REQUIRE(p->have_forward, "ps_adjoint_vjp needs a preceding ps_run_parareal on this problem");
+  if (p->delta32) throw Error(PS_ERR_UNSUPPORTED, "the adjoint runs with the FP64 coarse propagator");
+  if (p->dr) throw Error(PS_ERR_UNSUPPORTED, "the adjoint differentiates the FIE fine propagator");
+  if (grad_a_dev) {
+    if (p->F.sp->kind != PS_SPLIT_DIM || p->G.sp->kind != PS_SPLIT_DIM)
+      throw Error(PS_ERR_UNSUPPORTED, "the coefficient gradient is implemented for the dimensional splitting");
+    if (p->F.f32) throw Error(PS_ERR_UNSUPPORTED, "the coefficient gradient runs in FP64 (PS_PREC_FP64)");
+    PS_REQUIRE(p->op->a.p, "the coefficient gradient needs an operator created with a nodal coefficient");
+  }
+  const long long nt = p->g.nt;
+  const size_t ubytes = sizeof(double) * (size_t)(p->N + 1) * nt;
+  if (!p->Uchk.p) p->Uchk.alloc((size_t)(p->N + 1) * nt);
+  PS_CUDA(cudaMemcpyAsync(p->Uchk.p, p->U.p, ubytes, cudaMemcpyDeviceToDevice, st));
+  const int saved_mode = p->prm.tol_mode;
+  const std::vector<double> saved_hist = p->hist;
+  const int saved_iters = p->iters;
+  p->transposed = true;
+  p->prm.tol_mode = 1;
+  try {
+    do_run(p, gN_dev, tol, max_iter, st, iters_out);
+  } catch (...) {
+    p->transposed = false;
+    p->prm.tol_mode = saved_mode;
+    throw;
+  }
+  p->transposed = false;
+  p->prm.tol_mode = saved_mode;
+  PS_CUDA(cudaMemcpyAsync(grad_u0_dev, p->U.p + (long long)p->N * nt, sizeof(double) * nt, cudaMemcpyDeviceToDevice,
+                          st));
+  if (grad_a_dev) adjoint_coefficient_gradient(p, grad_a_dev, st);
+  // the problem's states are the forward ones again
+  PS_CUDA(cudaMemcpyAsync(p->U.p, p->Uchk.p, ubytes, cudaMemcpyDeviceToDevice, st));
+  p->hist = saved_hist;
+  p->iters = saved_iters;
+  p->have_forward = true;
+  tile_flag_check(p, st);
+}
 }  // namespace
 
 int ps_adjoint_vjp(ps_problem* p, const double* gN_dev, double tol, int max_iter, double* grad_u0_dev,
                    double* grad_a_dev, uintptr_t stream, int* iters_out) {
   return guarded([&] {
     PS_REQUIRE(p && gN_dev && grad_u0_dev, "null argument");
-    PS_REQUIRE(p->have_forward, "ps_adjoint_vjp needs a preceding ps_run_parareal on this problem");
-    if (p->delta32) throw Error(PS_ERR_UNSUPPORTED, "the adjoint runs with the FP64 coarse propagator");
-    if (p->dr) throw Error(PS_ERR_UNSUPPORTED, "the adjoint differentiates the FIE fine propagator");
-    if (grad_a_dev) {
-      if (p->F.sp->kind != PS_SPLIT_DIM || p->G.sp->kind != PS_SPLIT_DIM)
-        throw Error(PS_ERR_UNSUPPORTED, "the coefficient gradient is implemented for the dimensional splitting");
-      if (p->F.f32) throw Error(PS_ERR_UNSUPPORTED, "the coefficient gradient runs in FP64 (PS_PREC_FP64)");
-      PS_REQUIRE(p->op->a.p, "the coefficient gradient needs an operator created with a nodal coefficient");
-    }
+    require_slices(p);
+    adjoint_vjp(p, gN_dev, tol, max_iter, grad_u0_dev, grad_a_dev, S(stream), iters_out);
+  });
+}
+
+int ps_adjoint(ps_problem* p, const double* u_target_dev, double tol, int max_iter, double* grad_u0_dev,
+               double* grad_a_dev, uintptr_t stream, double* J_out, int* iters_out) {
+  return guarded([&] {
+    PS_REQUIRE(p && u_target_dev && grad_u0_dev, "null argument");
+    require_slices(p);
+    PS_REQUIRE(p->have_forward, "ps_adjoint needs a preceding ps_run_parareal on this problem");
     cudaStream_t st = S(stream);
     const long long nt = p->g.nt;
-    const size_t ubytes = sizeof(double) * (size_t)(p->N + 1) * nt;
-    if (!p->Uchk.p) p->Uchk.alloc((size_t)(p->N + 1) * nt);
-    PS_CUDA(cudaMemcpyAsync(p->Uchk.p, p->U.p, ubytes, cudaMemcpyDeviceToDevice, st));
-    const int saved_mode = p->prm.tol_mode;
-    const std::vector<double> saved_hist = p->hist;
-    const int saved_iters = p->iters;
-    p->transposed = true;
-    p->prm.tol_mode = 1;
-    try {
-      do_run(p, gN_dev, tol, max_iter, st, iters_out);
-    } catch (...) {
-      p->transposed = false;
-      p->prm.tol_mode = saved_mode;
-      throw;
-    }
-    p->transposed = false;
-    p->prm.tol_mode = saved_mode;
-    PS_CUDA(cudaMemcpyAsync(grad_u0_dev, p->U.p + (long long)p->N * nt, sizeof(double) * nt, cudaMemcpyDeviceToDevice,
-                            st));
-    if (grad_a_dev) adjoint_coefficient_gradient(p, grad_a_dev, st);
-    // the problem's states are the forward ones again
-    PS_CUDA(cudaMemcpyAsync(p->U.p, p->Uchk.p, ubytes, cudaMemcpyDeviceToDevice, st));
-    p->hist = saved_hist;
-    p->iters = saved_iters;
-    p->have_forward = true;
-    tile_flag_check(p, st);
+    // g = U_N - u_target into the coarse scratch state (the adjoint run copies it to its U_0
+    // before the scratch state is reused), and J = 1/2 |g|^2 summed in a fixed order
+    loss_residual_kernel<<<kLossBlocks, 256, 0, st>>>(p->U.p + (long long)p->N * nt, u_target_dev, p->gtmp.p, nt,
+                                                     p->jpart.p);
+    PS_CUDA(cudaGetLastError());
+    loss_sum_kernel<<<1, 256, 0, st>>>(p->jpart.p, kLossBlocks, p->jpart.p + kLossBlocks);
+    PS_CUDA(cudaGetLastError());
+    double J = 0.0;
+    PS_CUDA(cudaMemcpyAsync(&J, p->jpart.p + kLossBlocks, sizeof(double), cudaMemcpyDeviceToHost, st));
+    adjoint_vjp(p, p->gtmp.p, tol, max_iter, grad_u0_dev, grad_a_dev, st, iters_out);
+    if (J_out) *J_out = J;  // the copy completed: adjoint_vjp synchronised the stream
   });
 }
 
 int ps_run_coarse_sequential_noalloc(ps_problem* p, const double* u0_dev, double* U_out_dev, uintptr_t stream) {
   return guarded([&] {
     PS_REQUIRE(p && u0_dev && U_out_dev, "null argument");
+    require_slices(p);
     const long long nt = p->g.nt;
     if (nt > PS_NOALLOC_MAX_UNKNOWNS)
       throw Error(PS_ERR_INVALID, "grid has " + std::to_string(nt) + " unknowns; the no-allocation coarse solve holds at most " +

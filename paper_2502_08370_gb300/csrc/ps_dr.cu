@@ -90,13 +90,12 @@ __global__ void dr_add_kernel(const double* u, const double* __restrict__ w, dou
     out[e] = u[e] + w[e];
 }
 
+// SM count of the current device, queried per launch (the attribute query is cheap and a
+// cached value would be wrong for a problem that lives on another device).
 int sm_count() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    PS_CUDA(cudaGetDevice(&dev));
-    PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  }
+  int dev = 0, sms = 0;
+  PS_CUDA(cudaGetDevice(&dev));
+  PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   return sms;
 }
 

@@ -141,6 +141,7 @@ struct ps_problem {
   bool adj_ready = false;
   ps::DevBuf<unsigned long long> inc;
   ps::DevBuf<int> flag;
+  ps::DevBuf<double> jpart;  // per-block partial sums of the loss of ps_adjoint, then J
   unsigned long long* h_inc = nullptr;
   int* h_flag = nullptr;
   std::vector<double> hist;

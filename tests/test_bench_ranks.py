@@ -73,8 +73,21 @@ def test_reference_arm_dr_times_douglas_rachford_steps():
     assert "DR step" in d["cpu_baseline"]["sample"] and d["value"] > 0
 
 
-def test_fine_dr_refuses_workloads_without_the_dimensional_splitting():
-    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "dd2d_1023",
-           "--fine", "dr", "--steps", "1", "--warmup", "3"]
-    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
-    assert r.returncode != 0 and "dimensional-splitting" in (r.stderr + r.stdout)
+def test_fine_dr_refuses_batch_and_adjoint_workloads():
+    for w in ("batch256", "adjoint2d_511"):
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", w,
+               "--fine", "dr", "--steps", "1", "--warmup", "3"]
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+        assert r.returncode != 0 and "single-problem workloads" in (r.stderr + r.stdout), w
+
+
+def test_scalability_workload_recipe():
+    """The Sec. 5.1 scalability workload: 99^2, q = 2 fine strips of overlap 1/16, q coarse strips
+    of overlap 1/32, five iterations, the manufactured solution for the error."""
+    sys.path.insert(0, ROOT)
+    import bench
+    cfg = bench.workload("dd_scal99_q8")
+    assert cfg["n"] == (99, 99) and cfg["N"] == 32 and cfg["s"] == 100 and cfg["max_iter"] == 5
+    assert cfg["boxes"] == (4, 1) and cfg["coarse_boxes"] == (16, 1)
+    assert cfg["overlap"] == 1 / 16 and cfg["coarse_overlap"] == 1 / 32
+    assert cfg["src_t"].shape == (32 * 100 + 1,)

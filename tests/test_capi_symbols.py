@@ -29,9 +29,13 @@ def libps():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
+    # the calls of the boundary: handles, slices and step counts, run to tolerance, state and
+    # history, the plain comparator, the adjoint, batches and the autotuner
     for must in ("ps_grid_create", "ps_operator_create", "ps_splitting_create", "ps_problem_create",
-                 "ps_run_parareal", "ps_get_state", "ps_get_history", "ps_last_error"):
-        assert must in names
+                 "ps_problem_set_slices", "ps_run_parareal", "ps_get_state", "ps_get_history", "ps_last_error",
+                 "ps_run_fine_sequential", "ps_adjoint", "ps_adjoint_vjp", "ps_batch_create", "ps_batch_add",
+                 "ps_batch_run", "ps_batch_get_state", "ps_batch_destroy", "ps_autotune"):
+        assert must in names, must
 
 
 def test_every_declared_symbol_is_exported(libps):
@@ -66,3 +70,15 @@ def test_host_side_validation_without_gpu(libps):
     # the wait-limit self-test validates its limit before touching the device
     assert lib.ps_selftest_wait_timeout(0, 0) == 1
     assert b"limit_us" in lib.ps_last_error()
+
+
+def test_handle_calls_reject_null_handles(libps):
+    """The new handle calls check their arguments before any CUDA call."""
+    import paper_2502_08370_gb300 as ps
+    lib = ps.lib()
+    assert lib.ps_problem_set_slices(None, 4, 1, 4, 0) == 1
+    assert lib.ps_batch_add(None, None, 0) == 1
+    assert lib.ps_batch_get_state(None, 0, 0, None, 0) == 1
+    h = ctypes.c_void_p()
+    assert lib.ps_batch_create(None, -1, 0, ctypes.byref(h)) == 1
+    assert lib.ps_adjoint(None, None, 1e-8, 0, None, None, 0, None, None) == 1

@@ -89,17 +89,33 @@ def test_autotune_changes_no_result(ps):
 
 def test_batch256_sampled_against_individual_runs(ps):
     """The full heterogeneous batch (256 problems, grids up to 511^2, N up to 64, s up to 128):
-    eight sampled problems re-run alone must match their batched results bitwise."""
+    eight sampled problems re-run alone must match their batched results bitwise, and on each of
+    them a sampled slice of the converged batched iterate satisfies U_{j+1} ~ F(U_j) against the
+    oracle's FP64 fine steps, within the FP32 bound of one slice (4 s M 2^-24) plus twice the
+    problem's last increment (F and G are max-norm contractions); U_1 = F(u0) within the FP32
+    bound (finite termination)."""
     cfgs = wl.batch256()
     probs = [make(ps, c) for c in cfgs]
     u0s = [dev(c["u0"]) for c in cfgs]
     batch = ps.Batch(probs)
     its = batch.run(u0s, 1e-8)
     assert all(1 <= k <= c["N"] for k, c in zip(its, cfgs))
-    sample = np.random.default_rng(0).choice(len(cfgs), 8, replace=False)
-    batched = {int(i): (its[i], probs[i].state(probs[i].N).cpu().numpy()) for i in sample}
+    rng = np.random.default_rng(0)
+    sample = [int(i) for i in rng.choice(len(cfgs), 8, replace=False)]
+    batched = {i: (its[i], [batch.state(i, j).cpu().numpy() for j in range(cfgs[i]["N"] + 1)],
+                   probs[i].history()) for i in sample}
     for i in sample:
-        i = int(i)
+        c = cfgs[i]
+        k, U, hist = batched[i]
+        bound = 4.0 * c["s"] * 2 * 2.0 ** -24
+        orp = orc.Problem(c["n"], a=c["a"])
+        tau = c["T"] / c["N"] / c["s"]
+        u1 = orc.propagate(orp, tau, c["s"], c["u0"], t0=0, tstride=1)
+        assert np.abs(U[1] - u1).max() <= bound * np.abs(u1).max(), i
+        j = int(rng.integers(k, c["N"])) if k < c["N"] else c["N"] - 1
+        ref = orc.propagate(orp, tau, c["s"], U[j], t0=j * c["s"], tstride=1)
+        assert np.abs(U[j + 1] - ref).max() <= bound * np.abs(ref).max() + 2 * hist[-1], (i, j)
+    for i in sample:
         k = probs[i].run(u0s[i], 1e-8)
         assert k == batched[i][0]
-        assert np.array_equal(probs[i].state(probs[i].N).cpu().numpy(), batched[i][1])
+        assert np.array_equal(probs[i].state(probs[i].N).cpu().numpy(), batched[i][1][-1])

@@ -1,5 +1,6 @@
 """GPU parity of Parareal/FIE-DR (Sec. 4.2): the fine propagator takes s Douglas-Rachford
-steps (eq. DR_method), the coarse one FIE steps.  FP64 and the dimensional splitting only.
+steps (eq. DR_method), the coarse one FIE steps.  FP64, with the dimensional splitting and with
+the domain-decomposition splitting (Sec. 2.1; Fig. 4 runs FIE-DR with both).
 
 Every call goes through the C ABI.  Results must match the oracle's Parareal/FIE-DR to 1e-12
 in relative max-norm with equal iteration counts; the parareal states at n <= k equal the
@@ -36,13 +37,17 @@ def relmax(a, b):
 
 
 def make(ps, n, a=None, c=0.0, src=None, src_t=None, T=1.0, N=4, g=1, s=4, precision="fp64", split="dim",
-         boxes=(1, 1), overlap=0.0):
+         boxes=(1, 1), overlap=0.0, coarse=None):
+    """coarse = (boxes, overlap) of a separate DD decomposition for G, or None (G uses F's)."""
     grid = ps.Grid(n)
     op = ps.Operator(grid, a=None if a is None else dev(a), c=c, src=None if src is None else dev(src), src_t=src_t)
     sp = ps.Splitting(op, split, boxes, overlap)
-    prob = ps.Problem(sp, T, N, g, s, precision=precision, fine_method="dr")
-    prob._keep = (grid, op, sp)
+    spc = ps.Splitting(op, "dd", coarse[0], coarse[1]) if coarse else None
+    prob = ps.Problem(sp, T, N, g, s, coarse=spc, precision=precision, fine_method="dr")
+    prob._keep = (grid, op, sp, spc)
     orp = orc.Problem(n, a=a, c=c, src=src, src_t=src_t, split=split, boxes=boxes, overlap=overlap)
+    if coarse:
+        orp.pG = orc.Problem(n, a=a, c=c, src=src, src_t=src_t, split="dd", boxes=coarse[0], overlap=coarse[1])
     return prob, orp
 
 
@@ -106,13 +111,50 @@ def test_finite_termination_bitwise(ps):
             assert np.array_equal(prob.state(j).cpu().numpy(), fine[j]), (k, j)
 
 
+# DD splitting (Sec. 2.1): boxes, overlap in cells, and an optional coarse decomposition
+DD_CASES = [((31, 23), (4, 3), 3, None), ((40, 17), (4, 1), 4, ((8, 1), 2)), ((19, 26), (2, 2), 2, None)]
+
+
+@pytest.mark.parametrize("n,boxes,ovc,coarse", DD_CASES)
+def test_parareal_fie_dr_dd_matches_oracle(ps, n, boxes, ovc, coarse):
+    N, s, T = 8, 6, 0.25
+    a, src, src_t, u0 = inputs(n, N, s, 35)
+    h = 1.0 / (max(n) + 1)
+    cz = (coarse[0], coarse[1] * h) if coarse else None
+    prob, orp = make(ps, n, a=a, c=0.3, src=src, src_t=src_t, T=T, N=N, s=s, split="dd", boxes=boxes,
+                     overlap=ovc * h, coarse=cz)
+    # thin overlaps contract slowly (Fig. 7): compare the iterate after 3 iterations (every
+    # slice past the finite-termination front carries corrections) and the run to k = N
+    for max_iter in (3, 0):
+        it = prob.run(dev(u0), 1e-9, max_iter)
+        U_ref, hist_ref, it_ref = orc.parareal(orp, T, N, 1, s, u0, 1e-9, max_iter=max_iter or None, fine="dr",
+                                               pG=getattr(orp, "pG", None))
+        assert it == it_ref
+        np.testing.assert_allclose(prob.history(), hist_ref, rtol=1e-6)
+        for j in range(N + 1):
+            assert relmax(prob.state(j).cpu().numpy(), U_ref[j]) < RTOL64, (max_iter, j)
+
+
+def test_fine_sequential_dr_dd_and_finite_termination(ps):
+    n, N, s, T = (29, 21), 5, 4, 0.3
+    a, src, src_t, u0 = inputs(n, N, s, 36)
+    prob, orp = make(ps, n, a=a, c=0.2, src=src, src_t=src_t, T=T, N=N, s=s, split="dd", boxes=(3, 2),
+                     overlap=3.0 / 30)
+    u0d = dev(u0)
+    fine = prob.fine_sequential(u0d).cpu().numpy()
+    ref = orc.fine_sequential_dr(orp, T, N, s, u0)
+    for j in range(N + 1):
+        assert relmax(fine[j], ref[j]) < RTOL64, j
+    for k in (1, 3, N):
+        assert prob.run(u0d, 0.0, max_iter=k) == k
+        for j in range(k + 1):
+            assert np.array_equal(prob.state(j).cpu().numpy(), fine[j]), (k, j)
+
+
 def test_dr_is_rejected_where_unsupported(ps):
     n = (13, 11)
     with pytest.raises(ps.PsError) as e:
         make(ps, n, precision="mixed")
-    assert e.value.code == 6
-    with pytest.raises(ps.PsError) as e:
-        make(ps, n, split="dd", boxes=(2, 2), overlap=2.0 / 14)
     assert e.value.code == 6
     prob, _ = make(ps, n, a=np.ones((13, 15)), N=3, s=2)
     u0 = dev(np.ones((11, 13)))
