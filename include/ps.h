@@ -115,6 +115,31 @@ int ps_grid_destroy(ps_grid* g);
 int ps_operator_create(const ps_grid* g, const double* a_nodal_dev, double c, const double* src_dev,
                        const double* src_t_host, int src_t_len, uintptr_t stream, ps_operator** out);
 int ps_operator_destroy(ps_operator* op);
+/* Operator with every option (ps_operator_create covers a scalar diffusion and one source):
+ *   u_t = div(D grad u) - c u + src(x) src_t(t) + src2(x) src2_t(t),
+ * D = a I, or in 2-D the full tensor D = [[a, d12], [d12, a]] of Sec. 5.2 when d12_nodal_dev is
+ * given (nodal, boundary included, same layout as a; D must be SPD at every node).  The mixed
+ * derivatives make the stencil nine-point: only the DD splitting takes such an operator
+ * (ps_splitting_create returns PS_ERR_UNSUPPORTED for PS_SPLIT_DIM, as the paper notes in
+ * Sec. 2.1).  The operator is assembled cell by cell: on every grid cell, D is the mean of its
+ * four nodal values and the DD weight rho_j is taken at the cell centre; the cell's quadratic
+ * form uses the x-differences of its bottom and top edges, the y-differences of its left and
+ * right edges and its mean gradient for the d12 term.  With d12 = 0 this is a five-point
+ * scheme whose edge coefficient is the mean of the two adjacent cells' a (not the nodal mean of
+ * ps_operator_create).  src2 needs src and the DD splitting; src2_t is indexed like src_t.
+ * Fields left NULL / 0 are absent (a = 1, d12 = 0, no source). */
+typedef struct {
+  const double* a_nodal_dev;   /* diagonal diffusion a, nodal, or NULL (a = 1) */
+  const double* d12_nodal_dev; /* off-diagonal diffusion, nodal, or NULL (D = a I) */
+  double c;                    /* reaction, >= 0 */
+  const double* src_dev;       /* first source term, interior nodes, or NULL */
+  const double* src_t_host;    /* its time factors at t_j = j dt, or NULL (1) */
+  int src_t_len;
+  const double* src2_dev;      /* second source term, or NULL */
+  const double* src2_t_host;
+  int src2_t_len;
+} ps_operator_desc;
+int ps_operator_create_ex(const ps_grid* g, const ps_operator_desc* desc, uintptr_t stream, ps_operator** out);
 
 /* ---- splitting L = L_1 + ... + L_M (Sec. 2.1) ----------------------------------------- */
 typedef struct {

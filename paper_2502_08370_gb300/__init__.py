@@ -44,6 +44,12 @@ class _DD(C.Structure):
     _fields_ = [("boxes", C.c_int * 2), ("overlap", C.c_double)]
 
 
+class _OpDesc(C.Structure):
+    _fields_ = [("a_nodal_dev", C.c_void_p), ("d12_nodal_dev", C.c_void_p), ("c", C.c_double),
+                ("src_dev", C.c_void_p), ("src_t_host", C.c_void_p), ("src_t_len", C.c_int),
+                ("src2_dev", C.c_void_p), ("src2_t_host", C.c_void_p), ("src2_t_len", C.c_int)]
+
+
 class _Params(C.Structure):
     _fields_ = [("precision", C.c_int), ("schedule", C.c_int), ("timing", C.c_int), ("dd_slices_per_block", C.c_int),
                 ("tile_positions", C.c_int), ("tile_pipeline", C.c_int), ("tile_slots", C.c_int),
@@ -75,6 +81,7 @@ SIGNATURES = {
     "ps_grid_destroy": [_VP],
     "ps_operator_create": [_VP, _VP, _D, _VP, _VP, _I, _U, C.POINTER(_VP)],
     "ps_operator_destroy": [_VP],
+    "ps_operator_create_ex": [_VP, C.POINTER(_OpDesc), _U, C.POINTER(_VP)],
     "ps_splitting_create": [_VP, _I, C.POINTER(_DD), C.POINTER(_VP)],
     "ps_splitting_destroy": [_VP],
     "ps_problem_create": [_VP, _VP, _D, _I, _I, _I, C.POINTER(_Params), _U, C.POINTER(_VP)],
@@ -187,18 +194,28 @@ class Grid:
 
 
 class Operator:
-    """u_t = div(a grad u) - c u + src(x) src_t(t); a nodal incl. boundary (None: a = 1)."""
+    """u_t = div(D grad u) - c u + src(x) src_t(t) + src2(x) src2_t(t); D = a I with a nodal incl.
+    boundary (None: a = 1), or the full 2-D tensor [[a, d12], [d12, a]] when d12 (nodal) is given
+    (DD splitting only, Sec. 5.2)."""
 
-    def __init__(self, grid: Grid, a=None, c=0.0, src=None, src_t=None, stream=None):
+    def __init__(self, grid: Grid, a=None, c=0.0, src=None, src_t=None, d12=None, src2=None, src2_t=None,
+                 stream=None):
         import numpy as np
         self.grid = grid
-        st = None
-        if src_t is not None:
-            st = np.ascontiguousarray(src_t, dtype=np.float64)
+        st = None if src_t is None else np.ascontiguousarray(src_t, dtype=np.float64)
+        st2 = None if src2_t is None else np.ascontiguousarray(src2_t, dtype=np.float64)
+        self._host = (st, st2)  # the library copies them during the call
         h = _VP()
-        check(lib().ps_operator_create(grid._h, _dev_ptr(a, grid.nodal_size), float(c), _dev_ptr(src, grid.nt),
-                                       None if st is None else st.ctypes.data_as(_VP), 0 if st is None else st.size,
-                                       _stream(stream), C.byref(h)))
+        if d12 is None and src2 is None:
+            check(lib().ps_operator_create(grid._h, _dev_ptr(a, grid.nodal_size), float(c), _dev_ptr(src, grid.nt),
+                                           None if st is None else st.ctypes.data_as(_VP),
+                                           0 if st is None else st.size, _stream(stream), C.byref(h)))
+        else:
+            d = _OpDesc(_dev_ptr(a, grid.nodal_size), _dev_ptr(d12, grid.nodal_size), float(c), _dev_ptr(src, grid.nt),
+                        None if st is None else st.ctypes.data_as(_VP), 0 if st is None else st.size,
+                        _dev_ptr(src2, grid.nt), None if st2 is None else st2.ctypes.data_as(_VP),
+                        0 if st2 is None else st2.size)
+            check(lib().ps_operator_create_ex(grid._h, C.byref(d), _stream(stream), C.byref(h)))
         self._h = h
 
     def __del__(self):

@@ -72,7 +72,7 @@ void build_prop(ps_problem* p, Prop& P, const ps_splitting* sp, double tau, int 
   } else {
     if (f32) throw Error(PS_ERR_UNSUPPORTED, "DD splitting runs in FP64 only");
     P.dd = std::make_unique<DDFactors>();
-    dd_factor(p->g, sp->dd, op->a.p, op->c, tau, *P.dd, st);
+    dd_factor(p->g, sp->dd, op->a.p, op->d12.p, op->c, tau, *P.dd, st);
   }
 }
 
@@ -85,6 +85,8 @@ SourceArgs source_for(const ps_problem* p, const Prop& P, int t0, int tslice) {
   sa.tstride = tslice;
   sa.src_t_len = p->op->src_t_len;
   sa.tau = P.tau;
+  sa.src2 = p->op->src2.p;
+  sa.src2_t = p->op->src2_t.p;
   return sa;
 }
 
@@ -232,7 +234,10 @@ void run_F_dr(ps_problem* p, int n_first, int nsl, const double* in, double* out
     const double* u = q == 0 ? in : out;
     SourceArgs sa = source_for(p, P, n_first * p->fs + (q + 1) * P.tstride, p->fs);
     p->kt.begin(st);
-    dr_increment(p->g, nsl, p->op->a.p, p->op->c, P.tau, u, W, sa, st);
+    if (p->op->d12.p)
+      dr_increment_tensor(p->g, nsl, p->op->a.p, p->op->d12.p, p->op->c, P.tau, u, W, sa, st);
+    else
+      dr_increment(p->g, nsl, p->op->a.p, p->op->c, P.tau, u, W, sa, st);
     if (p->kt.on)
       p->kt.end("F.drW.f64", dnt * 16.0 + (p->op->a.p ? nt * 8.0 : 0.0) + (sa.src ? nt * 8.0 : 0.0),
                 dnt * (1.0 + 6.0 * M + (sa.src ? 3.0 : 0.0)));
@@ -498,6 +503,8 @@ void configure_slices(ps_problem* p, int N, int g_steps, int f_steps, cudaStream
   PS_REQUIRE(f_steps % g_steps == 0, "f_steps must be a multiple of g_steps");
   if (p->op->src_t.p)
     PS_REQUIRE(p->op->src_t_len >= (long long)N * f_steps + 1, "src_t must cover the fine times 0..N*f_steps");
+  if (p->op->src2_t.p)
+    PS_REQUIRE(p->op->src2_t_len >= (long long)N * f_steps + 1, "src2_t must cover the fine times 0..N*f_steps");
   PS_REQUIRE((long long)(N + 1) * p->g.nt * 8 < (1LL << 46), "slice states too large");
   const ps_splitting* fine = p->fine;
   const ps_splitting* coarse = p->coarse;
@@ -717,34 +724,59 @@ int ps_grid_destroy(ps_grid* g) {
   return PS_OK;
 }
 
-int ps_operator_create(const ps_grid* g, const double* a_nodal_dev, double c, const double* src_dev,
-                       const double* src_t_host, int src_t_len, uintptr_t stream, ps_operator** out) {
+int ps_operator_create_ex(const ps_grid* g, const ps_operator_desc* d, uintptr_t stream, ps_operator** out) {
   return guarded([&] {
-    PS_REQUIRE(g && out, "null argument");
-    PS_REQUIRE(c >= 0.0 && std::isfinite(c), "c must be finite and >= 0");
-    PS_REQUIRE(!src_t_host || src_t_len > 0, "src_t_len must be positive");
+    PS_REQUIRE(g && d && out, "null argument");
+    PS_REQUIRE(d->c >= 0.0 && std::isfinite(d->c), "c must be finite and >= 0");
+    PS_REQUIRE(!d->src_t_host || d->src_t_len > 0, "src_t_len must be positive");
+    PS_REQUIRE(!d->src2_t_host || d->src2_t_len > 0, "src2_t_len must be positive");
+    PS_REQUIRE(!d->src2_dev || d->src_dev, "a second source term needs the first");
+    const Geom& G = g->g;
+    if (d->d12_nodal_dev && G.dim != 2)
+      throw Error(PS_ERR_UNSUPPORTED, "the full diffusion tensor is implemented in 2-D");
     auto op = std::make_unique<ps_operator>();
     op->grid = g;
-    op->c = c;
+    op->c = d->c;
     cudaStream_t st = S(stream);
-    const Geom& G = g->g;
-    if (a_nodal_dev) {
-      long long na = (long long)(G.n[0] + 2) * (G.n[1] + 2) * (G.dim == 3 ? G.n[2] + 2 : 1);
-      op->a.alloc(na);
-      PS_CUDA(cudaMemcpyAsync(op->a.p, a_nodal_dev, sizeof(double) * na, cudaMemcpyDeviceToDevice, st));
+    const long long na = (long long)(G.n[0] + 2) * (G.n[1] + 2) * (G.dim == 3 ? G.n[2] + 2 : 1);
+    auto copy_dev = [&](DevBuf<double>& b, const double* src, long long n) {
+      b.alloc(n);
+      PS_CUDA(cudaMemcpyAsync(b.p, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    };
+    auto copy_host = [&](DevBuf<double>& b, const double* src, int n) {
+      b.alloc(n);
+      PS_CUDA(cudaMemcpyAsync(b.p, src, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    };
+    if (d->a_nodal_dev) copy_dev(op->a, d->a_nodal_dev, na);
+    if (d->d12_nodal_dev) copy_dev(op->d12, d->d12_nodal_dev, na);
+    if (d->src_dev) {
+      copy_dev(op->src, d->src_dev, G.nt);
+      if (d->src_t_host) {
+        copy_host(op->src_t, d->src_t_host, d->src_t_len);
+        op->src_t_len = d->src_t_len;
+      }
     }
-    if (src_dev) {
-      op->src.alloc(G.nt);
-      PS_CUDA(cudaMemcpyAsync(op->src.p, src_dev, sizeof(double) * G.nt, cudaMemcpyDeviceToDevice, st));
-      if (src_t_host) {
-        op->src_t.alloc(src_t_len);
-        op->src_t_len = src_t_len;
-        PS_CUDA(cudaMemcpyAsync(op->src_t.p, src_t_host, sizeof(double) * src_t_len, cudaMemcpyHostToDevice, st));
+    if (d->src2_dev) {
+      copy_dev(op->src2, d->src2_dev, G.nt);
+      if (d->src2_t_host) {
+        copy_host(op->src2_t, d->src2_t_host, d->src2_t_len);
+        op->src2_t_len = d->src2_t_len;
       }
     }
     PS_CUDA(cudaStreamSynchronize(st));
     *out = op.release();
   });
+}
+
+int ps_operator_create(const ps_grid* g, const double* a_nodal_dev, double c, const double* src_dev,
+                       const double* src_t_host, int src_t_len, uintptr_t stream, ps_operator** out) {
+  ps_operator_desc d{};
+  d.a_nodal_dev = a_nodal_dev;
+  d.c = c;
+  d.src_dev = src_dev;
+  d.src_t_host = src_t_host;
+  d.src_t_len = src_t_len;
+  return ps_operator_create_ex(g, &d, stream, out);
 }
 
 int ps_operator_destroy(ps_operator* op) {
@@ -760,6 +792,8 @@ int ps_splitting_create(const ps_operator* op, int kind, const ps_dd_params* dd,
     sp->kind = kind;
     const Geom& G = op->grid->g;
     if (kind == PS_SPLIT_DIM) {
+      if (op->d12.p)
+        throw Error(PS_ERR_UNSUPPORTED, "the full diffusion tensor's mixed derivatives need the DD splitting (Sec. 2.1)");
       sp->M = G.dim;
     } else if (kind == PS_SPLIT_DD) {
       PS_REQUIRE(dd, "DD splitting needs ps_dd_params");
@@ -805,6 +839,8 @@ int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, doub
     p->dr = p->prm.fine_method == PS_FINE_DR;
     if (p->dr && p->prm.precision != PS_PREC_FP64)
       throw Error(PS_ERR_UNSUPPORTED, "the Douglas-Rachford fine propagator runs in FP64");
+    if (p->op->src2.p && (fine->kind != PS_SPLIT_DD || coarse->kind != PS_SPLIT_DD))
+      throw Error(PS_ERR_UNSUPPORTED, "a second source term is implemented with the DD splitting");
     p->delta32 = p->prm.coarse == PS_COARSE_DELTA32;
     if (p->delta32 && (fine->kind != PS_SPLIT_DIM || coarse->kind != PS_SPLIT_DIM))
       throw Error(PS_ERR_UNSUPPORTED, "the FP32 coarse increment form needs the dimensional splitting");
@@ -932,6 +968,8 @@ int ps_propagate(ps_problem* p, int which, int nsteps, int t0, int tstride, doub
     Prop& P = which == 0 ? p->F : p->G;
     if (p->op->src_t.p)
       PS_REQUIRE(t0 >= 0 && t0 + (long long)nsteps * tstride < p->op->src_t_len, "time index outside src_t");
+    if (p->op->src2_t.p)
+      PS_REQUIRE(t0 >= 0 && t0 + (long long)nsteps * tstride < p->op->src2_t_len, "time index outside src2_t");
     cudaStream_t st = S(stream);
     tile_flag_reset(p, st);
     for (int q = 0; q < nsteps; ++q) {
@@ -1090,7 +1128,7 @@ int ps_problem_update_coefficients(ps_problem* p, const double* a_nodal_dev, uin
           else if (p->delta32 && m == 0) factor_lines(g3, *P->dim[m], true, st);
         }
       } else {
-        dd_factor(p->g, P->sp->dd, op->a.p, op->c, P->tau, *P->dd, st);
+        dd_factor(p->g, P->sp->dd, op->a.p, op->d12.p, op->c, P->tau, *P->dd, st);
       }
     }
     p->have_forward = false;

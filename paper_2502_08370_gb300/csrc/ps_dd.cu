@@ -15,7 +15,19 @@
 // is a dense (w x w)(w x slices) product spread over a CTA.
 //
 // Factors per box and line k, contiguous: S_k^{-1} (w x w, column-major; symmetric),
-// F_k = S_k^{-1} C_{k+1} (w x w, column-major), c_k (w); each padded to 16 bytes.
+// F_k = S_k^{-1} C_{k+1}^T (w x w, column-major), then the couplings of line k to line k-1:
+// c_k (w), and for the full tensor also its neighbours c^-_k, c^+_k (C_k tridiagonal); each
+// padded to 16 bytes.
+//
+// Full diffusion tensor D = [[a, d12], [d12, a]] (Sec. 5.2): the mixed derivatives couple
+// every node to its eight neighbours ("nonadiagonal" systems).  The operator is assembled
+// from one quadratic form per grid cell, with D the mean of the cell's four nodal values and
+// rho_j taken at the cell centre: with the cell's edge differences and its mean gradient,
+//     Q(u, v) = a/(2hx^2) (dx_b u dx_b v + dx_t u dx_t v) + a/(2hy^2) (dy_l u dy_l v + dy_r u dy_r v)
+//             + d12 (g_x u g_y v + g_x v g_y u),
+// (I - tau A_j) = I + tau sum over cells of rho_j Q (plus tau rho_j c on the diagonal).  Each
+// cell's form is positive semidefinite when D is SPD, so every block stays SPD.  In the
+// line-by-line order C_k becomes tridiagonal; S_k and F_k keep their dense form.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -45,13 +57,14 @@ __host__ __device__ inline double phi1d(int b, int B, double w, double x) {
   return left * right;
 }
 
-// Assembled band row r of (I - tau A_j) restricted to the box, entries (r, r - d),
-// d = 0..w: diagonal, and the couplings to the previous node in the lead direction
-// (d = 1) and in the other direction (d = w).
+// Assembled row r of (I - tau A_j) restricted to the box: the diagonal, the coupling to the
+// previous position on the same line (lead), and the couplings to the previous line at the
+// same position (other) and, for the full tensor, at the positions before and after it
+// (other_m, other_p).  Couplings that leave the box are dropped (their weights vanish).
 struct RowEntries {
-  double diag, lead, other;
+  double diag, lead, other, other_m, other_p;
 };
-__device__ RowEntries assemble_row(const DDBox& bx, const DDGeomArgs& ga, int r) {
+__device__ RowEntries assemble_row_5pt(const DDBox& bx, const DDGeomArgs& ga, int r) {
   int slow = r / bx.lead, fast = r - slow * bx.lead;
   int i, j;  // 1-based interior node
   if (bx.xfast) {
@@ -81,17 +94,76 @@ __device__ RowEntries assemble_row(const DDBox& bx, const DDGeomArgs& ga, int r)
     e.lead = fast > 0 ? -ga.tau * wym : 0.0;
     e.other = slow > 0 ? -ga.tau * wxm : 0.0;
   }
+  e.other_m = e.other_p = 0.0;
   return e;
 }
 
-// Band row r: entry d = 0 is the diagonal, d = 1 the previous node in the lead direction,
-// d = w the previous node in the other direction (both at d = 1 when w = 1).
-__device__ __forceinline__ void store_row(double* row, const RowEntries& e, int w) {
-  row[0] = e.diag;
-  if (w >= 1) {
-    row[1] = e.lead;
-    row[w] += e.other;
+// Weights of cell (ci, cj) (lower-left node; 0..nx, 0..ny, boundary nodes included) in the
+// full-tensor form: rho a / (2 hx^2), rho a / (2 hy^2), rho d12 / (hx hy), with a and d12 the
+// means of the cell's four nodal values and rho the box weight at the cell centre.
+struct CellW {
+  double ax, ay, g;
+};
+__device__ CellW cell_weights(const DDBox& bx, const DDGeomArgs& ga, int ci, int cj, double hx, double hy) {
+  const int nx2 = ga.nx + 2;
+  auto mean4 = [&](const double* f) {
+    if (!f) return 1.0;
+    const long long i0 = (long long)cj * nx2 + ci;
+    return 0.25 * (f[i0] + f[i0 + 1] + f[i0 + nx2] + f[i0 + nx2 + 1]);
+  };
+  const double rho = phi1d(bx.bx, ga.Bx, ga.overlap, (ci + 0.5) * hx) * phi1d(bx.by, ga.By, ga.overlap, (cj + 0.5) * hy);
+  const double a = mean4(ga.a);
+  const double b = ga.d12 ? mean4(ga.d12) : 0.0;
+  CellW w;
+  w.ax = rho * a / (2.0 * hx * hx);
+  w.ay = rho * a / (2.0 * hy * hy);
+  w.g = rho * b / (hx * hy);
+  return w;
+}
+
+// Full-tensor row of node P = (i, j): the four cells around P (SW, SE, NW, NE) each add their
+// form's entries.  With (ax, ay, g) of a cell and P at its corner, the diagonal takes
+// ax + ay + g/2 from SW and NE and ax + ay - g/2 from SE and NW; the edge neighbours take
+// -ax (W: from SW and NW) or -ay (S: from SW and SE); the corner neighbours take -g/2 (SW)
+// and +g/2 (SE from cell SE, NW from cell NW).  Rows of (I - tau A_j) carry these times tau.
+__device__ RowEntries assemble_row_full(const DDBox& bx, const DDGeomArgs& ga, int r) {
+  const int slow = r / bx.lead, fast = r - slow * bx.lead;
+  int i, j;
+  if (bx.xfast) {
+    i = bx.x0 + fast;
+    j = bx.y0 + slow;
+  } else {
+    i = bx.x0 + slow;
+    j = bx.y0 + fast;
   }
+  const double hx = 1.0 / (ga.nx + 1), hy = 1.0 / (ga.ny + 1);
+  const CellW sw = cell_weights(bx, ga, i - 1, j - 1, hx, hy), se = cell_weights(bx, ga, i, j - 1, hx, hy);
+  const CellW nw = cell_weights(bx, ga, i - 1, j, hx, hy), ne = cell_weights(bx, ga, i, j, hx, hy);
+  const double t = ga.tau;
+  const double rho0 = phi1d(bx.bx, ga.Bx, ga.overlap, i * hx) * phi1d(bx.by, ga.By, ga.overlap, j * hy);
+  RowEntries e;
+  e.diag = 1.0 + t * ((sw.ax + sw.ay + 0.5 * sw.g) + (se.ax + se.ay - 0.5 * se.g) + (nw.ax + nw.ay - 0.5 * nw.g) +
+                      (ne.ax + ne.ay + 0.5 * ne.g)) +
+           t * ga.c * rho0;
+  const double W = -t * (sw.ax + nw.ax), Sv = -t * (sw.ay + se.ay);
+  const double cSW = -t * 0.5 * sw.g, cSE = t * 0.5 * se.g, cNW = t * 0.5 * nw.g;
+  const bool first_pos = fast == 0, last_pos = fast == bx.lead - 1, first_line = slow == 0;
+  if (bx.xfast) {  // positions along x, lines along y: previous line = (., j - 1)
+    e.lead = first_pos ? 0.0 : W;
+    e.other = first_line ? 0.0 : Sv;
+    e.other_m = (first_line || first_pos) ? 0.0 : cSW;
+    e.other_p = (first_line || last_pos) ? 0.0 : cSE;
+  } else {  // positions along y, lines along x: previous line = (i - 1, .)
+    e.lead = first_pos ? 0.0 : Sv;
+    e.other = first_line ? 0.0 : W;
+    e.other_m = (first_line || first_pos) ? 0.0 : cSW;
+    e.other_p = (first_line || last_pos) ? 0.0 : cNW;
+  }
+  return e;
+}
+
+__device__ __forceinline__ RowEntries assemble_row(const DDBox& bx, const DDGeomArgs& ga, int r) {
+  return ga.full ? assemble_row_full(bx, ga, r) : assemble_row_5pt(bx, ga, r);
 }
 
 // Entries of the box block: line k, position i (0-based, w positions per line).
@@ -106,18 +178,25 @@ __device__ __forceinline__ long long line_node(const DDBox& bx, int nx, int k, i
 
 __host__ __device__ inline long long dd_sq(int w) { return ((long long)w * w + 1) & ~1LL; }
 __host__ __device__ inline long long dd_vec(int w) { return (w + 1) & ~1; }
-__host__ __device__ inline long long dd_line_stride(int w) { return 2 * dd_sq(w) + dd_vec(w); }
+// one line's record: S_k^{-1}, F_k, then c_k (and c^-_k, c^+_k for the full tensor)
+__host__ __device__ inline long long dd_line_stride(int w, int full) { return 2 * dd_sq(w) + (full ? 3 : 1) * dd_vec(w); }
 
-// The factorisation holds one w x w Schur complement and five w-vectors in shared memory, and
+// The factorisation holds one w x w Schur complement and ten w-vectors in shared memory, and
 // the solve runs one thread per line position (at most 192).
 constexpr int kMaxLead = 160;
+constexpr int kFactorVecs = 10;
 
 // ---------------------------------------------------------------------------------------
 // a1 (DD): one CTA per box.  The Schur complement of the current line lives in shared
 // memory; it is inverted in place by Gauss-Jordan elimination without pivoting (SPD), its
 // inverse stored, and the next line's complement formed from it.  *status = 1 on a
 // non-positive pivot (the blocks are SPD, so only on bad input).
-// Shared memory: A (w x w, row-major), then the vectors rs, cp, cprev, dg, ld (w each).
+//     S_k = T_k - C_k S_{k-1}^{-1} C_k^T,   F_k = S_k^{-1} C_{k+1}^T
+// With the five-point operator C_k = diag(c_k) and the product is formed in place; for the
+// full tensor C_k is tridiagonal and entry (i, j) of C_k S_{k-1}^{-1} C_k^T sums nine terms
+// of S_{k-1}^{-1}, read from its stored copy (global memory, written by this CTA).
+// Shared memory: A (w x w, row-major), then kFactorVecs w-vectors.
+template <bool FULL>
 __global__ void __launch_bounds__(512) dd_factor_kernel(const DDBox* __restrict__ boxes, DDGeomArgs ga,
                                                         double* __restrict__ fac, int* status) {
   const DDBox bx = boxes[blockIdx.x];
@@ -126,30 +205,63 @@ __global__ void __launch_bounds__(512) dd_factor_kernel(const DDBox* __restrict_
   double* A = sm;
   double* rs = A + w * w;  // pivot row / pivot
   double* cp = rs + w;     // pivot column
-  double* cprev = cp + w;  // c_k: coupling of line k to line k - 1
-  double* dg = cprev + w;  // diagonal of T_k
+  double* dg = cp + w;     // diagonal of T_k
   double* ld = dg + w;     // sub-diagonal of T_k (entry (i, i-1))
+  double* k0 = ld + w;     // C_k: coupling of line k to line k-1, same position
+  double* km = k0 + w;     //      ... position - 1 (full tensor)
+  double* kp = km + w;     //      ... position + 1 (full tensor)
+  double* n0 = kp + w;     // C_{k+1}, same layout (for F_k)
+  double* nm = n0 + w;
+  double* np = nm + w;
   __shared__ double s_inv;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + ty * blockDim.x, nthr = blockDim.x * blockDim.y;
   double* base = fac + bx.offset;
-  const long long ls = dd_line_stride(w), sq = dd_sq(w);
-  for (int e = tid; e < w; e += nthr) cprev[e] = 0.0;
+  const long long ls = dd_line_stride(w, FULL), sq = dd_sq(w), vec = dd_vec(w);
   for (int k = 0; k < m; ++k) {
     double* Sinv = base + k * ls;
     double* Fk = Sinv + sq;
-    double* ck = Sinv + 2 * sq;
+    double* ck = Sinv + 2 * sq;  // c_k, then (full tensor) c^-_k, c^+_k
     for (int e = tid; e < w; e += nthr) {
       const RowEntries re = assemble_row(bx, ga, box_row(bx, k, e));
       dg[e] = re.diag;
       ld[e] = re.lead;
-      ck[e] = cprev[e];
+      k0[e] = re.other;
+      ck[e] = re.other;
+      if (FULL) {
+        km[e] = re.other_m;
+        kp[e] = re.other_p;
+        ck[vec + e] = re.other_m;
+        ck[2 * vec + e] = re.other_p;
+      }
     }
     __syncthreads();
-    // S_k = T_k - C_k S_{k-1}^{-1} C_k   (A holds S_{k-1}^{-1}; cprev = c_k)
+    // S_k = T_k - C_k S_{k-1}^{-1} C_k^T   (A holds S_{k-1}^{-1}; full tensor: its stored copy)
+    const double* Pg = base + (k - 1) * ls;  // S_{k-1}^{-1}, column-major, symmetric
     for (int i = ty; i < w; i += blockDim.y)
       for (int j = tx; j < w; j += blockDim.x) {
         double t = (i == j) ? dg[i] : (j == i - 1 ? ld[i] : (i == j - 1 ? ld[j] : 0.0));
-        if (k > 0) t -= cprev[i] * A[i * w + j] * cprev[j];
+        if (k > 0) {
+          if (FULL) {
+            double acc = 0.0;
+            for (int da = -1; da <= 1; ++da) {
+              const int a = i + da;
+              if (a < 0 || a >= w) continue;
+              const double cia = da < 0 ? km[i] : (da == 0 ? k0[i] : kp[i]);
+              if (cia == 0.0) continue;
+              double row = 0.0;
+              for (int db = -1; db <= 1; ++db) {
+                const int b = j + db;
+                if (b < 0 || b >= w) continue;
+                const double cjb = db < 0 ? km[j] : (db == 0 ? k0[j] : kp[j]);
+                row = fma(Pg[(long long)b * w + a], cjb, row);
+              }
+              acc = fma(cia, row, acc);
+            }
+            t -= acc;
+          } else {
+            t -= k0[i] * A[i * w + j] * k0[j];
+          }
+        }
         A[i * w + j] = t;
       }
     __syncthreads();
@@ -183,11 +295,31 @@ __global__ void __launch_bounds__(512) dd_factor_kernel(const DDBox* __restrict_
     // S_k^{-1}, column-major
     for (int i = ty; i < w; i += blockDim.y)
       for (int j = tx; j < w; j += blockDim.x) Sinv[(long long)j * w + i] = A[i * w + j];
-    // c_{k+1} and F_k = S_k^{-1} C_{k+1}, column-major
-    for (int e = tid; e < w; e += nthr) cprev[e] = (k + 1 < m) ? assemble_row(bx, ga, box_row(bx, k + 1, e)).other : 0.0;
+    // C_{k+1} and F_k = S_k^{-1} C_{k+1}^T, column-major
+    for (int e = tid; e < w; e += nthr) {
+      if (k + 1 < m) {
+        const RowEntries re = assemble_row(bx, ga, box_row(bx, k + 1, e));
+        n0[e] = re.other;
+        nm[e] = re.other_m;
+        np[e] = re.other_p;
+      } else {
+        n0[e] = nm[e] = np[e] = 0.0;
+      }
+    }
     __syncthreads();
     for (int i = ty; i < w; i += blockDim.y)
-      for (int j = tx; j < w; j += blockDim.x) Fk[(long long)j * w + i] = A[i * w + j] * cprev[j];
+      for (int j = tx; j < w; j += blockDim.x) {
+        double f;
+        if (FULL) {
+          // sum over b of S_k^{-1}[i][b] C_{k+1}[j][b], b = j - 1, j, j + 1
+          f = A[i * w + j] * n0[j];
+          if (j > 0) f = fma(A[i * w + j - 1], nm[j], f);
+          if (j + 1 < w) f = fma(A[i * w + j + 1], np[j], f);
+        } else {
+          f = A[i * w + j] * n0[j];
+        }
+        Fk[(long long)j * w + i] = f;
+      }
     __syncthreads();
   }
 }
@@ -226,7 +358,7 @@ __device__ __forceinline__ DDChunk dd_chunk(const double* base, long long ls, lo
   return ch;
 }
 
-template <int S>
+template <int S, bool FULL>
 __global__ void __launch_bounds__(192) dd_solve_kernel(const DDBox* __restrict__ boxes, int nx, long long nt,
                                                        const double* __restrict__ fac, double* state, int nslices,
                                                        int ld_buf, int* err) {
@@ -244,7 +376,7 @@ __global__ void __launch_bounds__(192) dd_solve_kernel(const DDBox* __restrict__
   const int r = threadIdx.x;
   const bool act = r < w;
   const double* base = fac + bx.offset;
-  const long long ls = dd_line_stride(w), sq = dd_sq(w);
+  const long long ls = dd_line_stride(w, FULL), sq = dd_sq(w), vec = dd_vec(w);
   const int nch = (w + kChunk - 1) / kChunk;
   const long long total = (long long)(2 * m - 1) * nch;
   if (r == 0) {
@@ -307,15 +439,24 @@ __global__ void __launch_bounds__(192) dd_solve_kernel(const DDBox* __restrict__
   // forward: y_k = S_k^{-1} (b_k - C_k y_{k-1})
   for (int k = 0; k < m && ok; ++k) {
     const long long node = act ? line_node(bx, nx, k, r) : 0;
+    // the full tensor's C_k reads y_{k-1} of the neighbouring positions: wait for all of v
+    if (FULL && k > 0) __syncthreads();
     if (act) {
       const double c = base[k * ls + 2 * sq + r];
+      const double cm = FULL ? base[k * ls + 2 * sq + vec + r] : 0.0;
+      const double cpl = FULL ? base[k * ls + 2 * sq + 2 * vec + r] : 0.0;
 #pragma unroll
       for (int q = 0; q < S; ++q)
         if (q < ns) {
           // explicit FMA: the same rounding in every instance of the kernel (any S), so the
           // solve of a slice does not depend on how many slices share its CTA
           const double b = st[q][node];
-          t[q * w + r] = k > 0 ? fma(-c, v[q * w + r], b) : b;
+          double tv = k > 0 ? fma(-c, v[q * w + r], b) : b;
+          if (FULL && k > 0) {
+            if (r > 0) tv = fma(-cm, v[q * w + r - 1], tv);
+            if (r + 1 < w) tv = fma(-cpl, v[q * w + r + 1], tv);
+          }
+          t[q * w + r] = tv;
         }
     }
     double a0[S], a1[S];
@@ -361,15 +502,20 @@ __global__ void __launch_bounds__(192) dd_solve_kernel(const DDBox* __restrict__
   }
 }
 
-// out = in + tau * src * src_t (all nodes, nslices states); out may alias in.
+// out = in + tau (src src_t + src2 src2_t) (all nodes, nslices states); out may alias in.
 __global__ void dd_rhs_kernel(const double* in, double* out, long long total, long long nt, SourceArgs sa) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     double v = in[i];
     if (sa.src) {
       const long long sl = i / nt;
-      const double ft = sa.src_t ? sa.src_t[sa.t0 + sl * sa.tstride] : 1.0;
+      const long long ti = sa.t0 + sl * sa.tstride;
+      const double ft = sa.src_t ? sa.src_t[ti] : 1.0;
       v = v + sa.tau * sa.src[i - sl * nt] * ft;
+      if (sa.src2) {
+        const double ft2 = sa.src2_t ? sa.src2_t[ti] : 1.0;
+        v = v + sa.tau * sa.src2[i - sl * nt] * ft2;
+      }
     }
     out[i] = v;
   }
@@ -422,8 +568,9 @@ static bool box_range(int n, int b, int B, double w, int* lo, int* hi) {
   return *hi >= *lo;
 }
 
-void dd_plan(const Geom& g, const ps_dd_params& dd, DDPlan& plan) {
+void dd_plan(const Geom& g, const ps_dd_params& dd, bool full, DDPlan& plan) {
   PS_REQUIRE(g.dim == 2, "DD splitting is 2-D");
+  plan.full = full ? 1 : 0;
   const int Bx = dd.boxes[0], By = dd.boxes[1];
   const int ncx = Bx > 1 ? 2 : 1;
   plan.M = ncx * (By > 1 ? 2 : 1);
@@ -455,7 +602,7 @@ void dd_plan(const Geom& g, const ps_dd_params& dd, DDPlan& plan) {
         throw Error(PS_ERR_UNSUPPORTED, "DD box too wide: its shorter extent must be at most " +
                                             std::to_string(kMaxLead) + " nodes (use more boxes)");
       b.offset = off;
-      off += (long long)(b.n / b.lead) * dd_line_stride(b.lead);
+      off += (long long)(b.n / b.lead) * dd_line_stride(b.lead, plan.full);
       plan.colours[(bxi % 2) + ncx * (by % 2)].push_back(b);
     }
   plan.fac_len = off;
@@ -466,13 +613,13 @@ void dd_plan(const Geom& g, const ps_dd_params& dd, DDPlan& plan) {
     for (auto& b : plan.colours[c]) {
       plan.max_lead = std::max(plan.max_lead, b.lead);
       plan.nodes[c] += b.n;
-      plan.fac_entries[c] += (double)(b.n / b.lead) * (2.0 * b.lead * b.lead + b.lead);
+      plan.fac_entries[c] += (double)(b.n / b.lead) * (2.0 * b.lead * b.lead + (plan.full ? 3.0 : 1.0) * b.lead);
     }
 }
 
-void dd_factor(const Geom& g, const ps_dd_params& dd, const double* a_nodal, double c, double tau, DDFactors& f,
-               cudaStream_t st) {
-  dd_plan(g, dd, f.plan);
+void dd_factor(const Geom& g, const ps_dd_params& dd, const double* a_nodal, const double* d12_nodal, double c,
+               double tau, DDFactors& f, cudaStream_t st) {
+  dd_plan(g, dd, d12_nodal != nullptr, f.plan);
   f.tau = tau;
   f.fac.alloc((size_t)f.plan.fac_len);
   f.status.alloc(1);
@@ -482,18 +629,21 @@ void dd_factor(const Geom& g, const ps_dd_params& dd, const double* a_nodal, dou
   ga.nx = g.n[0];
   ga.ny = g.n[1];
   ga.a = a_nodal;
+  ga.d12 = d12_nodal;
+  ga.full = d12_nodal != nullptr ? 1 : 0;
   ga.c = c;
   ga.tau = tau;
   ga.Bx = dd.boxes[0];
   ga.By = dd.boxes[1];
   ga.overlap = dd.overlap;
   const int w = f.plan.max_lead;
-  const size_t smem = ((size_t)w * w + 5 * (size_t)w) * sizeof(double);
+  const size_t smem = ((size_t)w * w + kFactorVecs * (size_t)w) * sizeof(double);
   int dev = 0, maxsm = 0;
   PS_CUDA(cudaGetDevice(&dev));
   PS_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   if ((int)smem + 64 > maxsm) throw Error(PS_ERR_UNSUPPORTED, "DD box too wide for the shared-memory factorisation");
-  PS_CUDA(cudaFuncSetAttribute(dd_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  auto fkern = ga.full ? dd_factor_kernel<true> : dd_factor_kernel<false>;
+  PS_CUDA(cudaFuncSetAttribute(fkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   std::vector<DDBox> all;
   for (int c = 0; c < f.plan.M; ++c) {
     auto& boxes = f.plan.colours[c];
@@ -507,7 +657,7 @@ void dd_factor(const Geom& g, const ps_dd_params& dd, const double* a_nodal, dou
     // every box of every colour in one launch: each CTA runs its box's m dense inversions
     f.dev_all.alloc(all.size());
     PS_CUDA(cudaMemcpyAsync(f.dev_all.p, all.data(), sizeof(DDBox) * all.size(), cudaMemcpyHostToDevice, st));
-    dd_factor_kernel<<<(unsigned)all.size(), dim3(32, 16), smem, st>>>(f.dev_all.p, ga, f.fac.p, f.status.p);
+    fkern<<<(unsigned)all.size(), dim3(32, 16), smem, st>>>(f.dev_all.p, ga, f.fac.p, f.status.p);
     PS_CUDA(cudaGetLastError());
   }
   int h = 0;
@@ -530,9 +680,15 @@ void dd_solve(const Geom& g, int nslices, const DDFactors& f, int colour, double
     PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, threads, smem, st>>>(f.dev_boxes[colour].p, g.n[0], g.nt, f.fac.p, state, nslices, ld, err);
   };
-  if (S == 1) launch(dd_solve_kernel<1>);
-  else if (S == 2) launch(dd_solve_kernel<2>);
-  else launch(dd_solve_kernel<4>);
+  if (f.plan.full) {
+    if (S == 1) launch(dd_solve_kernel<1, true>);
+    else if (S == 2) launch(dd_solve_kernel<2, true>);
+    else launch(dd_solve_kernel<4, true>);
+  } else {
+    if (S == 1) launch(dd_solve_kernel<1, false>);
+    else if (S == 2) launch(dd_solve_kernel<2, false>);
+    else launch(dd_solve_kernel<4, false>);
+  }
   PS_CUDA(cudaGetLastError());
 }
 

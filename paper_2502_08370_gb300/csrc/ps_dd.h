@@ -16,18 +16,21 @@ struct DDBox {
   int lead;           // half-bandwidth
   int n;              // nodes in the box
   int pad;
-  long long offset;   // of the box's factors in DDFactors::fac (per line: S^{-1}, F, c; see ps_dd.cu)
+  long long offset;   // of the box's factors in DDFactors::fac (per line: S^{-1}, F, C; see ps_dd.cu)
 };
 
 struct DDGeomArgs {
   int nx, ny, Bx, By;
-  const double* a;    // nodal coefficient or null
+  const double* a;    // nodal coefficient (diagonal of D) or null (1)
+  const double* d12;  // nodal off-diagonal of D, or null: full = 0
   double c, tau, overlap;
+  int full;           // 1: cell-based nine-point operator of the full tensor (d12 given)
 };
 
 struct DDPlan {
   int M = 0;
   int max_lead = 0;
+  int full = 0;       // full-tensor operator (line couplings C_k tridiagonal)
   long long fac_len = 0;
   std::vector<std::vector<DDBox>> colours;
   std::vector<double> nodes, fac_entries;  // per colour: box nodes, factor doubles
@@ -44,9 +47,11 @@ struct DDFactors {
   DDFactors(const DDFactors&) = delete;
 };
 
-void dd_plan(const Geom& g, const ps_dd_params& dd, DDPlan& plan);
-void dd_factor(const Geom& g, const ps_dd_params& dd, const double* a_nodal, double c, double tau, DDFactors& f,
-               cudaStream_t st);
+// full: plan for the full-tensor operator (its factors hold three coupling vectors per line).
+void dd_plan(const Geom& g, const ps_dd_params& dd, bool full, DDPlan& plan);
+// d12_nodal: off-diagonal diffusion on the nodal grid (boundary included), or null for D = a I.
+void dd_factor(const Geom& g, const ps_dd_params& dd, const double* a_nodal, const double* d12_nodal, double c,
+               double tau, DDFactors& f, cudaStream_t st);
 // Colour `colour`'s substep on nslices consecutive states, in place.  err: device flag set to
 // 1 when a bounded wait for a streamed factor chunk ran out (the launch is then abandoned);
 // a launch does nothing while the flag is set.

@@ -74,12 +74,82 @@ __global__ void __launch_bounds__(kThreads) dr_increment_kernel(int nx, int ny, 
           acc = fma(-wm[j], uc - um, acc);
         }
         if (SRC) {
-          const double ft = sa.src_t ? sa.src_t[sa.t0 + (long long)sl * sa.tstride] : 1.0;
+          const long long ti = sa.t0 + (long long)sl * sa.tstride;
+          const double ft = sa.src_t ? sa.src_t[ti] : 1.0;
           acc = fma(sa.tau, sv * ft, acc);
+          if (sa.src2) acc = fma(sa.tau, sa.src2[node] * (sa.src2_t ? sa.src2_t[ti] : 1.0), acc);
         }
         w[e] = acc;
       }
     }
+  }
+}
+
+// w = tau (A u + f) for the full tensor D = [[a, d12], [d12, a]] (2-D, Sec. 5.2): A is the
+// cell-based nine-point operator, the sum of the colour suboperators of the DD splitting
+// (their weights rho_j add up to 1 at every cell centre).  Cell (ci, cj) (lower-left node)
+// contributes through ax = a/(2hx^2), ay = a/(2hy^2), g = d12/(hx hy), with a and d12 the means
+// of its four nodal values; -(A u)_P = sum over the four cells at P of their rows at P:
+//     diagonal  ax + ay + g/2 (cells SW, NE of P),  ax + ay - g/2 (SE, NW),
+//     W, E      -ax of the two cells sharing that edge;  S, N  -ay likewise,
+//     SW, NE    -g/2 of the cell between;  SE, NW  +g/2 of the cell between,
+// plus c u_P; u = 0 on the boundary.  One thread per node; the slices of blockIdx.y.
+__global__ void __launch_bounds__(kThreads) dr_increment_tensor_kernel(int nx, int ny, int nsl, long long nt,
+                                                                       const double* __restrict__ a,
+                                                                       const double* __restrict__ d12, double hx,
+                                                                       double hy, double ctau,
+                                                                       const double* __restrict__ u,
+                                                                       double* __restrict__ w, SourceArgs sa) {
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= nt) return;
+  const int i = (int)(node % nx) + 1, j = (int)(node / nx) + 1;  // 1-based interior node
+  const long long nx2 = nx + 2;
+  // nodal values around P (boundary included): f[dy][dx] at (i + dx - 1, j + dy - 1)
+  double av[3][3], bv[3][3];
+#pragma unroll
+  for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) {
+      const long long k = (long long)(j + dy - 1) * nx2 + (i + dx - 1);
+      av[dy][dx] = a ? a[k] : 1.0;
+      bv[dy][dx] = d12[k];
+    }
+  // cells: c = 0 SW, 1 SE, 2 NW, 3 NE; lower-left corner offset (cx, cy) in {0,1}^2
+  double ax[4], ay[4], g[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int cx = c & 1, cy = c >> 1;
+    const double am = 0.25 * (av[cy][cx] + av[cy][cx + 1] + av[cy + 1][cx] + av[cy + 1][cx + 1]);
+    const double bm = 0.25 * (bv[cy][cx] + bv[cy][cx + 1] + bv[cy + 1][cx] + bv[cy + 1][cx + 1]);
+    ax[c] = am / (2.0 * hx * hx);
+    ay[c] = am / (2.0 * hy * hy);
+    g[c] = bm / (hx * hy);
+  }
+  const double dgl = (ax[0] + ay[0] + 0.5 * g[0]) + (ax[1] + ay[1] - 0.5 * g[1]) + (ax[2] + ay[2] - 0.5 * g[2]) +
+                     (ax[3] + ay[3] + 0.5 * g[3]);
+  const double eW = -(ax[0] + ax[2]), eE = -(ax[1] + ax[3]), eS = -(ay[0] + ay[1]), eN = -(ay[2] + ay[3]);
+  const double eSW = -0.5 * g[0], eNE = -0.5 * g[3], eSE = 0.5 * g[1], eNW = 0.5 * g[2];
+  const bool hasW = i > 1, hasE = i < nx, hasS = j > 1, hasN = j < ny;
+  for (int sl = blockIdx.y; sl < nsl; sl += gridDim.y) {
+    const double* us = u + (long long)sl * nt;
+    const double uc = us[node];
+    // sum of the row's entries times u (the negative of A u without reaction)
+    double r = dgl * uc;
+    if (hasW) r = fma(eW, us[node - 1], r);
+    if (hasE) r = fma(eE, us[node + 1], r);
+    if (hasS) r = fma(eS, us[node - nx], r);
+    if (hasN) r = fma(eN, us[node + nx], r);
+    if (hasS && hasW) r = fma(eSW, us[node - nx - 1], r);
+    if (hasN && hasE) r = fma(eNE, us[node + nx + 1], r);
+    if (hasS && hasE) r = fma(eSE, us[node - nx + 1], r);
+    if (hasN && hasW) r = fma(eNW, us[node + nx - 1], r);
+    double acc = sa.tau * (-r) - ctau * uc;
+    if (sa.src) {
+      const long long ti = sa.t0 + (long long)sl * sa.tstride;
+      acc = fma(sa.tau, sa.src[node] * (sa.src_t ? sa.src_t[ti] : 1.0), acc);
+      if (sa.src2) acc = fma(sa.tau, sa.src2[node] * (sa.src2_t ? sa.src2_t[ti] : 1.0), acc);
+    }
+    w[(long long)sl * nt + node] = acc;
   }
 }
 
@@ -125,6 +195,18 @@ void dr_increment(const Geom& g, int nsl, const double* a_nodal, double c, doubl
     else { if (src) PS_DR_LAUNCH(2, false, true); else PS_DR_LAUNCH(2, false, false); }
   }
 #undef PS_DR_LAUNCH
+  PS_CUDA(cudaGetLastError());
+}
+
+void dr_increment_tensor(const Geom& g, int nsl, const double* a_nodal, const double* d12_nodal, double c, double tau,
+                         const double* u, double* w, const SourceArgs& sa, cudaStream_t st) {
+  PS_REQUIRE(g.dim == 2 && d12_nodal, "the full-tensor stencil is 2-D with a d12 field");
+  const int sms = sm_count();
+  const unsigned bx = (unsigned)((g.nt + kThreads - 1) / kThreads);
+  const long long by_want = ((long long)sms * 8 + bx - 1) / bx;
+  const unsigned by = (unsigned)std::max<long long>(1, std::min<long long>({by_want, (long long)nsl, 65535LL}));
+  dr_increment_tensor_kernel<<<dim3(bx, by), kThreads, 0, st>>>(g.n[0], g.n[1], nsl, g.nt, a_nodal, d12_nodal,
+                                                                1.0 / (g.n[0] + 1), 1.0 / (g.n[1] + 1), tau * c, u, w, sa);
   PS_CUDA(cudaGetLastError());
 }
 

@@ -16,9 +16,13 @@ struct ps_grid {
 struct ps_operator {
   const ps_grid* grid = nullptr;
   ps::DevBuf<double> a;
+  ps::DevBuf<double> d12;     // off-diagonal diffusion (full tensor, 2-D DD only), nodal
   ps::DevBuf<double> src;
   ps::DevBuf<double> src_t;
   int src_t_len = 0;
+  ps::DevBuf<double> src2;    // second separable source term
+  ps::DevBuf<double> src2_t;
+  int src2_t_len = 0;
   double c = 0.0;
 };
 

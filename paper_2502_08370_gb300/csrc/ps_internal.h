@@ -98,6 +98,8 @@ struct SourceArgs {
   int tstride = 0;                // added per slice of the launch
   int src_t_len = 0;              // entries of src_t
   double tau = 0.0;
+  const double* src2 = nullptr;   // second separable term src2(x) * src2_t(t_j) (DD and DR paths), or null
+  const double* src2_t = nullptr; // its time factors (same time index as src_t) or null (factor 1)
 };
 
 // Epilogue of the last sweep of a coarse step (the parareal correction, Sec. 3).
@@ -158,6 +160,10 @@ void sweep_x_warp(const Geom& g, const LineFactors& f, const Tin* in, float* out
 // out = u + w (out may alias u).
 void dr_increment(const Geom& g, int nsl, const double* a_nodal, double c, double tau, const double* u, double* w,
                   const SourceArgs& sa, cudaStream_t st);
+// Same for the full diffusion tensor D = [[a, d12], [d12, a]] in 2-D: A is the cell-based
+// nine-point operator (the sum of the DD suboperators of ps_dd.cu, with rho = 1).
+void dr_increment_tensor(const Geom& g, int nsl, const double* a_nodal, const double* d12_nodal, double c, double tau,
+                         const double* u, double* w, const SourceArgs& sa, cudaStream_t st);
 void dr_add(const Geom& g, int nsl, const double* u, const double* w, double* out, cudaStream_t st);
 // dst <- src with the increment max |src - dst| (and per-slice stats); when dout is set it
 // also receives src - dst rounded to FP32 (the increment the coarse increment form propagates).
