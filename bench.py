@@ -176,6 +176,9 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+TILE_KW = {}  # fine tile shape overrides from the command line (tile_positions, tile_slots, ...)
+
+
 def make_problem(ps, torch, cfg, precision, timing, coarse_mode="fp64", fine_method="fie"):
     grid = ps.Grid(cfg["n"])
     a = None if cfg["a"] is None else torch.as_tensor(cfg["a"]).cuda()
@@ -185,7 +188,7 @@ def make_problem(ps, torch, cfg, precision, timing, coarse_mode="fp64", fine_met
     spc = ps.Splitting(op, cfg["split"], cfg["coarse_boxes"], cfg["coarse_overlap"]) if "coarse_boxes" in cfg \
         else None
     prob = ps.Problem(sp, cfg["T"], cfg["N"], cfg["g"], cfg["s"], coarse=spc, precision=precision, timing=timing,
-                      coarse_mode=coarse_mode, fine_method=fine_method)
+                      coarse_mode=coarse_mode, fine_method=fine_method, **TILE_KW)
     prob._keep = (grid, op, sp, spc, a, src)
     return prob
 
@@ -284,6 +287,7 @@ def config_of(args, cfg):
            "coarse_steps": cfg["g"], "fine_steps": cfg["s"], "T": cfg["T"], "tol": cfg["tol"],
            "precision": args.precision, "coarse": getattr(args, "coarse", "fp64"),
            "fine": "dr" if getattr(args, "fine", "fie") == "dr" else "fie",
+           "tiles": {k: v for k, v in TILE_KW.items() if v not in (0, "auto")} or "auto",
            "l2": (f"inputs larger than L2 ({gb:.1f} GB of slice states streamed per step)" if gb > 0.2 else
                   f"working set {gb * 1e3:.0f} MB fits in L2: latency-bound case, no roofline claim")}
     if cfg["split"] == "dd":
@@ -467,7 +471,7 @@ def run_adjoint(args, cfg, ps, torch, rank, ws):
         return (16.0 * fd4(eps / 2) - fd4(eps)) / 15.0
 
     errs_a, errs_u = [], []
-    eps = 0.1
+    eps = 0.4
     for d in wl.random_directions(tuple(a.shape), args.fd_dirs, cfg["dirs_seed"]):
         dd = torch.as_tensor(d).cuda()
         fd = fd6(lambda e: J_of(a + e * dd, u0), eps)
@@ -481,6 +485,7 @@ def run_adjoint(args, cfg, ps, torch, rank, ws):
                           "fd_stencil": "4-point central at eps and eps/2, Richardson-extrapolated (6th order)", "fd_eps": eps,
                           "fd_max_rel_err_a": max(errs_a), "fd_median_rel_err_a": float(np.median(errs_a)),
                           "fd_dirs_within_1e-6_a": int(sum(e <= 1e-6 for e in errs_a)),
+                          "fd_rel_errs_a": errs_a,
                           "fd_directions_u0": len(errs_u),
                           "fd_max_rel_err_u0": max(errs_u),
                           "fd_gradient": "exact (forward and adjoint parareal to k = N)",
@@ -508,7 +513,14 @@ def main():
                          "dimensional or DD splitting)")
     ap.add_argument("--slices", type=int, default=0,
                     help="override the workload's slice count N (small-footprint profiling runs; named in config)")
+    ap.add_argument("--tile-positions", type=int, default=0, help="fine tiles: line positions per tile (0 = auto)")
+    ap.add_argument("--tile-slots", type=int, default=0, help="fine tiles: time slices per tile (0 = auto)")
+    ap.add_argument("--tile-lines-per-thread", type=int, default=0, help="fine FP32 tiles: lines per thread (0 = auto)")
+    ap.add_argument("--coarse-sweep", default="auto", choices=["auto", "staged", "streamed"],
+                    help="coarse line solves on one slice: staged through shared memory or streamed")
     args = ap.parse_args()
+    TILE_KW.update(tile_positions=args.tile_positions, tile_slots=args.tile_slots,
+                   tile_lines_per_thread=args.tile_lines_per_thread, coarse_sweep=args.coarse_sweep)
     if args.warmup < 3:
         args.warmup = 3
     cfg = workload(args.workload)

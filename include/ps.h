@@ -75,11 +75,26 @@ extern "C" {
 #define PS_FINE_FIE 0 /* fractional implicit Euler (eq. FIE_method) */
 #define PS_FINE_DR 1  /* Douglas-Rachford (eq. DR_method) */
 
-#define PS_SCHED_AUTO 0   /* library default for dimensional line solves (= PS_SCHED_THOMAS) */
-#define PS_SCHED_THOMAS 1 /* Thomas/LDL^T recurrences: one thread per line (fine tiles, coarse
-                             y/z sweeps), segmented warp scans for the coarse FP32 x-sweep */
-#define PS_SCHED_PCR 2    /* parallel cyclic reduction: not built, ps_problem_create returns
-                             PS_ERR_UNSUPPORTED */
+/* Line-solve schedule (ps_params.schedule) of the one sweep that offers all three, the coarse
+ * x-substep of the FP32 increment form (PS_COARSE_DELTA32; rows of at most 256 nodes for PCR).
+ * Every other line solve runs the Thomas/LDL^T recurrences one thread per line (fine tiles,
+ * coarse sweeps staged or streamed, PS_COARSE_SWEEP_*).  The three compute the same solution
+ * in different orders; they agree to FP32 rounding of the coarse increment. */
+#define PS_SCHED_AUTO 0   /* the hybrid, unless ps_autotune picked another */
+#define PS_SCHED_THOMAS 1 /* Thomas/LDL^T recurrences, one thread per row */
+#define PS_SCHED_PCR 2    /* parallel cyclic reduction, one warp per row (log2 L shuffle/register steps) */
+#define PS_SCHED_HYBRID 3 /* one warp per row: lane segments run sequentially, a log-depth shuffle scan
+                             joins them (segmented scans of the two first-order recurrences) */
+
+/* Schedules of the coarse propagator's line solves (ps_params.coarse_sweep).  The coarse chain
+ * advances one slice at a time, so its sweeps see only that slice's lines.  STAGED: a CTA copies
+ * its lines and their factors into shared memory with asynchronous copies, one thread per line
+ * runs the Thomas/LDL^T recurrences there, and the CTA writes back with the correction fused.
+ * STREAMED: one thread per line runs them from global memory with its loads issued a chunk
+ * ahead.  Both compute the same recurrence; results agree to rounding. */
+#define PS_COARSE_SWEEP_AUTO 0
+#define PS_COARSE_SWEEP_STAGED 1
+#define PS_COARSE_SWEEP_STREAMED 2
 
 typedef struct ps_grid ps_grid;
 typedef struct ps_operator ps_operator;
@@ -154,8 +169,7 @@ int ps_splitting_destroy(ps_splitting* sp);
 /* ---- parareal problem (Sec. 3) ----------------------------------------------------------- */
 typedef struct {
   int precision; /* PS_PREC_FP64 or PS_PREC_MIXED */
-  int schedule;  /* PS_SCHED_AUTO or PS_SCHED_THOMAS (PS_SCHED_PCR: PS_ERR_UNSUPPORTED; other
-                    values: PS_ERR_INVALID) */
+  int schedule;  /* PS_SCHED_* (other values: PS_ERR_INVALID) */
   int timing;    /* 1: per-phase CUDA events (ps_problem_stats); 2: also per-kernel
                     events (ps_problem_kernel_times) */
   int dd_slices_per_block; /* DD subdomain solves: time slices per CTA (1, 2 or 4); 0 = 2 */
@@ -170,6 +184,9 @@ typedef struct {
   int tile_lines_per_thread; /* fine line solves (FP32 tiles of 32+ slots): lines a thread solves
                                 side by side, 1 or 2; 0 = auto (1) */
   int fine_method;         /* PS_FINE_FIE (0) or PS_FINE_DR */
+  int coarse_sweep;        /* coarse-propagator line solves on one slice (dimensional splitting):
+                              PS_COARSE_SWEEP_STAGED or PS_COARSE_SWEEP_STREAMED; 0 = staged where
+                              the line fits, ps_autotune may change it */
 } ps_params;
 
 /* fine, coarse: splittings of the same operator used by F and G (coarse = NULL: use
@@ -327,13 +344,25 @@ int ps_batch_stats(const ps_batch* b, ps_stats* out);
 const char* ps_batch_last_error(void);
 int ps_batch_destroy(ps_batch* b);
 
-/* Autotuner of the fine line-solve schedule: times the fine sweeps of this problem with each
+/* Autotuner of the line-solve schedules: times the fine sweeps of this problem with each
  * candidate tile shape (time slices per tile 16/32/64, line positions 1/2, lines per thread
  * 1/2, one tile per CTA or a persistent ring of three shared-memory stages) for about
- * budget_ms and installs the fastest.  Results do not depend on the schedule (each line's
- * arithmetic is the same).  *choice_out (may be NULL) receives
- * lines_per_thread*10000 + slots*100 + positions*10 + pipelined. */
+ * budget_ms and installs the fastest; with the dimensional splitting it also times one coarse
+ * step's sweeps staged and streamed (PS_COARSE_SWEEP_*) and installs the faster.  Results do
+ * not depend on the schedules (each line's arithmetic is the same).  *choice_out (may be NULL)
+ * receives coarse_sweep*100000 + lines_per_thread*10000 + slots*100 + positions*10 + pipelined. */
 int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out);
+/* The timing record of the last ps_autotune on this problem: one entry per candidate timed,
+ * name "fine:<slots>x<positions>/v<lines per thread>/<tile|ring>", "coarse:<staged|streamed>" or
+ * "coarse-x32:<thomas|pcr|hybrid>", and its time per candidate run (ms; fine: the sweeps of all
+ * directions over all slices; coarse: one coarse step's sweeps; coarse-x32: one x-sweep).
+ * chosen = 1 for the installed candidate of each group.  len = number of entries (<= cap). */
+typedef struct {
+  char name[48];
+  double ms;
+  int chosen;
+} ps_tune_entry;
+int ps_autotune_record(const ps_problem* p, ps_tune_entry* out, int cap, int* len);
 /* Same schedule on `dst` as on `src` (same grid and slice count). */
 int ps_copy_schedule(const ps_problem* src, ps_problem* dst);
 

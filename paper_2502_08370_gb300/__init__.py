@@ -25,9 +25,10 @@ ERRORS = {1: "PS_ERR_INVALID", 2: "PS_ERR_CUDA", 3: "PS_ERR_OOM", 4: "PS_ERR_NON
 PS_SPLIT_DIM, PS_SPLIT_DD = 0, 1
 PS_PREC_FP64, PS_PREC_MIXED = 0, 1
 PS_VERSION = 103  # the header's PS_VERSION this binding marshals for
-PS_SCHED_AUTO, PS_SCHED_THOMAS, PS_SCHED_PCR = 0, 1, 2
+PS_SCHED_AUTO, PS_SCHED_THOMAS, PS_SCHED_PCR, PS_SCHED_HYBRID = 0, 1, 2, 3
 PS_COARSE_FP64, PS_COARSE_DELTA32 = 0, 1
 PS_FINE_FIE, PS_FINE_DR = 0, 1
+PS_COARSE_SWEEP_AUTO, PS_COARSE_SWEEP_STAGED, PS_COARSE_SWEEP_STREAMED = 0, 1, 2
 PS_NOALLOC_MAX_UNKNOWNS = 1 << 20
 
 _lock = threading.Lock()
@@ -54,12 +55,16 @@ class _Params(C.Structure):
     _fields_ = [("precision", C.c_int), ("schedule", C.c_int), ("timing", C.c_int), ("dd_slices_per_block", C.c_int),
                 ("tile_positions", C.c_int), ("tile_pipeline", C.c_int), ("tile_slots", C.c_int),
                 ("tol_mode", C.c_int), ("coarse", C.c_int), ("tile_lines_per_thread", C.c_int),
-                ("fine_method", C.c_int)]
+                ("fine_method", C.c_int), ("coarse_sweep", C.c_int)]
 
 
 class _Stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("unknown_updates", C.c_double), ("ms_total", C.c_double),
                 ("ms_fine", C.c_double), ("ms_coarse", C.c_double), ("kernel_launches", C.c_int)]
+
+
+class _TuneEntry(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("ms", C.c_double), ("chosen", C.c_int)]
 
 
 class _KTime(C.Structure):
@@ -104,6 +109,7 @@ SIGNATURES = {
     "ps_batch_destroy": [_VP],
     "ps_autotune": [_VP, _I, _U, _IP],
     "ps_copy_schedule": [_VP, _VP],
+    "ps_autotune_record": [_VP, C.POINTER(_TuneEntry), _I, _IP],
     "ps_adjoint_vjp": [_VP, _VP, _D, _I, _VP, _VP, _U, _IP],
     "ps_adjoint": [_VP, _VP, _D, _I, _VP, _VP, _U, C.POINTER(C.c_double), _IP],
     "ps_problem_set_slices": [_VP, _I, _I, _I, _U],
@@ -245,7 +251,7 @@ class Problem:
     def __init__(self, fine: Splitting, T, N, g, s, coarse: Splitting = None, precision="fp64",
                  schedule=PS_SCHED_AUTO, timing=False, dd_slices_per_block=0, tile_positions=0, tile_pipeline=0,
                  tile_slots=0, tol_mode=0, coarse_mode="fp64", tile_lines_per_thread=0, fine_method="fie",
-                 stream=None):
+                 coarse_sweep="auto", stream=None):
         self.fine, self.coarse = fine, coarse
         self.grid = fine.op.grid
         self.N = int(N)
@@ -256,7 +262,8 @@ class Problem:
         prm = _Params(PS_PREC_FP64 if precision == "fp64" else PS_PREC_MIXED, int(schedule), int(timing),
                       int(dd_slices_per_block), int(tile_positions), int(tile_pipeline), int(tile_slots),
                       int(tol_mode), PS_COARSE_FP64 if coarse_mode == "fp64" else PS_COARSE_DELTA32,
-                      int(tile_lines_per_thread), PS_FINE_FIE if fine_method == "fie" else PS_FINE_DR)
+                      int(tile_lines_per_thread), PS_FINE_FIE if fine_method == "fie" else PS_FINE_DR,
+                      {"auto": 0, "staged": 1, "streamed": 2}[coarse_sweep])
         h = _VP()
         check(lib().ps_problem_create(fine._h, None if coarse is None else coarse._h, float(T), int(N), int(g),
                                       int(s), C.byref(prm), _stream(stream), C.byref(h)))
@@ -364,6 +371,13 @@ class Problem:
         check(lib().ps_autotune(self._h, int(budget_ms), _stream(stream), C.byref(ch)))
         return ch.value
 
+    def autotune_record(self):
+        """Timings of the last autotune: list of (name, ms, chosen)."""
+        buf = (_TuneEntry * 64)()
+        ln = C.c_int(0)
+        check(lib().ps_autotune_record(self._h, buf, 64, C.byref(ln)))
+        return [(buf[i].name.decode(), buf[i].ms, bool(buf[i].chosen)) for i in range(ln.value)]
+
     def copy_schedule_from(self, other: "Problem"):
         check(lib().ps_copy_schedule(other._h, self._h))
 
@@ -425,10 +439,12 @@ class Batch:
     def state(self, index, n, out=None, stream=None):
         """U_n of problem `index` after the last run (through ps_batch_get_state)."""
         import torch
-        p = self.problems[index]
+        p = self.problems[index] if 0 <= index < len(self.problems) else None
         if out is None:
-            out = torch.empty(p.grid.shape, dtype=torch.float64, device="cuda")
-        rc = lib().ps_batch_get_state(self._h, int(index), int(n), _dev_ptr(out, p.grid.nt), _stream(stream))
+            out = torch.empty(p.grid.shape if p else (1,), dtype=torch.float64, device="cuda")
+        # the library checks the index and slice (a bad one raises PsError below)
+        rc = lib().ps_batch_get_state(self._h, int(index), int(n), _dev_ptr(out, p.grid.nt if p else None),
+                                      _stream(stream))
         if rc != PS_OK:
             raise PsError(rc, lib().ps_batch_last_error().decode())
         return out

@@ -148,6 +148,14 @@ void fie_step_dd(ps_problem* p, Prop& P, int nsl, const double* in, double* out,
   }
 }
 
+// One FP64 sweep of the coarse propagator on one slice: staged through shared memory when the
+// shape fits (ps_coarse.cu), else the streaming sweeps of ps_dim.cu.
+void coarse_sweep64(ps_problem* p, const LineFactors& f, const double* in, double* out, const SourceArgs& sa,
+                    const CorrArgs& corr, cudaStream_t st) {
+  if (p->coarse_staged && coarse_sweep_staged<double>(p->g, f, in, out, sa, corr, st)) return;
+  sweep_dim<double, double>(p->g, 1, f, false, in, out, sa, corr, corr.mode != 0 ? out : nullptr, st);
+}
+
 void fie_step64(ps_problem* p, Prop& P, int nsl, const double* in, double* out, int t0, int tslice,
                 const CorrArgs& corr, cudaStream_t st, const char* phase) {
   if (P.sp->kind == PS_SPLIT_DD) {
@@ -167,7 +175,9 @@ void fie_step64(ps_problem* p, Prop& P, int nsl, const double* in, double* out, 
     double bytes = 0, flops = 0;
     if (p->kt.on) sweep_cost(p, *P.dim[m], nsl, 8, 8, 8, sa.src != nullptr, epi ? corr.mode : 0, &bytes, &flops);
     p->kt.begin(st);
-    if (epi)
+    if (&P == &p->G && nsl == 1)
+      coarse_sweep64(p, *P.dim[m], src_state, out, sa, epi ? corr : CorrArgs{}, st);
+    else if (epi)
       sweep_dim<double, double>(p->g, nsl, *P.dim[m], false, src_state, out, sa, corr, out, st);
     else
       sweep_dim<double, double>(p->g, nsl, *P.dim[m], false, src_state, out, sa, CorrArgs{}, nullptr, st);
@@ -299,6 +309,20 @@ void run_G(ps_problem* p, int n, const double* in, const CorrArgs& corr, cudaStr
   p->updates += (double)P.steps * (double)p->g.nt;
 }
 
+// The FP32 coarse x-sweep of the increment form on one slice, in the installed schedule:
+// hybrid (one warp per row, segmented scans), PCR (one warp per row), or Thomas (one thread
+// per row, rows staged in shared memory by sweep_dim).
+template <typename Tin>
+void coarse_x32(ps_problem* p, const Tin* in, float* out, const SourceArgs& sa, cudaStream_t st) {
+  const LineFactors& f = *p->G.dim[0];
+  if (p->xsched == PS_SCHED_PCR && sweep_x_pcr<Tin>(p->g, p->pcr_e.p, p->pcr_d.p, in, out, sa, st)) return;
+  if (p->xsched == PS_SCHED_THOMAS) {
+    sweep_dim<Tin, float>(p->g, 1, f, true, in, out, sa, CorrArgs{}, nullptr, st);
+    return;
+  }
+  sweep_x_warp<Tin>(p->g, f, in, out, sa, st);
+}
+
 // G's one FIE step in FP32 line solves for the coarse increment form (PS_COARSE_DELTA32):
 // init = true:  U_{n+1}^0 = G(U_n^0) on the state, source included (x-sweep reads FP64 U_n);
 // init = false: U_{n+1}^k = Fout_n + B d_n with d_n = U_n^k - U_n^{k-1} (FP32, in d32), no
@@ -325,13 +349,15 @@ void run_G32(ps_problem* p, int n, bool init, cudaStream_t st) {
     p->kt.begin(st);
     double bytes = 0;
     if (m == 0) {
-      // x-lines are contiguous rows: one warp per row, segmented scans (sweep_x_warp)
-      if (init) sweep_x_warp<double>(p->g, *P.dim[0], p->U.p + n * nt, p->g32.p, sa, st);
-      else sweep_x_warp<float>(p->g, *P.dim[0], p->d32.p, p->g32.p, SourceArgs{}, st);
+      // x-lines are contiguous rows: the schedule of ps_params.schedule (or the autotuner's)
+      if (init) coarse_x32(p, p->U.p + n * nt, p->g32.p, sa, st);
+      else coarse_x32(p, p->d32.p, p->g32.p, SourceArgs{}, st);
       bytes = dnt * ((init ? 8 : 4) + 4 + 8 + (sa.src ? 8 : 0));
     } else {
       const float* in = m == 0 ? p->d32.p : p->g32.p;
-      sweep_dim<float, float>(p->g, 1, *P.dim[m], true, in, p->g32.p, SourceArgs{}, last ? c : CorrArgs{}, nullptr, st);
+      const CorrArgs cm = last ? c : CorrArgs{};
+      if (!(p->coarse_staged && coarse_sweep_staged<float>(p->g, *P.dim[m], in, p->g32.p, SourceArgs{}, cm, st)))
+        sweep_dim<float, float>(p->g, 1, *P.dim[m], true, in, p->g32.p, SourceArgs{}, cm, nullptr, st);
       bytes = dnt * (4 + 4 + 8) + (last ? dnt * (init ? 8.0 : 28.0) : 0.0);
     }
     if (p->kt.on)
@@ -517,7 +543,7 @@ void configure_slices(ps_problem* p, int N, int g_steps, int f_steps, cudaStream
   for (auto* b : {&p->U, &p->Fout, &p->Gold, &p->gtmp, &p->dr_W, &p->W64, &p->srcrow64, &p->Uchk, &p->snap, &p->Lam})
     b->reset();
   for (auto& b : p->gedge) b.reset();
-  for (auto* b : {&p->d32, &p->g32, &p->W, &p->srcrow32}) b->reset();
+  for (auto* b : {&p->d32, &p->g32, &p->W, &p->srcrow32, &p->pcr_e, &p->pcr_d}) b->reset();
   p->sstats.reset();
   if (p->h_sstats) {
     cudaFreeHost(p->h_sstats);
@@ -533,6 +559,8 @@ void configure_slices(ps_problem* p, int N, int g_steps, int f_steps, cudaStream
     Geom g3 = p->g;
     if (g3.dim == 2) g3.n[2] = 1;
     factor_lines(g3, *p->G.dim[0], true, st);  // line-major x factors of the warp x-sweep
+    // rows of (I - DeltaT/g A_x) for the PCR schedule of that sweep
+    if (p->g.n[0] <= 256) tridiag_x_rows(p->g, p->op->a.p, p->op->c / p->g.dim, p->G.tau, p->pcr_e, p->pcr_d, st);
   }
   const long long nt = p->g.nt;
   p->U.alloc((size_t)(N + 1) * nt);
@@ -628,7 +656,7 @@ void coarse_step_into(ps_problem* p, int n, int q, const double* in, double* wor
   }
   for (int m = 0; m < M; ++m) {
     SourceArgs sa = m == 0 ? source_for(p, P, t_end, 0) : SourceArgs{};
-    sweep_dim<double, double>(p->g, 1, *P.dim[m], false, m == 0 ? in : work, work, sa, CorrArgs{}, nullptr, st);
+    coarse_sweep64(p, *P.dim[m], m == 0 ? in : work, work, sa, CorrArgs{}, st);
   }
 }
 // The bounded wait of the tile and DD kernels, on a barrier that nothing arrives at: the wait
@@ -829,13 +857,14 @@ int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, doub
     p->T = T;
     if (params) p->prm = *params;
     PS_REQUIRE(p->prm.precision == PS_PREC_FP64 || p->prm.precision == PS_PREC_MIXED, "unknown precision");
-    PS_REQUIRE(p->prm.schedule >= PS_SCHED_AUTO && p->prm.schedule <= PS_SCHED_PCR, "unknown schedule");
-    if (p->prm.schedule == PS_SCHED_PCR)
-      throw Error(PS_ERR_UNSUPPORTED, "the parallel-cyclic-reduction schedule is not built; the line solves run "
-                                      "the Thomas/LDL^T recurrences (PS_SCHED_AUTO or PS_SCHED_THOMAS)");
+    PS_REQUIRE(p->prm.schedule >= PS_SCHED_AUTO && p->prm.schedule <= PS_SCHED_HYBRID, "unknown schedule");
+    p->xsched = p->prm.schedule == PS_SCHED_AUTO ? PS_SCHED_HYBRID : p->prm.schedule;
     PS_REQUIRE(p->prm.coarse == PS_COARSE_FP64 || p->prm.coarse == PS_COARSE_DELTA32, "unknown coarse mode");
     PS_REQUIRE(p->prm.fine_method == PS_FINE_FIE || p->prm.fine_method == PS_FINE_DR, "unknown fine method");
     PS_REQUIRE(p->prm.tol_mode == 0 || p->prm.tol_mode == 1, "tol_mode must be 0 or 1");
+    PS_REQUIRE(p->prm.coarse_sweep >= PS_COARSE_SWEEP_AUTO && p->prm.coarse_sweep <= PS_COARSE_SWEEP_STREAMED,
+               "unknown coarse sweep schedule");
+    p->coarse_staged = p->prm.coarse_sweep != PS_COARSE_SWEEP_STREAMED;
     p->dr = p->prm.fine_method == PS_FINE_DR;
     if (p->dr && p->prm.precision != PS_PREC_FP64)
       throw Error(PS_ERR_UNSUPPORTED, "the Douglas-Rachford fine propagator runs in FP64");
@@ -1036,6 +1065,7 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
       cands.erase(std::remove_if(cands.begin(), cands.end(), [](const Cand& c) { return c.pipe || c.vec == 2; }),
                   cands.end());
     tile_flag_reset(p, st);
+    p->tune_log.clear();
     cudaEvent_t e0, e1;
     PS_CUDA(cudaEventCreate(&e0));
     PS_CUDA(cudaEventCreate(&e1));
@@ -1077,6 +1107,9 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
           reps *= 2;
         }
         const float per = ms / reps;
+        p->tune_log.push_back({"fine:" + std::to_string(c.slots) + "x" + std::to_string(c.positions) + "/v" +
+                                   std::to_string(c.vec) + (c.pipe ? "/ring" : "/tile"),
+                               per, 0});
         if (per < best) {
           best = per;
           bestc = c;
@@ -1087,16 +1120,104 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
       cudaEventDestroy(e1);
       throw;
     }
+    // coarse line solves on one slice: staged through shared memory or streamed, timed on one
+    // coarse step's sweeps of this problem (both schedules compute the same recurrences with the
+    // same roundings, so the choice changes no result)
+    int coarse_choice = 0;
+    if (p->G.sp->kind == PS_SPLIT_DIM) {
+      const int MG = p->g.dim;
+      auto coarse_step = [&]() {
+        for (int m = 0; m < MG; ++m) {
+          if (p->delta32) {
+            if (m == 0) {
+              coarse_x32<float>(p, p->g32.p, p->g32.p, SourceArgs{}, st);
+            } else if (!(p->coarse_staged &&
+                         coarse_sweep_staged<float>(p->g, *p->G.dim[m], p->g32.p, p->g32.p, SourceArgs{}, CorrArgs{}, st))) {
+              sweep_dim<float, float>(p->g, 1, *p->G.dim[m], true, p->g32.p, p->g32.p, SourceArgs{}, CorrArgs{}, nullptr,
+                                      st);
+            }
+          } else {
+            coarse_sweep64(p, *p->G.dim[m], m == 0 ? p->U.p : p->gtmp.p, p->gtmp.p, SourceArgs{}, CorrArgs{}, st);
+          }
+        }
+      };
+      auto time4 = [&](auto&& fn) {
+        fn();  // warm-up
+        PS_CUDA(cudaEventRecord(e0, st));
+        for (int r = 0; r < 4; ++r) fn();
+        PS_CUDA(cudaEventRecord(e1, st));
+        PS_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        PS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        return ms / 4.f;
+      };
+      // the FP32 increment form's x-sweep: Thomas per row, PCR per warp, hybrid per warp
+      if (p->delta32) {
+        const char* names[4] = {"", "thomas", "pcr", "hybrid"};
+        float xbest = 1e30f;
+        int xchoice = p->xsched;
+        for (int sc = PS_SCHED_THOMAS; sc <= PS_SCHED_HYBRID; ++sc) {
+          if (sc == PS_SCHED_PCR && !p->pcr_e.p) continue;  // rows longer than 256 nodes
+          p->xsched = sc;
+          const float ms = time4([&] { coarse_x32<float>(p, p->g32.p, p->g32.p, SourceArgs{}, st); });
+          p->tune_log.push_back({std::string("coarse-x32:") + names[sc], ms, 0});
+          if (ms < xbest) {
+            xbest = ms;
+            xchoice = sc;
+          }
+        }
+        p->xsched = xchoice;
+        p->prm.schedule = xchoice;
+        for (auto& e : p->tune_log)
+          if (e.name == std::string("coarse-x32:") + names[xchoice]) e.chosen = 1;
+      }
+      float tbest = 1e30f;
+      const bool saved = p->coarse_staged;
+      for (int sched = PS_COARSE_SWEEP_STAGED; sched <= PS_COARSE_SWEEP_STREAMED; ++sched) {
+        p->coarse_staged = sched == PS_COARSE_SWEEP_STAGED;
+        const float ms = time4(coarse_step);
+        p->tune_log.push_back({sched == PS_COARSE_SWEEP_STAGED ? "coarse:staged" : "coarse:streamed", ms, 0});
+        if (ms < tbest) {
+          tbest = ms;
+          coarse_choice = sched;
+        }
+      }
+      p->coarse_staged = coarse_choice ? coarse_choice == PS_COARSE_SWEEP_STAGED : saved;
+      if (coarse_choice) p->prm.coarse_sweep = coarse_choice;
+      for (auto& e : p->tune_log)
+        if (e.name == (coarse_choice == PS_COARSE_SWEEP_STAGED ? "coarse:staged" : "coarse:streamed")) e.chosen = 1;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (bestc.slots == 0) {
       rebuild_tiles(p, old_slots, old_pos, old_pipe == 1 ? 1 : 0, old_vec);
+      if (choice_out) *choice_out = coarse_choice * 100000;
       return;
     }
     rebuild_tiles(p, bestc.slots, bestc.positions, bestc.pipe, bestc.vec);
+    for (auto& e : p->tune_log)
+      if (e.name == "fine:" + std::to_string(bestc.slots) + "x" + std::to_string(bestc.positions) + "/v" +
+                        std::to_string(bestc.vec) + (bestc.pipe ? "/ring" : "/tile"))
+        e.chosen = 1;
     tile_flag_check(p, st);
-    // choice code: lines per thread, slots, positions, pipeline as decimal digits vSSpq
-    if (choice_out) *choice_out = bestc.vec * 10000 + bestc.slots * 100 + bestc.positions * 10 + bestc.pipe;
+    // choice code: coarse schedule, lines per thread, slots, positions, pipeline as decimal digits cvSSpq
+    if (choice_out)
+      *choice_out = coarse_choice * 100000 + bestc.vec * 10000 + bestc.slots * 100 + bestc.positions * 10 + bestc.pipe;
+  });
+}
+
+int ps_autotune_record(const ps_problem* p, ps_tune_entry* out, int cap, int* len) {
+  return guarded([&] {
+    PS_REQUIRE(p && len && (out || cap == 0), "null argument");
+    const int n = std::min<int>(cap, (int)p->tune_log.size());
+    for (int i = 0; i < n; ++i) {
+      const auto& e = p->tune_log[i];
+      std::memset(out[i].name, 0, sizeof out[i].name);
+      std::strncpy(out[i].name, e.name.c_str(), sizeof out[i].name - 1);
+      out[i].ms = e.ms;
+      out[i].chosen = e.chosen;
+    }
+    *len = n;
   });
 }
 
@@ -1105,6 +1226,10 @@ int ps_copy_schedule(const ps_problem* src, ps_problem* dst) {
     PS_REQUIRE(src && dst, "null argument");
     rebuild_tiles(dst, src->prm.tile_slots, src->prm.tile_positions, src->prm.tile_pipeline == 1 ? 1 : 0,
                   src->prm.tile_lines_per_thread);
+    dst->coarse_staged = src->coarse_staged;
+    dst->prm.coarse_sweep = src->prm.coarse_sweep;
+    dst->xsched = src->xsched;
+    dst->prm.schedule = src->prm.schedule;
   });
 }
 
@@ -1125,7 +1250,10 @@ int ps_problem_update_coefficients(ps_problem* p, const double* a_nodal_dev, uin
         for (int m = 0; m < p->g.dim; ++m) {
           factor_dim(p->g, m, op->a.p, op->c / p->g.dim, P->tau, *P->dim[m], fine ? mixed : p->delta32, st);
           if (fine) factor_lines(g3, *P->dim[m], mixed, st);
-          else if (p->delta32 && m == 0) factor_lines(g3, *P->dim[m], true, st);
+          else if (p->delta32 && m == 0) {
+            factor_lines(g3, *P->dim[m], true, st);
+            if (p->g.n[0] <= 256) tridiag_x_rows(p->g, op->a.p, op->c / p->g.dim, P->tau, p->pcr_e, p->pcr_d, st);
+          }
         }
       } else {
         dd_factor(p->g, P->sp->dd, op->a.p, op->d12.p, op->c, P->tau, *P->dd, st);

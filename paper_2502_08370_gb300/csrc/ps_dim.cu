@@ -96,7 +96,12 @@ __device__ __forceinline__ void sweep_x_body(long long blk, Tc* sm, const Tin* i
       const long long sl = row / rows_per_slice;
       const double* s = sa.src + (row - sl * rows_per_slice) * nx;
       const double c = sa.tau * (sa.src_t ? sa.src_t[sa.t0 + sl * sa.tstride] : 1.0);
-      for (int cc = lane; cc < nx; cc += 32) srow[cc] = (Tc)grow[cc] + to<Tc>(c * s[cc]);
+      if constexpr (sizeof(Tc) == 8) {
+        // one rounding, as the staged coarse sweep (ps_coarse.cu) forms b + tau f
+        for (int cc = lane; cc < nx; cc += 32) srow[cc] = fma(c, s[cc], (double)grow[cc]);
+      } else {
+        for (int cc = lane; cc < nx; cc += 32) srow[cc] = (Tc)grow[cc] + to<Tc>(c * s[cc]);
+      }
     } else {
       for (int cc = lane; cc < nx; cc += 32) srow[cc] = (Tc)grow[cc];
     }
@@ -126,7 +131,7 @@ __device__ __forceinline__ void sweep_x_body(long long blk, Tc* sm, const Tin* i
 #pragma unroll
       for (int u = 0; u < K; ++u) {
         if (i0 + u < nx) {
-          y = b[u] - l[u] * y;
+          y = fma(-l[u], y, b[u]);  // explicit: the same rounding as the staged sweeps
           x[i0 + u] = y;
         }
       }
@@ -145,7 +150,7 @@ __device__ __forceinline__ void sweep_x_body(long long blk, Tc* sm, const Tin* i
       for (int u = 0; u < KB; ++u) {
         const int i = i0 - u;
         if (i >= 0) {
-          xn = (i == nx - 1) ? r[u] * yy[u] : r[u] * yy[u] - l[u] * xn;
+          xn = (i == nx - 1) ? r[u] * yy[u] : fma(-l[u], xn, r[u] * yy[u]);
           x[i] = xn;
         }
       }
@@ -338,7 +343,7 @@ __device__ __forceinline__ void sweep_strided_body(long long blk, const Tin* in,
 #pragma unroll
         for (int u = 0; u < K; ++u) {
           if (i0 + u < nm) {
-            y = b[u] - l[u] * y;
+            y = fma(-l[u], y, b[u]);
             tmp[base + (i0 + u) * S] = (Tout)y;
           }
         }
@@ -357,7 +362,7 @@ __device__ __forceinline__ void sweep_strided_body(long long blk, const Tin* in,
 #pragma unroll
         for (int u = 0; u < K; ++u) {
           if (i0 + u < nm) {
-            y = b[u] - l[u] * y;
+            y = fma(-l[u], y, b[u]);
             tmp[base + (i0 + u) * S] = (Tout)y;
           }
         }
@@ -387,7 +392,7 @@ __device__ __forceinline__ void sweep_strided_body(long long blk, const Tin* in,
       for (int u = 0; u < KB; ++u) {
         const int i = i0 - u;
         if (i >= 0) {
-          xn = (i == nm - 1) ? r[u] * yy[u] : r[u] * yy[u] - l[u] * xn;
+          xn = (i == nm - 1) ? r[u] * yy[u] : fma(-l[u], xn, r[u] * yy[u]);
           const long long gi = base + i * S;
           if (EPI == 0) {
             out[gi] = (Tout)xn;

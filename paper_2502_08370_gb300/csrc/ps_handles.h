@@ -125,6 +125,15 @@ struct ps_problem {
   ps::DevBuf<double> U, Fout, Gold, gtmp;
   bool delta32 = false;       // coarse increment form in FP32 (PS_COARSE_DELTA32); no Gold then
   bool dr = false;            // fine propagator: Douglas-Rachford steps (PS_FINE_DR)
+  bool coarse_staged = true;  // coarse sweeps staged through shared memory (ps_coarse.cu), else streamed
+  int xsched = PS_SCHED_HYBRID;  // schedule of the FP32 increment form's coarse x-sweep
+  ps::DevBuf<float> pcr_e, pcr_d;  // its tridiagonal rows for the PCR schedule (line-major FP32)
+  struct TuneEntry {
+    std::string name;
+    double ms;
+    int chosen;
+  };
+  std::vector<TuneEntry> tune_log;  // the last ps_autotune's timings
   ps::DevBuf<double> dr_W;    // its increments U_{n,j} - U_n, N states
   ps::DevBuf<float> d32, g32; // its increment U_n^k - U_n^{k-1} and coarse working state
   ps::DevBuf<float> W;      // fine working state, slice-interleaved (FP32 line solves)

@@ -155,6 +155,22 @@ void sweep_dim(const Geom& g, int nslices, const LineFactors& f, bool fp32, cons
 template <typename Tin>
 void sweep_x_warp(const Geom& g, const LineFactors& f, const Tin* in, float* out, const SourceArgs& sa,
                   cudaStream_t st);
+// Coarse-propagator sweep of direction f.m on ONE slice, staged through shared memory
+// (ps_coarse.cu); in may alias out.  T = double: x, y, z (x carries the source, y/z the
+// epilogues of CorrArgs modes 0-2); T = float: y, z with modes 0, 2, 3.  Returns false (nothing
+// launched) when the shape does not fit the kernels' shared-memory budget; the caller then runs
+// sweep_dim.
+template <typename T>
+bool coarse_sweep_staged(const Geom& g, const LineFactors& f, const T* in, T* out, const SourceArgs& sa,
+                         const CorrArgs& ca, cudaStream_t st);
+// Coarse x-substep in FP32 on one slice by parallel cyclic reduction, one warp per row (rows
+// of at most 256 nodes; returns false otherwise).  et/dt: line-major FP32 rows of the
+// sub-diagonal and diagonal of (I - tau A_x), built by tridiag_x_rows.
+template <typename Tin>
+bool sweep_x_pcr(const Geom& g, const float* et, const float* dt, const Tin* in, float* out, const SourceArgs& sa,
+                 cudaStream_t st);
+void tridiag_x_rows(const Geom& g, const double* a_nodal, double c_over_M, double tau, DevBuf<float>& et,
+                    DevBuf<float>& dt, cudaStream_t st);
 // Douglas-Rachford fine step in increment form (ps_dr.cu), nsl consecutive states of the
 // natural layout: w = tau (A u + f) (A with reaction c, f from sa at t0 + slice * tstride);
 // out = u + w (out may alias u).

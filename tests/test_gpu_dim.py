@@ -181,9 +181,6 @@ def test_invalid_arguments_are_rejected(ps):
     with pytest.raises(ps.PsError):
         ps.Problem(sp, -1.0, 4, 1, 8)
     with pytest.raises(ps.PsError) as e:
-        ps.Problem(sp, 1.0, 4, 1, 8, schedule=ps.PS_SCHED_PCR)  # not built
-    assert e.value.code == 6
-    with pytest.raises(ps.PsError) as e:
         ps.Problem(sp, 1.0, 4, 1, 8, schedule=7)
     assert e.value.code == 1
     prob = ps.Problem(sp, 1.0, 4, 1, 8)
@@ -308,3 +305,58 @@ def test_fp32_tiles_one_line_per_thread(ps, n, positions):
         assert np.array_equal(out[0][j], out[1][j]), j
     U_ref, _, _ = orc.parareal(orc.Problem(n, a=a, src=src), 0.5, 6, 1, 5, u0.cpu().numpy(), 1e-8)
     assert relmax(out[1][6], U_ref[6]) < mixed_bound(5, 6, len(n))
+
+
+@pytest.mark.parametrize("n", [(63, 63), (255, 9, 7), (40, 37, 33)])
+def test_coarse_x_schedules_thomas_pcr_hybrid(ps, n):
+    """The FP32 increment form's coarse x-sweep in its three schedules (Thomas per row, PCR per
+    warp, hybrid segmented scans per warp): the same iteration count and states within the FP32
+    rounding of the coarse increment of each other, and within the FP32 bound of the oracle."""
+    rng = np.random.default_rng(71)
+    a = np.exp(0.3 * rng.standard_normal([v + 2 for v in reversed(n)]))
+    src = rng.standard_normal(n[::-1])
+    u0 = dev(rng.standard_normal(n[::-1]))
+    N, s, T = 8, 6, 0.4
+    out = {}
+    for sched in (ps.PS_SCHED_THOMAS, ps.PS_SCHED_PCR, ps.PS_SCHED_HYBRID):
+        grid = ps.Grid(n)
+        op = ps.Operator(grid, a=dev(a), src=dev(src))
+        sp = ps.Splitting(op)
+        prob = ps.Problem(sp, T, N, 1, s, precision="mixed", coarse_mode="delta32", schedule=sched)
+        it = prob.run(u0, 1e-10)
+        out[sched] = (it, [prob.state(j).cpu().numpy() for j in range(N + 1)])
+    its = {v[0] for v in out.values()}
+    assert len(its) == 1, its
+    ref = out[ps.PS_SCHED_HYBRID][1]
+    # the coarse propagator only steers the iteration: at convergence every schedule sits within
+    # the increment tolerance of the same FP32-fine fixed point
+    for sched in (ps.PS_SCHED_THOMAS, ps.PS_SCHED_PCR):
+        for j in range(N + 1):
+            assert relmax(out[sched][1][j], ref[j]) < 1e-8, (sched, j)
+    U_ref, _, _ = orc.parareal(orc.Problem(n, a=a, src=src), T, N, 1, s, u0.cpu().numpy(), 1e-10)
+    assert relmax(out[ps.PS_SCHED_PCR][1][N], U_ref[N]) < mixed_bound(s, N, len(n))
+
+
+def test_autotune_record_lists_every_schedule(ps):
+    n = (127, 63, 31)
+    rng = np.random.default_rng(72)
+    a = np.exp(0.3 * rng.standard_normal([v + 2 for v in reversed(n)]))
+    grid = ps.Grid(n)
+    op = ps.Operator(grid, a=dev(a))
+    sp = ps.Splitting(op)
+    prob = ps.Problem(sp, 0.5, 32, 1, 4, precision="mixed", coarse_mode="delta32")
+    u0 = dev(rng.standard_normal(n[::-1]))
+    prob.run(u0, 1e-8)
+    before = prob.state(32).cpu().numpy()
+    choice = prob.autotune(budget_ms=40)
+    rec = prob.autotune_record()
+    names = [r[0] for r in rec]
+    assert {"coarse-x32:thomas", "coarse-x32:pcr", "coarse-x32:hybrid", "coarse:staged", "coarse:streamed"} <= set(names)
+    assert any(nm.startswith("fine:") for nm in names)
+    for group in ("fine:", "coarse-x32:", "coarse:"):
+        chosen = [r for r in rec if r[0].startswith(group) and r[2]]
+        assert len(chosen) == 1, (group, rec)
+        assert chosen[0][1] == min(r[1] for r in rec if r[0].startswith(group))
+    assert choice // 100000 in (1, 2)
+    prob.run(u0, 1e-8)
+    assert relmax(prob.state(32).cpu().numpy(), before) < 1e-7
