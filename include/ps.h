@@ -91,7 +91,10 @@ extern "C" {
  * its lines and their factors into shared memory with asynchronous copies, one thread per line
  * runs the Thomas/LDL^T recurrences there, and the CTA writes back with the correction fused.
  * STREAMED: one thread per line runs them from global memory with its loads issued a chunk
- * ahead.  Both compute the same recurrence; results agree to rounding. */
+ * ahead.  Both compute the same recurrences with the same roundings (bitwise equal results).
+ * On GB300 the streamed form is faster for FP64 (measured): an FP64 FMA's dependent latency is
+ * long, and the staged form runs only the lines of its shared-memory tiles per SM, too few
+ * independent chains to hide it. */
 #define PS_COARSE_SWEEP_AUTO 0
 #define PS_COARSE_SWEEP_STAGED 1
 #define PS_COARSE_SWEEP_STREAMED 2
@@ -184,9 +187,13 @@ typedef struct {
   int tile_lines_per_thread; /* fine line solves (FP32 tiles of 32+ slots): lines a thread solves
                                 side by side, 1 or 2; 0 = auto (1) */
   int fine_method;         /* PS_FINE_FIE (0) or PS_FINE_DR */
+  int serial_phases;       /* 0: with the dimensional splitting, the fine phase of an iteration runs on
+                              a side stream, slot group by slot group, and the coarse chain follows
+                              each group as it finishes (the same values, computed concurrently);
+                              1: the fine phase completes before the chain starts */
   int coarse_sweep;        /* coarse-propagator line solves on one slice (dimensional splitting):
-                              PS_COARSE_SWEEP_STAGED or PS_COARSE_SWEEP_STREAMED; 0 = staged where
-                              the line fits, ps_autotune may change it */
+                              PS_COARSE_SWEEP_STAGED or PS_COARSE_SWEEP_STREAMED; 0 = streamed
+                              unless ps_autotune picks staged */
 } ps_params;
 
 /* fine, coarse: splittings of the same operator used by F and G (coarse = NULL: use

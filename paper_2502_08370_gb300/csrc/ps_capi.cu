@@ -198,7 +198,8 @@ void fie_step64(ps_problem* p, Prop& P, int nsl, const double* in, double* out, 
 // dimensional splitting the slices are packed into the interleaved working state, every
 // substep is one TMA tile sweep over all of them, and the result is unpacked into `out`.
 template <typename T>
-void run_F_tiles(ps_problem* p, int n_first, int nsl, const double* in, double* out, cudaStream_t st) {
+void run_F_tiles(ps_problem* p, int n_first, int nsl, const double* in, double* out, cudaStream_t st,
+                 cudaEvent_t after_pack = nullptr) {
   Prop& P = p->F;
   const int M = P.sp->M;
   T* W = sizeof(T) == 4 ? reinterpret_cast<T*>(p->W.p) : reinterpret_cast<T*>(p->W64.p);
@@ -208,6 +209,7 @@ void run_F_tiles(ps_problem* p, int n_first, int nsl, const double* in, double* 
   to_interleaved<T>(p->g, in, W, p->S_pad, n_first, nsl, st);
   if (p->kt.on) p->kt.end(std::string("F.pack.") + tn, nsl * nt * (8.0 + sizeof(T)), 0.0);
   p->launches++;
+  if (after_pack) PS_CUDA(cudaEventRecord(after_pack, st));
   for (int j = 0; j < P.steps; ++j) {
     for (int q = 0; q < M; ++q) {
       const int m = p->transposed ? M - 1 - q : q;
@@ -446,6 +448,65 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
     const int nlo = k - 1;
     PS_CUDA(cudaMemsetAsync(p->inc.p, 0, sizeof(unsigned long long), st));
     PS_CUDA(cudaMemsetAsync(p->sstats.p, 0, sizeof(unsigned long long) * 2 * (N + 1), st));
+    // Fine phase beside the chain: F needs only U^{k-1}, and the chain's step n needs only F of
+    // slice n, so F runs slot group by slot group on the side stream while the chain follows the
+    // groups as they finish.  Only the ordering changes; every value is computed as before.
+    std::vector<int> bounds;  // slot groups [bounds[g], bounds[g+1]) of this iteration's fine phase
+    if (p->overlap && p->side && !p->dr && !p->transposed && p->F.sp->kind == PS_SPLIT_DIM) {
+      const int TS = p->F.tiles[0].TS;
+      bounds.push_back(nlo);
+      for (int b = (nlo / TS + 1) * TS; b < N; b += TS) bounds.push_back(b);
+      bounds.push_back(N);
+      if (bounds.size() < 3 || (int)bounds.size() - 1 > (int)p->ev_done.size()) bounds.clear();
+    }
+    if (!bounds.empty()) {
+      TraceRange r("ps.fine_and_chain_overlapped");
+      const int ng = (int)bounds.size() - 1;
+      PS_CUDA(cudaEventRecord(p->ev_fine[0], st));  // U^{k-1} complete (the initial sweep, or the last chain)
+      PS_CUDA(cudaStreamWaitEvent(p->side, p->ev_fine[0], 0));
+      if (timing) PS_CUDA(cudaEventRecord(p->ev[1], p->side));
+      for (int g = 0; g < ng; ++g) {
+        const int a = bounds[g], nsl = bounds[g + 1] - bounds[g];
+        if (p->F.f32)
+          run_F_tiles<float>(p, a, nsl, p->U.p + a * nt, p->Fout.p + a * nt, p->side, p->ev_pack[g]);
+        else
+          run_F_tiles<double>(p, a, nsl, p->U.p + a * nt, p->Fout.p + a * nt, p->side, p->ev_pack[g]);
+        p->updates += (double)nsl * p->F.steps * (double)nt;
+        PS_CUDA(cudaEventRecord(p->ev_done[g], p->side));
+      }
+      if (timing) PS_CUDA(cudaEventRecord(p->ev[2], p->side));
+      TraceRange r2("ps.coarse_chain_correction");
+      auto group_of = [&](int slice) {
+        int g = 0;
+        while (g + 1 < ng && slice >= bounds[g + 1]) ++g;
+        return g;
+      };
+      int waited_done = -1, waited_pack = 0;
+      // before the chain reads F of slice n: its group has been unpacked
+      auto need_F = [&](int n) {
+        const int g = group_of(n);
+        while (waited_done < g) PS_CUDA(cudaStreamWaitEvent(st, p->ev_done[++waited_done], 0));
+      };
+      // before the chain writes U_j: the group holding slice j has read its U^{k-1} (packed)
+      auto writes_U = [&](int j) {
+        if (j >= N) return;
+        const int g = group_of(j);
+        while (waited_pack < g && waited_done < g) PS_CUDA(cudaStreamWaitEvent(st, p->ev_pack[++waited_pack], 0));
+      };
+      need_F(nlo);
+      writes_U(k);
+      copy_with_increment(nt, p->Fout.p + nlo * nt, p->U.p + k * nt, p->inc.p, p->flag.p, p->sstats.p + 2 * k,
+                          p->delta32 ? p->d32.p : nullptr, st);
+      p->launches++;
+      for (int n = k; n < N; ++n) {
+        need_F(n);
+        writes_U(n + 1);
+        if (p->delta32) run_G32(p, n, false, st);
+        else run_G(p, n, p->U.p + n * nt, corr_args(p, 1, n), st);
+      }
+      // the side stream's last group is part of this iteration: the chain ends after it
+      while (waited_done < ng - 1) PS_CUDA(cudaStreamWaitEvent(st, p->ev_done[++waited_done], 0));
+    } else {
     if (timing) PS_CUDA(cudaEventRecord(p->ev[1], st));
     {
       TraceRange r("ps.fine_all_slices");
@@ -462,6 +523,7 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
         if (p->delta32) run_G32(p, n, false, st);
         else run_G(p, n, p->U.p + n * nt, corr_args(p, 1, n), st);
       }
+    }
     }
     if (timing) PS_CUDA(cudaEventRecord(p->ev[3], st));
     TraceRange test("ps.increment_test");
@@ -609,6 +671,15 @@ void configure_slices(ps_problem* p, int N, int g_steps, int f_steps, cudaStream
       }
       source_rows(g3, p->op->src.p, out, elem, st);
     }
+  }
+  // events of the overlapped fine phase: one pair per slot group
+  const int groups = p->S_pad > 0 ? p->S_pad / std::max(1, p->F.tiles[0].TS) + 1 : 0;
+  while ((int)p->ev_done.size() < groups) {
+    cudaEvent_t a, b;
+    PS_CUDA(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+    PS_CUDA(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+    p->ev_pack.push_back(a);
+    p->ev_done.push_back(b);
   }
   PS_CUDA(cudaStreamSynchronize(st));
   p->N = N;
@@ -864,7 +935,9 @@ int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, doub
     PS_REQUIRE(p->prm.tol_mode == 0 || p->prm.tol_mode == 1, "tol_mode must be 0 or 1");
     PS_REQUIRE(p->prm.coarse_sweep >= PS_COARSE_SWEEP_AUTO && p->prm.coarse_sweep <= PS_COARSE_SWEEP_STREAMED,
                "unknown coarse sweep schedule");
-    p->coarse_staged = p->prm.coarse_sweep != PS_COARSE_SWEEP_STREAMED;
+    p->coarse_staged = p->prm.coarse_sweep == PS_COARSE_SWEEP_STAGED;
+    PS_REQUIRE(p->prm.serial_phases == 0 || p->prm.serial_phases == 1, "serial_phases must be 0 or 1");
+    p->overlap = p->prm.serial_phases == 0;
     p->dr = p->prm.fine_method == PS_FINE_DR;
     if (p->dr && p->prm.precision != PS_PREC_FP64)
       throw Error(PS_ERR_UNSUPPORTED, "the Douglas-Rachford fine propagator runs in FP64");
@@ -877,6 +950,8 @@ int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, doub
     PS_CUDA(cudaMallocHost(&p->h_inc, sizeof(unsigned long long)));
     PS_CUDA(cudaMallocHost(&p->h_flag, 2 * sizeof(int)));
     for (auto& e : p->ev) PS_CUDA(cudaEventCreate(&e));
+    for (auto& e : p->ev_fine) PS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    PS_CUDA(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
     p->inc.alloc(1);
     p->tmo.alloc(1);
     p->flag.alloc(1);

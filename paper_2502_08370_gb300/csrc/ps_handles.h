@@ -125,7 +125,7 @@ struct ps_problem {
   ps::DevBuf<double> U, Fout, Gold, gtmp;
   bool delta32 = false;       // coarse increment form in FP32 (PS_COARSE_DELTA32); no Gold then
   bool dr = false;            // fine propagator: Douglas-Rachford steps (PS_FINE_DR)
-  bool coarse_staged = true;  // coarse sweeps staged through shared memory (ps_coarse.cu), else streamed
+  bool coarse_staged = false;  // coarse sweeps staged through shared memory (ps_coarse.cu), else streamed
   int xsched = PS_SCHED_HYBRID;  // schedule of the FP32 increment form's coarse x-sweep
   ps::DevBuf<float> pcr_e, pcr_d;  // its tridiagonal rows for the PCR schedule (line-major FP32)
   struct TuneEntry {
@@ -163,6 +163,13 @@ struct ps_problem {
   int launches = 0;
   float ms_total = 0, ms_fine = 0, ms_coarse = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // overlap of the fine phase (side stream, slot group by slot group) with the coarse chain:
+  // per group, an event after its pack (its inputs U^{k-1} have been read) and after its unpack
+  // (its F results are in Fout)
+  cudaStream_t side = nullptr;
+  std::vector<cudaEvent_t> ev_pack, ev_done;
+  cudaEvent_t ev_fine[2] = {nullptr, nullptr};
+  bool overlap = true;  // run the fine phase beside the chain when it spans several slot groups
   ps::KernelTimer kt;
   ~ps_problem() {
     if (h_sstats) cudaFreeHost(h_sstats);
@@ -170,6 +177,11 @@ struct ps_problem {
     if (h_flag) cudaFreeHost(h_flag);
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
+    for (auto& e : ev_fine)
+      if (e) cudaEventDestroy(e);
+    for (auto e : ev_pack) cudaEventDestroy(e);
+    for (auto e : ev_done) cudaEventDestroy(e);
+    if (side) cudaStreamDestroy(side);
   }
 };
 

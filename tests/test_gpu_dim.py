@@ -360,3 +360,30 @@ def test_autotune_record_lists_every_schedule(ps):
     assert choice // 100000 in (1, 2)
     prob.run(u0, 1e-8)
     assert relmax(prob.state(32).cpu().numpy(), before) < 1e-7
+
+
+@pytest.mark.parametrize("prec,coarse,N", [("mixed", "fp64", 70), ("mixed", "delta32", 64), ("fp64", "fp64", 40)])
+def test_fine_phase_beside_chain_is_bitwise_serial(ps, prec, coarse, N):
+    """The fine phase run slot group by slot group on a side stream, with the coarse chain
+    following each group, computes exactly what the serial order computes: every state and the
+    history bitwise equal, for runs ending at convergence and at k = N."""
+    n = (31, 27, 23)
+    rng = np.random.default_rng(73)
+    a = np.exp(0.3 * rng.standard_normal([v + 2 for v in reversed(n)]))
+    src = rng.standard_normal(n[::-1])
+    u0 = dev(rng.standard_normal(n[::-1]))
+    res = []
+    for serial in (False, True):
+        grid = ps.Grid(n)
+        op = ps.Operator(grid, a=dev(a), src=dev(src))
+        sp = ps.Splitting(op)
+        prob = ps.Problem(sp, 0.5, N, 1, 4, precision=prec, coarse_mode=coarse, serial_phases=serial)
+        out = []
+        for tol, mi in ((1e-9, 0), (0.0, 5)):
+            it = prob.run(u0, tol, mi)
+            out.append((it, prob.history(), [prob.state(j).cpu().numpy() for j in range(N + 1)]))
+        res.append(out)
+    for (it1, h1, s1), (it2, h2, s2) in zip(res[0], res[1]):
+        assert it1 == it2 and np.array_equal(h1, h2)
+        for j in range(N + 1):
+            assert np.array_equal(s1[j], s2[j]), j
