@@ -231,6 +231,25 @@ int ps_run_parareal_host(ps_problem* p, const double* u0_host, double* uN_host, 
 int ps_get_state(const ps_problem* p, int slice, double* out_dev, uintptr_t stream);
 /* inc_k for k = 1..len of the last run; len = min(iterations, cap). */
 int ps_get_history(const ps_problem* p, double* inc_host, int cap, int* len);
+/* Overwrite U_slice (0..N) with in_dev.  The problem's iterate is then no longer resumable. */
+int ps_set_state(ps_problem* p, int slice, const double* in_dev, uintptr_t stream);
+
+/* Checkpoint and resume of a parareal run (no counterpart in the paper).  After
+ * ps_run_parareal (or ps_resume_parareal) stopped at iteration k -- at its tolerance or at
+ * max_iter -- ps_checkpoint_save writes k, the history inc_1..inc_k, the slice states U^k and,
+ * with the FP64 coarse propagator, the coarse values G(U_n^k) that the next correction
+ * subtracts, into host memory (ps_checkpoint_bytes gives the size).  ps_checkpoint_load puts
+ * them into a problem of the same grid, slice count and coarse form (PS_ERR_INVALID
+ * otherwise), and ps_resume_parareal continues with iteration k+1 to the given tolerance or
+ * max_iter (counted from the start of the run; <= 0: N).  The continued run computes exactly
+ * the values the uninterrupted run computes.  A run that had already met `tol` does not
+ * iterate further.  ps_resume_parareal also continues the problem's own stopped run.  The
+ * adjoint, ps_set_state, ps_problem_set_slices and ps_problem_update_coefficients end the
+ * resumability of the current iterate. */
+int ps_checkpoint_bytes(const ps_problem* p, size_t* bytes);
+int ps_checkpoint_save(const ps_problem* p, void* host_buf, size_t bytes, uintptr_t stream);
+int ps_checkpoint_load(ps_problem* p, const void* host_buf, size_t bytes, uintptr_t stream);
+int ps_resume_parareal(ps_problem* p, double tol, int max_iter, uintptr_t stream, int* iters_out);
 
 /* Sequential fine solution (the plain comparator): U_out_dev gets (N+1) states at T_n. */
 int ps_run_fine_sequential(ps_problem* p, const double* u0_dev, double* U_out_dev, uintptr_t stream);

@@ -95,6 +95,11 @@ SIGNATURES = {
     "ps_run_parareal_host": [_VP, _VP, _VP, _D, _I, _U, _IP],
     "ps_get_state": [_VP, _I, _VP, _U],
     "ps_get_history": [_VP, _VP, _I, _IP],
+    "ps_set_state": [_VP, _I, _VP, _U],
+    "ps_checkpoint_bytes": [_VP, C.POINTER(C.c_size_t)],
+    "ps_checkpoint_save": [_VP, _VP, C.c_size_t, _U],
+    "ps_checkpoint_load": [_VP, _VP, C.c_size_t, _U],
+    "ps_resume_parareal": [_VP, _D, _I, _U, _IP],
     "ps_run_fine_sequential": [_VP, _VP, _VP, _U],
     "ps_run_coarse_sequential": [_VP, _VP, _VP, _U],
     "ps_run_coarse_sequential_noalloc": [_VP, _VP, _VP, _U],
@@ -288,6 +293,26 @@ class Problem:
             out = torch.empty(self.grid.shape, dtype=torch.float64, device="cuda")
         check(lib().ps_get_state(self._h, int(n), _dev_ptr(out, self.grid.nt), _stream(stream)))
         return out
+
+    def set_state(self, n, x, stream=None):
+        check(lib().ps_set_state(self._h, int(n), _dev_ptr(x, self.grid.nt), _stream(stream)))
+
+    def checkpoint(self, stream=None):
+        """The current parareal iterate as bytes (k, history, U^k, coarse values)."""
+        nb = C.c_size_t(0)
+        check(lib().ps_checkpoint_bytes(self._h, C.byref(nb)))
+        buf = C.create_string_buffer(nb.value)
+        check(lib().ps_checkpoint_save(self._h, buf, nb, _stream(stream)))
+        return buf.raw
+
+    def load_checkpoint(self, data, stream=None):
+        buf = C.create_string_buffer(bytes(data), len(data))
+        check(lib().ps_checkpoint_load(self._h, buf, len(data), _stream(stream)))
+
+    def resume(self, tol, max_iter=0, stream=None):
+        it = C.c_int(0)
+        check(lib().ps_resume_parareal(self._h, float(tol), int(max_iter), _stream(stream), C.byref(it)))
+        return it.value
 
     def history(self):
         import numpy as np

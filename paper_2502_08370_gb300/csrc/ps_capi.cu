@@ -417,13 +417,18 @@ struct TraceRange {
   TraceRange& operator=(const TraceRange&) = delete;
 };
 
-void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStream_t st, int* iters_out) {
+// resume_k < 0: a new run from u0.  resume_k >= 0: continue after iteration resume_k from the
+// problem's states U^k, coarse values Gold and history (a stopped run, or a loaded checkpoint).
+void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStream_t st, int* iters_out,
+            int resume_k = -1) {
   TraceRange whole(p->transposed ? "ps.adjoint_parareal" : "ps.parareal");
   require_slices(p);
   const long long nt = p->g.nt;
   const int N = p->N;
   if (max_iter <= 0 || max_iter > N) max_iter = N;
-  p->hist.clear();
+  const bool resume = resume_k >= 0;
+  if (!resume) p->hist.clear();
+  p->resumable = false;
   p->updates = 0;
   p->launches = 0;
   p->ms_total = p->ms_fine = p->ms_coarse = 0;
@@ -431,19 +436,21 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
   p->kt.on = p->prm.timing >= 2;
   p->kt.reset();
   if (timing) PS_CUDA(cudaEventRecord(p->ev[0], st));
-  PS_CUDA(cudaMemcpyAsync(p->U.p, u0, sizeof(double) * nt, cudaMemcpyDeviceToDevice, st));
+  if (!resume) PS_CUDA(cudaMemcpyAsync(p->U.p, u0, sizeof(double) * nt, cudaMemcpyDeviceToDevice, st));
   PS_CUDA(cudaMemsetAsync(p->flag.p, 0, sizeof(int), st));
   tile_flag_reset(p, st);
   // k = 0: sequential coarse sweep, U_{n+1}^0 = G(U_n^0), Gold_n = G(U_n^0)
-  {
+  if (!resume) {
     TraceRange r("ps.coarse_initial");
     for (int n = 0; n < N; ++n) {
       if (p->delta32) run_G32(p, n, true, st);
       else run_G(p, n, p->U.p + n * nt, corr_args(p, 2, n), st);
     }
   }
-  int k = 0;
-  while (k < max_iter) {
+  int k = resume ? resume_k : 0;
+  // a resumed run that had already met its stopping rule stays where it stopped
+  const bool done = resume && k > 0 && ((int)p->hist.size() == k && p->hist[k - 1] < tol);
+  while (k < max_iter && !done) {
     ++k;
     const int nlo = k - 1;
     PS_CUDA(cudaMemsetAsync(p->inc.p, 0, sizeof(unsigned long long), st));
@@ -573,7 +580,10 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
     PS_CUDA(cudaEventElapsedTime(&p->ms_total, p->ev[0], p->ev[1]));
   }
   p->iters = k;
-  if (!p->transposed) p->have_forward = true;
+  if (!p->transposed) {
+    p->have_forward = true;
+    p->resumable = true;
+  }
   if (iters_out) *iters_out = k;
 }
 
@@ -601,6 +611,7 @@ void configure_slices(ps_problem* p, int N, int g_steps, int f_steps, cudaStream
   p->iters = 0;
   p->hist.clear();
   p->have_forward = false;
+  p->resumable = false;
   p->adj_ready = false;
   for (auto* b : {&p->U, &p->Fout, &p->Gold, &p->gtmp, &p->dr_W, &p->W64, &p->srcrow64, &p->Uchk, &p->snap, &p->Lam})
     b->reset();
@@ -1007,6 +1018,112 @@ int ps_get_state(const ps_problem* p, int slice, double* out_dev, uintptr_t stre
   });
 }
 
+int ps_set_state(ps_problem* p, int slice, const double* in_dev, uintptr_t stream) {
+  return guarded([&] {
+    PS_REQUIRE(p && in_dev, "null argument");
+    check_state_len(p, slice);
+    const long long nt = p->g.nt;
+    PS_CUDA(cudaMemcpyAsync(p->U.p + slice * nt, in_dev, sizeof(double) * nt, cudaMemcpyDeviceToDevice, S(stream)));
+    p->resumable = false;  // a state edited by hand is not an iterate of the run
+  });
+}
+
+namespace {
+// Checkpoint layout (host memory, native byte order): this header, the history (hist_len
+// doubles), U^k ((N+1) states), and Gold (N states) when the coarse propagator is FP64.
+struct CkptHeader {
+  char magic[8];
+  int version, N, dim, n[3], k, delta32, has_gold, hist_len, pad;
+  long long nt;
+};
+constexpr char kCkptMagic[8] = {'P', 'S', 'C', 'K', 'P', 'T', '1', 0};
+size_t ckpt_bytes(const ps_problem* p) {
+  const size_t nt = (size_t)p->g.nt;
+  return sizeof(CkptHeader) + sizeof(double) * ((size_t)p->N + (size_t)(p->N + 1) * nt +
+                                                (p->delta32 ? 0 : (size_t)p->N * nt));
+}
+}  // namespace
+
+int ps_checkpoint_bytes(const ps_problem* p, size_t* bytes) {
+  return guarded([&] {
+    PS_REQUIRE(p && bytes, "null argument");
+    require_slices(p);
+    *bytes = ckpt_bytes(p);
+  });
+}
+
+int ps_checkpoint_save(const ps_problem* p, void* host_buf, size_t bytes, uintptr_t stream) {
+  return guarded([&] {
+    PS_REQUIRE(p && host_buf, "null argument");
+    require_slices(p);
+    PS_REQUIRE(p->resumable, "no parareal iterate to save: run ps_run_parareal first");
+    PS_REQUIRE(bytes >= ckpt_bytes(p), "checkpoint buffer too small (ps_checkpoint_bytes)");
+    cudaStream_t st = S(stream);
+    CkptHeader h{};
+    std::memcpy(h.magic, kCkptMagic, sizeof h.magic);
+    h.version = PS_VERSION;
+    h.N = p->N;
+    h.dim = p->g.dim;
+    for (int d = 0; d < 3; ++d) h.n[d] = p->g.n[d];
+    h.k = p->iters;
+    h.delta32 = p->delta32 ? 1 : 0;
+    h.has_gold = p->delta32 ? 0 : 1;
+    h.hist_len = (int)p->hist.size();
+    h.nt = p->g.nt;
+    char* out = static_cast<char*>(host_buf);
+    std::memcpy(out, &h, sizeof h);
+    double* hist = reinterpret_cast<double*>(out + sizeof h);
+    for (int i = 0; i < p->N; ++i) hist[i] = i < h.hist_len ? p->hist[i] : 0.0;
+    double* U = hist + p->N;
+    const size_t nt = (size_t)p->g.nt;
+    PS_CUDA(cudaMemcpyAsync(U, p->U.p, sizeof(double) * (p->N + 1) * nt, cudaMemcpyDeviceToHost, st));
+    if (h.has_gold)
+      PS_CUDA(cudaMemcpyAsync(U + (size_t)(p->N + 1) * nt, p->Gold.p, sizeof(double) * p->N * nt,
+                              cudaMemcpyDeviceToHost, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+int ps_checkpoint_load(ps_problem* p, const void* host_buf, size_t bytes, uintptr_t stream) {
+  return guarded([&] {
+    PS_REQUIRE(p && host_buf, "null argument");
+    require_slices(p);
+    PS_REQUIRE(bytes >= sizeof(CkptHeader), "checkpoint too short");
+    CkptHeader h;
+    std::memcpy(&h, host_buf, sizeof h);
+    PS_REQUIRE(std::memcmp(h.magic, kCkptMagic, sizeof h.magic) == 0, "not a parareal checkpoint");
+    PS_REQUIRE(h.version == PS_VERSION, "checkpoint written by another ABI version");
+    PS_REQUIRE(h.N == p->N && h.dim == p->g.dim && h.n[0] == p->g.n[0] && h.n[1] == p->g.n[1] &&
+                   h.n[2] == p->g.n[2] && h.nt == p->g.nt,
+               "checkpoint of another grid or slice count");
+    PS_REQUIRE(h.delta32 == (p->delta32 ? 1 : 0), "checkpoint of another coarse propagator form");
+    PS_REQUIRE(h.k >= 0 && h.k <= p->N && h.hist_len == h.k, "corrupt checkpoint header");
+    PS_REQUIRE(bytes >= ckpt_bytes(p), "checkpoint truncated");
+    const double* hist = reinterpret_cast<const double*>(static_cast<const char*>(host_buf) + sizeof h);
+    const double* U = hist + p->N;
+    const size_t nt = (size_t)p->g.nt;
+    cudaStream_t st = S(stream);
+    PS_CUDA(cudaMemcpyAsync(p->U.p, U, sizeof(double) * (p->N + 1) * nt, cudaMemcpyHostToDevice, st));
+    if (h.has_gold)
+      PS_CUDA(cudaMemcpyAsync(p->Gold.p, U + (size_t)(p->N + 1) * nt, sizeof(double) * p->N * nt,
+                              cudaMemcpyHostToDevice, st));
+    PS_CUDA(cudaStreamSynchronize(st));
+    p->hist.assign(hist, hist + h.k);
+    p->iters = h.k;
+    p->have_forward = h.k > 0;
+    p->resumable = true;
+  });
+}
+
+int ps_resume_parareal(ps_problem* p, double tol, int max_iter, uintptr_t stream, int* iters_out) {
+  return guarded([&] {
+    PS_REQUIRE(p, "null argument");
+    require_slices(p);
+    PS_REQUIRE(p->resumable, "nothing to resume: no stopped run or loaded checkpoint on this problem");
+    do_run(p, nullptr, tol, max_iter, S(stream), iters_out, p->iters);
+  });
+}
+
 int ps_get_history(const ps_problem* p, double* inc_host, int cap, int* len) {
   return guarded([&] {
     PS_REQUIRE(p && len, "null argument");
@@ -1335,6 +1452,7 @@ int ps_problem_update_coefficients(ps_problem* p, const double* a_nodal_dev, uin
       }
     }
     p->have_forward = false;
+    p->resumable = false;
     PS_CUDA(cudaStreamSynchronize(st));
   });
 }

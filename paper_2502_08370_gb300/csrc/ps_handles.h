@@ -148,6 +148,7 @@ struct ps_problem {
   int batched = 0;          // batches holding this problem (their grouped kernels run one line per
                             // thread, one tile per work item: the autotuner keeps to such shapes)
   bool have_forward = false;
+  bool resumable = false;   // U, Gold and the history hold a forward run's iterate (or a loaded checkpoint)
   // adjoint workspaces (allocated by the first ps_adjoint_vjp with a coefficient gradient)
   ps::DevBuf<double> Uchk, snap, Lam, gedge[3];
   ps::TilePlan adj_tiles[3];

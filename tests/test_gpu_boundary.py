@@ -153,3 +153,48 @@ def test_adjoint_of_target_loss(ps):
     assert torch.equal(gu, gu2) and torch.equal(ga, ga2)
     J2, _, _ = prob.adjoint(dev(tgt), 1e-14)
     assert J2 == J  # fixed summation order
+
+
+@pytest.mark.parametrize("form", ["fp64", "delta32", "dd"])
+def test_checkpoint_resume_is_bitwise_the_uninterrupted_run(ps, form):
+    """A run stopped after 3 iterations, saved, loaded into a fresh problem and resumed to the
+    tolerance gives the uninterrupted run's iteration count, history and states bitwise; so does
+    resuming the stopped problem itself."""
+    n, N, s, T = (29, 23), 12, 6, 0.5
+    a, src, src_t, u0 = inputs(n, 55, N * s)
+
+    def make():
+        grid = ps.Grid(n)
+        op = ps.Operator(grid, a=dev(a), c=0.1, src=dev(src), src_t=src_t)
+        sp = ps.Splitting(op, "dd", (3, 2), 3.0 / 30) if form == "dd" else ps.Splitting(op)
+        prob = ps.Problem(sp, T, N, 1, s, precision="fp64" if form != "delta32" else "mixed",
+                          coarse_mode="delta32" if form == "delta32" else "fp64")
+        prob._keep = (grid, op, sp)
+        return prob
+
+    tol = 1e-10
+    full = make()
+    it = full.run(dev(u0), tol)
+    assert 3 < it <= N
+    ref = ([full.state(j).clone() for j in range(N + 1)], full.history())
+    stopped = make()
+    assert stopped.run(dev(u0), tol, 3) == 3
+    blob = stopped.checkpoint()
+    fresh = make()
+    fresh.load_checkpoint(blob)
+    for prob in (fresh, stopped):
+        assert prob.resume(tol) == it
+        assert np.array_equal(prob.history(), ref[1])
+        for j in range(N + 1):
+            assert torch.equal(prob.state(j), ref[0][j]), j
+        assert prob.resume(tol) == it  # already converged: no further iteration
+    # a checkpoint of another slice count is refused
+    other = make()
+    other.set_slices(6, 1, 12)
+    with pytest.raises(ps.PsError) as e:
+        other.load_checkpoint(blob)
+    assert e.value.code == 1
+    # an edited state is not an iterate to resume
+    fresh.set_state(2, fresh.state(2))
+    with pytest.raises(ps.PsError):
+        fresh.resume(tol)
