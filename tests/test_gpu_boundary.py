@@ -1,6 +1,7 @@
 """The handle calls of the boundary through the C ABI: changing a problem's slice and step
 counts (Sec. 3: N, G = g steps, F = s steps per slice), batches built problem by problem with
-their states read back through the batch, and the adjoint of a target loss.
+their states read back through the batch, the adjoint of a target loss, and checkpoint/resume
+of a parareal run.
 
 Bars: FP64 states within 1e-12 of the oracle with equal iteration counts; a reconfigured
 problem equals a freshly created one bitwise; batched states equal individual runs bitwise;
