@@ -177,6 +177,7 @@ class ClockSampler:
 
 
 TILE_KW = {}  # fine tile shape overrides from the command line (tile_positions, tile_slots, ...)
+AUTOTUNE = {"on": True, "seconds": 0.0}  # run ps_autotune on each single problem before timing it
 
 
 def make_problem(ps, torch, cfg, precision, timing, coarse_mode="fp64", fine_method="fie"):
@@ -190,6 +191,11 @@ def make_problem(ps, torch, cfg, precision, timing, coarse_mode="fp64", fine_met
     prob = ps.Problem(sp, cfg["T"], cfg["N"], cfg["g"], cfg["s"], coarse=spc, precision=precision, timing=timing,
                       coarse_mode=coarse_mode, fine_method=fine_method, **TILE_KW)
     prob._keep = (grid, op, sp, spc, a, src)
+    if AUTOTUNE["on"] and cfg["split"] == "dim" and not any(v not in (0, "auto") for v in TILE_KW.values()):
+        t0 = time.perf_counter()
+        prob.autotune(budget_ms=150)
+        AUTOTUNE["seconds"] += time.perf_counter() - t0
+        prob._tuned = prob.autotune_record()
     return prob
 
 
@@ -518,7 +524,9 @@ def main():
     ap.add_argument("--tile-lines-per-thread", type=int, default=0, help="fine FP32 tiles: lines per thread (0 = auto)")
     ap.add_argument("--coarse-sweep", default="auto", choices=["auto", "staged", "streamed"],
                     help="coarse line solves on one slice: staged through shared memory or streamed")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default schedules (no ps_autotune)")
     args = ap.parse_args()
+    AUTOTUNE["on"] = not args.no_autotune
     TILE_KW.update(tile_positions=args.tile_positions, tile_slots=args.tile_slots,
                    tile_lines_per_thread=args.tile_lines_per_thread, coarse_sweep=args.coarse_sweep)
     if args.warmup < 3:
@@ -563,6 +571,7 @@ def main():
         return run_adjoint(args, cfg, ps, torch, rank, ws)
 
     prob = make_problem(ps, torch, cfg, args.precision, timing=2, coarse_mode=args.coarse, fine_method=args.fine)
+    tuned = getattr(prob, "_tuned", [])
     max_iter = cfg.get("max_iter", 0)
     u0 = torch.as_tensor(cfg["u0"]).cuda()
     stream = torch.cuda.current_stream()
@@ -751,7 +760,11 @@ def main():
                                          if args.precision == "fp64" else None),
                 "config": config_of(args, cfg), "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
                 "roofline": roof, "cpu_baseline": cpu, "time_to_tol": compare, "accuracy": accuracy,
-                "parareal_iterations": iters, "kernels": kernels}
+                "parareal_iterations": iters, "kernels": kernels,
+                "autotune": ({"seconds_all_problems": AUTOTUNE["seconds"],
+                              "chosen": [r[0] for r in tuned if r[2]],
+                              "record_ms": {r[0]: round(r[1], 4) for r in tuned}}
+                             if AUTOTUNE["on"] else None)}
         if "exact" in cfg:
             # the scalability experiment: error of the final iterate against the manufactured solution,
             # measured like Sec. 5 (max over the coarse times of the h-weighted 2-norm)

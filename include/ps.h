@@ -75,12 +75,15 @@ extern "C" {
 #define PS_FINE_FIE 0 /* fractional implicit Euler (eq. FIE_method) */
 #define PS_FINE_DR 1  /* Douglas-Rachford (eq. DR_method) */
 
-/* Line-solve schedule (ps_params.schedule) of the one sweep that offers all three, the coarse
- * x-substep of the FP32 increment form (PS_COARSE_DELTA32; rows of at most 256 nodes for PCR).
- * Every other line solve runs the Thomas/LDL^T recurrences one thread per line (fine tiles,
- * coarse sweeps staged or streamed, PS_COARSE_SWEEP_*).  The three compute the same solution
- * in different orders; they agree to FP32 rounding of the coarse increment. */
-#define PS_SCHED_AUTO 0   /* the hybrid, unless ps_autotune picked another */
+/* Line-solve schedule (ps_params.schedule) of the coarse propagator's x-substep (the sweep
+ * over contiguous rows on one slice; dimensional splitting).  Every other line solve runs the
+ * Thomas/LDL^T recurrences one thread per line (fine tiles, coarse y/z sweeps staged or
+ * streamed, PS_COARSE_SWEEP_*).  The schedules compute the same solution in different orders:
+ * the coarse values change at rounding level (FP32 for the increment form, FP64 otherwise), the
+ * parareal fixed point does not.  PCR is built for the FP32 increment form (rows of at most 256
+ * nodes; PS_ERR_UNSUPPORTED otherwise). */
+#define PS_SCHED_AUTO 0   /* FP32 increment form: the hybrid; FP64 coarse: Thomas; unless ps_autotune
+                             picked another */
 #define PS_SCHED_THOMAS 1 /* Thomas/LDL^T recurrences, one thread per row */
 #define PS_SCHED_PCR 2    /* parallel cyclic reduction, one warp per row (log2 L shuffle/register steps) */
 #define PS_SCHED_HYBRID 3 /* one warp per row: lane segments run sequentially, a log-depth shuffle scan
@@ -187,10 +190,13 @@ typedef struct {
   int tile_lines_per_thread; /* fine line solves (FP32 tiles of 32+ slots): lines a thread solves
                                 side by side, 1 or 2; 0 = auto (1) */
   int fine_method;         /* PS_FINE_FIE (0) or PS_FINE_DR */
-  int serial_phases;       /* 0: with the dimensional splitting, the fine phase of an iteration runs on
+  int overlap_phases;      /* 1: with the dimensional splitting, the fine phase of an iteration runs on
                               a side stream, slot group by slot group, and the coarse chain follows
                               each group as it finishes (the same values, computed concurrently);
-                              1: the fine phase completes before the chain starts */
+                              0 (default): the fine phase completes before the chain starts.
+                              Measured on GB300 at 255^3 x 64 slices, the overlapped order is
+                              slower: the half-range tiles fetch whole 256-byte rows and the chain's
+                              latency-bound sweeps slow down beside the tiles */
   int coarse_sweep;        /* coarse-propagator line solves on one slice (dimensional splitting):
                               PS_COARSE_SWEEP_STAGED or PS_COARSE_SWEEP_STREAMED; 0 = streamed
                               unless ps_autotune picks staged */
@@ -373,15 +379,20 @@ int ps_batch_destroy(ps_batch* b);
 /* Autotuner of the line-solve schedules: times the fine sweeps of this problem with each
  * candidate tile shape (time slices per tile 16/32/64, line positions 1/2, lines per thread
  * 1/2, one tile per CTA or a persistent ring of three shared-memory stages) for about
- * budget_ms and installs the fastest; with the dimensional splitting it also times one coarse
- * step's sweeps staged and streamed (PS_COARSE_SWEEP_*) and installs the faster.  Results do
- * not depend on the schedules (each line's arithmetic is the same).  *choice_out (may be NULL)
- * receives coarse_sweep*100000 + lines_per_thread*10000 + slots*100 + positions*10 + pipelined. */
+ * budget_ms and installs the fastest; with the dimensional splitting it also times the coarse
+ * x-sweep's schedules (PS_SCHED_*) and one coarse step's sweeps staged and streamed
+ * (PS_COARSE_SWEEP_*) and installs the fastest of each.  The tile shapes and the staged/
+ * streamed choice change no result (the same arithmetic per line); the x-sweep schedule
+ * changes the coarse values at rounding level (see PS_SCHED_*), so for a problem that belongs
+ * to a batch with the FP64 coarse propagator only Thomas is considered.  *choice_out (may be
+ * NULL) receives coarse_sweep*100000 + lines_per_thread*10000 + slots*100 + positions*10 +
+ * pipelined; ps_params.schedule of the problem holds the x-sweep's choice. */
 int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out);
 /* The timing record of the last ps_autotune on this problem: one entry per candidate timed,
- * name "fine:<slots>x<positions>/v<lines per thread>/<tile|ring>", "coarse:<staged|streamed>" or
- * "coarse-x32:<thomas|pcr|hybrid>", and its time per candidate run (ms; fine: the sweeps of all
- * directions over all slices; coarse: one coarse step's sweeps; coarse-x32: one x-sweep).
+ * name "fine:<slots>x<positions>/v<lines per thread>/<tile|ring>", "coarse:<staged|streamed>",
+ * "coarse-x32:<thomas|pcr|hybrid>" (increment form) or "coarse-x64:<thomas|hybrid>", and its
+ * time per candidate run (ms; fine: the sweeps of all directions over all slices; coarse: one
+ * coarse step's sweeps; coarse-x*: one x-sweep).
  * chosen = 1 for the installed candidate of each group.  len = number of entries (<= cap). */
 typedef struct {
   char name[48];

@@ -55,7 +55,7 @@ class _Params(C.Structure):
     _fields_ = [("precision", C.c_int), ("schedule", C.c_int), ("timing", C.c_int), ("dd_slices_per_block", C.c_int),
                 ("tile_positions", C.c_int), ("tile_pipeline", C.c_int), ("tile_slots", C.c_int),
                 ("tol_mode", C.c_int), ("coarse", C.c_int), ("tile_lines_per_thread", C.c_int),
-                ("fine_method", C.c_int), ("serial_phases", C.c_int), ("coarse_sweep", C.c_int)]
+                ("fine_method", C.c_int), ("overlap_phases", C.c_int), ("coarse_sweep", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -256,7 +256,7 @@ class Problem:
     def __init__(self, fine: Splitting, T, N, g, s, coarse: Splitting = None, precision="fp64",
                  schedule=PS_SCHED_AUTO, timing=False, dd_slices_per_block=0, tile_positions=0, tile_pipeline=0,
                  tile_slots=0, tol_mode=0, coarse_mode="fp64", tile_lines_per_thread=0, fine_method="fie",
-                 coarse_sweep="auto", serial_phases=False, stream=None):
+                 coarse_sweep="auto", overlap_phases=False, stream=None):
         self.fine, self.coarse = fine, coarse
         self.grid = fine.op.grid
         self.N = int(N)
@@ -268,7 +268,7 @@ class Problem:
                       int(dd_slices_per_block), int(tile_positions), int(tile_pipeline), int(tile_slots),
                       int(tol_mode), PS_COARSE_FP64 if coarse_mode == "fp64" else PS_COARSE_DELTA32,
                       int(tile_lines_per_thread), PS_FINE_FIE if fine_method == "fie" else PS_FINE_DR,
-                      int(bool(serial_phases)), {"auto": 0, "staged": 1, "streamed": 2}[coarse_sweep])
+                      int(bool(overlap_phases)), {"auto": 0, "staged": 1, "streamed": 2}[coarse_sweep])
         h = _VP()
         check(lib().ps_problem_create(fine._h, None if coarse is None else coarse._h, float(T), int(N), int(g),
                                       int(s), C.byref(prm), _stream(stream), C.byref(h)))

@@ -152,6 +152,10 @@ void fie_step_dd(ps_problem* p, Prop& P, int nsl, const double* in, double* out,
 // shape fits (ps_coarse.cu), else the streaming sweeps of ps_dim.cu.
 void coarse_sweep64(ps_problem* p, const LineFactors& f, const double* in, double* out, const SourceArgs& sa,
                     const CorrArgs& corr, cudaStream_t st) {
+  if (f.m == 0 && p->xsched == PS_SCHED_HYBRID && f.lt64.p && corr.mode == 0) {
+    sweep_x_warp<double, double>(p->g, f, in, out, sa, st);
+    return;
+  }
   if (p->coarse_staged && coarse_sweep_staged<double>(p->g, f, in, out, sa, corr, st)) return;
   sweep_dim<double, double>(p->g, 1, f, false, in, out, sa, corr, corr.mode != 0 ? out : nullptr, st);
 }
@@ -634,6 +638,10 @@ void configure_slices(ps_problem* p, int N, int g_steps, int f_steps, cudaStream
     factor_lines(g3, *p->G.dim[0], true, st);  // line-major x factors of the warp x-sweep
     // rows of (I - DeltaT/g A_x) for the PCR schedule of that sweep
     if (p->g.n[0] <= 256) tridiag_x_rows(p->g, p->op->a.p, p->op->c / p->g.dim, p->G.tau, p->pcr_e, p->pcr_d, st);
+  } else if (coarse->kind == PS_SPLIT_DIM) {
+    Geom g3 = p->g;
+    if (g3.dim == 2) g3.n[2] = 1;
+    factor_lines(g3, *p->G.dim[0], false, st);  // line-major FP64 x factors of the hybrid x-sweep
   }
   const long long nt = p->g.nt;
   p->U.alloc((size_t)(N + 1) * nt);
@@ -940,21 +948,24 @@ int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, doub
     if (params) p->prm = *params;
     PS_REQUIRE(p->prm.precision == PS_PREC_FP64 || p->prm.precision == PS_PREC_MIXED, "unknown precision");
     PS_REQUIRE(p->prm.schedule >= PS_SCHED_AUTO && p->prm.schedule <= PS_SCHED_HYBRID, "unknown schedule");
-    p->xsched = p->prm.schedule == PS_SCHED_AUTO ? PS_SCHED_HYBRID : p->prm.schedule;
     PS_REQUIRE(p->prm.coarse == PS_COARSE_FP64 || p->prm.coarse == PS_COARSE_DELTA32, "unknown coarse mode");
     PS_REQUIRE(p->prm.fine_method == PS_FINE_FIE || p->prm.fine_method == PS_FINE_DR, "unknown fine method");
     PS_REQUIRE(p->prm.tol_mode == 0 || p->prm.tol_mode == 1, "tol_mode must be 0 or 1");
     PS_REQUIRE(p->prm.coarse_sweep >= PS_COARSE_SWEEP_AUTO && p->prm.coarse_sweep <= PS_COARSE_SWEEP_STREAMED,
                "unknown coarse sweep schedule");
     p->coarse_staged = p->prm.coarse_sweep == PS_COARSE_SWEEP_STAGED;
-    PS_REQUIRE(p->prm.serial_phases == 0 || p->prm.serial_phases == 1, "serial_phases must be 0 or 1");
-    p->overlap = p->prm.serial_phases == 0;
+    PS_REQUIRE(p->prm.overlap_phases == 0 || p->prm.overlap_phases == 1, "overlap_phases must be 0 or 1");
+    p->overlap = p->prm.overlap_phases == 1;
     p->dr = p->prm.fine_method == PS_FINE_DR;
     if (p->dr && p->prm.precision != PS_PREC_FP64)
       throw Error(PS_ERR_UNSUPPORTED, "the Douglas-Rachford fine propagator runs in FP64");
     if (p->op->src2.p && (fine->kind != PS_SPLIT_DD || coarse->kind != PS_SPLIT_DD))
       throw Error(PS_ERR_UNSUPPORTED, "a second source term is implemented with the DD splitting");
     p->delta32 = p->prm.coarse == PS_COARSE_DELTA32;
+    p->xsched = p->prm.schedule != PS_SCHED_AUTO ? p->prm.schedule
+                                                 : (p->delta32 ? PS_SCHED_HYBRID : PS_SCHED_THOMAS);
+    if (p->xsched == PS_SCHED_PCR && !p->delta32)
+      throw Error(PS_ERR_UNSUPPORTED, "the PCR schedule is built for the FP32 coarse increment form's x-sweep");
     if (p->delta32 && (fine->kind != PS_SPLIT_DIM || coarse->kind != PS_SPLIT_DIM))
       throw Error(PS_ERR_UNSUPPORTED, "the FP32 coarse increment form needs the dimensional splitting");
     cudaStream_t st = S(stream);
@@ -1343,16 +1354,25 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
         PS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         return ms / 4.f;
       };
-      // the FP32 increment form's x-sweep: Thomas per row, PCR per warp, hybrid per warp
-      if (p->delta32) {
+      // the coarse x-sweep's schedule: Thomas per row, PCR per warp (FP32 increment form) or the
+      // hybrid segmented scans per warp.  In a batch, whose grouped kernels run Thomas, only Thomas
+      // keeps the batched results bitwise equal to the problem's own runs.
+      {
         const char* names[4] = {"", "thomas", "pcr", "hybrid"};
+        const std::string pre = p->delta32 ? "coarse-x32:" : "coarse-x64:";
         float xbest = 1e30f;
         int xchoice = p->xsched;
         for (int sc = PS_SCHED_THOMAS; sc <= PS_SCHED_HYBRID; ++sc) {
-          if (sc == PS_SCHED_PCR && !p->pcr_e.p) continue;  // rows longer than 256 nodes
+          if (sc == PS_SCHED_PCR && (!p->delta32 || !p->pcr_e.p)) continue;  // FP32 rows of <= 256 nodes
+          if (sc != PS_SCHED_THOMAS && p->batched > 0 && !p->delta32) continue;
+          if (sc == PS_SCHED_HYBRID && !p->delta32 && !p->G.dim[0]->lt64.p) continue;
           p->xsched = sc;
-          const float ms = time4([&] { coarse_x32<float>(p, p->g32.p, p->g32.p, SourceArgs{}, st); });
-          p->tune_log.push_back({std::string("coarse-x32:") + names[sc], ms, 0});
+          const float ms = p->delta32
+                               ? time4([&] { coarse_x32<float>(p, p->g32.p, p->g32.p, SourceArgs{}, st); })
+                               : time4([&] {
+                                   coarse_sweep64(p, *p->G.dim[0], p->U.p, p->gtmp.p, SourceArgs{}, CorrArgs{}, st);
+                                 });
+          p->tune_log.push_back({pre + names[sc], ms, 0});
           if (ms < xbest) {
             xbest = ms;
             xchoice = sc;
@@ -1361,7 +1381,7 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
         p->xsched = xchoice;
         p->prm.schedule = xchoice;
         for (auto& e : p->tune_log)
-          if (e.name == std::string("coarse-x32:") + names[xchoice]) e.chosen = 1;
+          if (e.name == pre + names[xchoice]) e.chosen = 1;
       }
       float tbest = 1e30f;
       const bool saved = p->coarse_staged;
@@ -1445,6 +1465,8 @@ int ps_problem_update_coefficients(ps_problem* p, const double* a_nodal_dev, uin
           else if (p->delta32 && m == 0) {
             factor_lines(g3, *P->dim[m], true, st);
             if (p->g.n[0] <= 256) tridiag_x_rows(p->g, op->a.p, op->c / p->g.dim, P->tau, p->pcr_e, p->pcr_d, st);
+          } else if (m == 0) {
+            factor_lines(g3, *P->dim[m], false, st);
           }
         }
       } else {

@@ -183,53 +183,54 @@ __global__ void __launch_bounds__(kThreads) sweep_x_kernel(const Tin* in, Tout* 
 // The dependent chain is 3m + 10 operations per recurrence instead of L.  The row and its
 // factor rows are staged in shared memory with element i at i + i/m (m even), so the
 // segment reads of the 32 lanes fall in distinct banks.
-__device__ __forceinline__ void warp_line_solve_skewed(float* xb, const float* lb, const float* rb, int L, int m,
+template <typename T>
+__device__ __forceinline__ void warp_line_solve_skewed(T* xb, const T* lb, const T* rb, int L, int m,
                                                        int lane) {
   const unsigned full = 0xffffffffu;
   const int base = lane * (m + 1);
   const int cnt = max(0, min(m, L - lane * m));
-  float A = 1.f, B = 0.f;
+  T A = T(1), B = T(0);
   for (int u = 0; u < cnt; ++u) {
-    const float l = lb[base + u];
+    const T l = lb[base + u];
     B = xb[base + u] - l * B;
     A = -l * A;
   }
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    const float Ap = __shfl_up_sync(full, A, d), Bp = __shfl_up_sync(full, B, d);
+    const T Ap = __shfl_up_sync(full, A, d), Bp = __shfl_up_sync(full, B, d);
     if (lane >= d) {
       B = A * Bp + B;
       A = A * Ap;
     }
   }
-  float y = __shfl_up_sync(full, B, 1);
-  if (lane == 0) y = 0.f;
+  T y = __shfl_up_sync(full, B, 1);
+  if (lane == 0) y = T(0);
   for (int u = 0; u < cnt; ++u) {
     y = xb[base + u] - lb[base + u] * y;
     xb[base + u] = y;
   }
   __syncwarp();
   // l_{i+1} past the segment's end: the next segment's first factor (0 past the line)
-  const float lnext = (lane * m + cnt < L) ? lb[base + m + 1] : 0.f;
-  A = 1.f;
-  B = 0.f;
+  const T lnext = (lane * m + cnt < L) ? lb[base + m + 1] : T(0);
+  A = T(1);
+  B = T(0);
   for (int u = cnt - 1; u >= 0; --u) {
-    const float ln = (u + 1 < cnt) ? lb[base + u + 1] : lnext;
+    const T ln = (u + 1 < cnt) ? lb[base + u + 1] : lnext;
     B = rb[base + u] * xb[base + u] - ln * B;
     A = -ln * A;
   }
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    const float An = __shfl_down_sync(full, A, d), Bn = __shfl_down_sync(full, B, d);
+    const T An = __shfl_down_sync(full, A, d), Bn = __shfl_down_sync(full, B, d);
     if (lane + d < 32) {
       B = A * Bn + B;
       A = A * An;
     }
   }
-  float xv = __shfl_down_sync(full, B, 1);
-  if (lane == 31) xv = 0.f;
+  T xv = __shfl_down_sync(full, B, 1);
+  if (lane == 31) xv = T(0);
   for (int u = cnt - 1; u >= 0; --u) {
-    const float ln = (u + 1 < cnt) ? lb[base + u + 1] : lnext;
+    const T ln = (u + 1 < cnt) ? lb[base + u + 1] : lnext;
     xv = rb[base + u] * xb[base + u] - ln * xv;
     xb[base + u] = xv;
   }
@@ -238,31 +239,36 @@ __device__ __forceinline__ void warp_line_solve_skewed(float* xb, const float* l
 
 // One slice: rows of nx nodes, line-major factor rows lt/rt (pitch Lp).  SRC adds
 // tau * src * src_t[t0] to the right-hand side on the way in.
-template <typename Tin, bool SRC>
-__global__ void __launch_bounds__(256) sweep_x_warp_kernel(const Tin* __restrict__ in, float* __restrict__ out,
+template <typename T, typename Tin, bool SRC>
+__global__ void __launch_bounds__(256) sweep_x_warp_kernel(const Tin* __restrict__ in, T* __restrict__ out,
                                                            long long rows, int nx, int m, int span,
-                                                           const float* __restrict__ lt, const float* __restrict__ rt,
+                                                           const T* __restrict__ lt, const T* __restrict__ rt,
                                                            int Lp, SourceArgs sa) {
-  extern __shared__ float wsm[];
+  extern __shared__ __align__(16) unsigned char wsm_raw[];
+  T* wsm = reinterpret_cast<T*>(wsm_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  float* xb = wsm + (size_t)warp * 3 * span;
-  float* lb = xb + span;
-  float* rb = lb + span;
+  T* xb = wsm + (size_t)warp * 3 * span;
+  T* lb = xb + span;
+  T* rb = lb + span;
   const double c = SRC ? sa.tau * (sa.src_t ? sa.src_t[sa.t0] : 1.0) : 0.0;
   for (long long row = (long long)blockIdx.x * nw + warp; row < rows; row += (long long)gridDim.x * nw) {
     const Tin* gin = in + row * nx;
-    const float* gl = lt + row * Lp;
-    const float* gr = rt + row * Lp;
+    const T* gl = lt + row * Lp;
+    const T* gr = rt + row * Lp;
     for (int i = lane; i < nx; i += 32) {
       const int k = i + i / m;
-      float b = (float)gin[i];
-      if (SRC) b = b + (float)(c * sa.src[row * nx + i]);
+      T b = (T)gin[i];
+      if constexpr (sizeof(T) == 8) {
+        if (SRC) b = fma(c, sa.src[row * nx + i], (double)b);
+      } else {
+        if (SRC) b = b + (float)(c * sa.src[row * nx + i]);
+      }
       xb[k] = b;
       lb[k] = gl[i];
       rb[k] = gr[i];
     }
     // one slot past the line: the backward step reads the next segment's first factor there
-    if (lane == 0) lb[nx + nx / m] = 0.f;
+    if (lane == 0) lb[nx + nx / m] = T(0);
     __syncwarp();
     warp_line_solve_skewed(xb, lb, rb, nx, m, lane);
     for (int i = lane; i < nx; i += 32) out[row * nx + i] = xb[i + i / m];
@@ -696,17 +702,18 @@ template void sweep_dim<float, float>(const Geom&, int, const LineFactors&, bool
 template void sweep_dim<float, double>(const Geom&, int, const LineFactors&, bool, const float*, double*,
                                        const SourceArgs&, const CorrArgs&, double*, cudaStream_t);
 
-template <typename Tin>
-void sweep_x_warp(const Geom& g, const LineFactors& f, const Tin* in, float* out, const SourceArgs& sa,
-                  cudaStream_t st) {
-  PS_REQUIRE(f.m == 0 && f.lt32.p && f.rt32.p, "the warp x-sweep needs FP32 line-major x factors");
+template <typename Tin, typename T>
+void sweep_x_warp(const Geom& g, const LineFactors& f, const Tin* in, T* out, const SourceArgs& sa, cudaStream_t st) {
+  const T* lt = sizeof(T) == 4 ? reinterpret_cast<const T*>(f.lt32.p) : reinterpret_cast<const T*>(f.lt64.p);
+  const T* rt = sizeof(T) == 4 ? reinterpret_cast<const T*>(f.rt32.p) : reinterpret_cast<const T*>(f.rt64.p);
+  PS_REQUIRE(f.m == 0 && lt && rt, "the warp x-sweep needs line-major x factors of its precision");
   const int nx = g.n[0];
   const long long rows = g.nt / nx;
   const int m = ((nx + 31) / 32 + 1) & ~1;  // even: the skewed pitch m + 1 is odd
   const int span = nx + nx / m + 2;
   const int Lp = (nx + 3) & ~3;
   const int threads = 256;
-  const size_t smem = (size_t)(threads / 32) * 3 * span * sizeof(float);
+  const size_t smem = (size_t)(threads / 32) * 3 * span * sizeof(T);
   PS_REQUIRE(smem <= (size_t)max_dyn_smem(), "x-line too long for the warp x-sweep");
   int dev = 0, sms = 0;
   PS_CUDA(cudaGetDevice(&dev));
@@ -715,16 +722,18 @@ void sweep_x_warp(const Geom& g, const LineFactors& f, const Tin* in, float* out
   const unsigned grid = (unsigned)std::min<long long>(want, (long long)sms * 8);
   auto launch = [&](auto kern) {
     PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, threads, smem, st>>>(in, out, rows, nx, m, span, f.lt32.p, f.rt32.p, Lp, sa);
+    kern<<<grid, threads, smem, st>>>(in, out, rows, nx, m, span, lt, rt, Lp, sa);
   };
-  if (sa.src) launch(sweep_x_warp_kernel<Tin, true>);
-  else launch(sweep_x_warp_kernel<Tin, false>);
+  if (sa.src) launch(sweep_x_warp_kernel<T, Tin, true>);
+  else launch(sweep_x_warp_kernel<T, Tin, false>);
   PS_CUDA(cudaGetLastError());
 }
-template void sweep_x_warp<float>(const Geom&, const LineFactors&, const float*, float*, const SourceArgs&,
-                                  cudaStream_t);
-template void sweep_x_warp<double>(const Geom&, const LineFactors&, const double*, float*, const SourceArgs&,
-                                   cudaStream_t);
+template void sweep_x_warp<float, float>(const Geom&, const LineFactors&, const float*, float*, const SourceArgs&,
+                                         cudaStream_t);
+template void sweep_x_warp<double, float>(const Geom&, const LineFactors&, const double*, float*, const SourceArgs&,
+                                          cudaStream_t);
+template void sweep_x_warp<double, double>(const Geom&, const LineFactors&, const double*, double*,
+                                           const SourceArgs&, cudaStream_t);
 
 int max_dyn_smem_public() { return max_dyn_smem(); }
 

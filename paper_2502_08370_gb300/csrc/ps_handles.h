@@ -170,7 +170,7 @@ struct ps_problem {
   cudaStream_t side = nullptr;
   std::vector<cudaEvent_t> ev_pack, ev_done;
   cudaEvent_t ev_fine[2] = {nullptr, nullptr};
-  bool overlap = true;  // run the fine phase beside the chain when it spans several slot groups
+  bool overlap = false;  // run the fine phase beside the chain when it spans several slot groups
   ps::KernelTimer kt;
   ~ps_problem() {
     if (h_sstats) cudaFreeHost(h_sstats);

@@ -152,8 +152,9 @@ void sweep_dim(const Geom& g, int nslices, const LineFactors& f, bool fp32, cons
                const SourceArgs& srcargs, const CorrArgs& corr, double* tmp, cudaStream_t st);
 // Coarse x-substep in FP32 on one slice, one warp per row (segmented scans of the two
 // recurrences); needs the line-major FP32 factors of direction x (factor_lines).
-template <typename Tin>
-void sweep_x_warp(const Geom& g, const LineFactors& f, const Tin* in, float* out, const SourceArgs& sa,
+// T = double: the same segmented scans in FP64 (line-major FP64 x factors, factor_lines).
+template <typename Tin, typename T = float>
+void sweep_x_warp(const Geom& g, const LineFactors& f, const Tin* in, T* out, const SourceArgs& sa,
                   cudaStream_t st);
 // Coarse-propagator sweep of direction f.m on ONE slice, staged through shared memory
 // (ps_coarse.cu); in may alias out.  T = double: x, y, z (x carries the source, y/z the

@@ -660,6 +660,17 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
   }
   PS_REQUIRE((tp.TS * elem) % 128 == 0, "tile rows must be a multiple of 128 bytes");
   tp.pipe = pipe < 0 ? 1 : pipe;
+  {
+    // long lines: fewer slots per tile (down to 128-byte rows) until one tile fits in shared memory
+    int dev = 0, maxsm = 0;
+    PS_CUDA(cudaGetDevice(&dev));
+    PS_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int Lp4 = (L + 3) & ~3;
+    const int st = tp.pipe ? kPipeStages : 1;
+    while (tp.TS * elem > 128 && S_pad % (tp.TS / 2) == 0 &&
+           (size_t)st * ((size_t)tp.TS * L * elem + 3 * (size_t)Lp4 * elem + 64) + 512 > (size_t)maxsm)
+      tp.TS /= 2;
+  }
   const int stages = tp.pipe ? kPipeStages : 1;
   // per CTA, so that 2 (ring of stages) or 2-3 (one tile) CTAs share an SM
   const size_t budget = tp.pipe ? 110 * 1024 : 96 * 1024;

@@ -74,17 +74,40 @@ def test_small_batch_equals_individual_runs_bitwise(ps):
 
 
 def test_autotune_changes_no_result(ps):
+    """In a batch (FP64 coarse propagator) the autotuner only weighs schedules with the same
+    arithmetic per line: the tile shapes, staged or streamed coarse sweeps, Thomas for the coarse
+    x-sweep.  The problem's results stay bitwise the same."""
     c = wl.batch256(count=1, seed=11, sizes=(127,), slices=(32,), s_range=(16, 16))[0]
     p = make(ps, c)
     u0 = dev(c["u0"])
     p.run(u0, 1e-8)
     before = snapshot(p)
+    batch = ps.Batch([p])
     choice = p.autotune(budget_ms=50)
     assert choice > 0
+    assert all(not r[0].startswith("coarse-x64:") or r[0].endswith("thomas") for r in p.autotune_record())
     p.run(u0, 1e-8)
     after = snapshot(p)
     for a, b in zip(before, after):
         assert np.array_equal(a, b)
+    del batch
+
+
+def test_autotune_outside_a_batch_may_change_roundings_only(ps):
+    """Alone, the FP64 coarse x-sweep may take the hybrid schedule: the coarse values change at
+    FP64 rounding, the converged states stay within the tolerance of the same fixed point."""
+    c = wl.batch256(count=1, seed=12, sizes=(255,), slices=(16,), s_range=(16, 16))[0]
+    p = make(ps, c)
+    u0 = dev(c["u0"])
+    it = p.run(u0, 1e-10)
+    before = snapshot(p)
+    p.autotune(budget_ms=50)
+    names = [r[0] for r in p.autotune_record()]
+    assert {"coarse-x64:thomas", "coarse-x64:hybrid"} <= set(names)
+    assert p.run(u0, 1e-10) == it
+    after = snapshot(p)
+    for a, b in zip(before, after):
+        assert np.abs(a - b).max() <= 1e-8 * np.abs(b).max()
 
 
 def test_batch256_sampled_against_individual_runs(ps):

@@ -373,11 +373,11 @@ def test_fine_phase_beside_chain_is_bitwise_serial(ps, prec, coarse, N):
     src = rng.standard_normal(n[::-1])
     u0 = dev(rng.standard_normal(n[::-1]))
     res = []
-    for serial in (False, True):
+    for overlap in (True, False):
         grid = ps.Grid(n)
         op = ps.Operator(grid, a=dev(a), src=dev(src))
         sp = ps.Splitting(op)
-        prob = ps.Problem(sp, 0.5, N, 1, 4, precision=prec, coarse_mode=coarse, serial_phases=serial)
+        prob = ps.Problem(sp, 0.5, N, 1, 4, precision=prec, coarse_mode=coarse, overlap_phases=overlap)
         out = []
         for tol, mi in ((1e-9, 0), (0.0, 5)):
             it = prob.run(u0, tol, mi)
