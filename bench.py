@@ -180,7 +180,7 @@ TILE_KW = {}  # fine tile shape overrides from the command line (tile_positions,
 AUTOTUNE = {"on": True, "seconds": 0.0}  # run ps_autotune on each single problem before timing it
 
 
-def make_problem(ps, torch, cfg, precision, timing, coarse_mode="fp64", fine_method="fie"):
+def make_problem(ps, torch, cfg, precision, timing, coarse_mode="fp64", fine_method="fie", tune=True):
     grid = ps.Grid(cfg["n"])
     a = None if cfg["a"] is None else torch.as_tensor(cfg["a"]).cuda()
     src = None if cfg["src"] is None else torch.as_tensor(cfg["src"]).cuda()
@@ -191,7 +191,7 @@ def make_problem(ps, torch, cfg, precision, timing, coarse_mode="fp64", fine_met
     prob = ps.Problem(sp, cfg["T"], cfg["N"], cfg["g"], cfg["s"], coarse=spc, precision=precision, timing=timing,
                       coarse_mode=coarse_mode, fine_method=fine_method, **TILE_KW)
     prob._keep = (grid, op, sp, spc, a, src)
-    if AUTOTUNE["on"] and cfg["split"] == "dim" and not any(v not in (0, "auto") for v in TILE_KW.values()):
+    if tune and AUTOTUNE["on"] and cfg["split"] == "dim" and not any(v not in (0, "auto") for v in TILE_KW.values()):
         t0 = time.perf_counter()
         prob.autotune(budget_ms=150)
         AUTOTUNE["seconds"] += time.perf_counter() - t0
@@ -285,6 +285,7 @@ def config_of(args, cfg):
         tot = sum(int(np.prod(c["n"])) * (2 * c["N"] + 1) * 8 for c in b)
         return {"workload": args.workload, "problems": len(b), "grids": "nx, ny from {63,127,255,511}",
                 "N_slices": "{8,16,32,64}", "fine_steps": "16..128", "tol": cfg["tol"], "precision": "mixed",
+                "coarse": getattr(args, "coarse", "fp64"),
                 "l2": f"inputs larger than L2 ({tot / 1e9:.1f} GB of slice states)"}
     grid = "x".join(str(v) for v in cfg["n"])
     nt = int(np.prod(cfg["n"]))
@@ -321,7 +322,8 @@ def finish_line(args, cfg, value, ms_per_step, launches, extra, rank, ws, e2e=No
 def run_batch(args, cfg, ps, torch, rank, ws):
     """256 independent problems: batched (grouped launches + graph) vs one at a time."""
     cfgs = cfg["batch"]
-    probs = [make_problem(ps, torch, c, "mixed", timing=0) for c in cfgs]
+    # the batch's own autotuner (after creation) keeps each problem on the batch's schedules
+    probs = [make_problem(ps, torch, c, "mixed", timing=0, coarse_mode=args.coarse, tune=False) for c in cfgs]
     u0s = [torch.as_tensor(c["u0"]).cuda() for c in cfgs]
     batch = ps.Batch(probs)
     t0 = time.perf_counter()

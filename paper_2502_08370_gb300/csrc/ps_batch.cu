@@ -32,6 +32,10 @@ struct ps_batch {
   int count = 0;
   int maxS = 0, maxN = 0;
   bool var = true;
+  bool delta32 = false;             // the problems' coarse propagator: FP32 increment form
+  DevBuf<XWarpJob> xjobs32;         // [maxN][count] x-sweeps of the increment form
+  std::vector<XWarpJob> h_xjobs32;
+  int span_max = 0;
   // device tables
   DevBuf<unsigned char> tile_jobs;  // [2][count] TileJob
   DevBuf<WorkSeg> tile_segs;        // [2][count]
@@ -120,6 +124,15 @@ CoarseJob coarse_job(ps_batch* b, int i, int n) {
   j.ca.inc = b->inc.p + i;
   j.ca.nonfinite = b->flag.p + i;
   j.ca.slice_stats = nullptr;
+  if (p->op->src.p) {
+    // as the problem's own coarse step n: the source at the step's end time, step DeltaT
+    j.sa.src = p->op->src.p;
+    j.sa.src_t = p->op->src_t.p;
+    j.sa.t0 = n * p->fs + p->fs;
+    j.sa.tstride = 0;
+    j.sa.src_t_len = p->op->src_t_len;
+    j.sa.tau = p->G.tau;
+  }
   return j;
 }
 
@@ -142,7 +155,39 @@ void fill_coarse_tables(ps_batch* b, const std::vector<int>& active, int k) {
         ps_problem* p = b->probs[i];
         if (p->N <= n) break;
         b->h_cjobs[(size_t)n * P + cnt] = coarse_job(b, i, n);
-        const int bx = (p->g.n[1] + x_rows_per_block(p->g.n[0]) - 1) / x_rows_per_block(p->g.n[0]);
+        int bx = (p->g.n[1] + x_rows_per_block(p->g.n[0]) - 1) / x_rows_per_block(p->g.n[0]);
+        if (b->delta32) {
+          // the increment form, as the problem's own run_G32: x by warp rows (eight per item)
+          // from U_n with the source (initial sweep) or from the FP32 increment, y in place on
+          // g32 with the initial (mode 2) or increment (mode 3) epilogue
+          const long long nt = p->g.nt;
+          const int nx = p->g.n[0];
+          XWarpJob xj{};
+          xj.in64 = k == 0 ? p->U.p + n * nt : nullptr;
+          xj.in32 = k == 0 ? nullptr : p->d32.p;
+          xj.out = p->g32.p;
+          xj.rows = p->g.n[1];
+          xj.nx = nx;
+          xj.m = ((nx + 31) / 32 + 1) & ~1;
+          xj.span = nx + nx / xj.m + 2;
+          xj.Lp = (nx + 3) & ~3;
+          xj.lt = p->G.dim[0]->lt32.p;
+          xj.rt = p->G.dim[0]->rt32.p;
+          if (k == 0 && p->op->src.p) xj.sa = b->h_cjobs[(size_t)n * P + cnt].sa;
+          b->h_xjobs32[(size_t)n * P + cnt] = xj;
+          bx = (int)((xj.rows + 7) / 8);
+          CoarseJob& cj = b->h_cjobs[(size_t)n * P + cnt];
+          cj.g32 = p->g32.p;
+          cj.ly32 = p->G.dim[1]->l32.p;
+          cj.ry32 = p->G.dim[1]->r32.p;
+          cj.ca.Gold = nullptr;
+          if (k == 0) {
+            cj.ca.mode = 2;
+          } else {
+            cj.ca.mode = 3;
+            cj.ca.dnext = p->d32.p;
+          }
+        }
         const int by = (p->g.n[0] + 255) / 256;
         b->h_xsegs[(size_t)n * P + cnt] = WorkSeg{cnt, 0, bx, px};  // job index within step n
         b->h_ysegs[(size_t)n * P + cnt] = WorkSeg{cnt, 0, by, py};
@@ -169,8 +214,16 @@ void fill_iteration_tables(ps_batch* b, const std::vector<int>& active, int k) {
       const int nsl = p->N - (k - 1);
       Geom g3 = p->g;
       g3.n[2] = 1;
+      SourceArgs sa;
+      if (p->op->src.p && m == 0) {
+        sa.src = p->op->src.p;
+        sa.src_t = p->op->src_t.p;
+        sa.tstride = p->fs;
+        sa.src_t_len = p->op->src_t_len;
+        sa.tau = p->F.tau;
+      }
       const long long tiles = tile_job_fill(g3, p->F.tiles[m], *p->F.dim[m], p->S_pad, k - 1, nsl, b->tmo.p,
-                                            b->h_tile_jobs.data() + ((size_t)m * P + r) * jb);
+                                            b->h_tile_jobs.data() + ((size_t)m * P + r) * jb, sa, p->srcrow32.p);
       b->h_tile_segs[(size_t)m * P + r] = WorkSeg{(int)r, 0, (int)tiles, prefix};  // job index within axis m
       prefix += (int)tiles;
     }
@@ -199,6 +252,7 @@ void fill_iteration_tables(ps_batch* b, const std::vector<int>& active, int k) {
     cj.nt = nt;
     cj.ca.inc = b->inc.p + active[r];
     cj.ca.nonfinite = b->flag.p + active[r];
+    cj.ca.dnext = b->delta32 ? p->d32.p : nullptr;
     b->h_copy[r] = cj;
     const int cb = (int)((nt + 255) / 256);
     b->h_copy_segs[r] = WorkSeg{(int)r, 0, cb, cp};
@@ -221,6 +275,7 @@ void upload_tables(ps_batch* b, cudaStream_t st) {
   upload(b->copy_jobs, b->h_copy, st);
   upload(b->copy_segs, b->h_copy_segs, st);
   upload(b->cjobs, b->h_cjobs, st);
+  if (b->delta32) upload(b->xjobs32, b->h_xjobs32, st);
   upload(b->xsegs, b->h_xsegs, st);
   upload(b->ysegs, b->h_ysegs, st);
   upload(b->nseg_misc, b->h_nseg_misc, st);
@@ -237,7 +292,7 @@ int enqueue_sequence(ps_batch* b, int mode, cudaStream_t st) {
     for (int j = 0; j < b->maxS; ++j)
       for (int m = 0; m < 2; ++m) {
         tile_sweep_grouped(b->tile_jobs.p + (size_t)m * P * tile_job_bytes(), b->tile_segs.p + (size_t)m * P,
-                           b->tile_nseg.p + (size_t)j * 2 + m, grid, b->tile_threads, b->tile_smem, b->tmo.p, st);
+                           b->tile_nseg.p + (size_t)j * 2 + m, grid, b->tile_threads, b->tile_smem, b->tmo.p, j, st);
         ++n_launch;
       }
     pack_grouped(false, b->unpack_jobs.p, b->unpack_segs.p, b->nseg_misc.p + 1, grid, st);
@@ -245,6 +300,14 @@ int enqueue_sequence(ps_batch* b, int mode, cudaStream_t st) {
     n_launch += 2;
   }
   for (int n = 0; n < b->maxN; ++n) {
+    if (b->delta32) {
+      coarse_x32_grouped(b->xjobs32.p + (size_t)n * P, b->xsegs.p + (size_t)n * P, b->nseg_misc.p + 3 + n, grid,
+                         b->span_max, st);
+      coarse_y32_grouped(b->var, mode == 2 ? 2 : 3, b->cjobs.p + (size_t)n * P, b->ysegs.p + (size_t)n * P,
+                         b->nseg_misc.p + 3 + n, grid, st);
+      n_launch += 2;
+      continue;
+    }
     coarse_x_grouped(b->var, b->cjobs.p + (size_t)n * P, b->xsegs.p + (size_t)n * P, b->nseg_misc.p + 3 + n, grid,
                      b->x_smem, st);
     coarse_y_grouped(b->var, mode, b->cjobs.p + (size_t)n * P, b->ysegs.p + (size_t)n * P, b->nseg_misc.p + 3 + n,
@@ -283,12 +346,16 @@ void batch_check(const ps_batch* b, const ps_problem* p) {
   if (p->prm.precision != PS_PREC_MIXED)
     throw Error(PS_ERR_UNSUPPORTED, "batches run the FP32 line-solve form (PS_PREC_MIXED)");
   if (p->gs != 1) throw Error(PS_ERR_UNSUPPORTED, "batches use one coarse step per slice");
-  if (p->delta32) throw Error(PS_ERR_UNSUPPORTED, "batches run the FP64 coarse propagator");
+  if (p->delta32 && p->g.n[0] > 1024) throw Error(PS_ERR_UNSUPPORTED, "increment-form batches take rows of <= 1024 nodes");
+  // the grouped coarse x-sweep runs the hybrid (increment form) or Thomas (FP64 coarse)
+  if (p->xsched != (p->delta32 ? PS_SCHED_HYBRID : PS_SCHED_THOMAS))
+    throw Error(PS_ERR_UNSUPPORTED, "batches run the coarse x-sweep with the default schedule of the coarse form");
   if (p->dr) throw Error(PS_ERR_UNSUPPORTED, "batches run the FIE fine propagator");
-  if (p->op->src.p) throw Error(PS_ERR_UNSUPPORTED, "batches hold problems without a source term");
   const bool var = p->op->a.p != nullptr;
-  if (!b->probs.empty())
+  if (!b->probs.empty()) {
     PS_REQUIRE(var == (b->probs[0]->op->a.p != nullptr), "all problems of a batch need a nodal coefficient, or none");
+    PS_REQUIRE(p->delta32 == b->probs[0]->delta32, "all problems of a batch need the same coarse propagator form");
+  }
   for (const ps_problem* q : b->probs) PS_REQUIRE(q != p, "a problem appears twice in the batch");
 }
 
@@ -300,11 +367,17 @@ void batch_layout(ps_batch* b) {
   b->tile_smem = b->x_smem = 0;
   b->tile_threads = 0;
   b->var = P > 0 ? b->probs[0]->op->a.p != nullptr : true;
+  b->delta32 = P > 0 && b->probs[0]->delta32;
+  b->span_max = 0;
+  for (ps_problem* p : b->probs) {
+    const int nx = p->g.n[0], m = ((nx + 31) / 32 + 1) & ~1;
+    b->span_max = std::max(b->span_max, nx + nx / m + 2);
+  }
   for (ps_problem* p : b->probs) {
     b->maxS = std::max(b->maxS, p->fs);
     b->maxN = std::max(b->maxN, p->N);
-    b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[0]));
-    b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[1]));
+    b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[0], p->op->src.p != nullptr));
+    b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[1], false));
     // the grouped kernel runs one line per thread, whatever the plan's own split
     b->tile_threads = std::max(b->tile_threads, std::max(p->F.tiles[0].TS * p->F.tiles[0].P,
                                                          p->F.tiles[1].TS * p->F.tiles[1].P));
@@ -332,6 +405,8 @@ void batch_layout(ps_batch* b) {
   b->copy_jobs.alloc(Pz);
   b->copy_segs.alloc(Pz);
   b->cjobs.alloc((size_t)std::max(b->maxN, 1) * Pz);
+  if (b->delta32) b->xjobs32.alloc((size_t)std::max(b->maxN, 1) * Pz);
+  else b->xjobs32.reset();
   b->xsegs.alloc((size_t)std::max(b->maxN, 1) * Pz);
   b->ysegs.alloc((size_t)std::max(b->maxN, 1) * Pz);
   b->nseg_misc.alloc((size_t)3 + b->maxN);
@@ -349,6 +424,7 @@ void batch_layout(ps_batch* b) {
   b->h_copy.assign(P, CoarseJob{});
   b->h_copy_segs.assign(P, WorkSeg{});
   b->h_cjobs.assign((size_t)b->maxN * P, CoarseJob{});
+  b->h_xjobs32.assign(b->delta32 ? (size_t)b->maxN * P : 0, XWarpJob{});
   b->h_xsegs.assign((size_t)b->maxN * P, WorkSeg{});
   b->h_ysegs.assign((size_t)b->maxN * P, WorkSeg{});
   b->h_nseg_misc.assign((size_t)3 + b->maxN, 0);
@@ -438,7 +514,7 @@ int ps_batch_run(ps_batch* b, const double* const* u0_devs, double tol, int max_
     b->tile_smem = 0;
     b->tile_threads = 0;
     for (ps_problem* p : b->probs) {
-      b->tile_smem = std::max(b->tile_smem, std::max(tile_grouped_smem(p->F.tiles[0]), tile_grouped_smem(p->F.tiles[1])));
+      b->tile_smem = std::max(b->tile_smem, std::max(tile_grouped_smem(p->F.tiles[0], p->op->src.p != nullptr), tile_grouped_smem(p->F.tiles[1], false)));
       // the grouped kernel runs one line per thread, whatever the plan's own split
       b->tile_threads = std::max(b->tile_threads, std::max(p->F.tiles[0].TS * p->F.tiles[0].P,
                                                            p->F.tiles[1].TS * p->F.tiles[1].P));

@@ -1364,7 +1364,8 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
         int xchoice = p->xsched;
         for (int sc = PS_SCHED_THOMAS; sc <= PS_SCHED_HYBRID; ++sc) {
           if (sc == PS_SCHED_PCR && (!p->delta32 || !p->pcr_e.p)) continue;  // FP32 rows of <= 256 nodes
-          if (sc != PS_SCHED_THOMAS && p->batched > 0 && !p->delta32) continue;
+          // a batch's grouped kernels run Thomas (FP64 coarse) or the hybrid (increment form)
+          if (p->batched > 0 && sc != (p->delta32 ? PS_SCHED_HYBRID : PS_SCHED_THOMAS)) continue;
           if (sc == PS_SCHED_HYBRID && !p->delta32 && !p->G.dim[0]->lt64.p) continue;
           p->xsched = sc;
           const float ms = p->delta32

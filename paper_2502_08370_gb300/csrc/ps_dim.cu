@@ -239,6 +239,36 @@ __device__ __forceinline__ void warp_line_solve_skewed(T* xb, const T* lb, const
 
 // One slice: rows of nx nodes, line-major factor rows lt/rt (pitch Lp).  SRC adds
 // tau * src * src_t[t0] to the right-hand side on the way in.
+// One row by one warp: stage the row (plus tau f when SRC) and its line-major factor rows in
+// the warp's shared memory with the skewed pitch, solve, write back.
+template <typename T, typename Tin, bool SRC>
+__device__ __forceinline__ void warp_row(long long row, const Tin* __restrict__ in, T* __restrict__ out, int nx, int m,
+                                         const T* __restrict__ lt, const T* __restrict__ rt, int Lp,
+                                         const SourceArgs& sa, T* xb, T* lb, T* rb, int lane) {
+  const double c = SRC ? sa.tau * (sa.src_t ? sa.src_t[sa.t0] : 1.0) : 0.0;
+  const Tin* gin = in + row * nx;
+  const T* gl = lt + row * Lp;
+  const T* gr = rt + row * Lp;
+  for (int i = lane; i < nx; i += 32) {
+    const int k = i + i / m;
+    T b = (T)gin[i];
+    if constexpr (sizeof(T) == 8) {
+      if (SRC) b = fma(c, sa.src[row * nx + i], (double)b);
+    } else {
+      if (SRC) b = b + (float)(c * sa.src[row * nx + i]);
+    }
+    xb[k] = b;
+    lb[k] = gl[i];
+    rb[k] = gr[i];
+  }
+  // one slot past the line: the backward step reads the next segment's first factor there
+  if (lane == 0) lb[nx + nx / m] = T(0);
+  __syncwarp();
+  warp_line_solve_skewed(xb, lb, rb, nx, m, lane);
+  for (int i = lane; i < nx; i += 32) out[row * nx + i] = xb[i + i / m];
+  __syncwarp();
+}
+
 template <typename T, typename Tin, bool SRC>
 __global__ void __launch_bounds__(256) sweep_x_warp_kernel(const Tin* __restrict__ in, T* __restrict__ out,
                                                            long long rows, int nx, int m, int span,
@@ -250,30 +280,8 @@ __global__ void __launch_bounds__(256) sweep_x_warp_kernel(const Tin* __restrict
   T* xb = wsm + (size_t)warp * 3 * span;
   T* lb = xb + span;
   T* rb = lb + span;
-  const double c = SRC ? sa.tau * (sa.src_t ? sa.src_t[sa.t0] : 1.0) : 0.0;
-  for (long long row = (long long)blockIdx.x * nw + warp; row < rows; row += (long long)gridDim.x * nw) {
-    const Tin* gin = in + row * nx;
-    const T* gl = lt + row * Lp;
-    const T* gr = rt + row * Lp;
-    for (int i = lane; i < nx; i += 32) {
-      const int k = i + i / m;
-      T b = (T)gin[i];
-      if constexpr (sizeof(T) == 8) {
-        if (SRC) b = fma(c, sa.src[row * nx + i], (double)b);
-      } else {
-        if (SRC) b = b + (float)(c * sa.src[row * nx + i]);
-      }
-      xb[k] = b;
-      lb[k] = gl[i];
-      rb[k] = gr[i];
-    }
-    // one slot past the line: the backward step reads the next segment's first factor there
-    if (lane == 0) lb[nx + nx / m] = T(0);
-    __syncwarp();
-    warp_line_solve_skewed(xb, lb, rb, nx, m, lane);
-    for (int i = lane; i < nx; i += 32) out[row * nx + i] = xb[i + i / m];
-    __syncwarp();
-  }
+  for (long long row = (long long)blockIdx.x * nw + warp; row < rows; row += (long long)gridDim.x * nw)
+    warp_row<T, Tin, SRC>(row, in, out, nx, m, lt, rt, Lp, sa, xb, lb, rb, lane);
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
@@ -482,7 +490,11 @@ __global__ void __launch_bounds__(kThreads) sweep_x_grouped_kernel(const CoarseJ
   for (long long it = blockIdx.x; it < total; it += gridDim.x) {
     const WorkSeg sg = segs[find_segment(segs, nseg, it)];
     const CoarseJob& j = jobs[sg.job];
-    sweep_x_body<double, double, double, VAR, false>(sg.first + (it - sg.prefix), reinterpret_cast<double*>(smem_raw),
+    if (j.sa.src)
+      sweep_x_body<double, double, double, VAR, true>(sg.first + (it - sg.prefix), reinterpret_cast<double*>(smem_raw),
+                                                      j.xin, j.xout, j.rows, j.nx, j.ld, j.R, j.rows, j.lx, j.rx, j.sa);
+    else
+      sweep_x_body<double, double, double, VAR, false>(sg.first + (it - sg.prefix), reinterpret_cast<double*>(smem_raw),
                                                        j.xin, j.xout, j.rows, j.nx, j.ld, j.R, j.rows, j.lx, j.rx,
                                                        SourceArgs{});
     __syncthreads();  // the next item reuses the shared rows
@@ -505,6 +517,57 @@ __global__ void __launch_bounds__(kThreads) sweep_y_grouped_kernel(const CoarseJ
   }
 }
 
+// Grouped FP32 increment-form coarse steps (batches of PS_COARSE_DELTA32 problems), the same
+// per-row and per-line bodies as the single-problem launches.  x: one warp per row, eight rows
+// per work item; the input is the FP64 state with the source (initial sweep) or the FP32
+// increment.  y: one thread per line with the increment-form (mode 3) or initial (mode 2)
+// epilogue.
+__global__ void __launch_bounds__(256) sweep_x32_grouped_kernel(const XWarpJob* __restrict__ jobs,
+                                                                const WorkSeg* __restrict__ segs,
+                                                                const int* __restrict__ nseg_ptr, int span_max) {
+  extern __shared__ __align__(16) unsigned char wsm_raw[];
+  float* wsm = reinterpret_cast<float*>(wsm_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  float* xb = wsm + (size_t)warp * 3 * span_max;
+  float* lb = xb + span_max;
+  float* rb = lb + span_max;
+  const int nseg = *nseg_ptr;
+  if (nseg <= 0) return;
+  const long long total = (long long)segs[nseg - 1].prefix + segs[nseg - 1].count;
+  for (long long it = blockIdx.x; it < total; it += gridDim.x) {
+    const WorkSeg sg = segs[find_segment(segs, nseg, it)];
+    const XWarpJob& j = jobs[sg.job];
+    const long long row = (sg.first + (it - sg.prefix)) * nw + warp;
+    if (row < j.rows) {
+      if (j.in64) {
+        if (j.sa.src)
+          warp_row<float, double, true>(row, j.in64, j.out, j.nx, j.m, j.lt, j.rt, j.Lp, j.sa, xb, lb, rb, lane);
+        else
+          warp_row<float, double, false>(row, j.in64, j.out, j.nx, j.m, j.lt, j.rt, j.Lp, j.sa, xb, lb, rb, lane);
+      } else {
+        warp_row<float, float, false>(row, j.in32, j.out, j.nx, j.m, j.lt, j.rt, j.Lp, SourceArgs{}, xb, lb, rb,
+                                      lane);
+      }
+    }
+  }
+}
+
+template <bool VAR, int EPI>
+__global__ void __launch_bounds__(kThreads) sweep_y32_grouped_kernel(const CoarseJob* __restrict__ jobs,
+                                                                    const WorkSeg* __restrict__ segs,
+                                                                    const int* __restrict__ nseg_ptr) {
+  const int nseg = *nseg_ptr;
+  if (nseg <= 0) return;
+  const long long total = (long long)segs[nseg - 1].prefix + segs[nseg - 1].count;
+  for (long long it = blockIdx.x; it < total; it += gridDim.x) {
+    const WorkSeg sg = segs[find_segment(segs, nseg, it)];
+    const CoarseJob& j = jobs[sg.job];
+    sweep_strided_body<float, float, float, VAR, false, EPI, true>(sg.first + (it - sg.prefix), j.g32, j.g32, j.g32,
+                                                                   j.nx, j.ny, j.nx, j.nt, j.ly32, j.ry32,
+                                                                   SourceArgs{}, j.ca);
+  }
+}
+
 __global__ void copy_inc_grouped_kernel(const CoarseJob* __restrict__ jobs, const WorkSeg* __restrict__ segs,
                                         const int* __restrict__ nseg_ptr) {
   const int nseg = *nseg_ptr;
@@ -518,10 +581,12 @@ __global__ void copy_inc_grouped_kernel(const CoarseJob* __restrict__ jobs, cons
     bool bad = false;
     if (i < j.nt) {
       const double v = j.xin[i];
-      my = fabs(v - j.xout[i]);
+      const double d = v - j.xout[i];
+      my = fabs(d);
       nrm = fabs(v);
       bad = !isfinite(v);
       j.xout[i] = v;
+      if (j.ca.dnext) j.ca.dnext[i] = (float)d;  // the increment form's FP32 increment of slice k
     }
     for (int o = 16; o > 0; o >>= 1) {
       my = fmax(my, __shfl_xor_sync(0xffffffffu, my, o));
@@ -752,6 +817,24 @@ void coarse_y_grouped(bool var, int epi, const CoarseJob* jobs, const WorkSeg* s
   } else {
     if (epi == 1) sweep_y_grouped_kernel<false, 1><<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
     else sweep_y_grouped_kernel<false, 2><<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
+  }
+  PS_CUDA(cudaGetLastError());
+}
+void coarse_x32_grouped(const XWarpJob* jobs, const WorkSeg* segs, const int* nseg, int grid, int span_max,
+                        cudaStream_t st) {
+  const size_t smem = (size_t)(kThreads / 32) * 3 * span_max * sizeof(float);
+  PS_CUDA(cudaFuncSetAttribute(sweep_x32_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sweep_x32_grouped_kernel<<<grid, kThreads, smem, st>>>(jobs, segs, nseg, span_max);
+  PS_CUDA(cudaGetLastError());
+}
+void coarse_y32_grouped(bool var, int epi, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
+                        cudaStream_t st) {
+  if (var) {
+    if (epi == 3) sweep_y32_grouped_kernel<true, 3><<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
+    else sweep_y32_grouped_kernel<true, 2><<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
+  } else {
+    if (epi == 3) sweep_y32_grouped_kernel<false, 3><<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
+    else sweep_y32_grouped_kernel<false, 2><<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
   }
   PS_CUDA(cudaGetLastError());
 }

@@ -140,6 +140,24 @@ struct CoarseJob {
   const double* ly;
   const double* ry;
   CorrArgs ca;
+  SourceArgs sa;  // the coarse step's source (added on the x-sweep), or sa.src == null
+  // FP32 increment form: the y-sweep runs in place on g32 with the FP32 factors
+  float* g32;
+  const float* ly32;
+  const float* ry32;
+};
+
+// One batched problem's FP32 x-sweep of coarse step n (increment form): rows of the FP64 state
+// (in64, initial sweep, with the source sa) or of the FP32 increment (in32) into out.
+struct XWarpJob {
+  const double* in64;
+  const float* in32;
+  float* out;
+  long long rows;
+  int nx, m, span, Lp;
+  const float* lt;
+  const float* rt;
+  SourceArgs sa;
 };
 
 // Launchers (ps_dim.cu).  `in` and `out` may alias (in-place sweeps).  nslices states of
@@ -192,6 +210,10 @@ void coarse_x_grouped(bool var, const CoarseJob* jobs, const WorkSeg* segs, cons
 void coarse_y_grouped(bool var, int epi, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
                       cudaStream_t st);
 void copy_inc_grouped(const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid, cudaStream_t st);
+void coarse_x32_grouped(const XWarpJob* jobs, const WorkSeg* segs, const int* nseg, int grid, int span_max,
+                        cudaStream_t st);
+void coarse_y32_grouped(bool var, int epi, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
+                        cudaStream_t st);
 int max_dyn_smem_public();
 
 }  // namespace ps

@@ -102,8 +102,8 @@ __device__ __forceinline__ void issue_side_loads(const TileArgs& a, int b0, int 
 }
 // tau * src_t at the end time of the step, for interleaved slot `slot`.
 template <typename T>
-__device__ __forceinline__ T slot_time_factor(const TileArgs& a, int slot) {
-  const int ti = a.t_first + slot * a.t_slice;
+__device__ __forceinline__ T slot_time_factor(const TileArgs& a, int slot, int t_first) {
+  const int ti = t_first + slot * a.t_slice;
   const double f = a.src_t ? (ti >= 0 && ti < a.src_t_len ? a.src_t[ti] : 0.0) : 1.0;
   return (T)(a.tau * f);
 }
@@ -252,7 +252,7 @@ __device__ __forceinline__ void tile_coords(const TileArgs& a, int t, int* s0, i
 // Shared memory from `tile` (128-byte aligned): [tile data | factors l | factors r | source].
 template <typename T, int V, bool SRC>
 __device__ __forceinline__ bool tile_body(const CUtensorMap* map, const TileArgs& a, int t, T* tile, uint64_t* bar,
-                                          uint32_t parity) {
+                                          uint32_t parity, int t_first) {
   __shared__ int s_ok;
   const int lines = a.TS * a.P;
   const int Lp = a.Lp;
@@ -295,7 +295,7 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* map, const TileArgs
   if (p < a.P && b0 + p < a.nb) {
     T ft[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) ft[v] = SRC ? slot_time_factor<T>(a, s0 + s + v) : T(0);
+    for (int v = 0; v < V; ++v) ft[v] = SRC ? slot_time_factor<T>(a, s0 + s + v, t_first) : T(0);
     line_solve<T, V, SRC>(tile + tile_off(a, s, p, 0), a.axis == 0 ? a.TS : a.P * a.TS, a.L, fl_s + p * Lp,
                           fr_s + p * Lp, src_s + p * Lp, ft);
   }
@@ -345,16 +345,18 @@ __global__ void tile_sweep_kernel(const __grid_constant__ CUtensorMap map, TileA
   }
   __syncthreads();
   if (s_abort) return;
-  tile_body<T, V, SRC>(&map, a, blockIdx.x, tile, bar, 0);
+  tile_body<T, V, SRC>(&map, a, blockIdx.x, tile, bar, 0, a.t_first);
 }
 
 // Grouped, persistent form: many problems' tiles in one launch.  jobs[j] holds one
 // (problem, direction)'s tensor map and tile arguments (in global memory, 64-byte aligned);
 // the first *nseg segments of `segs` list which tiles of which job run, with running
 // prefix counts.  Each CTA walks the items t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// Jobs with a source (x tiles of problems with f != 0) add tau f at the end of fine step
+// `step` of each slot: time index step + 1 + slot * t_slice.
 template <typename T, int V>
 __global__ void tile_sweep_grouped_kernel(const TileJob* __restrict__ jobs, const WorkSeg* __restrict__ segs,
-                                          const int* __restrict__ nseg_ptr, int* err) {
+                                          const int* __restrict__ nseg_ptr, int* err, int step) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   T* tile = reinterpret_cast<T*>(smem_raw + 128);
@@ -390,7 +392,10 @@ __global__ void tile_sweep_grouped_kernel(const TileJob* __restrict__ jobs, cons
     // tensormap proxy before TMA reads it
     if (threadIdx.x == 0)
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&job.map) : "memory");
-    if (!tile_body<T, V, false>(&job.map, job.a, sg.first + (int)(it - sg.prefix), tile, bar, parity)) return;
+    const int tt = sg.first + (int)(it - sg.prefix);
+    const bool ok = job.a.src ? tile_body<T, V, true>(&job.map, job.a, tt, tile, bar, parity, step + 1)
+                              : tile_body<T, V, false>(&job.map, job.a, tt, tile, bar, parity, 0);
+    if (!ok) return;
     parity ^= 1u;
   }
 }
@@ -515,7 +520,7 @@ __global__ void tile_sweep_pipe_kernel(const __grid_constant__ CUtensorMap map, 
     if (p < a.P && b0 + p < a.nb) {
       T ft[V];
 #pragma unroll
-      for (int v = 0; v < V; ++v) ft[v] = SRC ? slot_time_factor<T>(a, s0 + s + v) : T(0);
+      for (int v = 0; v < V; ++v) ft[v] = SRC ? slot_time_factor<T>(a, s0 + s + v, a.t_first) : T(0);
       line_solve<T, V, SRC>(buf + tile_off(a, s, p, 0), a.axis == 0 ? a.TS : a.P * a.TS, a.L, fl_s + p * Lp,
                             fr_s + p * Lp, src_s + p * Lp, ft);
     }
@@ -856,7 +861,7 @@ void factor_lines(const Geom& g, LineFactors& f, bool fp32, cudaStream_t st) {
 }
 
 long long tile_job_fill(const Geom& g, const TilePlan& tp, const LineFactors& f, int S_pad, int s_first, int nsl,
-                        int* err, void* job_out) {
+                        int* err, void* job_out, const SourceArgs& sa, const float* srcrow) {
   TileJob* job = reinterpret_cast<TileJob*>(job_out);
   std::memset(job, 0, sizeof(TileJob));
   job->map = tp.map;
@@ -883,17 +888,28 @@ long long tile_job_fill(const Geom& g, const TilePlan& tp, const LineFactors& f,
   a.fr = f.rt32.p;
   a.err = err;
   PS_REQUIRE(a.fl && a.fr, "line-major FP32 factors missing");
+  if (sa.src && tp.axis == 0) {
+    PS_REQUIRE(srcrow, "line-major source rows missing");
+    a.src = sa.src;
+    a.srcrow = srcrow;
+    a.src_t = sa.src_t;
+    a.t_slice = sa.tstride;
+    a.src_t_len = sa.src_t_len;
+    a.tau = sa.tau;
+  }
   return (long long)(a.s_hi - a.s_lo) * a.nbt * g.n[cax];
 }
 size_t tile_job_bytes() { return sizeof(TileJob); }
 
-size_t tile_grouped_smem(const TilePlan& tp) { return tp.smem; }
+size_t tile_grouped_smem(const TilePlan& tp, bool src) {
+  return tp.smem + (src ? (size_t)tp.P * ((tp.L + 3) & ~3) * sizeof(float) + 64 : 0);
+}
 
 void tile_sweep_grouped(const void* jobs, const WorkSeg* segs, const int* nseg, int grid, int threads, size_t smem,
-                        int* err, cudaStream_t st) {
+                        int* err, int step, cudaStream_t st) {
   auto kern = tile_sweep_grouped_kernel<float, 1>;  // one line per thread, as the default single-problem plan
   PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<grid, threads, smem, st>>>(reinterpret_cast<const TileJob*>(jobs), segs, nseg, err);
+  kern<<<grid, threads, smem, st>>>(reinterpret_cast<const TileJob*>(jobs), segs, nseg, err, step);
   PS_CUDA(cudaGetLastError());
 }
 

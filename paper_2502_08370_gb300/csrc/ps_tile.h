@@ -49,12 +49,15 @@ struct PackJob {
 };
 // Fills one (problem, direction) job of a grouped FP32 tile launch (job_out must hold
 // tile_job_bytes(), 64-byte aligned) and returns its tile count.
+// sa/srcrow: the fine propagator's source (x tiles add it; sa.tstride = fine steps per slice),
+// or sa.src == null.
 long long tile_job_fill(const Geom& g, const TilePlan& tp, const LineFactors& f, int S_pad, int s_first, int nsl,
-                        int* err, void* job_out);
+                        int* err, void* job_out, const SourceArgs& sa, const float* srcrow);
 size_t tile_job_bytes();
-size_t tile_grouped_smem(const TilePlan& tp);
+size_t tile_grouped_smem(const TilePlan& tp, bool src);
+// step: the fine step of the launch (the source's time index is step + 1 + slot * t_slice)
 void tile_sweep_grouped(const void* jobs, const WorkSeg* segs, const int* nseg, int grid, int threads, size_t smem,
-                        int* err, cudaStream_t st);
+                        int* err, int step, cudaStream_t st);
 void pack_grouped(bool to_interleaved_dir, const PackJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
                   cudaStream_t st);
 

@@ -142,3 +142,42 @@ def test_batch256_sampled_against_individual_runs(ps):
         k = probs[i].run(u0s[i], 1e-8)
         assert k == batched[i][0]
         assert np.array_equal(probs[i].state(probs[i].N).cpu().numpy(), batched[i][1][-1])
+
+
+@pytest.mark.parametrize("coarse", ["fp64", "delta32"])
+def test_batch_with_sources_both_coarse_forms_bitwise(ps, coarse):
+    """Batches of problems with time-dependent sources, in the FP64 coarse form and the FP32
+    increment form: the batched run equals each problem's own run bitwise (iteration counts,
+    histories, states); one problem against the oracle within the FP32 bound."""
+    cfgs = wl.batch256(count=6, seed=13, sizes=(31, 47, 64), slices=(4, 8, 16), s_range=(3, 12))
+    rng = np.random.default_rng(14)
+    probs, u0s, srcs = [], [], []
+    for c in cfgs:
+        nx, ny = c["n"]
+        src = rng.standard_normal((ny, nx))
+        src_t = 1.0 + 0.5 * np.sin(0.4 * np.arange(c["N"] * c["s"] + 1))
+        grid = ps.Grid(c["n"])
+        op = ps.Operator(grid, a=dev(c["a"]), src=dev(src), src_t=src_t)
+        sp = ps.Splitting(op)
+        p = ps.Problem(sp, c["T"], c["N"], 1, c["s"], precision="mixed", coarse_mode=coarse)
+        p._keep = (grid, op, sp)
+        probs.append(p)
+        u0s.append(dev(c["u0"]))
+        srcs.append((src, src_t))
+    ref = []
+    for p, u in zip(probs, u0s):
+        k = p.run(u, 1e-8)
+        ref.append((k, p.history(), snapshot(p)))
+    batch = ps.Batch(probs)
+    its = batch.run(u0s, 1e-8)
+    assert its == [r[0] for r in ref]
+    for i, p in enumerate(probs):
+        assert np.array_equal(p.history(), ref[i][1]), i
+        got = snapshot(p)
+        for n in range(p.N + 1):
+            assert np.array_equal(got[n], ref[i][2][n]), (i, n)
+    c = cfgs[0]
+    orp = orc.Problem(c["n"], a=c["a"], src=srcs[0][0], src_t=srcs[0][1])
+    U_ref, _, _ = orc.parareal(orp, c["T"], c["N"], 1, c["s"], c["u0"], 1e-8)
+    err = np.abs(ref[0][2][-1] - U_ref[-1]).max() / np.abs(U_ref[-1]).max()
+    assert err < 4.0 * c["s"] * c["N"] * 2 * 2.0 ** -24
