@@ -392,7 +392,9 @@ int ps_batch_destroy(ps_batch* b);
 int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out);
 /* The timing record of the last ps_autotune on this problem: one entry per candidate timed,
  * name "fine:<slots>x<positions>/v<lines per thread>/<tile|ring>", "coarse:<staged|streamed>",
- * "coarse-x32:<thomas|pcr|hybrid>" (increment form) or "coarse-x64:<thomas|hybrid>", and its
+ * "coarse-x32:<thomas|pcr|hybrid>" (increment form) or "coarse-x64:<thomas|hybrid>",
+ * "coarse-corr:<fused|split>" (FP64 coarse form: the correction in the last sweep's epilogue or
+ * as its own pass; the same values either way), and its
  * time per candidate run (ms; fine: the sweeps of all directions over all slices; coarse: one
  * coarse step's sweeps; coarse-x*: one x-sweep).
  * chosen = 1 for the installed candidate of each group.  len = number of entries (<= cap). */

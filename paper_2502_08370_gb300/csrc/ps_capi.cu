@@ -179,6 +179,21 @@ void fie_step64(ps_problem* p, Prop& P, int nsl, const double* in, double* out, 
     double bytes = 0, flops = 0;
     if (p->kt.on) sweep_cost(p, *P.dim[m], nsl, 8, 8, 8, sa.src != nullptr, epi ? corr.mode : 0, &bytes, &flops);
     p->kt.begin(st);
+    if (&P == &p->G && nsl == 1 && epi && p->coarse_split) {
+      // the last sweep without the epilogue, then the correction as one coalesced pass over the
+      // slice: the same expressions as the fused epilogue, so the same values
+      coarse_sweep64(p, *P.dim[m], src_state, out, sa, CorrArgs{}, st);
+      if (p->kt.on) {
+        sweep_cost(p, *P.dim[m], nsl, 8, 8, 8, sa.src != nullptr, 0, &bytes, &flops);
+        p->kt.end(std::string(phase) + "." + kAxis[m] + ".f64", bytes, flops);
+      }
+      p->launches++;
+      p->kt.begin(st);
+      dd_correct(p->g, out, corr, st);
+      if (p->kt.on) p->kt.end(std::string(phase) + (corr.mode == 1 ? ".corr.f64" : ".init.f64"), p->g.nt * 48.0, 0.0);
+      p->launches++;
+      continue;
+    }
     if (&P == &p->G && nsl == 1)
       coarse_sweep64(p, *P.dim[m], src_state, out, sa, epi ? corr : CorrArgs{}, st);
     else if (epi)
@@ -1399,6 +1414,38 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
       if (coarse_choice) p->prm.coarse_sweep = coarse_choice;
       for (auto& e : p->tune_log)
         if (e.name == (coarse_choice == PS_COARSE_SWEEP_STAGED ? "coarse:staged" : "coarse:streamed")) e.chosen = 1;
+      // FP64 coarse form: the correction fused into the last sweep, or as its own pass.  Timed on
+      // the last sweep with an epilogue whose target is the scratch state (the values are
+      // discarded; the next run clears the flags it may set)
+      if (!p->delta32) {
+        CorrArgs scratch;
+        scratch.mode = 1;
+        scratch.U_next = scratch.Gold = p->gtmp.p;
+        scratch.Fout = p->gtmp.p;
+        scratch.inc = p->inc.p;
+        scratch.nonfinite = p->flag.p;
+        const LineFactors& fz = *p->G.dim[MG - 1];
+        float sbest = 1e30f;
+        bool split_choice = p->coarse_split;
+        for (int split = 0; split < 2; ++split) {
+          const float ms = time4([&] {
+            if (split) {
+              coarse_sweep64(p, fz, p->gtmp.p, p->gtmp.p, SourceArgs{}, CorrArgs{}, st);
+              dd_correct(p->g, p->gtmp.p, scratch, st);
+            } else {
+              coarse_sweep64(p, fz, p->gtmp.p, p->gtmp.p, SourceArgs{}, scratch, st);
+            }
+          });
+          p->tune_log.push_back({split ? "coarse-corr:split" : "coarse-corr:fused", ms, 0});
+          if (ms < sbest) {
+            sbest = ms;
+            split_choice = split != 0;
+          }
+        }
+        p->coarse_split = split_choice;
+        for (auto& e : p->tune_log)
+          if (e.name == (split_choice ? "coarse-corr:split" : "coarse-corr:fused")) e.chosen = 1;
+      }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1443,6 +1490,7 @@ int ps_copy_schedule(const ps_problem* src, ps_problem* dst) {
     dst->prm.coarse_sweep = src->prm.coarse_sweep;
     dst->xsched = src->xsched;
     dst->prm.schedule = src->prm.schedule;
+    dst->coarse_split = src->coarse_split;
   });
 }
 

@@ -126,6 +126,7 @@ struct ps_problem {
   bool delta32 = false;       // coarse increment form in FP32 (PS_COARSE_DELTA32); no Gold then
   bool dr = false;            // fine propagator: Douglas-Rachford steps (PS_FINE_DR)
   bool coarse_staged = false;  // coarse sweeps staged through shared memory (ps_coarse.cu), else streamed
+  bool coarse_split = false;   // FP64 coarse correction as its own pass after the last sweep (same values)
   int xsched = PS_SCHED_HYBRID;  // schedule of the FP32 increment form's coarse x-sweep
   ps::DevBuf<float> pcr_e, pcr_d;  // its tridiagonal rows for the PCR schedule (line-major FP32)
   struct TuneEntry {

@@ -103,7 +103,7 @@ def test_autotune_outside_a_batch_may_change_roundings_only(ps):
     before = snapshot(p)
     p.autotune(budget_ms=50)
     names = [r[0] for r in p.autotune_record()]
-    assert {"coarse-x64:thomas", "coarse-x64:hybrid"} <= set(names)
+    assert {"coarse-x64:thomas", "coarse-x64:hybrid", "coarse-corr:fused", "coarse-corr:split"} <= set(names)
     assert p.run(u0, 1e-10) == it
     after = snapshot(p)
     for a, b in zip(before, after):

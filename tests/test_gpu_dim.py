@@ -352,6 +352,7 @@ def test_autotune_record_lists_every_schedule(ps):
     rec = prob.autotune_record()
     names = [r[0] for r in rec]
     assert {"coarse-x32:thomas", "coarse-x32:pcr", "coarse-x32:hybrid", "coarse:staged", "coarse:streamed"} <= set(names)
+    assert not any(nm.startswith("coarse-corr:") for nm in names)  # the increment form fuses its epilogue
     assert any(nm.startswith("fine:") for nm in names)
     for group in ("fine:", "coarse-x32:", "coarse:"):
         chosen = [r for r in rec if r[0].startswith(group) and r[2]]
