@@ -277,9 +277,15 @@ def test_coarse_increment_form_is_rejected_where_unsupported(ps):
     with pytest.raises(ps.PsError) as e:
         prob.vjp(prob.state(4), 1e-8)
     assert e.value.code == 6
+    # a batch takes increment-form problems, but not mixed with FP64-coarse ones
+    other, _ = make_delta(ps, (17, 15), a=np.ones((17, 19)), N=4, s=4)
+    ps.Batch([prob, other])
+    grid = ps.Grid((17, 15))
+    op = ps.Operator(grid, a=dev(np.ones((17, 19))))
+    fp64_coarse = ps.Problem(ps.Splitting(op), 1.0, 4, 1, 4, precision="mixed")
     with pytest.raises(ps.PsError) as e:
-        ps.Batch([prob])
-    assert e.value.code == 6
+        ps.Batch([prob, fp64_coarse])
+    assert e.value.code == 1
     # the sequential coarse solution keeps the FP64 coarse steps
     ref = orc.coarse_sequential(orc.Problem((17, 15), a=np.ones((17, 19))), 1.0, 4, 1, 4, np.ones((15, 17)))
     assert relmax(prob.coarse_sequential(u0).cpu().numpy(), ref) < RTOL64
