@@ -388,13 +388,16 @@ int ps_batch_destroy(ps_batch* b);
  * changes the coarse values at rounding level (see PS_SCHED_*), so for a problem that belongs
  * to a batch with the FP64 coarse propagator only Thomas is considered.  *choice_out (may be
  * NULL) receives coarse_sweep*100000 + lines_per_thread*10000 + slots*100 + positions*10 +
- * pipelined; ps_params.schedule of the problem holds the x-sweep's choice. */
+ * pipelined; ps_params.schedule of the problem holds the x-sweep's choice.  With the DD
+ * splitting (FIE fine steps) it times the fine colour solves with 1, 2 and 4 time slices per
+ * CTA instead and installs the fastest as dd_slices_per_block (*choice_out = that count; the
+ * same arithmetic per slice in every case). */
 int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out);
 /* The timing record of the last ps_autotune on this problem: one entry per candidate timed,
  * name "fine:<slots>x<positions>/v<lines per thread>/<tile|ring>", "coarse:<staged|streamed>",
  * "coarse-x32:<thomas|pcr|hybrid>" (increment form) or "coarse-x64:<thomas|hybrid>",
  * "coarse-corr:<fused|split>" (FP64 coarse form: the correction in the last sweep's epilogue or
- * as its own pass; the same values either way), and its
+ * as its own pass; the same values either way), "dd:<S>-slices-per-cta" (DD), and its
  * time per candidate run (ms; fine: the sweeps of all directions over all slices; coarse: one
  * coarse step's sweeps; coarse-x*: one x-sweep).
  * chosen = 1 for the installed candidate of each group.  len = number of entries (<= cap). */

@@ -1270,7 +1270,50 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
     PS_REQUIRE(p, "null argument");
     require_slices(p);
     if (choice_out) *choice_out = 0;
-    if (p->F.sp->kind != PS_SPLIT_DIM) return;
+    if (p->F.sp->kind != PS_SPLIT_DIM) {
+      // DD: time slices per CTA of the fine colour solves (1, 2, 4) on all slices at once, in the
+      // F-result buffer (recomputed by every run); each slice's arithmetic does not depend on it
+      p->tune_log.clear();
+      cudaStream_t st = S(stream);
+      if (p->dr) return;
+      tile_flag_reset(p, st);
+      cudaEvent_t e0, e1;
+      PS_CUDA(cudaEventCreate(&e0));
+      PS_CUDA(cudaEventCreate(&e1));
+      float best = 1e30f;
+      int bestS = p->prm.dd_slices_per_block > 0 ? p->prm.dd_slices_per_block : 2;
+      try {
+        for (int spb : {1, 2, 4}) {
+          auto solve = [&] {
+            for (int c = 0; c < p->F.sp->M; ++c) dd_solve(p->g, p->N, *p->F.dd, c, p->Fout.p, spb, p->tmo.p, st);
+          };
+          solve();
+          PS_CUDA(cudaEventRecord(e0, st));
+          solve();
+          PS_CUDA(cudaEventRecord(e1, st));
+          PS_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          PS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          p->tune_log.push_back({"dd:" + std::to_string(spb) + "-slices-per-cta", ms, 0});
+          if (ms < best) {
+            best = ms;
+            bestS = spb;
+          }
+        }
+      } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      p->prm.dd_slices_per_block = bestS;
+      for (auto& e : p->tune_log)
+        if (e.name == "dd:" + std::to_string(bestS) + "-slices-per-cta") e.chosen = 1;
+      tile_flag_check(p, st);
+      if (choice_out) *choice_out = bestS;
+      return;
+    }
     cudaStream_t st = S(stream);
     const bool mixed = p->prm.precision == PS_PREC_MIXED;
     struct Cand {

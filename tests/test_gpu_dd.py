@@ -129,3 +129,23 @@ def test_dd2d_1023_full_size_substeps_and_run(ps):
     x = dev(u0)
     prob.propagate(0, cfg["s"], x, t0=0, tstride=1)
     assert np.array_equal(prob.state(1).cpu().numpy(), x.cpu().numpy())
+
+
+def test_dd_autotune_slices_per_cta_changes_no_result(ps):
+    """The autotuner picks the time slices per CTA of the colour solves; every slice's arithmetic
+    is the same for any count, so the states stay bitwise equal."""
+    rng = np.random.default_rng(24)
+    n, N, s = (41, 37), 10, 6
+    a = np.exp(0.3 * rng.standard_normal((n[1] + 2, n[0] + 2)))
+    prob, _, _ = make(ps, n, (4, 4), 4 / 42.0, a=a, T=0.5, N=N, s=s, spb=1)
+    u0 = dev(rng.standard_normal(n[::-1]))
+    it = prob.run(u0, 1e-10)
+    before = [prob.state(j).cpu().numpy() for j in range(N + 1)]
+    choice = prob.autotune(budget_ms=20)
+    assert choice in (1, 2, 4)
+    rec = prob.autotune_record()
+    assert sorted(r[0] for r in rec) == ["dd:1-slices-per-cta", "dd:2-slices-per-cta", "dd:4-slices-per-cta"]
+    assert sum(r[2] for r in rec) == 1
+    assert prob.run(u0, 1e-10) == it
+    for j in range(N + 1):
+        assert np.array_equal(prob.state(j).cpu().numpy(), before[j]), j
