@@ -419,6 +419,152 @@ __global__ void tridiag_x_rows_kernel(int dim, int nx, int ny, long long rows, c
   et[e] = i > 0 ? (float)(-tau * am / h2) : 0.f;
 }
 
+
+// ---------------------------------------------------------------------------------------
+// FP64 x-substep by chunks: Thomas, one thread per row, the same operations in the same order
+// as the whole-row sweep of ps_dim.cu (so the two give the same bits).  A CTA takes XC_R rows;
+// the rows pass through shared memory XC_C nodes at a time in two stages (cp.async), so a
+// CTA holds 2 x XC_R x XC_C values of each array instead of XC_R whole rows, and two CTAs
+// keep 256 rows' recurrences in flight on an SM.  On GB300 the FP64 pipe takes a warp
+// instruction about every 68 cycles per SM sub-partition: the dependent chains need at least
+// two warps per sub-partition to keep it busy, which whole-row staging (96 rows per SM at
+// 255 nodes) cannot give.  The forward pass writes y to `out` chunk by chunk (it is read back
+// within microseconds, from L2) and the backward pass overwrites it with x; the last chunk's
+// y stays in shared memory across the turn.
+//   u, s chunks: row-major [r][j] with pitch XC_C + 1 (thread t's row at t * pitch: distinct
+//   bank pairs for the 16 threads of a half-warp's 64-bit accesses);
+//   factor chunks: node-major [j][r] from the transposed factor layout (entry (row, i) at
+//   i * rows_per_slice + row), so both copies and reads are coalesced.
+constexpr int XC_R = 128, XC_C = 16, XC_P = XC_C + 1;
+constexpr size_t kXcSmem = (size_t)(2 * XC_R * XC_P * 2 + 2 * XC_C * XC_R) * sizeof(double);
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <bool VAR, bool SRC>
+__global__ void __launch_bounds__(XC_R, 2)
+    sweep_x_chunk_kernel(const double* in, double* out, long long rows, int nx, int rps,
+                         const double* __restrict__ fl, const double* __restrict__ fr, SourceArgs sa) {
+  extern __shared__ __align__(16) double xsm[];
+  double* ub = xsm;                           // [2][XC_R][XC_P]: u, then y, then x
+  double* sb = ub + 2 * XC_R * XC_P;          // [2][XC_R][XC_P]: source (forward), r factors (backward)
+  double* lb = sb + 2 * XC_R * XC_P;          // [2][XC_C][XC_R]: l factors
+  const int tid = threadIdx.x;
+  const long long row0 = (long long)blockIdx.x * XC_R;
+  const long long myrow = row0 + tid;
+  const bool active = myrow < rows;
+  const int ris = (int)(myrow % rps);         // row inside its slice (factor and source index)
+  const int base_ris = (int)(row0 % rps);
+  double cst = 0.0;
+  if (SRC && active) {
+    const long long sl = myrow / rps;
+    cst = sa.tau * (sa.src_t ? sa.src_t[sa.t0 + sl * sa.tstride] : 1.0);
+  }
+  const int nch = (nx + XC_C - 1) / XC_C;
+  // the rows-by-chunk copies: element e = tid + 128 q is row (e >> 4), node (e & 15)
+  auto stage_rows = [&](double* dst, const double* g, bool per_slice, int k) {
+#pragma unroll 4
+    for (int q = 0; q < XC_C; ++q) {
+      const int r = (tid >> 4) + 8 * q, j = tid & 15, i = k * XC_C + j;
+      const long long row = row0 + r;
+      double* d = dst + r * XC_P + j;
+      if (row < rows && i < nx) {
+        const long long off = per_slice ? (long long)((base_ris + r) % rps) * nx : row * nx;
+        cp_async(d, g + off + i);
+      } else {
+        *d = 0.0;
+      }
+    }
+  };
+  // the factor copies: thread t copies its own row's factors of the chunk's nodes (+ shift)
+  auto stage_factor = [&](double* dst, const double* f, int k, int shift) {
+#pragma unroll 4
+    for (int j = 0; j < XC_C; ++j) {
+      const int i = k * XC_C + j + shift;
+      double* d = dst + j * XC_R + tid;
+      if (active && i < nx) cp_async(d, f + (long long)i * rps + ris);
+      else *d = 0.0;
+    }
+  };
+  auto store_rows = [&](const double* srcb, int k) {
+#pragma unroll 4
+    for (int q = 0; q < XC_C; ++q) {
+      const int r = (tid >> 4) + 8 * q, j = tid & 15, i = k * XC_C + j;
+      const long long row = row0 + r;
+      if (row < rows && i < nx) out[row * nx + i] = srcb[r * XC_P + j];
+    }
+  };
+  auto stage_forward = [&](int k) {
+    const int b = k & 1;
+    stage_rows(ub + b * XC_R * XC_P, in, false, k);
+    if (SRC) stage_rows(sb + b * XC_R * XC_P, sa.src, true, k);
+    if (VAR) stage_factor(lb + b * XC_C * XC_R, fl, k, 0);
+    cp_async_commit();
+  };
+  // forward recurrence  y_i = b_i - l_i y_{i-1},  b_i = u_i + c f_i (one rounding)
+  double y = 0.0;
+  stage_forward(0);
+  for (int k = 0; k < nch; ++k) {
+    const int b = k & 1;
+    cp_async_wait0();
+    __syncthreads();
+    if (k + 1 < nch) stage_forward(k + 1);
+    if (active) {
+      double* u = ub + b * XC_R * XC_P + tid * XC_P;
+      const double* sv = sb + b * XC_R * XC_P + tid * XC_P;
+      const double* lv = lb + b * XC_C * XC_R + tid;
+      const int len = min(XC_C, nx - k * XC_C);
+#pragma unroll
+      for (int j = 0; j < XC_C; ++j) {
+        if (j < len) {
+          const int i = k * XC_C + j;
+          const double bi = SRC ? fma(cst, sv[j], u[j]) : u[j];
+          const double li = VAR ? lv[j * XC_R] : fl[i];
+          y = i == 0 ? bi : fma(-li, y, bi);
+          u[j] = y;
+        }
+      }
+    }
+    __syncthreads();
+    if (k + 1 < nch) store_rows(ub + b * XC_R * XC_P, k);
+  }
+  // backward recurrence  x_i = r_i y_i - l_{i+1} x_{i+1}; the last chunk's y is in shared memory
+  auto stage_backward = [&](int k, bool with_y) {
+    const int b = k & 1;
+    if (with_y) stage_rows(ub + b * XC_R * XC_P, out, false, k);
+    if (VAR) {
+      stage_factor(sb + b * XC_R * XC_P, fr, k, 0);  // r: node-major inside the source buffer
+      stage_factor(lb + b * XC_C * XC_R, fl, k, 1);  // l_{i+1}
+    }
+    cp_async_commit();
+  };
+  stage_backward(nch - 1, false);
+  double x = 0.0;
+  for (int k = nch - 1; k >= 0; --k) {
+    const int b = k & 1;
+    cp_async_wait0();
+    __syncthreads();
+    if (k > 0) stage_backward(k - 1, true);
+    if (active) {
+      double* u = ub + b * XC_R * XC_P + tid * XC_P;
+      const double* rv = sb + b * XC_R * XC_P + tid;
+      const double* lv = lb + b * XC_C * XC_R + tid;
+      const int len = min(XC_C, nx - k * XC_C);
+#pragma unroll
+      for (int j = XC_C - 1; j >= 0; --j) {
+        if (j < len) {
+          const int i = k * XC_C + j;
+          const double ri = VAR ? rv[j * XC_R] : fr[i];
+          const double li = i + 1 < nx ? (VAR ? lv[j * XC_R] : fl[i + 1]) : 0.0;
+          x = i == nx - 1 ? ri * u[j] : fma(-li, x, ri * u[j]);
+          u[j] = x;
+        }
+      }
+    }
+    __syncthreads();
+    store_rows(ub + b * XC_R * XC_P, k);
+  }
+}
 }  // namespace
 
 template <typename T>
@@ -542,5 +688,33 @@ template bool sweep_x_pcr<float>(const Geom&, const float*, const float*, const 
                                  cudaStream_t);
 template bool sweep_x_pcr<double>(const Geom&, const float*, const float*, const double*, float*, const SourceArgs&,
                                   cudaStream_t);
+
+bool sweep_x_chunked(const Geom& g, int nslices, const LineFactors& f, const double* in, double* out,
+                     const SourceArgs& sa, cudaStream_t st) {
+  if (f.m != 0 || f.l64.p == nullptr) return false;
+  const int nx = g.n[0];
+  const long long rps = g.nt / nx;
+  const long long rows = rps * nslices;
+  if (rps > (1LL << 30) || nx < 2 * XC_C) return false;  // short rows: the whole-row sweep
+  const bool var = f.var != 0, src = sa.src != nullptr;
+  const long long blocks = (rows + XC_R - 1) / XC_R;
+  static bool attr[4] = {false, false, false, false};
+  auto launch = [&](auto kern, int which) {
+    if (!attr[which]) {
+      PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXcSmem));
+      attr[which] = true;
+    }
+    kern<<<(unsigned)blocks, XC_R, kXcSmem, st>>>(in, out, rows, nx, (int)rps, f.l64.p, f.r64.p, sa);
+  };
+  if (var) {
+    if (src) launch(sweep_x_chunk_kernel<true, true>, 0);
+    else launch(sweep_x_chunk_kernel<true, false>, 1);
+  } else {
+    if (src) launch(sweep_x_chunk_kernel<false, true>, 2);
+    else launch(sweep_x_chunk_kernel<false, false>, 3);
+  }
+  PS_CUDA(cudaGetLastError());
+  return true;
+}
 
 }  // namespace ps

@@ -466,6 +466,186 @@ __global__ void __launch_bounds__(kThreads) sweep_strided_kernel(const Tin* in, 
 }
 
 // ---------------------------------------------------------------------------------------
+// FP64 y/z-substep without source, the loads pipelined through shared memory: the same
+// operations in the same order as sweep_strided_body, so the two give the same bits.  Each
+// thread copies its own line's next chunk (right-hand side or stored y, factors, and the
+// correction's Gold / Fout / old U_{n+1}) with cp.async into its column of a node-major
+// [array][j][t] stage while it runs the recurrences on the current chunk; no other thread
+// reads that column, so the thread's own wait_group is the only synchronisation.  Every copy
+// and store of a warp is one 256-byte row segment.  On GB300 the FP64 pipe, not HBM, sets the
+// pace of these sweeps (6 FP64 operations per node with the correction, against 56 bytes):
+// the point is to keep every line's next loads in flight so that the pipe never waits on
+// memory, with one wave of 4 CTAs x 128 lines per SM.
+constexpr int SC_T = 128;
+constexpr int SC_STAGE = 3072;  // doubles per stage and CTA column block: 12 x 2 x 128 or 4 x 6 x 128
+constexpr size_t kScSmem = 2 * SC_STAGE * sizeof(double);
+
+__device__ __forceinline__ void cpa8(double* dst, const double* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+template <bool VAR, int EPI>
+__global__ void __launch_bounds__(SC_T, 4)
+    sweep_strided_chunk_kernel(const double* in, double* out, double* tmp, long long lines, int nm, long long S,
+                               long long nt, const double* __restrict__ fl, const double* __restrict__ fr,
+                               CorrArgs ca) {
+  extern __shared__ __align__(16) double csm[];
+  constexpr int CF = VAR ? 12 : 24;                      // forward chunk: u (+ l)
+  constexpr int NB = 1 + (VAR ? 2 : 0) + (EPI == 1 ? 3 : EPI == 3 ? 2 : 0);  // backward arrays
+  constexpr int CB = SC_STAGE / (NB * SC_T) < 24 ? SC_STAGE / (NB * SC_T) : 24;
+  const int tid = threadIdx.x;
+  const long long L = (long long)blockIdx.x * SC_T + tid;
+  const bool active = L < lines;
+  long long base = 0, pos = 0;
+  if (active) {
+    const long long outer = L / S;
+    base = outer * S * nm + (L - outer * S);
+    pos = base - (base / nt) * nt;
+  }
+  const double* Lf = fl + (VAR ? pos : 0);
+  const double* Rf = fr + (VAR ? pos : 0);
+  const long long fs = VAR ? S : 1;
+  unsigned long long my_inc = 0, my_norm = 0;
+  bool bad = false;
+  // forward  y_i = b_i - l_i y_{i-1}, stored to tmp
+  const int nchF = (nm + CF - 1) / CF;
+  auto stage_f = [&](int k) {
+    double* st = csm + (k & 1) * SC_STAGE;
+    if (active)
+      for (int j = 0; j < CF; ++j) {
+        const int i = k * CF + j;
+        if (i < nm) {
+          cpa8(st + j * SC_T + tid, in + base + i * S);
+          if (VAR) cpa8(st + (CF + j) * SC_T + tid, Lf + i * fs);
+        }
+      }
+    cpa_commit();
+  };
+  double y = 0.0;
+  stage_f(0);
+  for (int k = 0; k < nchF; ++k) {
+    if (k + 1 < nchF) stage_f(k + 1);
+    else cpa_commit();
+    cpa_wait1();
+    if (active) {
+      const double* st = csm + (k & 1) * SC_STAGE;
+      const int len = min(CF, nm - k * CF);
+#pragma unroll
+      for (int j = 0; j < CF; ++j) {
+        if (j < len) {
+          const int i = k * CF + j;
+          const double b = st[j * SC_T + tid];
+          const double l = VAR ? st[(CF + j) * SC_T + tid] : Lf[i * fs];
+          y = i == 0 ? b : fma(-l, y, b);
+          tmp[base + i * S] = y;
+        }
+      }
+    }
+  }
+  // backward  x_i = r_i y_i - l_{i+1} x_{i+1}, nodes from the end, with the epilogue
+  const int nchB = (nm + CB - 1) / CB;
+  auto stage_b = [&](int k) {
+    double* st = csm + (k & 1) * SC_STAGE;
+    if (active)
+      for (int j = 0; j < CB; ++j) {
+        const int i = nm - 1 - (k * CB + j);
+        if (i >= 0) {
+          int a = 0;
+          cpa8(st + (a++ * CB + j) * SC_T + tid, tmp + base + i * S);
+          if (VAR) {
+            cpa8(st + (a++ * CB + j) * SC_T + tid, Rf + i * fs);
+            if (i + 1 < nm) cpa8(st + (a * CB + j) * SC_T + tid, Lf + (i + 1) * fs);
+            ++a;
+          }
+          const long long si = pos + (long long)i * S;
+          if (EPI == 1) cpa8(st + (a++ * CB + j) * SC_T + tid, ca.Gold + si);
+          if (EPI == 1 || EPI == 3) {
+            cpa8(st + (a++ * CB + j) * SC_T + tid, ca.Fout + si);
+            cpa8(st + (a++ * CB + j) * SC_T + tid, ca.U_next + si);
+          }
+        }
+      }
+    cpa_commit();
+  };
+  // y_{nm-1} is read back like every other y: the stored value is the register's
+  double xn = 0.0;
+  stage_b(0);
+  for (int k = 0; k < nchB; ++k) {
+    if (k + 1 < nchB) stage_b(k + 1);
+    else cpa_commit();
+    cpa_wait1();
+    if (active) {
+      const double* st = csm + (k & 1) * SC_STAGE;
+#pragma unroll
+      for (int j = 0; j < CB; ++j) {
+        const int i = nm - 1 - (k * CB + j);
+        if (i >= 0) {
+          int a = 0;
+          const double yy = st[(a++ * CB + j) * SC_T + tid];
+          double r, l;
+          if (VAR) {
+            r = st[(a++ * CB + j) * SC_T + tid];
+            l = i + 1 < nm ? st[(a * CB + j) * SC_T + tid] : 0.0;
+            ++a;
+          } else {
+            r = Rf[i * fs];
+            l = i + 1 < nm ? Lf[(i + 1) * fs] : 0.0;
+          }
+          xn = i == nm - 1 ? r * yy : fma(-l, xn, r * yy);
+          const long long si = pos + (long long)i * S;
+          if (EPI == 0) {
+            out[base + i * S] = xn;
+          } else if (EPI == 1) {
+            const double go = st[(a++ * CB + j) * SC_T + tid];
+            const double fo = st[(a++ * CB + j) * SC_T + tid];
+            const double uo = st[(a++ * CB + j) * SC_T + tid];
+            const double unew = fo + (xn - go);
+            const unsigned long long an = abs_bits(unew);
+            bad |= an >= kInfBits;
+            my_inc = max(my_inc, abs_bits(unew - uo));
+            my_norm = max(my_norm, an);
+            ca.Gold[si] = xn;
+            ca.U_next[si] = unew;
+          } else if (EPI == 3) {
+            const double fo = st[(a++ * CB + j) * SC_T + tid];
+            const double uo = st[(a++ * CB + j) * SC_T + tid];
+            const double unew = fo + xn;
+            const double d = unew - uo;
+            const unsigned long long an = abs_bits(unew);
+            bad |= an >= kInfBits;
+            my_inc = max(my_inc, abs_bits(d));
+            my_norm = max(my_norm, an);
+            ca.U_next[si] = unew;
+            ca.dnext[si] = (float)d;
+          } else {
+            bad |= abs_bits(xn) >= kInfBits;
+            if (ca.Gold) ca.Gold[si] = xn;
+            ca.U_next[si] = xn;
+          }
+        }
+      }
+    }
+  }
+  if (EPI == 1 || EPI == 3) {
+    for (int o = 16; o > 0; o >>= 1) {
+      my_inc = max(my_inc, __shfl_xor_sync(0xffffffffu, my_inc, o));
+      my_norm = max(my_norm, __shfl_xor_sync(0xffffffffu, my_norm, o));
+    }
+    if ((threadIdx.x & 31) == 0 && my_inc > 0) atomicMax(ca.inc, my_inc);
+    if ((threadIdx.x & 31) == 0 && ca.slice_stats) {
+      if (my_inc > 0) atomicMax(ca.slice_stats, my_inc);
+      if (my_norm > 0) atomicMax(ca.slice_stats + 1, my_norm);
+    }
+  }
+  if (EPI != 0) {
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(ca.nonfinite, 1);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Grouped coarse steps (batched problems, 2-D, FP64, no source): one launch runs the same
 // sweep of many problems' coarse step n.  jobs[j] describes problem j's sweep; the first
 // *nseg segments of `segs` list (job, first block, block count, prefix) runs of blocks.
@@ -668,6 +848,14 @@ void launch_strided(const Geom& g, int m, int nslices, const Tc* fl, const Tc* f
   const int nm = g.n[m];
   const long long S = g.stride(m);
   const long long lines = (g.nt / nm) * nslices;
+  if constexpr (sizeof(Tin) == 8 && sizeof(Tout) == 8 && sizeof(Tc) == 8 && !SRC && EPI != 3) {
+    const long long cblocks = (lines + SC_T - 1) / SC_T;
+    sweep_strided_chunk_kernel<VAR, EPI><<<(unsigned)cblocks, SC_T, kScSmem, st>>>(
+        reinterpret_cast<const double*>(in), reinterpret_cast<double*>(out), reinterpret_cast<double*>(tmp), lines, nm,
+        S, g.nt, reinterpret_cast<const double*>(fl), reinterpret_cast<const double*>(fr), ca);
+    PS_CUDA(cudaGetLastError());
+    return;
+  }
   long long blocks = (lines + kThreads - 1) / kThreads;
   if (S * (long long)sizeof(Tin) <= 8192)
     sweep_strided_kernel<Tin, Tout, Tc, VAR, SRC, EPI, true>
@@ -685,6 +873,10 @@ void dispatch(const Geom& g, int nslices, const LineFactors& f, const Tc* fl, co
   const bool var = f.var != 0, src = sa.src != nullptr;
   if (f.m == 0) {
     PS_REQUIRE(ca.mode == 0, "the correction is fused into a y/z sweep only");
+    if constexpr (sizeof(Tin) == 8 && sizeof(Tout) == 8 && sizeof(Tc) == 8) {
+      // FP64 rows of 32 nodes or more: the chunked sweep (same arithmetic, more rows in flight)
+      if (sweep_x_chunked(g, nslices, f, in, out, sa, st)) return;
+    }
     if (var) {
       if (src) launch_x<Tin, Tout, Tc, true, true>(g, nslices, fl, fr, in, out, sa, st);
       else launch_x<Tin, Tout, Tc, true, false>(g, nslices, fl, fr, in, out, sa, st);
