@@ -423,28 +423,31 @@ __global__ void tridiag_x_rows_kernel(int dim, int nx, int ny, long long rows, c
 // ---------------------------------------------------------------------------------------
 // FP64 x-substep by chunks: Thomas, one thread per row, the same operations in the same order
 // as the whole-row sweep of ps_dim.cu (so the two give the same bits).  A CTA takes XC_R rows;
-// the rows pass through shared memory XC_C nodes at a time in two stages (cp.async), so a
-// CTA holds 2 x XC_R x XC_C values of each array instead of XC_R whole rows, and two CTAs
-// keep 256 rows' recurrences in flight on an SM.  On GB300 the FP64 pipe takes a warp
+// the rows pass through shared memory C = 8 or 16 nodes at a time in two stages (cp.async), so
+// a CTA holds 2 x XC_R x C values of each array instead of XC_R whole rows, and four (C = 8) or
+// two (C = 16) CTAs keep 512 or 256 rows' recurrences in flight on an SM.  On GB300 the FP64 pipe takes a warp
 // instruction about every 68 cycles per SM sub-partition: the dependent chains need at least
 // two warps per sub-partition to keep it busy, which whole-row staging (96 rows per SM at
 // 255 nodes) cannot give.  The forward pass writes y to `out` chunk by chunk (it is read back
 // within microseconds, from L2) and the backward pass overwrites it with x; the last chunk's
 // y stays in shared memory across the turn.
-//   u, s chunks: row-major [r][j] with pitch XC_C + 1 (thread t's row at t * pitch: distinct
+//   u, s chunks: row-major [r][j] with pitch C + 1 (thread t's row at t * pitch: distinct
 //   bank pairs for the 16 threads of a half-warp's 64-bit accesses);
 //   factor chunks: node-major [j][r] from the transposed factor layout (entry (row, i) at
 //   i * rows_per_slice + row), so both copies and reads are coalesced.
-constexpr int XC_R = 128, XC_C = 16, XC_P = XC_C + 1;
-constexpr size_t kXcSmem = (size_t)(2 * XC_R * XC_P * 2 + 2 * XC_C * XC_R) * sizeof(double);
+constexpr int XC_R = 128;
+template <int C>
+constexpr size_t xc_smem() { return (size_t)(2 * XC_R * (C + 1) * 2 + 2 * C * XC_R) * sizeof(double); }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-template <bool VAR, bool SRC>
-__global__ void __launch_bounds__(XC_R, 2)
+// C = 16: two CTAs per SM (100 KB each); C = 8: four (52 KB each), shorter chunks
+template <int C, bool VAR, bool SRC>
+__global__ void __launch_bounds__(XC_R, C == 8 ? 4 : 2)
     sweep_x_chunk_kernel(const double* in, double* out, long long rows, int nx, int rps,
                          const double* __restrict__ fl, const double* __restrict__ fr, SourceArgs sa) {
+  constexpr int XC_C = C, XC_P = C + 1, RPQ = XC_R / C;  // rows covered per copy pass
   extern __shared__ __align__(16) double xsm[];
   double* ub = xsm;                           // [2][XC_R][XC_P]: u, then y, then x
   double* sb = ub + 2 * XC_R * XC_P;          // [2][XC_R][XC_P]: source (forward), r factors (backward)
@@ -461,11 +464,11 @@ __global__ void __launch_bounds__(XC_R, 2)
     cst = sa.tau * (sa.src_t ? sa.src_t[sa.t0 + sl * sa.tstride] : 1.0);
   }
   const int nch = (nx + XC_C - 1) / XC_C;
-  // the rows-by-chunk copies: element e = tid + 128 q is row (e >> 4), node (e & 15)
+  // the rows-by-chunk copies: element e = tid + 128 q is row e / C, node e % C
   auto stage_rows = [&](double* dst, const double* g, bool per_slice, int k) {
 #pragma unroll 4
     for (int q = 0; q < XC_C; ++q) {
-      const int r = (tid >> 4) + 8 * q, j = tid & 15, i = k * XC_C + j;
+      const int r = tid / XC_C + RPQ * q, j = tid % XC_C, i = k * XC_C + j;
       const long long row = row0 + r;
       double* d = dst + r * XC_P + j;
       if (row < rows && i < nx) {
@@ -489,7 +492,7 @@ __global__ void __launch_bounds__(XC_R, 2)
   auto store_rows = [&](const double* srcb, int k) {
 #pragma unroll 4
     for (int q = 0; q < XC_C; ++q) {
-      const int r = (tid >> 4) + 8 * q, j = tid & 15, i = k * XC_C + j;
+      const int r = tid / XC_C + RPQ * q, j = tid % XC_C, i = k * XC_C + j;
       const long long row = row0 + r;
       if (row < rows && i < nx) out[row * nx + i] = srcb[r * XC_P + j];
     }
@@ -690,28 +693,40 @@ template bool sweep_x_pcr<double>(const Geom&, const float*, const float*, const
                                   cudaStream_t);
 
 bool sweep_x_chunked(const Geom& g, int nslices, const LineFactors& f, const double* in, double* out,
-                     const SourceArgs& sa, cudaStream_t st) {
+                     const SourceArgs& sa, cudaStream_t st, int chunk) {
   if (f.m != 0 || f.l64.p == nullptr) return false;
   const int nx = g.n[0];
   const long long rps = g.nt / nx;
   const long long rows = rps * nslices;
-  if (rps > (1LL << 30) || nx < 2 * XC_C) return false;  // short rows: the whole-row sweep
+  if (rps > (1LL << 30) || nx < 32) return false;  // short rows: the whole-row sweep
   const bool var = f.var != 0, src = sa.src != nullptr;
   const long long blocks = (rows + XC_R - 1) / XC_R;
-  static bool attr[4] = {false, false, false, false};
-  auto launch = [&](auto kern, int which) {
+  static bool attr[8] = {};
+  auto launch = [&](auto kern, size_t smem, int which) {
     if (!attr[which]) {
-      PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXcSmem));
+      PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       attr[which] = true;
     }
-    kern<<<(unsigned)blocks, XC_R, kXcSmem, st>>>(in, out, rows, nx, (int)rps, f.l64.p, f.r64.p, sa);
+    kern<<<(unsigned)blocks, XC_R, smem, st>>>(in, out, rows, nx, (int)rps, f.l64.p, f.r64.p, sa);
   };
-  if (var) {
-    if (src) launch(sweep_x_chunk_kernel<true, true>, 0);
-    else launch(sweep_x_chunk_kernel<true, false>, 1);
+  if (chunk == 8) {
+    constexpr size_t sm = xc_smem<8>();
+    if (var) {
+      if (src) launch(sweep_x_chunk_kernel<8, true, true>, sm, 0);
+      else launch(sweep_x_chunk_kernel<8, true, false>, sm, 1);
+    } else {
+      if (src) launch(sweep_x_chunk_kernel<8, false, true>, sm, 2);
+      else launch(sweep_x_chunk_kernel<8, false, false>, sm, 3);
+    }
   } else {
-    if (src) launch(sweep_x_chunk_kernel<false, true>, 2);
-    else launch(sweep_x_chunk_kernel<false, false>, 3);
+    constexpr size_t sm = xc_smem<16>();
+    if (var) {
+      if (src) launch(sweep_x_chunk_kernel<16, true, true>, sm, 4);
+      else launch(sweep_x_chunk_kernel<16, true, false>, sm, 5);
+    } else {
+      if (src) launch(sweep_x_chunk_kernel<16, false, true>, sm, 6);
+      else launch(sweep_x_chunk_kernel<16, false, false>, sm, 7);
+    }
   }
   PS_CUDA(cudaGetLastError());
   return true;
