@@ -395,8 +395,7 @@ int ps_batch_destroy(ps_batch* b);
 int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out);
 /* The timing record of the last ps_autotune on this problem: one entry per candidate timed,
  * name "fine:<slots>x<positions>/v<lines per thread>/<tile|ring>", "coarse:<staged|streamed>",
- * "coarse-x32:<thomas|pcr|hybrid>" (increment form) or "coarse-x64:<thomas|thomas-c8|hybrid>"
- * (FP64; thomas-c8: rows staged 8 nodes at a time instead of 16, the same values),
+ * "coarse-x32:<thomas|pcr|hybrid>" (increment form) or "coarse-x64:<thomas|hybrid>",
  * "coarse-corr:<fused|split>" (FP64 coarse form: the correction in the last sweep's epilogue or
  * as its own pass; the same values either way), "dd:<S>-slices-per-cta" (DD), and its
  * time per candidate run (ms; fine: the sweeps of all directions over all slices; coarse: one

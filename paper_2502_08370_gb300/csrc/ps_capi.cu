@@ -157,7 +157,7 @@ void coarse_sweep64(ps_problem* p, const LineFactors& f, const double* in, doubl
     return;
   }
   if (p->coarse_staged && coarse_sweep_staged<double>(p->g, f, in, out, sa, corr, st)) return;
-  if (f.m == 0 && corr.mode == 0 && sweep_x_chunked(p->g, 1, f, in, out, sa, st, p->xchunk)) return;
+  if (f.m == 0 && corr.mode == 0 && sweep_x_chunked(p->g, 1, f, in, out, sa, st)) return;
   sweep_dim<double, double>(p->g, 1, f, false, in, out, sa, corr, corr.mode != 0 ? out : nullptr, st);
 }
 
@@ -1420,36 +1420,28 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
         const char* names[4] = {"", "thomas", "pcr", "hybrid"};
         const std::string pre = p->delta32 ? "coarse-x32:" : "coarse-x64:";
         float xbest = 1e30f;
-        int xchoice = p->xsched, cchoice = p->xchunk;
+        int xchoice = p->xsched;
         std::string xname;
         for (int sc = PS_SCHED_THOMAS; sc <= PS_SCHED_HYBRID; ++sc) {
           if (sc == PS_SCHED_PCR && (!p->delta32 || !p->pcr_e.p)) continue;  // FP32 rows of <= 256 nodes
           // a batch's grouped kernels run Thomas (FP64 coarse) or the hybrid (increment form)
           if (p->batched > 0 && sc != (p->delta32 ? PS_SCHED_HYBRID : PS_SCHED_THOMAS)) continue;
           if (sc == PS_SCHED_HYBRID && !p->delta32 && !p->G.dim[0]->lt64.p) continue;
-          // FP64 Thomas: rows through shared memory 16 or 8 nodes at a time (the same values)
-          const bool chunks = sc == PS_SCHED_THOMAS && !p->delta32;
-          for (int ch : {16, 8}) {
-            if (ch == 8 && !chunks) continue;
-            p->xsched = sc;
-            p->xchunk = ch;
-            const float ms = p->delta32
-                                 ? time4([&] { coarse_x32<float>(p, p->g32.p, p->g32.p, SourceArgs{}, st); })
-                                 : time4([&] {
-                                     coarse_sweep64(p, *p->G.dim[0], p->U.p, p->gtmp.p, SourceArgs{}, CorrArgs{}, st);
-                                   });
-            const std::string nm = pre + names[sc] + (chunks && ch == 8 ? "-c8" : "");
-            p->tune_log.push_back({nm, ms, 0});
-            if (ms < xbest) {
-              xbest = ms;
-              xchoice = sc;
-              cchoice = ch;
-              xname = nm;
-            }
+          p->xsched = sc;
+          const float ms = p->delta32
+                               ? time4([&] { coarse_x32<float>(p, p->g32.p, p->g32.p, SourceArgs{}, st); })
+                               : time4([&] {
+                                   coarse_sweep64(p, *p->G.dim[0], p->U.p, p->gtmp.p, SourceArgs{}, CorrArgs{}, st);
+                                 });
+          const std::string nm = pre + names[sc];
+          p->tune_log.push_back({nm, ms, 0});
+          if (ms < xbest) {
+            xbest = ms;
+            xchoice = sc;
+            xname = nm;
           }
         }
         p->xsched = xchoice;
-        p->xchunk = cchoice;
         p->prm.schedule = xchoice;
         for (auto& e : p->tune_log)
           if (e.name == xname) e.chosen = 1;
@@ -1544,7 +1536,6 @@ int ps_copy_schedule(const ps_problem* src, ps_problem* dst) {
     dst->coarse_staged = src->coarse_staged;
     dst->prm.coarse_sweep = src->prm.coarse_sweep;
     dst->xsched = src->xsched;
-    dst->xchunk = src->xchunk;
     dst->prm.schedule = src->prm.schedule;
     dst->coarse_split = src->coarse_split;
   });

@@ -421,153 +421,151 @@ __global__ void tridiag_x_rows_kernel(int dim, int nx, int ny, long long rows, c
 
 
 // ---------------------------------------------------------------------------------------
-// FP64 x-substep by chunks: Thomas, one thread per row, the same operations in the same order
-// as the whole-row sweep of ps_dim.cu (so the two give the same bits).  A CTA takes XC_R rows;
-// the rows pass through shared memory C = 8 or 16 nodes at a time in two stages (cp.async), so
-// a CTA holds 2 x XC_R x C values of each array instead of XC_R whole rows, and four (C = 8) or
-// two (C = 16) CTAs keep 512 or 256 rows' recurrences in flight on an SM.  On GB300 the FP64 pipe takes a warp
-// instruction about every 68 cycles per SM sub-partition: the dependent chains need at least
-// two warps per sub-partition to keep it busy, which whole-row staging (96 rows per SM at
-// 255 nodes) cannot give.  The forward pass writes y to `out` chunk by chunk (it is read back
-// within microseconds, from L2) and the backward pass overwrites it with x; the last chunk's
-// y stays in shared memory across the turn.
-//   u, s chunks: row-major [r][j] with pitch C + 1 (thread t's row at t * pitch: distinct
-//   bank pairs for the 16 threads of a half-warp's 64-bit accesses);
-//   factor chunks: node-major [j][r] from the transposed factor layout (entry (row, i) at
-//   i * rows_per_slice + row), so both copies and reads are coalesced.
-constexpr int XC_R = 128;
-template <int C>
-constexpr size_t xc_smem() { return (size_t)(2 * XC_R * (C + 1) * 2 + 2 * C * XC_R) * sizeof(double); }
+// FP64 x-substep, Thomas per thread, in warp-private chunks: the same operations in the same
+// order as the whole-row sweep of ps_dim.cu, so the two give the same bits.  Each warp owns 32
+// consecutive rows (lane = row) and works alone -- no CTA barrier couples the warps of an SM:
+//   - the rows' right-hand side (and source) pass through the warp's shared memory XW_C nodes at
+//     a time in two stages (cp.async; every copy instruction covers four 64-byte row segments),
+//     read back by the lane of each row (row pitch XW_C + 1: distinct bank pairs);
+//   - the factors l, r of the next chunk are prefetched into registers: in the transposed factor
+//     layout (entry (row, i) at i * rows_per_slice + row) one node of the warp's 32 rows is one
+//     coalesced 256-byte load;
+//   - the forward pass writes y to `out` chunk by chunk; the backward pass copies it back one
+//     chunk ahead and overwrites it with x; the last chunk's y stays in shared memory.
+// On GB300 the FP64 pipe (a warp instruction per ~64 cycles per SM sub-partition, ~72 cycles of
+// dependent latency) sets the pace; 9 KB of shared memory per warp leaves room for every row
+// of a 255^3 slice in one wave (13-14 warps per SM), each warp never waiting on a barrier.
+constexpr int XW_C = 8, XW_P = XW_C + 1, XW_WARPS = 2;
+constexpr int XW_WARP_DOUBLES = 2 * 2 * 32 * XW_P;  // two stages of u and s
+constexpr size_t kXwSmem = (size_t)XW_WARPS * (XW_WARP_DOUBLES + 32) * sizeof(double);
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// C = 16: two CTAs per SM (100 KB each); C = 8: four (52 KB each), shorter chunks
-template <int C, bool VAR, bool SRC>
-__global__ void __launch_bounds__(XC_R, C == 8 ? 4 : 2)
-    sweep_x_chunk_kernel(const double* in, double* out, long long rows, int nx, int rps,
-                         const double* __restrict__ fl, const double* __restrict__ fr, SourceArgs sa) {
-  constexpr int XC_C = C, XC_P = C + 1, RPQ = XC_R / C;  // rows covered per copy pass
-  extern __shared__ __align__(16) double xsm[];
-  double* ub = xsm;                           // [2][XC_R][XC_P]: u, then y, then x
-  double* sb = ub + 2 * XC_R * XC_P;          // [2][XC_R][XC_P]: source (forward), r factors (backward)
-  double* lb = sb + 2 * XC_R * XC_P;          // [2][XC_C][XC_R]: l factors
-  const int tid = threadIdx.x;
-  const long long row0 = (long long)blockIdx.x * XC_R;
-  const long long myrow = row0 + tid;
+template <bool VAR, bool SRC>
+__global__ void __launch_bounds__(32 * XW_WARPS)
+    sweep_x_thomas_warp_kernel(const double* in, double* out, long long rows, int nx, int rps,
+                               const double* __restrict__ fl, const double* __restrict__ fr, SourceArgs sa) {
+  extern __shared__ __align__(16) double xwsm[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double* ub = xwsm + w * (XW_WARP_DOUBLES + 32);  // [stage][32][XW_P]: u, then y, then x
+  double* sb = ub + 2 * 32 * XW_P;                 // [stage][32][XW_P]: source
+  long long* soff = reinterpret_cast<long long*>(sb + 2 * 32 * XW_P);  // [32]: source row offsets
+  const long long row0 = ((long long)blockIdx.x * XW_WARPS + w) * 32;
+  if (row0 >= rows) return;  // the whole warp: nothing below waits on another warp
+  const long long myrow = row0 + lane;
   const bool active = myrow < rows;
-  const int ris = (int)(myrow % rps);         // row inside its slice (factor and source index)
-  const int base_ris = (int)(row0 % rps);
+  const int ris = active ? (int)(myrow % rps) : 0;  // row inside its slice: factor index
   double cst = 0.0;
-  if (SRC && active) {
-    const long long sl = myrow / rps;
-    cst = sa.tau * (sa.src_t ? sa.src_t[sa.t0 + sl * sa.tstride] : 1.0);
+  if (SRC) {
+    soff[lane] = (long long)ris * nx;
+    if (active) cst = sa.tau * (sa.src_t ? sa.src_t[sa.t0 + (myrow / rps) * sa.tstride] : 1.0);
   }
-  const int nch = (nx + XC_C - 1) / XC_C;
-  // the rows-by-chunk copies: element e = tid + 128 q is row e / C, node e % C
-  auto stage_rows = [&](double* dst, const double* g, bool per_slice, int k) {
-#pragma unroll 4
-    for (int q = 0; q < XC_C; ++q) {
-      const int r = tid / XC_C + RPQ * q, j = tid % XC_C, i = k * XC_C + j;
-      const long long row = row0 + r;
-      double* d = dst + r * XC_P + j;
-      if (row < rows && i < nx) {
-        const long long off = per_slice ? (long long)((base_ris + r) % rps) * nx : row * nx;
-        cp_async(d, g + off + i);
-      } else {
-        *d = 0.0;
-      }
+  __syncwarp();
+  const int nch = (nx + XW_C - 1) / XW_C;
+  // copies of a chunk: element (r, j) of the warp's 32 x XW_C block, lane -> j = lane % 8,
+  // r = lane / 8 + 4 q (q = 0..7)
+  const int jl = lane % XW_C, rl = lane / XW_C;
+  auto stage = [&](double* dst, const double* g, bool src_rows, int k) {
+    const int i = k * XW_C + jl;
+#pragma unroll
+    for (int q = 0; q < XW_C; ++q) {
+      const int r = rl + 4 * q;
+      double* d = dst + r * XW_P + jl;
+      if (row0 + r < rows && i < nx) cp_async(d, g + (src_rows ? soff[r] : (row0 + r) * nx) + i);
     }
   };
-  // the factor copies: thread t copies its own row's factors of the chunk's nodes (+ shift)
-  auto stage_factor = [&](double* dst, const double* f, int k, int shift) {
-#pragma unroll 4
-    for (int j = 0; j < XC_C; ++j) {
-      const int i = k * XC_C + j + shift;
-      double* d = dst + j * XC_R + tid;
-      if (active && i < nx) cp_async(d, f + (long long)i * rps + ris);
-      else *d = 0.0;
+  auto store = [&](const double* srcb, int k) {
+    const int i = k * XW_C + jl;
+#pragma unroll
+    for (int q = 0; q < XW_C; ++q) {
+      const int r = rl + 4 * q;
+      if (row0 + r < rows && i < nx) out[(row0 + r) * nx + i] = srcb[r * XW_P + jl];
     }
   };
-  auto store_rows = [&](const double* srcb, int k) {
-#pragma unroll 4
-    for (int q = 0; q < XC_C; ++q) {
-      const int r = tid / XC_C + RPQ * q, j = tid % XC_C, i = k * XC_C + j;
-      const long long row = row0 + r;
-      if (row < rows && i < nx) out[row * nx + i] = srcb[r * XC_P + j];
+  // factors of nodes k * XW_C + j (+ shift) of this lane's row
+  auto load_f = [&](double (&dst)[XW_C], const double* f, int k, int shift) {
+#pragma unroll
+    for (int j = 0; j < XW_C; ++j) {
+      const int i = k * XW_C + j + shift;
+      dst[j] = (active && i < nx) ? (VAR ? f[(long long)i * rps + ris] : f[i]) : 0.0;
     }
   };
-  auto stage_forward = [&](int k) {
-    const int b = k & 1;
-    stage_rows(ub + b * XC_R * XC_P, in, false, k);
-    if (SRC) stage_rows(sb + b * XC_R * XC_P, sa.src, true, k);
-    if (VAR) stage_factor(lb + b * XC_C * XC_R, fl, k, 0);
-    cp_async_commit();
-  };
-  // forward recurrence  y_i = b_i - l_i y_{i-1},  b_i = u_i + c f_i (one rounding)
+  // forward  y_i = b_i - l_i y_{i-1},  b_i = u_i + c f_i (one rounding)
+  double lc[XW_C], ln[XW_C];
+  stage(ub, in, false, 0);
+  if (SRC) stage(sb, sa.src, true, 0);
+  cp_async_commit();
+  load_f(lc, fl, 0, 0);
   double y = 0.0;
-  stage_forward(0);
   for (int k = 0; k < nch; ++k) {
     const int b = k & 1;
-    cp_async_wait0();
-    __syncthreads();
-    if (k + 1 < nch) stage_forward(k + 1);
+    if (k + 1 < nch) {
+      stage(ub + (b ^ 1) * 32 * XW_P, in, false, k + 1);
+      if (SRC) stage(sb + (b ^ 1) * 32 * XW_P, sa.src, true, k + 1);
+      load_f(ln, fl, k + 1, 0);
+    }
+    cp_async_commit();
+    cp_async_wait1();
+    __syncwarp();
     if (active) {
-      double* u = ub + b * XC_R * XC_P + tid * XC_P;
-      const double* sv = sb + b * XC_R * XC_P + tid * XC_P;
-      const double* lv = lb + b * XC_C * XC_R + tid;
-      const int len = min(XC_C, nx - k * XC_C);
+      double* u = ub + b * 32 * XW_P + lane * XW_P;
+      const double* sv = sb + b * 32 * XW_P + lane * XW_P;
+      const int len = min(XW_C, nx - k * XW_C);
 #pragma unroll
-      for (int j = 0; j < XC_C; ++j) {
+      for (int j = 0; j < XW_C; ++j) {
         if (j < len) {
-          const int i = k * XC_C + j;
+          const int i = k * XW_C + j;
           const double bi = SRC ? fma(cst, sv[j], u[j]) : u[j];
-          const double li = VAR ? lv[j * XC_R] : fl[i];
-          y = i == 0 ? bi : fma(-li, y, bi);
+          y = i == 0 ? bi : fma(-lc[j], y, bi);
           u[j] = y;
         }
       }
     }
-    __syncthreads();
-    if (k + 1 < nch) store_rows(ub + b * XC_R * XC_P, k);
+    __syncwarp();
+    if (k + 1 < nch) store(ub + b * 32 * XW_P, k);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < XW_C; ++j) lc[j] = ln[j];
   }
-  // backward recurrence  x_i = r_i y_i - l_{i+1} x_{i+1}; the last chunk's y is in shared memory
-  auto stage_backward = [&](int k, bool with_y) {
-    const int b = k & 1;
-    if (with_y) stage_rows(ub + b * XC_R * XC_P, out, false, k);
-    if (VAR) {
-      stage_factor(sb + b * XC_R * XC_P, fr, k, 0);  // r: node-major inside the source buffer
-      stage_factor(lb + b * XC_C * XC_R, fl, k, 1);  // l_{i+1}
-    }
-    cp_async_commit();
-  };
-  stage_backward(nch - 1, false);
+  // backward  x_i = r_i y_i - l_{i+1} x_{i+1}
+  double rc[XW_C], rn[XW_C];
+  load_f(rc, fr, nch - 1, 0);
+  load_f(lc, fl, nch - 1, 1);
   double x = 0.0;
   for (int k = nch - 1; k >= 0; --k) {
     const int b = k & 1;
-    cp_async_wait0();
-    __syncthreads();
-    if (k > 0) stage_backward(k - 1, true);
+    if (k > 0) {
+      stage(ub + (b ^ 1) * 32 * XW_P, out, false, k - 1);
+      load_f(rn, fr, k - 1, 0);
+      load_f(ln, fl, k - 1, 1);
+    }
+    cp_async_commit();
+    cp_async_wait1();
+    __syncwarp();
     if (active) {
-      double* u = ub + b * XC_R * XC_P + tid * XC_P;
-      const double* rv = sb + b * XC_R * XC_P + tid;
-      const double* lv = lb + b * XC_C * XC_R + tid;
-      const int len = min(XC_C, nx - k * XC_C);
+      double* u = ub + b * 32 * XW_P + lane * XW_P;
+      const int len = min(XW_C, nx - k * XW_C);
 #pragma unroll
-      for (int j = XC_C - 1; j >= 0; --j) {
+      for (int j = XW_C - 1; j >= 0; --j) {
         if (j < len) {
-          const int i = k * XC_C + j;
-          const double ri = VAR ? rv[j * XC_R] : fr[i];
-          const double li = i + 1 < nx ? (VAR ? lv[j * XC_R] : fl[i + 1]) : 0.0;
-          x = i == nx - 1 ? ri * u[j] : fma(-li, x, ri * u[j]);
+          const int i = k * XW_C + j;
+          x = i == nx - 1 ? rc[j] * u[j] : fma(-lc[j], x, rc[j] * u[j]);
           u[j] = x;
         }
       }
     }
-    __syncthreads();
-    store_rows(ub + b * XC_R * XC_P, k);
+    __syncwarp();
+    store(ub + b * 32 * XW_P, k);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < XW_C; ++j) {
+      rc[j] = rn[j];
+      lc[j] = ln[j];
+    }
   }
 }
+
 }  // namespace
 
 template <typename T>
@@ -693,43 +691,26 @@ template bool sweep_x_pcr<double>(const Geom&, const float*, const float*, const
                                   cudaStream_t);
 
 bool sweep_x_chunked(const Geom& g, int nslices, const LineFactors& f, const double* in, double* out,
-                     const SourceArgs& sa, cudaStream_t st, int chunk) {
+                     const SourceArgs& sa, cudaStream_t st) {
   if (f.m != 0 || f.l64.p == nullptr) return false;
   const int nx = g.n[0];
   const long long rps = g.nt / nx;
   const long long rows = rps * nslices;
-  if (rps > (1LL << 30) || nx < 32) return false;  // short rows: the whole-row sweep
+  if (rps > (1LL << 30) || nx < 2 * XW_C) return false;  // short rows: the whole-row sweep
   const bool var = f.var != 0, src = sa.src != nullptr;
-  const long long blocks = (rows + XC_R - 1) / XC_R;
-  static bool attr[8] = {};
-  auto launch = [&](auto kern, size_t smem, int which) {
-    if (!attr[which]) {
-      PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      attr[which] = true;
-    }
-    kern<<<(unsigned)blocks, XC_R, smem, st>>>(in, out, rows, nx, (int)rps, f.l64.p, f.r64.p, sa);
+  const long long warps = (rows + 31) / 32;
+  const long long blocks = (warps + XW_WARPS - 1) / XW_WARPS;
+  auto launch = [&](auto kern) {
+    kern<<<(unsigned)blocks, 32 * XW_WARPS, kXwSmem, st>>>(in, out, rows, nx, (int)rps, f.l64.p, f.r64.p, sa);
   };
-  if (chunk == 8) {
-    constexpr size_t sm = xc_smem<8>();
-    if (var) {
-      if (src) launch(sweep_x_chunk_kernel<8, true, true>, sm, 0);
-      else launch(sweep_x_chunk_kernel<8, true, false>, sm, 1);
-    } else {
-      if (src) launch(sweep_x_chunk_kernel<8, false, true>, sm, 2);
-      else launch(sweep_x_chunk_kernel<8, false, false>, sm, 3);
-    }
+  if (var) {
+    if (src) launch(sweep_x_thomas_warp_kernel<true, true>);
+    else launch(sweep_x_thomas_warp_kernel<true, false>);
   } else {
-    constexpr size_t sm = xc_smem<16>();
-    if (var) {
-      if (src) launch(sweep_x_chunk_kernel<16, true, true>, sm, 4);
-      else launch(sweep_x_chunk_kernel<16, true, false>, sm, 5);
-    } else {
-      if (src) launch(sweep_x_chunk_kernel<16, false, true>, sm, 6);
-      else launch(sweep_x_chunk_kernel<16, false, false>, sm, 7);
-    }
+    if (src) launch(sweep_x_thomas_warp_kernel<false, true>);
+    else launch(sweep_x_thomas_warp_kernel<false, false>);
   }
   PS_CUDA(cudaGetLastError());
   return true;
 }
-
 }  // namespace ps

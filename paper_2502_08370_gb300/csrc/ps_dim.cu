@@ -477,15 +477,18 @@ __global__ void __launch_bounds__(kThreads) sweep_strided_kernel(const Tin* in, 
 // the point is to keep every line's next loads in flight so that the pipe never waits on
 // memory, with one wave of 4 CTAs x 128 lines per SM.
 constexpr int SC_T = 128;
-constexpr int SC_STAGE = 3072;  // doubles per stage and CTA column block: 12 x 2 x 128 or 4 x 6 x 128
-constexpr size_t kScSmem = 2 * SC_STAGE * sizeof(double);
+constexpr int SC_NS = 3;        // stages: the copies run two chunks ahead of the recurrences
+constexpr int SC_STAGE = 2048;  // doubles per stage: 8 x 2 x 128 (forward), 2..16 x up to 6 x 128 (backward)
+constexpr size_t kScSmem = SC_NS * SC_STAGE * sizeof(double);
 
 __device__ __forceinline__ void cpa8(double* dst, const double* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                : "memory");
 }
 __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cpa_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait_ahead() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(SC_NS - 1) : "memory");
+}
 
 template <bool VAR, int EPI>
 __global__ void __launch_bounds__(SC_T, 4)
@@ -493,7 +496,7 @@ __global__ void __launch_bounds__(SC_T, 4)
                                long long nt, const double* __restrict__ fl, const double* __restrict__ fr,
                                CorrArgs ca) {
   extern __shared__ __align__(16) double csm[];
-  constexpr int CF = VAR ? 12 : 24;                      // forward chunk: u (+ l)
+  constexpr int CF = SC_STAGE / ((VAR ? 2 : 1) * SC_T);   // forward chunk: u (+ l)
   constexpr int NB = 1 + (VAR ? 2 : 0) + (EPI == 1 ? 3 : EPI == 3 ? 2 : 0);  // backward arrays
   constexpr int CB = SC_STAGE / (NB * SC_T) < 24 ? SC_STAGE / (NB * SC_T) : 24;
   const int tid = threadIdx.x;
@@ -513,7 +516,7 @@ __global__ void __launch_bounds__(SC_T, 4)
   // forward  y_i = b_i - l_i y_{i-1}, stored to tmp
   const int nchF = (nm + CF - 1) / CF;
   auto stage_f = [&](int k) {
-    double* st = csm + (k & 1) * SC_STAGE;
+    double* st = csm + (k % SC_NS) * SC_STAGE;
     if (active)
       for (int j = 0; j < CF; ++j) {
         const int i = k * CF + j;
@@ -525,13 +528,18 @@ __global__ void __launch_bounds__(SC_T, 4)
     cpa_commit();
   };
   double y = 0.0;
-  stage_f(0);
-  for (int k = 0; k < nchF; ++k) {
-    if (k + 1 < nchF) stage_f(k + 1);
+  for (int k = 0; k < SC_NS - 1; ++k) {
+    if (k < nchF) stage_f(k);
     else cpa_commit();
-    cpa_wait1();
+  }
+  for (int k = 0; k < nchF; ++k) {
+    // chunk k + NS - 1 goes into the stage that chunk k - 1 used (its reads are done); then all
+    // but the NS - 1 newest groups are complete, chunk k among them
+    if (k + SC_NS - 1 < nchF) stage_f(k + SC_NS - 1);
+    else cpa_commit();
+    cpa_wait_ahead();
     if (active) {
-      const double* st = csm + (k & 1) * SC_STAGE;
+      const double* st = csm + (k % SC_NS) * SC_STAGE;
       const int len = min(CF, nm - k * CF);
 #pragma unroll
       for (int j = 0; j < CF; ++j) {
@@ -548,7 +556,7 @@ __global__ void __launch_bounds__(SC_T, 4)
   // backward  x_i = r_i y_i - l_{i+1} x_{i+1}, nodes from the end, with the epilogue
   const int nchB = (nm + CB - 1) / CB;
   auto stage_b = [&](int k) {
-    double* st = csm + (k & 1) * SC_STAGE;
+    double* st = csm + (k % SC_NS) * SC_STAGE;
     if (active)
       for (int j = 0; j < CB; ++j) {
         const int i = nm - 1 - (k * CB + j);
@@ -572,13 +580,16 @@ __global__ void __launch_bounds__(SC_T, 4)
   };
   // y_{nm-1} is read back like every other y: the stored value is the register's
   double xn = 0.0;
-  stage_b(0);
-  for (int k = 0; k < nchB; ++k) {
-    if (k + 1 < nchB) stage_b(k + 1);
+  for (int k = 0; k < SC_NS - 1; ++k) {
+    if (k < nchB) stage_b(k);
     else cpa_commit();
-    cpa_wait1();
+  }
+  for (int k = 0; k < nchB; ++k) {
+    if (k + SC_NS - 1 < nchB) stage_b(k + SC_NS - 1);
+    else cpa_commit();
+    cpa_wait_ahead();
     if (active) {
-      const double* st = csm + (k & 1) * SC_STAGE;
+      const double* st = csm + (k % SC_NS) * SC_STAGE;
 #pragma unroll
       for (int j = 0; j < CB; ++j) {
         const int i = nm - 1 - (k * CB + j);

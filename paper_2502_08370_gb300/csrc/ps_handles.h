@@ -128,7 +128,6 @@ struct ps_problem {
   bool coarse_staged = false;  // coarse sweeps staged through shared memory (ps_coarse.cu), else streamed
   bool coarse_split = false;   // FP64 coarse correction as its own pass after the last sweep (same values)
   int xsched = PS_SCHED_HYBRID;  // schedule of the FP32 increment form's coarse x-sweep
-  int xchunk = 16;               // FP64 Thomas x-sweep: nodes per shared-memory chunk (8 or 16; same values)
   ps::DevBuf<float> pcr_e, pcr_d;  // its tridiagonal rows for the PCR schedule (line-major FP32)
   struct TuneEntry {
     std::string name;

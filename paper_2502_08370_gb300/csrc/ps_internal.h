@@ -174,12 +174,11 @@ void sweep_dim(const Geom& g, int nslices, const LineFactors& f, bool fp32, cons
 template <typename Tin, typename T = float>
 void sweep_x_warp(const Geom& g, const LineFactors& f, const Tin* in, T* out, const SourceArgs& sa,
                   cudaStream_t st);
-// FP64 x-substep of nslices states (in may alias out) by chunks of the rows through shared
-// memory, Thomas per thread, bitwise equal to the whole-row sweep (ps_coarse.cu); chunk = 8 or
-// 16 nodes.  Returns false (nothing launched) for rows shorter than 32 nodes or without FP64 x
-// factors.
+// FP64 x-substep of nslices states (in may alias out), Thomas per thread in warp-private
+// chunks through shared memory (ps_coarse.cu), bitwise equal to the whole-row sweep.  Returns
+// false (nothing launched) for rows shorter than 16 nodes or without FP64 x factors.
 bool sweep_x_chunked(const Geom& g, int nslices, const LineFactors& f, const double* in, double* out,
-                     const SourceArgs& sa, cudaStream_t st, int chunk = 16);
+                     const SourceArgs& sa, cudaStream_t st);
 // Coarse-propagator sweep of direction f.m on ONE slice, staged through shared memory
 // (ps_coarse.cu); in may alias out.  T = double: x, y, z (x carries the source, y/z the
 // epilogues of CorrArgs modes 0-2); T = float: y, z with modes 0, 2, 3.  Returns false (nothing
