@@ -177,6 +177,7 @@ class ClockSampler:
 
 
 TILE_KW = {}  # fine tile shape overrides from the command line (tile_positions, tile_slots, ...)
+PROB_KW = {}  # other problem options from the command line (overlap_phases)
 AUTOTUNE = {"on": True, "seconds": 0.0}  # run ps_autotune on each single problem before timing it
 
 
@@ -189,7 +190,7 @@ def make_problem(ps, torch, cfg, precision, timing, coarse_mode="fp64", fine_met
     spc = ps.Splitting(op, cfg["split"], cfg["coarse_boxes"], cfg["coarse_overlap"]) if "coarse_boxes" in cfg \
         else None
     prob = ps.Problem(sp, cfg["T"], cfg["N"], cfg["g"], cfg["s"], coarse=spc, precision=precision, timing=timing,
-                      coarse_mode=coarse_mode, fine_method=fine_method, **TILE_KW)
+                      coarse_mode=coarse_mode, fine_method=fine_method, **TILE_KW, **PROB_KW)
     prob._keep = (grid, op, sp, spc, a, src)
     if tune and AUTOTUNE["on"] and cfg["split"] == "dim" and not any(v not in (0, "auto") for v in TILE_KW.values()):
         t0 = time.perf_counter()
@@ -295,6 +296,7 @@ def config_of(args, cfg):
            "precision": args.precision, "coarse": getattr(args, "coarse", "fp64"),
            "fine": "dr" if getattr(args, "fine", "fie") == "dr" else "fie",
            "tiles": {k: v for k, v in TILE_KW.items() if v not in (0, "auto")} or "auto",
+           **({"overlap_phases": True} if PROB_KW.get("overlap_phases") else {}),
            "l2": (f"inputs larger than L2 ({gb:.1f} GB of slice states streamed per step)" if gb > 0.2 else
                   f"working set {gb * 1e3:.0f} MB fits in L2: latency-bound case, no roofline claim")}
     if cfg["split"] == "dd":
@@ -527,8 +529,12 @@ def main():
     ap.add_argument("--coarse-sweep", default="auto", choices=["auto", "staged", "streamed"],
                     help="coarse line solves on one slice: staged through shared memory or streamed")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default schedules (no ps_autotune)")
+    ap.add_argument("--overlap-phases", action="store_true",
+                    help="run the fine phase slot group by slot group beside the coarse chain (same values)")
     args = ap.parse_args()
     AUTOTUNE["on"] = not args.no_autotune
+    if args.overlap_phases:
+        PROB_KW["overlap_phases"] = True
     TILE_KW.update(tile_positions=args.tile_positions, tile_slots=args.tile_slots,
                    tile_lines_per_thread=args.tile_lines_per_thread, coarse_sweep=args.coarse_sweep)
     if args.warmup < 3:

@@ -443,7 +443,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 template <bool VAR, bool SRC>
-__global__ void __launch_bounds__(32 * XW_WARPS)
+__global__ void __launch_bounds__(32 * XW_WARPS, 8)
     sweep_x_thomas_warp_kernel(const double* in, double* out, long long rows, int nx, int rps,
                                const double* __restrict__ fl, const double* __restrict__ fr, SourceArgs sa) {
   extern __shared__ __align__(16) double xwsm[];
