@@ -119,6 +119,21 @@ struct alignas(sizeof(T) * 4) Quad {
   T q[4];
 };
 
+// The three roundings of a node, written as explicit FMAs so that every kernel that solves a
+// line (one tile per CTA, pipelined chunks, persistent, grouped) computes the same bits:
+//     b + f * ft (source),   y = b - l y,   x = r y - l' x
+template <typename T>
+__device__ __forceinline__ T fmat(T a, T b, T c) {
+  if constexpr (sizeof(T) == 4) return fmaf(a, b, c);
+  else return fma(a, b, c);
+}
+template <typename T>
+__device__ __forceinline__ T rhs_node(T b, T f, T ft) { return fmat(f, ft, b); }
+template <typename T>
+__device__ __forceinline__ T fwd_node(T y, T b, T l) { return fmat(-l, y, b); }
+template <typename T>
+__device__ __forceinline__ T bwd_node(T x, T yv, T r, T ln) { return fmat(-ln, x, r * yv); }
+
 // The two recurrences of the L D L^T solve for V lines (adjacent slots, one thread) held
 // in shared memory, element i of the V lines at x + i*st.  Factors are shared by the V
 // lines and read four at a time; l_0 = 0 and the zero padding past L make the first and
@@ -164,8 +179,8 @@ __device__ __forceinline__ void line_solve(T* x, int st, int L, const T* Lf, con
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         T bb = b[u].v[v];
-        if (SRC) bb = bb + s4.q[u] * ft[v];
-        y[v] = bb - l4.q[u] * y[v];
+        if (SRC) bb = rhs_node(bb, s4.q[u], ft[v]);
+        y[v] = fwd_node(y[v], bb, l4.q[u]);
         b[u].v[v] = y[v];
       }
     }
@@ -178,8 +193,8 @@ __device__ __forceinline__ void line_solve(T* x, int st, int L, const T* Lf, con
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       T bb = b.v[v];
-      if (SRC) bb = bb + S[i] * ft[v];
-      y[v] = bb - li * y[v];
+      if (SRC) bb = rhs_node(bb, S[i], ft[v]);
+      y[v] = fwd_node(y[v], bb, li);
       b.v[v] = y[v];
     }
     *reinterpret_cast<VT*>(x + i * st) = b;
@@ -193,7 +208,7 @@ __device__ __forceinline__ void line_solve(T* x, int st, int L, const T* Lf, con
     const T ri = Rf[i];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      xn[v] = ri * yy.v[v] - lnext * xn[v];
+      xn[v] = bwd_node(xn[v], yy.v[v], ri, lnext);
       yy.v[v] = xn[v];
     }
     *reinterpret_cast<VT*>(x + i * st) = yy;
@@ -226,7 +241,7 @@ __device__ __forceinline__ void line_solve(T* x, int st, int L, const T* Lf, con
       const T l1 = u == 3 ? lnext : l4.q[u + 1];
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        xn[v] = r4.q[u] * yy[u].v[v] - l1 * xn[v];
+        xn[v] = bwd_node(xn[v], yy[u].v[v], r4.q[u], l1);
         yy[u].v[v] = xn[v];
       }
     }
@@ -346,6 +361,214 @@ __global__ void tile_sweep_kernel(const __grid_constant__ CUtensorMap map, TileA
   __syncthreads();
   if (s_abort) return;
   tile_body<T, V, SRC>(&map, a, blockIdx.x, tile, bar, 0, a.t_first);
+}
+
+// One tile by one warp (P = 1, at most 32 threads) with its line chunks pipelined: chunk k of
+// the line lands on its own mbarrier, the forward recurrence starts on chunk 0 while the later
+// chunks are still in flight, and the backward recurrence hands every chunk to a TMA store as
+// soon as its lowest node is final.  Load, solve and store of a tile then overlap instead of
+// following one another, so more of each tile's bytes are moving at any time.  The arithmetic
+// is line_solve's, node for node (the same helpers, the same order).
+template <typename T, int V, bool SRC>
+__device__ __forceinline__ bool tile_body_piped(const CUtensorMap* map, const TileArgs& a, int t, T* tile,
+                                                uint64_t* bars, int t_first) {
+  using VT = VecT<T, V>;
+  using QT = Quad<T>;
+  const int lines = a.TS;
+  const int L = a.L, CH = a.chunk, NC = a.chunks, Lp = a.Lp;
+  T* fl_s = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(tile + (size_t)lines * L) + 31) & ~(uintptr_t)31);
+  T* fr_s = fl_s + Lp;
+  T* src_s = fr_s + Lp;
+  int s0, b0, c;
+  tile_coords(a, t, &s0, &b0, &c);
+  const int lane = threadIdx.x;
+  const unsigned mask = blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
+  if (lane == 0) {
+    for (int k = 0; k < NC; ++k) {
+      const int i0 = k * CH;
+      mbar_expect_tx(&bars[k], (uint32_t)(CH * lines * (int)sizeof(T)) + (k == 0 ? side_bytes<T, SRC>(a, 1) : 0u));
+      if (k == 0) issue_side_loads<T, SRC>(a, b0, c, 1, fl_s, fr_s, src_s, &bars[0]);
+      T* dst = tile + (size_t)i0 * lines;
+      if (a.axis == 0) tma_load_4d(dst, map, &bars[k], s0, i0, b0, c);
+      else if (a.axis == 1) tma_load_4d(dst, map, &bars[k], s0, b0, i0, c);
+      else tma_load_4d(dst, map, &bars[k], s0, b0, c, i0);
+    }
+  }
+  // every lane polls the barriers of the chunks it is about to read; a wait that runs out of
+  // time abandons the tile (no store has been issued by then: stores start in the backward pass)
+  int waited = -1;
+  auto need = [&](int node) -> bool {
+    const int k = node / CH;
+    while (waited < k) {
+      const bool got = mbar_wait(&bars[waited + 1], 0);
+      if (!__all_sync(mask, got)) {
+        if (lane == 0) atomicExch(a.err, 1);
+        return false;
+      }
+      ++waited;
+    }
+    return true;
+  };
+  int stored = NC;  // chunks [stored, NC) are with the TMA engine
+  auto release = [&](int lowest_final) {
+    while (stored > 0 && (stored - 1) * CH >= lowest_final) {
+      --stored;
+      fence_async_smem();
+      __syncwarp(mask);
+      if (lane == 0) {
+        const int i0 = stored * CH;
+        const T* srcp = tile + (size_t)i0 * lines;
+        if (a.axis == 0) tma_store_4d(map, srcp, s0, i0, b0, c);
+        else if (a.axis == 1) tma_store_4d(map, srcp, s0, b0, i0, c);
+        else tma_store_4d(map, srcp, s0, b0, c, i0);
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
+    }
+  };
+  if (!need(0)) return false;  // chunk 0 and the factor / source rows
+  const int sl = lane * V;
+  T ft[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) ft[v] = SRC ? slot_time_factor<T>(a, s0 + sl + v, t_first) : T(0);
+  T* x = tile + sl;
+  const int st = lines;
+  const T* Lf = fl_s;
+  const T* Rf = fr_s;
+  const T* S = src_s;
+  // forward
+  T y[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) y[v] = T(0);
+  const int nq = L / 4;
+  QT l4n{}, s4n{};
+  VT bn[4];
+  if (nq > 0) {
+    if (!need(3)) return false;
+    l4n = *reinterpret_cast<const QT*>(Lf);
+    if (SRC) s4n = *reinterpret_cast<const QT*>(S);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) bn[u] = *reinterpret_cast<const VT*>(x + u * st);
+  }
+  for (int cq = 0; cq < nq; ++cq) {
+    const int i0 = 4 * cq;
+    const QT l4 = l4n;
+    const QT s4 = s4n;
+    VT b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) b[u] = bn[u];
+    if (cq + 1 < nq) {
+      if (!need(i0 + 7)) return false;
+      l4n = *reinterpret_cast<const QT*>(Lf + i0 + 4);
+      if (SRC) s4n = *reinterpret_cast<const QT*>(S + i0 + 4);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) bn[u] = *reinterpret_cast<const VT*>(x + (i0 + 4 + u) * st);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        T bb = b[u].v[v];
+        if (SRC) bb = rhs_node(bb, s4.q[u], ft[v]);
+        y[v] = fwd_node(y[v], bb, l4.q[u]);
+        b[u].v[v] = y[v];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) *reinterpret_cast<VT*>(x + (i0 + u) * st) = b[u];
+  }
+  for (int i = 4 * nq; i < L; ++i) {
+    if (!need(i)) return false;
+    VT b = *reinterpret_cast<const VT*>(x + i * st);
+    const T li = Lf[i];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      T bb = b.v[v];
+      if (SRC) bb = rhs_node(bb, S[i], ft[v]);
+      y[v] = fwd_node(y[v], bb, li);
+      b.v[v] = y[v];
+    }
+    *reinterpret_cast<VT*>(x + i * st) = b;
+  }
+  // backward, releasing chunks to the TMA stores from the top down
+  T xn[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) xn[v] = T(0);
+  T lnext = T(0);
+  for (int i = L - 1; i >= 4 * nq; --i) {
+    VT yy = *reinterpret_cast<const VT*>(x + i * st);
+    const T ri = Rf[i];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      xn[v] = bwd_node(xn[v], yy.v[v], ri, lnext);
+      yy.v[v] = xn[v];
+    }
+    *reinterpret_cast<VT*>(x + i * st) = yy;
+    lnext = Lf[i];
+  }
+  release(4 * nq);
+  QT r4n{};
+  VT yyn[4];
+  if (nq > 0) {
+    const int i0 = 4 * (nq - 1);
+    r4n = *reinterpret_cast<const QT*>(Rf + i0);
+    l4n = *reinterpret_cast<const QT*>(Lf + i0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) yyn[u] = *reinterpret_cast<const VT*>(x + (i0 + u) * st);
+  }
+  for (int cq = nq - 1; cq >= 0; --cq) {
+    const int i0 = 4 * cq;
+    const QT r4 = r4n;
+    const QT l4 = l4n;
+    VT yy[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) yy[u] = yyn[u];
+    if (cq > 0) {
+      r4n = *reinterpret_cast<const QT*>(Rf + i0 - 4);
+      l4n = *reinterpret_cast<const QT*>(Lf + i0 - 4);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) yyn[u] = *reinterpret_cast<const VT*>(x + (i0 - 4 + u) * st);
+    }
+#pragma unroll
+    for (int u = 3; u >= 0; --u) {
+      const T l1 = u == 3 ? lnext : l4.q[u + 1];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        xn[v] = bwd_node(xn[v], yy[u].v[v], r4.q[u], l1);
+        yy[u].v[v] = xn[v];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) *reinterpret_cast<VT*>(x + (i0 + u) * st) = yy[u];
+    lnext = l4.q[0];
+    release(i0);
+  }
+  release(0);
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+  __syncwarp(mask);
+  return true;
+}
+
+// Shared memory: [chunk barriers (up to 16, 128 bytes) | tile ...].
+template <typename T, int V, bool SRC>
+__global__ void tile_sweep_piped_kernel(const __grid_constant__ CUtensorMap map, TileArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  T* tile = reinterpret_cast<T*>(smem_raw + 128);
+  __shared__ int s_abort;
+  if (threadIdx.x == 0) {
+    s_abort = *reinterpret_cast<volatile int*>(a.err);
+    if (smem_addr(tile) & 127) {
+      atomicExch(a.err, 2);
+      s_abort = 1;
+    }
+    if (!s_abort) {
+      for (int k = 0; k < a.chunks; ++k) mbar_init(&bars[k], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
+  __syncthreads();
+  if (s_abort) return;
+  tile_body_piped<T, V, SRC>(&map, a, blockIdx.x, tile, bars, a.t_first);
 }
 
 // Grouped, persistent form: many problems' tiles in one launch.  jobs[j] holds one
@@ -692,10 +915,25 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
     tp.P = 1;
     while (tp.P < 4 && tp.P * 2 <= nb && (size_t)stages * tp.TS * (tp.P * 2) * L * elem <= budget) tp.P *= 2;
   }
+  // lines per thread: one by default (more threads per tile); FP32 threads can take two
+  // adjacent lines (paired 8-byte shared-memory accesses) when asked for
+  tp.V = (elem == 4 && tp.TS >= 32 && vec == 2) ? 2 : 1;
   // a TMA box extent is at most 256: split the line into the fewest equal chunks
   tp.chunks = (L + 255) / 256;
   while (L % tp.chunks) ++tp.chunks;
   tp.chunk = L / tp.chunks;
+  // one-warp tiles of long lines: equal chunks of about 40-80 nodes, each on its own barrier,
+  // so that the solve starts on the first chunk and the stores leave chunk by chunk
+  tp.piped = 0;
+  if (!tp.pipe && tp.P == 1 && L > 128 && tp.TS / tp.V <= 32) {
+    for (int nc = (L + 79) / 80; nc <= 16 && L / nc >= 8; ++nc)
+      if (L % nc == 0) {
+        tp.chunks = nc;
+        tp.chunk = L / nc;
+        tp.piped = 1;
+        break;
+      }
+  }
   // globals: dims (S_pad, nx, ny, nz), strides in bytes of dims 1..3
   cuuint64_t dims[4] = {(cuuint64_t)S_pad, (cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
   cuuint64_t strides[3] = {(cuuint64_t)S_pad * elem, (cuuint64_t)S_pad * elem * g.n[0],
@@ -717,9 +955,6 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
   if (r != CUDA_SUCCESS) throw Error(PS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
   const int lines = tp.TS * tp.P;
   const int Lp = (L + 3) & ~3;
-  // lines per thread: one by default (more threads per tile); FP32 threads can take two
-  // adjacent lines (paired 8-byte shared-memory accesses) when asked for
-  tp.V = (elem == 4 && tp.TS >= 32 && vec == 2) ? 2 : 1;
   // stages x (tile + factor rows l, r) + alignment + barriers; the source, when added, takes
   // one more factor row per position and stage
   tp.smem = (size_t)stages * ((size_t)lines * L * elem + 2 * (size_t)tp.P * Lp * elem + 64) + 64 + 128;
@@ -777,7 +1012,12 @@ void tile_sweep(const Geom& g, const TilePlan& tp, const LineFactors& f, int S_p
   const int stages = tp.pipe ? kPipeStages : 1;
   const int Lp = (tp.L + 3) & ~3;
   const size_t smem = tp.smem + (src ? (size_t)stages * tp.P * Lp * sizeof(T) : 0);
-  if (!tp.pipe) {
+  if (!tp.pipe && tp.piped) {
+    auto kern = tp.V == 2 ? (src ? tile_sweep_piped_kernel<T, 2, true> : tile_sweep_piped_kernel<T, 2, false>)
+                          : (src ? tile_sweep_piped_kernel<T, 1, true> : tile_sweep_piped_kernel<T, 1, false>);
+    PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)tiles, tp.threads, smem, st>>>(tp.map, a);
+  } else if (!tp.pipe) {
     auto kern = tp.V == 2 ? (src ? tile_sweep_kernel<T, 2, true> : tile_sweep_kernel<T, 2, false>)
                           : (src ? tile_sweep_kernel<T, 1, true> : tile_sweep_kernel<T, 1, false>);
     PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

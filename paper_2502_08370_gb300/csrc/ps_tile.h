@@ -13,6 +13,7 @@ struct TilePlan {
   int axis = 0, L = 0, TS = 32, P = 1, chunks = 1, chunk = 0, threads = 0;
   int V = 1;         // adjacent slots (lines) per thread
   int pipe = 1;      // persistent double-buffered CTAs (1) or one tile per CTA (0)
+  int piped = 0;     // one tile per one-warp CTA with its line chunks on separate barriers
   int ctas_per_sm = 1;
   size_t smem = 0;   // dynamic shared memory per CTA without the source staging
 };
