@@ -690,7 +690,7 @@ void configure_slices(ps_problem* p, int N, int g_steps, int f_steps, cudaStream
     if (g3.dim == 2) g3.n[2] = 1;
     for (int m = 0; m < p->g.dim; ++m) {
       tile_plan(g3, p->S_pad, elem, m, p->F.tiles[m], W, p->prm.tile_positions,
-                p->prm.tile_pipeline == 0 ? 0 : (p->prm.tile_pipeline == 1 ? 1 : 0), p->prm.tile_slots,
+                p->prm.tile_pipeline == 1 ? 1 : (p->prm.tile_pipeline == 3 ? 2 : 0), p->prm.tile_slots,
                 p->prm.tile_lines_per_thread);
       factor_lines(g3, *p->F.dim[m], mixed, st);
     }
@@ -1261,7 +1261,7 @@ void rebuild_tiles(ps_problem* p, int slots, int positions, int pipe, int vec) {
   for (int m = 0; m < p->g.dim; ++m) p->F.tiles[m] = tmp[m];
   p->prm.tile_slots = slots;
   p->prm.tile_positions = positions;
-  p->prm.tile_pipeline = pipe ? 1 : 2;
+  p->prm.tile_pipeline = pipe == 1 ? 1 : (pipe == 2 ? 3 : 2);
   p->prm.tile_lines_per_thread = vec;
 }
 }  // namespace
@@ -1321,11 +1321,21 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
       int slots, positions, pipe, vec;
     };
     // slots per tile, line positions per tile, persistent double-buffered CTAs, lines per thread
+    // pipe: 0 one tile per CTA, 1 persistent ring of stages, 2 one tile per one-warp CTA with the
+    // line's chunks pipelined
     std::vector<Cand> cands = {{32, 2, 0, 2}, {32, 1, 0, 2}, {32, 1, 0, 1}, {32, 2, 0, 1}, {64, 1, 0, 2},
-                               {16, 1, 0, 1}, {32, 1, 1, 2}, {32, 1, 1, 1}};
+                               {16, 1, 0, 1}, {32, 1, 1, 2}, {32, 1, 1, 1}, {32, 1, 2, 1}, {32, 1, 2, 2}};
     if (p->batched > 0)  // the grouped kernels of a batch run one tile per item, one line per thread
       cands.erase(std::remove_if(cands.begin(), cands.end(), [](const Cand& c) { return c.pipe || c.vec == 2; }),
                   cands.end());
+    // FP32 tiles need 128-byte rows: 16 slots would run as 32 (a duplicate candidate)
+    if (mixed)
+      cands.erase(std::remove_if(cands.begin(), cands.end(), [](const Cand& c) { return c.slots * 4 < 128; }),
+                  cands.end());
+    auto cand_name = [](const Cand& c) {
+      return "fine:" + std::to_string(c.slots) + "x" + std::to_string(c.positions) + "/v" + std::to_string(c.vec) +
+             (c.pipe == 1 ? "/ring" : c.pipe == 2 ? "/chunks" : "/tile");
+    };
     tile_flag_reset(p, st);
     p->tune_log.clear();
     cudaEvent_t e0, e1;
@@ -1369,8 +1379,7 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
           reps *= 2;
         }
         const float per = ms / reps;
-        p->tune_log.push_back({"fine:" + std::to_string(c.slots) + "x" + std::to_string(c.positions) + "/v" +
-                                   std::to_string(c.vec) + (c.pipe ? "/ring" : "/tile"),
+        p->tune_log.push_back({cand_name(c),
                                per, 0});
         if (per < best) {
           best = per;
@@ -1497,14 +1506,13 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (bestc.slots == 0) {
-      rebuild_tiles(p, old_slots, old_pos, old_pipe == 1 ? 1 : 0, old_vec);
+      rebuild_tiles(p, old_slots, old_pos, old_pipe == 1 ? 1 : (old_pipe == 3 ? 2 : 0), old_vec);
       if (choice_out) *choice_out = coarse_choice * 100000;
       return;
     }
     rebuild_tiles(p, bestc.slots, bestc.positions, bestc.pipe, bestc.vec);
     for (auto& e : p->tune_log)
-      if (e.name == "fine:" + std::to_string(bestc.slots) + "x" + std::to_string(bestc.positions) + "/v" +
-                        std::to_string(bestc.vec) + (bestc.pipe ? "/ring" : "/tile"))
+      if (e.name == cand_name(bestc))
         e.chosen = 1;
     tile_flag_check(p, st);
     // choice code: coarse schedule, lines per thread, slots, positions, pipeline as decimal digits cvSSpq
@@ -1531,7 +1539,8 @@ int ps_autotune_record(const ps_problem* p, ps_tune_entry* out, int cap, int* le
 int ps_copy_schedule(const ps_problem* src, ps_problem* dst) {
   return guarded([&] {
     PS_REQUIRE(src && dst, "null argument");
-    rebuild_tiles(dst, src->prm.tile_slots, src->prm.tile_positions, src->prm.tile_pipeline == 1 ? 1 : 0,
+    rebuild_tiles(dst, src->prm.tile_slots, src->prm.tile_positions,
+                  src->prm.tile_pipeline == 1 ? 1 : (src->prm.tile_pipeline == 3 ? 2 : 0),
                   src->prm.tile_lines_per_thread);
     dst->coarse_staged = src->coarse_staged;
     dst->prm.coarse_sweep = src->prm.coarse_sweep;

@@ -396,23 +396,26 @@ __device__ __forceinline__ bool tile_body_piped(const CUtensorMap* map, const Ti
   }
   // every lane polls the barriers of the chunks it is about to read; a wait that runs out of
   // time abandons the tile (no store has been issued by then: stores start in the backward pass)
-  int waited = -1;
+  // (one compare per four-node group on the fast path: the next chunk's first node is kept)
+  int waited = -1, wait_at = 0;  // chunks [0, waited] have landed; node wait_at starts the next
   auto need = [&](int node) -> bool {
-    const int k = node / CH;
-    while (waited < k) {
+    while (node >= wait_at) {
       const bool got = mbar_wait(&bars[waited + 1], 0);
       if (!__all_sync(mask, got)) {
         if (lane == 0) atomicExch(a.err, 1);
         return false;
       }
       ++waited;
+      wait_at = waited + 1 < NC ? (waited + 1) * CH : 0x7fffffff;
     }
     return true;
   };
-  int stored = NC;  // chunks [stored, NC) are with the TMA engine
+  int stored = NC;                  // chunks [stored, NC) are with the TMA engine
+  int release_at = (NC - 1) * CH;   // first node of chunk stored - 1
   auto release = [&](int lowest_final) {
-    while (stored > 0 && (stored - 1) * CH >= lowest_final) {
+    while (lowest_final <= release_at) {
       --stored;
+      release_at = stored > 0 ? (stored - 1) * CH : -1;
       fence_async_smem();
       __syncwarp(mask);
       if (lane == 0) {
@@ -887,7 +890,8 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
     if ((ts * elem) % 128 == 0 && S_pad % ts == 0) tp.TS = ts;
   }
   PS_REQUIRE((tp.TS * elem) % 128 == 0, "tile rows must be a multiple of 128 bytes");
-  tp.pipe = pipe < 0 ? 1 : pipe;
+  const bool want_chunks = pipe == 2;  // one-warp tiles with the line's chunks pipelined
+  tp.pipe = pipe < 0 ? 1 : (pipe == 2 ? 0 : pipe);
   {
     // long lines: fewer slots per tile (down to 128-byte rows) until one tile fits in shared memory
     int dev = 0, maxsm = 0;
@@ -925,7 +929,7 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
   // one-warp tiles of long lines: equal chunks of about 40-80 nodes, each on its own barrier,
   // so that the solve starts on the first chunk and the stores leave chunk by chunk
   tp.piped = 0;
-  if (!tp.pipe && tp.P == 1 && L > 128 && tp.TS / tp.V <= 32) {
+  if (want_chunks && !tp.pipe && tp.P == 1 && L > 128 && tp.TS / tp.V <= 32) {
     for (int nc = (L + 79) / 80; nc <= 16 && L / nc >= 8; ++nc)
       if (L % nc == 0) {
         tp.chunks = nc;

@@ -19,7 +19,8 @@ struct TilePlan {
 };
 
 // positions: 1, 2 or 4 line positions per tile (0 = largest that fits); pipe: 1 persistent
-// double-buffered, 0 one tile per CTA, -1 auto.
+// double-buffered, 0 one tile per CTA, 2 one tile per one-warp CTA with the line's chunks
+// pipelined (lines longer than 128 nodes, one position; else as 0), -1 auto.
 void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void* W, int positions = 0, int pipe = -1,
                int slots = 0, int vec = 0);
 // One substep along tp.axis on slots [s_first, s_first + nsl) (whole TS-slot groups are
