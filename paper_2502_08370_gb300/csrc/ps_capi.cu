@@ -1328,10 +1328,6 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
     if (p->batched > 0)  // the grouped kernels of a batch run one tile per item, one line per thread
       cands.erase(std::remove_if(cands.begin(), cands.end(), [](const Cand& c) { return c.pipe || c.vec == 2; }),
                   cands.end());
-    // FP32 tiles need 128-byte rows: 16 slots would run as 32 (a duplicate candidate)
-    if (mixed)
-      cands.erase(std::remove_if(cands.begin(), cands.end(), [](const Cand& c) { return c.slots * 4 < 128; }),
-                  cands.end());
     auto cand_name = [](const Cand& c) {
       return "fine:" + std::to_string(c.slots) + "x" + std::to_string(c.positions) + "/v" + std::to_string(c.vec) +
              (c.pipe == 1 ? "/ring" : c.pipe == 2 ? "/chunks" : "/tile");
@@ -1356,6 +1352,7 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
         } catch (const Error&) {
           continue;  // shape does not fit this grid / precision
         }
+        if (p->F.tiles[0].TS != c.slots) continue;  // the plan could not take these slots: a duplicate
         auto sweep_all = [&]() {
           for (int m = 0; m < M; ++m) {
             if (mixed)

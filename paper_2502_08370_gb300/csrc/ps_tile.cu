@@ -877,19 +877,24 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
   const int L = g.n[axis];
   tp.axis = axis;
   tp.L = L;
-  // slots per tile: 256-byte rows of slots when the slot count allows, else 128-byte rows
-  // 32 slots per tile (128-byte rows in FP32, 256-byte rows in FP64): measured best on
-  // 255^3 x 64 slices among 16/32/64 slots and 1/2/4 positions
+  // slots per tile by default: 32 (128-byte rows in FP32, 256-byte rows in FP64)
   tp.TS = S_pad % 32 == 0 ? 32 : 128 / elem;
+  bool short_rows = false;
   if (slots > 0) {
-    // requested slots per tile: a divisor of S_pad whose rows are a multiple of 128 bytes,
-    // so that every TMA destination in the tile (rows, positions, chunks) is 128-byte
-    // aligned as tensor copies require
+    // requested slots per tile: a divisor of S_pad whose rows are a multiple of 128 bytes, so
+    // that every TMA destination in the tile (rows, positions, chunks) is 128-byte aligned as
+    // tensor copies require -- or shorter rows (16-byte multiples) for tiles of a single box
+    // (one position, lines of at most 256 nodes), whose only destination is the tile's start
     int ts = slots;
     while (ts > 1 && S_pad % ts != 0) ts /= 2;
-    if ((ts * elem) % 128 == 0 && S_pad % ts == 0) tp.TS = ts;
+    if (S_pad % ts == 0 && (ts * elem) % 128 == 0) {
+      tp.TS = ts;
+    } else if (S_pad % ts == 0 && (ts * elem) % 16 == 0 && L <= 256 && positions <= 1 && pipe != 1) {
+      tp.TS = ts;
+      short_rows = true;
+    }
   }
-  PS_REQUIRE((tp.TS * elem) % 128 == 0, "tile rows must be a multiple of 128 bytes");
+  PS_REQUIRE((tp.TS * elem) % 128 == 0 || short_rows, "tile rows must be a multiple of 128 bytes");
   const bool want_chunks = pipe == 2;  // one-warp tiles with the line's chunks pipelined
   tp.pipe = pipe < 0 ? 1 : (pipe == 2 ? 0 : pipe);
   {
@@ -899,7 +904,7 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
     PS_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const int Lp4 = (L + 3) & ~3;
     const int st = tp.pipe ? kPipeStages : 1;
-    while (tp.TS * elem > 128 && S_pad % (tp.TS / 2) == 0 &&
+    while (!short_rows && tp.TS * elem > 128 && S_pad % (tp.TS / 2) == 0 &&
            (size_t)st * ((size_t)tp.TS * L * elem + 3 * (size_t)Lp4 * elem + 64) + 512 > (size_t)maxsm)
       tp.TS /= 2;
   }
@@ -907,7 +912,9 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
   // per CTA, so that 2 (ring of stages) or 2-3 (one tile) CTAs share an SM
   const size_t budget = tp.pipe ? 110 * 1024 : 96 * 1024;
   const int nb = g.n[axis == 0 ? 1 : 0];  // the paired axis: y for x-lines, x otherwise
-  if (positions > 0) {
+  if (short_rows) {
+    tp.P = 1;  // one box per tile
+  } else if (positions > 0) {
     tp.P = positions >= 4 ? 4 : (positions >= 2 ? 2 : 1);
     // fewer positions when the paired axis is short or the stages would not fit in shared memory
     while (tp.P > 1 && (tp.P > nb || (size_t)stages * tp.TS * tp.P * L * elem > 200 * 1024)) tp.P /= 2;
@@ -929,7 +936,7 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
   // one-warp tiles of long lines: equal chunks of about 40-80 nodes, each on its own barrier,
   // so that the solve starts on the first chunk and the stores leave chunk by chunk
   tp.piped = 0;
-  if (want_chunks && !tp.pipe && tp.P == 1 && L > 128 && tp.TS / tp.V <= 32) {
+  if (want_chunks && !short_rows && !tp.pipe && tp.P == 1 && L > 128 && tp.TS / tp.V <= 32) {
     for (int nc = (L + 79) / 80; nc <= 16 && L / nc >= 8; ++nc)
       if (L % nc == 0) {
         tp.chunks = nc;
