@@ -51,7 +51,6 @@ struct ps_batch {
   DevBuf<int> flag, tmo;
   size_t tile_smem = 0;
   int tile_threads = 0;
-  size_t x_smem = 0;
   int sms = 152;
   cudaStream_t cs = nullptr;
   cudaGraphExec_t iter_graph = nullptr, init_graph = nullptr;
@@ -97,11 +96,6 @@ int bguarded(F&& f) {
   }
 }
 
-int x_rows_per_block(int nx) {
-  const int ld = (nx % 2) ? nx : nx + 1;
-  return std::max(1, std::min(256, 96 * 1024 / (ld * 8)));
-}
-
 CoarseJob coarse_job(ps_batch* b, int i, int n) {
   ps_problem* p = b->probs[i];
   CoarseJob j{};
@@ -112,8 +106,6 @@ CoarseJob coarse_job(ps_batch* b, int i, int n) {
   j.ny = p->g.n[1];
   j.rows = p->g.n[1];
   j.nt = nt;
-  j.ld = (j.nx % 2) ? j.nx : j.nx + 1;
-  j.R = x_rows_per_block(j.nx);
   j.lx = p->G.dim[0]->l64.p;
   j.rx = p->G.dim[0]->r64.p;
   j.ly = p->G.dim[1]->l64.p;
@@ -155,7 +147,7 @@ void fill_coarse_tables(ps_batch* b, const std::vector<int>& active, int k) {
         ps_problem* p = b->probs[i];
         if (p->N <= n) break;
         b->h_cjobs[(size_t)n * P + cnt] = coarse_job(b, i, n);
-        int bx = (p->g.n[1] + x_rows_per_block(p->g.n[0]) - 1) / x_rows_per_block(p->g.n[0]);
+        int bx = (p->g.n[1] + coarse_x_grouped_rows() - 1) / coarse_x_grouped_rows();
         if (b->delta32) {
           // the increment form, as the problem's own run_G32: x by warp rows (eight per item)
           // from U_n with the source (initial sweep) or from the FP32 increment, y in place on
@@ -188,7 +180,7 @@ void fill_coarse_tables(ps_batch* b, const std::vector<int>& active, int k) {
             cj.ca.dnext = p->d32.p;
           }
         }
-        const int by = (p->g.n[0] + 255) / 256;
+        const int by = (p->g.n[0] + coarse_y_grouped_lines() - 1) / coarse_y_grouped_lines();
         b->h_xsegs[(size_t)n * P + cnt] = WorkSeg{cnt, 0, bx, px};  // job index within step n
         b->h_ysegs[(size_t)n * P + cnt] = WorkSeg{cnt, 0, by, py};
         px += bx;
@@ -309,7 +301,7 @@ int enqueue_sequence(ps_batch* b, int mode, cudaStream_t st) {
       continue;
     }
     coarse_x_grouped(b->var, b->cjobs.p + (size_t)n * P, b->xsegs.p + (size_t)n * P, b->nseg_misc.p + 3 + n, grid,
-                     b->x_smem, st);
+                     st);
     coarse_y_grouped(b->var, mode, b->cjobs.p + (size_t)n * P, b->ysegs.p + (size_t)n * P, b->nseg_misc.p + 3 + n,
                      grid, st);
     n_launch += 2;
@@ -364,7 +356,7 @@ void batch_layout(ps_batch* b) {
   const int P = (int)b->probs.size();
   b->count = P;
   b->maxS = b->maxN = 0;
-  b->tile_smem = b->x_smem = 0;
+  b->tile_smem = 0;
   b->tile_threads = 0;
   b->var = P > 0 ? b->probs[0]->op->a.p != nullptr : true;
   b->delta32 = P > 0 && b->probs[0]->delta32;
@@ -381,9 +373,6 @@ void batch_layout(ps_batch* b) {
     // the grouped kernel runs one line per thread, whatever the plan's own split
     b->tile_threads = std::max(b->tile_threads, std::max(p->F.tiles[0].TS * p->F.tiles[0].P,
                                                          p->F.tiles[1].TS * p->F.tiles[1].P));
-    const int nx = p->g.n[0];
-    const int ld = (nx % 2) ? nx : nx + 1;
-    b->x_smem = std::max(b->x_smem, (size_t)x_rows_per_block(nx) * ld * sizeof(double));
   }
   b->tile_threads = (b->tile_threads + 31) / 32 * 32;
   if (b->iter_graph) {

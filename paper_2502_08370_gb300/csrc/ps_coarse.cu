@@ -442,16 +442,16 @@ constexpr size_t kXwSmem = (size_t)XW_WARPS * (XW_WARP_DOUBLES + 32) * sizeof(do
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+// Rows [row0, row0 + 32) of one x-sweep by one warp; wsm: the warp's XW_WARP_DOUBLES + 32
+// doubles of shared memory.  Every copy of the warp is complete when it returns.
 template <bool VAR, bool SRC>
-__global__ void __launch_bounds__(32 * XW_WARPS, 8)
-    sweep_x_thomas_warp_kernel(const double* in, double* out, long long rows, int nx, int rps,
-                               const double* __restrict__ fl, const double* __restrict__ fr, SourceArgs sa) {
-  extern __shared__ __align__(16) double xwsm[];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  double* ub = xwsm + w * (XW_WARP_DOUBLES + 32);  // [stage][32][XW_P]: u, then y, then x
-  double* sb = ub + 2 * 32 * XW_P;                 // [stage][32][XW_P]: source
+__device__ __forceinline__ void x_thomas_warp_rows(const double* in, double* out, long long rows, int nx, int rps,
+                                                   const double* __restrict__ fl, const double* __restrict__ fr,
+                                                   const SourceArgs& sa, long long row0, double* wsm) {
+  const int lane = threadIdx.x & 31;
+  double* ub = wsm;                  // [stage][32][XW_P]: u, then y, then x
+  double* sb = ub + 2 * 32 * XW_P;   // [stage][32][XW_P]: source
   long long* soff = reinterpret_cast<long long*>(sb + 2 * 32 * XW_P);  // [32]: source row offsets
-  const long long row0 = ((long long)blockIdx.x * XW_WARPS + w) * 32;
   if (row0 >= rows) return;  // the whole warp: nothing below waits on another warp
   const long long myrow = row0 + lane;
   const bool active = myrow < rows;
@@ -563,6 +563,46 @@ __global__ void __launch_bounds__(32 * XW_WARPS, 8)
       rc[j] = rn[j];
       lc[j] = ln[j];
     }
+  }
+}
+
+template <bool VAR, bool SRC>
+__global__ void __launch_bounds__(32 * XW_WARPS, 8)
+    sweep_x_thomas_warp_kernel(const double* in, double* out, long long rows, int nx, int rps,
+                               const double* __restrict__ fl, const double* __restrict__ fr, SourceArgs sa) {
+  extern __shared__ __align__(16) double xwsm[];
+  const int w = threadIdx.x >> 5;
+  x_thomas_warp_rows<VAR, SRC>(in, out, rows, nx, rps, fl, fr, sa, ((long long)blockIdx.x * XW_WARPS + w) * 32,
+                               xwsm + w * (XW_WARP_DOUBLES + 32));
+}
+
+// Grouped coarse x-sweeps (batched 2-D problems, FP64): an item is 32 * XW_WARPS rows of one job.
+template <bool VAR>
+__global__ void __launch_bounds__(32 * XW_WARPS, 8)
+    sweep_x_warp_grouped_kernel(const CoarseJob* __restrict__ jobs, const WorkSeg* __restrict__ segs,
+                                const int* __restrict__ nseg_ptr) {
+  extern __shared__ __align__(16) double xwsm[];
+  const int w = threadIdx.x >> 5;
+  const int nseg = *nseg_ptr;
+  if (nseg <= 0) return;
+  const long long total = (long long)segs[nseg - 1].prefix + segs[nseg - 1].count;
+  for (long long it = blockIdx.x; it < total; it += gridDim.x) {
+    int lo = 0, hi = nseg - 1;  // the last segment whose prefix is <= it
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (segs[mid].prefix <= it) lo = mid;
+      else hi = mid - 1;
+    }
+    const WorkSeg sg = segs[lo];
+    const CoarseJob& j = jobs[sg.job];
+    const long long row0 = ((sg.first + (it - sg.prefix)) * XW_WARPS + w) * 32;
+    if (j.sa.src)
+      x_thomas_warp_rows<VAR, true>(j.xin, j.xout, j.rows, j.nx, (int)j.rows, j.lx, j.rx, j.sa, row0,
+                                    xwsm + w * (XW_WARP_DOUBLES + 32));
+    else
+      x_thomas_warp_rows<VAR, false>(j.xin, j.xout, j.rows, j.nx, (int)j.rows, j.lx, j.rx, j.sa, row0,
+                                     xwsm + w * (XW_WARP_DOUBLES + 32));
+    __syncwarp();
   }
 }
 
@@ -712,5 +752,13 @@ bool sweep_x_chunked(const Geom& g, int nslices, const LineFactors& f, const dou
   }
   PS_CUDA(cudaGetLastError());
   return true;
+}
+int coarse_x_grouped_rows() { return 32 * XW_WARPS; }
+
+void coarse_x_grouped(bool var, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
+                      cudaStream_t st) {
+  if (var) sweep_x_warp_grouped_kernel<true><<<grid, 32 * XW_WARPS, kXwSmem, st>>>(jobs, segs, nseg);
+  else sweep_x_warp_grouped_kernel<false><<<grid, 32 * XW_WARPS, kXwSmem, st>>>(jobs, segs, nseg);
+  PS_CUDA(cudaGetLastError());
 }
 }  // namespace ps

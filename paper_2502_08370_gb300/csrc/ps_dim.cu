@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "ps_internal.h"
 
@@ -466,23 +467,27 @@ __global__ void __launch_bounds__(kThreads) sweep_strided_kernel(const Tin* in, 
 }
 
 // ---------------------------------------------------------------------------------------
-// FP64 y/z-substep without source, the loads pipelined through shared memory: the same
-// operations in the same order as sweep_strided_body, so the two give the same bits.  Each
+// y/z-substep without source (FP64, or FP32 for the coarse increment form), the loads pipelined
+// through shared memory: the same operations in the same order as sweep_strided_body, so the
+// two give the same bits.  Each
 // thread copies its own line's next chunk (right-hand side or stored y, factors, and the
 // correction's Gold / Fout / old U_{n+1}) with cp.async into its column of a node-major
 // [array][j][t] stage while it runs the recurrences on the current chunk; no other thread
 // reads that column, so the thread's own wait_group is the only synchronisation.  Every copy
-// and store of a warp is one 256-byte row segment.  On GB300 the FP64 pipe, not HBM, sets the
+// and store of a warp is one 128- or 256-byte row segment.  On GB300 the FP64 pipe, not HBM, sets the
 // pace of these sweeps (6 FP64 operations per node with the correction, against 56 bytes):
 // the point is to keep every line's next loads in flight so that the pipe never waits on
 // memory, with one wave of 4 CTAs x 128 lines per SM.
 constexpr int SC_T = 128;
-constexpr int SC_NS = 3;        // stages: the copies run two chunks ahead of the recurrences
-constexpr int SC_STAGE = 2048;  // doubles per stage: 8 x 2 x 128 (forward), 2..16 x up to 6 x 128 (backward)
-constexpr size_t kScSmem = SC_NS * SC_STAGE * sizeof(double);
+constexpr int SC_NS = 3;                // stages: the copies run two chunks ahead of the recurrences
+constexpr int SC_STAGE_BYTES = 16384;   // per stage and CTA
+constexpr size_t kScSmem = (size_t)SC_NS * SC_STAGE_BYTES;
 
-__device__ __forceinline__ void cpa8(double* dst, const double* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+template <typename E>
+__device__ __forceinline__ void cpa(E* dst, const E* src) {
+  static_assert(sizeof(E) == 4 || sizeof(E) == 8, "4- or 8-byte elements");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src),
+               "n"(sizeof(E))
                : "memory");
 }
 __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
@@ -490,17 +495,23 @@ __device__ __forceinline__ void cpa_wait_ahead() {
   asm volatile("cp.async.wait_group %0;" ::"n"(SC_NS - 1) : "memory");
 }
 
-template <bool VAR, int EPI>
-__global__ void __launch_bounds__(SC_T, 4)
-    sweep_strided_chunk_kernel(const double* in, double* out, double* tmp, long long lines, int nm, long long S,
-                               long long nt, const double* __restrict__ fl, const double* __restrict__ fr,
-                               CorrArgs ca) {
-  extern __shared__ __align__(16) double csm[];
-  constexpr int CF = SC_STAGE / ((VAR ? 2 : 1) * SC_T);   // forward chunk: u (+ l)
-  constexpr int NB = 1 + (VAR ? 2 : 0) + (EPI == 1 ? 3 : EPI == 3 ? 2 : 0);  // backward arrays
-  constexpr int CB = SC_STAGE / (NB * SC_T) < 24 ? SC_STAGE / (NB * SC_T) : 24;
+// Lines [blk * SC_T, blk * SC_T + SC_T) of one sweep.  T: the recurrences' type (right-hand
+// side, y, x, factors); the correction's arrays (Gold, Fout, old U_{n+1}) are FP64.  csm:
+// SC_NS stages of SC_STAGE_BYTES, each laid out as the sweep arrays [a][j][t] of T, then the
+// correction arrays [e][j][t] of double.  Thread t touches only its own columns, and all its
+// copies are complete when it returns.
+template <typename T, bool VAR, int EPI>
+__device__ __forceinline__ void strided_chunk_lines(long long blk, const T* in, T* out, T* tmp, long long lines,
+                                                    int nm, long long S, long long nt, const T* __restrict__ fl,
+                                                    const T* __restrict__ fr, const CorrArgs& ca,
+                                                    unsigned char* csm) {
+  constexpr int CF = SC_STAGE_BYTES / ((VAR ? 2 : 1) * SC_T * (int)sizeof(T));  // forward chunk: u (+ l)
+  constexpr int NSB = 1 + (VAR ? 2 : 0);                                        // y (+ r, l)
+  constexpr int NEB = EPI == 1 ? 3 : EPI == 3 ? 2 : 0;                          // Gold, Fout, old U
+  constexpr int CBr = SC_STAGE_BYTES / (SC_T * (NSB * (int)sizeof(T) + NEB * 8));
+  constexpr int CB = CBr < 24 ? CBr : 24;                                       // backward chunk
   const int tid = threadIdx.x;
-  const long long L = (long long)blockIdx.x * SC_T + tid;
+  const long long L = blk * SC_T + tid;
   const bool active = L < lines;
   long long base = 0, pos = 0;
   if (active) {
@@ -508,26 +519,26 @@ __global__ void __launch_bounds__(SC_T, 4)
     base = outer * S * nm + (L - outer * S);
     pos = base - (base / nt) * nt;
   }
-  const double* Lf = fl + (VAR ? pos : 0);
-  const double* Rf = fr + (VAR ? pos : 0);
+  const T* Lf = fl + (VAR ? pos : 0);
+  const T* Rf = fr + (VAR ? pos : 0);
   const long long fs = VAR ? S : 1;
   unsigned long long my_inc = 0, my_norm = 0;
   bool bad = false;
   // forward  y_i = b_i - l_i y_{i-1}, stored to tmp
   const int nchF = (nm + CF - 1) / CF;
   auto stage_f = [&](int k) {
-    double* st = csm + (k % SC_NS) * SC_STAGE;
+    T* st = reinterpret_cast<T*>(csm + (k % SC_NS) * SC_STAGE_BYTES);
     if (active)
       for (int j = 0; j < CF; ++j) {
         const int i = k * CF + j;
         if (i < nm) {
-          cpa8(st + j * SC_T + tid, in + base + i * S);
-          if (VAR) cpa8(st + (CF + j) * SC_T + tid, Lf + i * fs);
+          cpa(st + j * SC_T + tid, in + base + i * S);
+          if (VAR) cpa(st + (CF + j) * SC_T + tid, Lf + i * fs);
         }
       }
     cpa_commit();
   };
-  double y = 0.0;
+  T y = T(0);
   for (int k = 0; k < SC_NS - 1; ++k) {
     if (k < nchF) stage_f(k);
     else cpa_commit();
@@ -539,14 +550,14 @@ __global__ void __launch_bounds__(SC_T, 4)
     else cpa_commit();
     cpa_wait_ahead();
     if (active) {
-      const double* st = csm + (k % SC_NS) * SC_STAGE;
+      const T* st = reinterpret_cast<const T*>(csm + (k % SC_NS) * SC_STAGE_BYTES);
       const int len = min(CF, nm - k * CF);
 #pragma unroll
       for (int j = 0; j < CF; ++j) {
         if (j < len) {
           const int i = k * CF + j;
-          const double b = st[j * SC_T + tid];
-          const double l = VAR ? st[(CF + j) * SC_T + tid] : Lf[i * fs];
+          const T b = st[j * SC_T + tid];
+          const T l = VAR ? st[(CF + j) * SC_T + tid] : Lf[i * fs];
           y = i == 0 ? b : fma(-l, y, b);
           tmp[base + i * S] = y;
         }
@@ -556,30 +567,30 @@ __global__ void __launch_bounds__(SC_T, 4)
   // backward  x_i = r_i y_i - l_{i+1} x_{i+1}, nodes from the end, with the epilogue
   const int nchB = (nm + CB - 1) / CB;
   auto stage_b = [&](int k) {
-    double* st = csm + (k % SC_NS) * SC_STAGE;
+    T* st = reinterpret_cast<T*>(csm + (k % SC_NS) * SC_STAGE_BYTES);
+    double* se = reinterpret_cast<double*>(st + NSB * CB * SC_T);
     if (active)
       for (int j = 0; j < CB; ++j) {
         const int i = nm - 1 - (k * CB + j);
         if (i >= 0) {
-          int a = 0;
-          cpa8(st + (a++ * CB + j) * SC_T + tid, tmp + base + i * S);
+          cpa(st + j * SC_T + tid, tmp + base + i * S);
           if (VAR) {
-            cpa8(st + (a++ * CB + j) * SC_T + tid, Rf + i * fs);
-            if (i + 1 < nm) cpa8(st + (a * CB + j) * SC_T + tid, Lf + (i + 1) * fs);
-            ++a;
+            cpa(st + (CB + j) * SC_T + tid, Rf + i * fs);
+            if (i + 1 < nm) cpa(st + (2 * CB + j) * SC_T + tid, Lf + (i + 1) * fs);
           }
           const long long si = pos + (long long)i * S;
-          if (EPI == 1) cpa8(st + (a++ * CB + j) * SC_T + tid, ca.Gold + si);
+          int e = 0;
+          if (EPI == 1) cpa(se + (e++ * CB + j) * SC_T + tid, ca.Gold + si);
           if (EPI == 1 || EPI == 3) {
-            cpa8(st + (a++ * CB + j) * SC_T + tid, ca.Fout + si);
-            cpa8(st + (a++ * CB + j) * SC_T + tid, ca.U_next + si);
+            cpa(se + (e++ * CB + j) * SC_T + tid, ca.Fout + si);
+            cpa(se + (e++ * CB + j) * SC_T + tid, ca.U_next + si);
           }
         }
       }
     cpa_commit();
   };
   // y_{nm-1} is read back like every other y: the stored value is the register's
-  double xn = 0.0;
+  T xn = T(0);
   for (int k = 0; k < SC_NS - 1; ++k) {
     if (k < nchB) stage_b(k);
     else cpa_commit();
@@ -589,41 +600,43 @@ __global__ void __launch_bounds__(SC_T, 4)
     else cpa_commit();
     cpa_wait_ahead();
     if (active) {
-      const double* st = csm + (k % SC_NS) * SC_STAGE;
+      const T* st = reinterpret_cast<const T*>(csm + (k % SC_NS) * SC_STAGE_BYTES);
+      const double* se = reinterpret_cast<const double*>(st + NSB * CB * SC_T);
 #pragma unroll
       for (int j = 0; j < CB; ++j) {
         const int i = nm - 1 - (k * CB + j);
         if (i >= 0) {
-          int a = 0;
-          const double yy = st[(a++ * CB + j) * SC_T + tid];
-          double r, l;
+          const T yy = st[j * SC_T + tid];
+          T r, l;
           if (VAR) {
-            r = st[(a++ * CB + j) * SC_T + tid];
-            l = i + 1 < nm ? st[(a * CB + j) * SC_T + tid] : 0.0;
-            ++a;
+            r = st[(CB + j) * SC_T + tid];
+            l = i + 1 < nm ? st[(2 * CB + j) * SC_T + tid] : T(0);
           } else {
             r = Rf[i * fs];
-            l = i + 1 < nm ? Lf[(i + 1) * fs] : 0.0;
+            l = i + 1 < nm ? Lf[(i + 1) * fs] : T(0);
           }
           xn = i == nm - 1 ? r * yy : fma(-l, xn, r * yy);
           const long long si = pos + (long long)i * S;
+          const double g = (double)xn;
+          int e = 0;
           if (EPI == 0) {
             out[base + i * S] = xn;
           } else if (EPI == 1) {
-            const double go = st[(a++ * CB + j) * SC_T + tid];
-            const double fo = st[(a++ * CB + j) * SC_T + tid];
-            const double uo = st[(a++ * CB + j) * SC_T + tid];
-            const double unew = fo + (xn - go);
+            const double go = se[(e++ * CB + j) * SC_T + tid];
+            const double fo = se[(e++ * CB + j) * SC_T + tid];
+            const double uo = se[(e++ * CB + j) * SC_T + tid];
+            const double unew = fo + (g - go);
             const unsigned long long an = abs_bits(unew);
             bad |= an >= kInfBits;
             my_inc = max(my_inc, abs_bits(unew - uo));
             my_norm = max(my_norm, an);
-            ca.Gold[si] = xn;
+            ca.Gold[si] = g;
             ca.U_next[si] = unew;
           } else if (EPI == 3) {
-            const double fo = st[(a++ * CB + j) * SC_T + tid];
-            const double uo = st[(a++ * CB + j) * SC_T + tid];
-            const double unew = fo + xn;
+            // G is affine, so G(U^k) - G(U^{k-1}) is its linear part applied to the increment
+            const double fo = se[(e++ * CB + j) * SC_T + tid];
+            const double uo = se[(e++ * CB + j) * SC_T + tid];
+            const double unew = fo + g;
             const double d = unew - uo;
             const unsigned long long an = abs_bits(unew);
             bad |= an >= kInfBits;
@@ -632,9 +645,9 @@ __global__ void __launch_bounds__(SC_T, 4)
             ca.U_next[si] = unew;
             ca.dnext[si] = (float)d;
           } else {
-            bad |= abs_bits(xn) >= kInfBits;
-            if (ca.Gold) ca.Gold[si] = xn;
-            ca.U_next[si] = xn;
+            bad |= abs_bits(g) >= kInfBits;
+            if (ca.Gold) ca.Gold[si] = g;
+            ca.U_next[si] = g;
           }
         }
       }
@@ -656,6 +669,14 @@ __global__ void __launch_bounds__(SC_T, 4)
   }
 }
 
+template <typename T, bool VAR, int EPI>
+__global__ void __launch_bounds__(SC_T, 4)
+    sweep_strided_chunk_kernel(const T* in, T* out, T* tmp, long long lines, int nm, long long S, long long nt,
+                               const T* __restrict__ fl, const T* __restrict__ fr, CorrArgs ca) {
+  extern __shared__ __align__(16) unsigned char csm[];
+  strided_chunk_lines<T, VAR, EPI>(blockIdx.x, in, out, tmp, lines, nm, S, nt, fl, fr, ca, csm);
+}
+
 // ---------------------------------------------------------------------------------------
 // Grouped coarse steps (batched problems, 2-D, FP64, no source): one launch runs the same
 // sweep of many problems' coarse step n.  jobs[j] describes problem j's sweep; the first
@@ -670,41 +691,20 @@ __device__ __forceinline__ int find_segment(const WorkSeg* segs, int nseg, long 
   return lo;
 }
 
-template <bool VAR>
-__global__ void __launch_bounds__(kThreads) sweep_x_grouped_kernel(const CoarseJob* __restrict__ jobs,
-                                                                  const WorkSeg* __restrict__ segs,
-                                                                  const int* __restrict__ nseg_ptr) {
-  extern __shared__ unsigned char smem_raw[];
-  const int nseg = *nseg_ptr;
-  if (nseg <= 0) return;
-  const long long total = (long long)segs[nseg - 1].prefix + segs[nseg - 1].count;
-  for (long long it = blockIdx.x; it < total; it += gridDim.x) {
-    const WorkSeg sg = segs[find_segment(segs, nseg, it)];
-    const CoarseJob& j = jobs[sg.job];
-    if (j.sa.src)
-      sweep_x_body<double, double, double, VAR, true>(sg.first + (it - sg.prefix), reinterpret_cast<double*>(smem_raw),
-                                                      j.xin, j.xout, j.rows, j.nx, j.ld, j.R, j.rows, j.lx, j.rx, j.sa);
-    else
-      sweep_x_body<double, double, double, VAR, false>(sg.first + (it - sg.prefix), reinterpret_cast<double*>(smem_raw),
-                                                       j.xin, j.xout, j.rows, j.nx, j.ld, j.R, j.rows, j.lx, j.rx,
-                                                       SourceArgs{});
-    __syncthreads();  // the next item reuses the shared rows
-  }
-}
 
 template <bool VAR, int EPI>
-__global__ void __launch_bounds__(kThreads) sweep_y_grouped_kernel(const CoarseJob* __restrict__ jobs,
+__global__ void __launch_bounds__(SC_T, 4) sweep_y_grouped_kernel(const CoarseJob* __restrict__ jobs,
                                                                   const WorkSeg* __restrict__ segs,
                                                                   const int* __restrict__ nseg_ptr) {
+  extern __shared__ __align__(16) unsigned char csm[];
   const int nseg = *nseg_ptr;
   if (nseg <= 0) return;
   const long long total = (long long)segs[nseg - 1].prefix + segs[nseg - 1].count;
   for (long long it = blockIdx.x; it < total; it += gridDim.x) {
     const WorkSeg sg = segs[find_segment(segs, nseg, it)];
     const CoarseJob& j = jobs[sg.job];
-    sweep_strided_body<double, double, double, VAR, false, EPI, true>(sg.first + (it - sg.prefix), j.xout, j.xout,
-                                                                      j.xout,
-                                                                j.nx, j.ny, j.nx, j.nt, j.ly, j.ry, SourceArgs{}, j.ca);
+    strided_chunk_lines<double, VAR, EPI>(sg.first + (it - sg.prefix), j.xout, j.xout, j.xout, j.nx, j.ny, j.nx,
+                                          j.nt, j.ly, j.ry, j.ca, csm);
   }
 }
 
@@ -744,18 +744,18 @@ __global__ void __launch_bounds__(256) sweep_x32_grouped_kernel(const XWarpJob* 
 }
 
 template <bool VAR, int EPI>
-__global__ void __launch_bounds__(kThreads) sweep_y32_grouped_kernel(const CoarseJob* __restrict__ jobs,
+__global__ void __launch_bounds__(SC_T, 4) sweep_y32_grouped_kernel(const CoarseJob* __restrict__ jobs,
                                                                     const WorkSeg* __restrict__ segs,
                                                                     const int* __restrict__ nseg_ptr) {
+  extern __shared__ __align__(16) unsigned char csm[];
   const int nseg = *nseg_ptr;
   if (nseg <= 0) return;
   const long long total = (long long)segs[nseg - 1].prefix + segs[nseg - 1].count;
   for (long long it = blockIdx.x; it < total; it += gridDim.x) {
     const WorkSeg sg = segs[find_segment(segs, nseg, it)];
     const CoarseJob& j = jobs[sg.job];
-    sweep_strided_body<float, float, float, VAR, false, EPI, true>(sg.first + (it - sg.prefix), j.g32, j.g32, j.g32,
-                                                                   j.nx, j.ny, j.nx, j.nt, j.ly32, j.ry32,
-                                                                   SourceArgs{}, j.ca);
+    strided_chunk_lines<float, VAR, EPI>(sg.first + (it - sg.prefix), j.g32, j.g32, j.g32, j.nx, j.ny, j.nx, j.nt,
+                                         j.ly32, j.ry32, j.ca, csm);
   }
 }
 
@@ -859,11 +859,12 @@ void launch_strided(const Geom& g, int m, int nslices, const Tc* fl, const Tc* f
   const int nm = g.n[m];
   const long long S = g.stride(m);
   const long long lines = (g.nt / nm) * nslices;
-  if constexpr (sizeof(Tin) == 8 && sizeof(Tout) == 8 && sizeof(Tc) == 8 && !SRC && EPI != 3) {
+  if constexpr (std::is_same<Tin, Tc>::value && std::is_same<Tout, Tc>::value && !SRC &&
+                (sizeof(Tc) == 8 ? EPI != 3 : EPI != 1)) {
+    // the loads pipelined through shared memory (same arithmetic as sweep_strided_body)
     const long long cblocks = (lines + SC_T - 1) / SC_T;
-    sweep_strided_chunk_kernel<VAR, EPI><<<(unsigned)cblocks, SC_T, kScSmem, st>>>(
-        reinterpret_cast<const double*>(in), reinterpret_cast<double*>(out), reinterpret_cast<double*>(tmp), lines, nm,
-        S, g.nt, reinterpret_cast<const double*>(fl), reinterpret_cast<const double*>(fr), ca);
+    sweep_strided_chunk_kernel<Tc, VAR, EPI><<<(unsigned)cblocks, SC_T, kScSmem, st>>>(
+        in, out, tmp, lines, nm, S, g.nt, fl, fr, ca);
     PS_CUDA(cudaGetLastError());
     return;
   }
@@ -1005,21 +1006,16 @@ template void sweep_x_warp<double, double>(const Geom&, const LineFactors&, cons
 
 int max_dyn_smem_public() { return max_dyn_smem(); }
 
-void coarse_x_grouped(bool var, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid, size_t smem,
-                      cudaStream_t st) {
-  auto kern = var ? sweep_x_grouped_kernel<true> : sweep_x_grouped_kernel<false>;
-  PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<grid, kThreads, smem, st>>>(jobs, segs, nseg);
-  PS_CUDA(cudaGetLastError());
-}
+int coarse_y_grouped_lines() { return SC_T; }
+
 void coarse_y_grouped(bool var, int epi, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
                       cudaStream_t st) {
   if (var) {
-    if (epi == 1) sweep_y_grouped_kernel<true, 1><<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
-    else sweep_y_grouped_kernel<true, 2><<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
+    if (epi == 1) sweep_y_grouped_kernel<true, 1><<<grid, SC_T, kScSmem, st>>>(jobs, segs, nseg);
+    else sweep_y_grouped_kernel<true, 2><<<grid, SC_T, kScSmem, st>>>(jobs, segs, nseg);
   } else {
-    if (epi == 1) sweep_y_grouped_kernel<false, 1><<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
-    else sweep_y_grouped_kernel<false, 2><<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
+    if (epi == 1) sweep_y_grouped_kernel<false, 1><<<grid, SC_T, kScSmem, st>>>(jobs, segs, nseg);
+    else sweep_y_grouped_kernel<false, 2><<<grid, SC_T, kScSmem, st>>>(jobs, segs, nseg);
   }
   PS_CUDA(cudaGetLastError());
 }
@@ -1033,11 +1029,11 @@ void coarse_x32_grouped(const XWarpJob* jobs, const WorkSeg* segs, const int* ns
 void coarse_y32_grouped(bool var, int epi, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
                         cudaStream_t st) {
   if (var) {
-    if (epi == 3) sweep_y32_grouped_kernel<true, 3><<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
-    else sweep_y32_grouped_kernel<true, 2><<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
+    if (epi == 3) sweep_y32_grouped_kernel<true, 3><<<grid, SC_T, kScSmem, st>>>(jobs, segs, nseg);
+    else sweep_y32_grouped_kernel<true, 2><<<grid, SC_T, kScSmem, st>>>(jobs, segs, nseg);
   } else {
-    if (epi == 3) sweep_y32_grouped_kernel<false, 3><<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
-    else sweep_y32_grouped_kernel<false, 2><<<grid, kThreads, 0, st>>>(jobs, segs, nseg);
+    if (epi == 3) sweep_y32_grouped_kernel<false, 3><<<grid, SC_T, kScSmem, st>>>(jobs, segs, nseg);
+    else sweep_y32_grouped_kernel<false, 2><<<grid, SC_T, kScSmem, st>>>(jobs, segs, nseg);
   }
   PS_CUDA(cudaGetLastError());
 }

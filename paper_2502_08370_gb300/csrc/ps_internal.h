@@ -134,7 +134,7 @@ struct CoarseJob {
   const double* xin;
   double* xout;
   long long rows, nt;
-  int nx, ny, ld, R;
+  int nx, ny;
   const double* lx;
   const double* rx;
   const double* ly;
@@ -210,7 +210,12 @@ void dr_add(const Geom& g, int nsl, const double* u, const double* w, double* ou
 void copy_with_increment(long long nt, const double* src, double* dst, unsigned long long* inc, int* nonfinite,
                          unsigned long long* slice_stats, float* dout, cudaStream_t st);
 // Grouped coarse-step launches (persistent grids of `grid` CTAs; *nseg work segments).
-void coarse_x_grouped(bool var, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid, size_t smem,
+// x (ps_coarse.cu): a work item is coarse_x_grouped_rows() rows of one job, warp-private
+// Thomas chunks as the single-problem FP64 x-sweep; y: an item is coarse_y_grouped_lines()
+// lines, pipelined as the single-problem strided sweeps.
+int coarse_x_grouped_rows();
+int coarse_y_grouped_lines();
+void coarse_x_grouped(bool var, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
                       cudaStream_t st);
 void coarse_y_grouped(bool var, int epi, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
                       cudaStream_t st);
