@@ -528,7 +528,9 @@ __device__ __forceinline__ void x_thomas_warp_rows(const double* in, double* out
 #pragma unroll
     for (int j = 0; j < XW_C; ++j) lc[j] = ln[j];
   }
-  // backward  x_i = r_i y_i - l_{i+1} x_{i+1}
+  // backward  x_i = r_i y_i - l_{i+1} x_{i+1}; its copies read back y stored above: the fence
+  // orders those stores before them
+  __threadfence_block();
   double rc[XW_C], rn[XW_C];
   load_f(rc, fr, nch - 1, 0);
   load_f(lc, fl, nch - 1, 1);

@@ -498,8 +498,9 @@ __device__ __forceinline__ void cpa_wait_ahead() {
 // Lines [blk * SC_T, blk * SC_T + SC_T) of one sweep.  T: the recurrences' type (right-hand
 // side, y, x, factors); the correction's arrays (Gold, Fout, old U_{n+1}) are FP64.  csm:
 // SC_NS stages of SC_STAGE_BYTES, each laid out as the sweep arrays [a][j][t] of T, then the
-// correction arrays [e][j][t] of double.  Thread t touches only its own columns, and all its
-// copies are complete when it returns.
+// correction arrays [e][j][t] of double.  Within a pass thread t touches only its own columns;
+// between the passes (and between calls) the CTA synchronises.  All copies are complete when
+// it returns.  Every thread of the CTA calls it.
 template <typename T, bool VAR, int EPI>
 __device__ __forceinline__ void strided_chunk_lines(long long blk, const T* in, T* out, T* tmp, long long lines,
                                                     int nm, long long S, long long nt, const T* __restrict__ fl,
@@ -564,6 +565,11 @@ __device__ __forceinline__ void strided_chunk_lines(long long blk, const T* in, 
       }
     }
   }
+  // The backward stages use another layout than the forward ones: with FP32 sweeps a thread's
+  // FP64 correction slots overlap other threads' forward columns, so no thread may stage a
+  // backward chunk while another still reads its forward chunks.  The barrier also orders this
+  // thread's y stores before the copies that read them back.
+  __syncthreads();
   // backward  x_i = r_i y_i - l_{i+1} x_{i+1}, nodes from the end, with the epilogue
   const int nchB = (nm + CB - 1) / CB;
   auto stage_b = [&](int k) {
@@ -705,6 +711,7 @@ __global__ void __launch_bounds__(SC_T, 4) sweep_y_grouped_kernel(const CoarseJo
     const CoarseJob& j = jobs[sg.job];
     strided_chunk_lines<double, VAR, EPI>(sg.first + (it - sg.prefix), j.xout, j.xout, j.xout, j.nx, j.ny, j.nx,
                                           j.nt, j.ly, j.ry, j.ca, csm);
+    __syncthreads();  // the next item stages in the forward layout again
   }
 }
 
@@ -756,6 +763,7 @@ __global__ void __launch_bounds__(SC_T, 4) sweep_y32_grouped_kernel(const Coarse
     const CoarseJob& j = jobs[sg.job];
     strided_chunk_lines<float, VAR, EPI>(sg.first + (it - sg.prefix), j.g32, j.g32, j.g32, j.nx, j.ny, j.nx, j.nt,
                                          j.ly32, j.ry32, j.ca, csm);
+    __syncthreads();  // the next item stages in the forward layout again
   }
 }
 
