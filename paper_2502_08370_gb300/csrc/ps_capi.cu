@@ -1328,6 +1328,11 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
     if (p->batched > 0)  // the grouped kernels of a batch run one tile per item, one line per thread
       cands.erase(std::remove_if(cands.begin(), cands.end(), [](const Cand& c) { return c.pipe || c.vec == 2; }),
                   cands.end());
+    // FP32 tiles of 16 slots (64-byte rows) are valid for one-box tiles but measured far slower
+    // on GB300 (the z-sweep's 64-byte rows): not timed
+    if (mixed)
+      cands.erase(std::remove_if(cands.begin(), cands.end(), [](const Cand& c) { return c.slots * 4 < 128; }),
+                  cands.end());
     auto cand_name = [](const Cand& c) {
       return "fine:" + std::to_string(c.slots) + "x" + std::to_string(c.positions) + "/v" + std::to_string(c.vec) +
              (c.pipe == 1 ? "/ring" : c.pipe == 2 ? "/chunks" : "/tile");
