@@ -57,9 +57,9 @@ FP64_PEAK_TFLOPS = 1.19
 # (127^3 x 64 slices, scaled to any launch by the node-slices it processes).  A kernel whose
 # source changed since is reported with traffic null.
 _UNITS_127 = 127 ** 3 * 64
-TRAFFIC = {"F.x.f32": {"bytes_per_node_slice": (549.214464e6 + 463.352576e6) / _UNITS_127, "tile_src_sha": "5cfc5af1f8be1b45"},
-           "F.y.f32": {"bytes_per_node_slice": (540.974592e6 + 463.164416e6) / _UNITS_127, "tile_src_sha": "5cfc5af1f8be1b45"},
-           "F.z.f32": {"bytes_per_node_slice": (540.970496e6 + 463.757312e6) / _UNITS_127, "tile_src_sha": "5cfc5af1f8be1b45"}}
+TRAFFIC = {"F.x.f32": {"bytes_per_node_slice": (549.215744e6 + 463.143680e6) / _UNITS_127, "tile_src_sha": "b4be5a9e65cc44b5"},
+           "F.y.f32": {"bytes_per_node_slice": (541.017344e6 + 463.126016e6) / _UNITS_127, "tile_src_sha": "b4be5a9e65cc44b5"},
+           "F.z.f32": {"bytes_per_node_slice": (541.020672e6 + 462.866688e6) / _UNITS_127, "tile_src_sha": "b4be5a9e65cc44b5"}}
 
 
 def tile_src_sha():

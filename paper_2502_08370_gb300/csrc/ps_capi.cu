@@ -219,7 +219,7 @@ void fie_step64(ps_problem* p, Prop& P, int nsl, const double* in, double* out, 
 // substep is one TMA tile sweep over all of them, and the result is unpacked into `out`.
 template <typename T>
 void run_F_tiles(ps_problem* p, int n_first, int nsl, const double* in, double* out, cudaStream_t st,
-                 cudaEvent_t after_pack = nullptr) {
+                 cudaEvent_t after_pack = nullptr, bool part_of_slots = false) {
   Prop& P = p->F;
   const int M = P.sp->M;
   T* W = sizeof(T) == 4 ? reinterpret_cast<T*>(p->W.p) : reinterpret_cast<T*>(p->W64.p);
@@ -239,7 +239,7 @@ void run_F_tiles(ps_problem* p, int n_first, int nsl, const double* in, double* 
       if (p->kt.on) sweep_cost(p, f, nsl, sizeof(T), sizeof(T), sizeof(T), sa.src != nullptr, 0, &bytes, &flops);
       p->kt.begin(st);
       const T* srow = sizeof(T) == 4 ? reinterpret_cast<const T*>(p->srcrow32.p) : reinterpret_cast<const T*>(p->srcrow64.p);
-      tile_sweep<T>(p->g, P.tiles[m], f, p->S_pad, n_first, nsl, sa, srow, p->tmo.p, st);
+      tile_sweep<T>(p->g, P.tiles[m], f, p->S_pad, n_first, nsl, sa, srow, p->tmo.p, st, part_of_slots);
       if (p->kt.on) p->kt.end(std::string("F.") + kAxis[m] + "." + tn, bytes, flops);
       p->launches++;
     }
@@ -495,14 +495,20 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
       for (int g = 0; g < ng; ++g) {
         const int a = bounds[g], nsl = bounds[g + 1] - bounds[g];
         if (p->F.f32)
-          run_F_tiles<float>(p, a, nsl, p->U.p + a * nt, p->Fout.p + a * nt, p->side, p->ev_pack[g]);
+          run_F_tiles<float>(p, a, nsl, p->U.p + a * nt, p->Fout.p + a * nt, p->side, p->ev_pack[g], true);
         else
-          run_F_tiles<double>(p, a, nsl, p->U.p + a * nt, p->Fout.p + a * nt, p->side, p->ev_pack[g]);
+          run_F_tiles<double>(p, a, nsl, p->U.p + a * nt, p->Fout.p + a * nt, p->side, p->ev_pack[g], true);
         p->updates += (double)nsl * p->F.steps * (double)nt;
         PS_CUDA(cudaEventRecord(p->ev_done[g], p->side));
       }
       if (timing) PS_CUDA(cudaEventRecord(p->ev[2], p->side));
       TraceRange r2("ps.coarse_chain_correction");
+      // the chain runs on a high-priority stream, its FP64 sweeps on a persistent grid of two CTAs
+      // per SM, so that its CTAs are scheduled ahead of the fine tiles' and leave them most of
+      // every SM
+      cudaStream_t cs = p->hi ? p->hi : st;
+      if (cs != st) PS_CUDA(cudaStreamWaitEvent(cs, p->ev_fine[0], 0));
+      ChainResidency residency(2);
       auto group_of = [&](int slice) {
         int g = 0;
         while (g + 1 < ng && slice >= bounds[g + 1]) ++g;
@@ -512,27 +518,31 @@ void do_run(ps_problem* p, const double* u0, double tol, int max_iter, cudaStrea
       // before the chain reads F of slice n: its group has been unpacked
       auto need_F = [&](int n) {
         const int g = group_of(n);
-        while (waited_done < g) PS_CUDA(cudaStreamWaitEvent(st, p->ev_done[++waited_done], 0));
+        while (waited_done < g) PS_CUDA(cudaStreamWaitEvent(cs, p->ev_done[++waited_done], 0));
       };
       // before the chain writes U_j: the group holding slice j has read its U^{k-1} (packed)
       auto writes_U = [&](int j) {
         if (j >= N) return;
         const int g = group_of(j);
-        while (waited_pack < g && waited_done < g) PS_CUDA(cudaStreamWaitEvent(st, p->ev_pack[++waited_pack], 0));
+        while (waited_pack < g && waited_done < g) PS_CUDA(cudaStreamWaitEvent(cs, p->ev_pack[++waited_pack], 0));
       };
       need_F(nlo);
       writes_U(k);
       copy_with_increment(nt, p->Fout.p + nlo * nt, p->U.p + k * nt, p->inc.p, p->flag.p, p->sstats.p + 2 * k,
-                          p->delta32 ? p->d32.p : nullptr, st);
+                          p->delta32 ? p->d32.p : nullptr, cs);
       p->launches++;
       for (int n = k; n < N; ++n) {
         need_F(n);
         writes_U(n + 1);
-        if (p->delta32) run_G32(p, n, false, st);
-        else run_G(p, n, p->U.p + n * nt, corr_args(p, 1, n), st);
+        if (p->delta32) run_G32(p, n, false, cs);
+        else run_G(p, n, p->U.p + n * nt, corr_args(p, 1, n), cs);
       }
       // the side stream's last group is part of this iteration: the chain ends after it
-      while (waited_done < ng - 1) PS_CUDA(cudaStreamWaitEvent(st, p->ev_done[++waited_done], 0));
+      while (waited_done < ng - 1) PS_CUDA(cudaStreamWaitEvent(cs, p->ev_done[++waited_done], 0));
+      if (cs != st) {
+        PS_CUDA(cudaEventRecord(p->ev_fine[1], cs));
+        PS_CUDA(cudaStreamWaitEvent(st, p->ev_fine[1], 0));
+      }
     } else {
     if (timing) PS_CUDA(cudaEventRecord(p->ev[1], st));
     {
@@ -990,6 +1000,11 @@ int ps_problem_create(const ps_splitting* fine, const ps_splitting* coarse, doub
     for (auto& e : p->ev) PS_CUDA(cudaEventCreate(&e));
     for (auto& e : p->ev_fine) PS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     PS_CUDA(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+    {
+      int least = 0, greatest = 0;
+      PS_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+      PS_CUDA(cudaStreamCreateWithPriority(&p->hi, cudaStreamNonBlocking, greatest));
+    }
     p->inc.alloc(1);
     p->tmo.alloc(1);
     p->flag.alloc(1);

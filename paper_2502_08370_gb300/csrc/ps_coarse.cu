@@ -574,8 +574,12 @@ __global__ void __launch_bounds__(32 * XW_WARPS, 8)
                                const double* __restrict__ fl, const double* __restrict__ fr, SourceArgs sa) {
   extern __shared__ __align__(16) double xwsm[];
   const int w = threadIdx.x >> 5;
-  x_thomas_warp_rows<VAR, SRC>(in, out, rows, nx, rps, fl, fr, sa, ((long long)blockIdx.x * XW_WARPS + w) * 32,
-                               xwsm + w * (XW_WARP_DOUBLES + 32));
+  const long long nblk = (rows + 32 * XW_WARPS - 1) / (32 * XW_WARPS);
+  for (long long b = blockIdx.x; b < nblk; b += gridDim.x) {
+    x_thomas_warp_rows<VAR, SRC>(in, out, rows, nx, rps, fl, fr, sa, (b * XW_WARPS + w) * 32,
+                                 xwsm + w * (XW_WARP_DOUBLES + 32));
+    __syncwarp();
+  }
 }
 
 // Grouped coarse x-sweeps (batched 2-D problems, FP64): an item is 32 * XW_WARPS rows of one job.
@@ -741,7 +745,13 @@ bool sweep_x_chunked(const Geom& g, int nslices, const LineFactors& f, const dou
   if (rps > (1LL << 30) || nx < 2 * XW_C) return false;  // short rows: the whole-row sweep
   const bool var = f.var != 0, src = sa.src != nullptr;
   const long long warps = (rows + 31) / 32;
-  const long long blocks = (warps + XW_WARPS - 1) / XW_WARPS;
+  long long blocks = (warps + XW_WARPS - 1) / XW_WARPS;
+  if (chain_ctas_per_sm > 0) {
+    int dev = 0, sms = 0;
+    PS_CUDA(cudaGetDevice(&dev));
+    PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    blocks = std::min<long long>(blocks, (long long)sms * 2 * chain_ctas_per_sm);  // CTAs of two warps
+  }
   auto launch = [&](auto kern) {
     kern<<<(unsigned)blocks, 32 * XW_WARPS, kXwSmem, st>>>(in, out, rows, nx, (int)rps, f.l64.p, f.r64.p, sa);
   };

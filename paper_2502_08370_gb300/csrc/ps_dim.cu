@@ -18,6 +18,8 @@
 #include "ps_internal.h"
 
 namespace ps {
+thread_local int chain_ctas_per_sm = 0;
+
 namespace {
 
 constexpr int kThreads = 256;
@@ -680,7 +682,11 @@ __global__ void __launch_bounds__(SC_T, 4)
     sweep_strided_chunk_kernel(const T* in, T* out, T* tmp, long long lines, int nm, long long S, long long nt,
                                const T* __restrict__ fl, const T* __restrict__ fr, CorrArgs ca) {
   extern __shared__ __align__(16) unsigned char csm[];
-  strided_chunk_lines<T, VAR, EPI>(blockIdx.x, in, out, tmp, lines, nm, S, nt, fl, fr, ca, csm);
+  const long long nblk = (lines + SC_T - 1) / SC_T;
+  for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    strided_chunk_lines<T, VAR, EPI>(blk, in, out, tmp, lines, nm, S, nt, fl, fr, ca, csm);
+    __syncthreads();  // the next group of lines stages in the forward layout again
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -751,19 +757,21 @@ __global__ void __launch_bounds__(256) sweep_x32_grouped_kernel(const XWarpJob* 
 }
 
 template <bool VAR, int EPI>
-__global__ void __launch_bounds__(SC_T, 4) sweep_y32_grouped_kernel(const CoarseJob* __restrict__ jobs,
-                                                                    const WorkSeg* __restrict__ segs,
-                                                                    const int* __restrict__ nseg_ptr) {
-  extern __shared__ __align__(16) unsigned char csm[];
+__global__ void __launch_bounds__(SC_T) sweep_y32_grouped_kernel(const CoarseJob* __restrict__ jobs,
+                                                                 const WorkSeg* __restrict__ segs,
+                                                                 const int* __restrict__ nseg_ptr) {
+  // FP32 lines of a batch: the streamed body (loads one chunk ahead in registers); the staged
+  // chunk body measured slower here, where each problem has few lines and every line's chain
+  // of dependent FP32 steps is short in time
   const int nseg = *nseg_ptr;
   if (nseg <= 0) return;
   const long long total = (long long)segs[nseg - 1].prefix + segs[nseg - 1].count;
   for (long long it = blockIdx.x; it < total; it += gridDim.x) {
     const WorkSeg sg = segs[find_segment(segs, nseg, it)];
     const CoarseJob& j = jobs[sg.job];
-    strided_chunk_lines<float, VAR, EPI>(sg.first + (it - sg.prefix), j.g32, j.g32, j.g32, j.nx, j.ny, j.nx, j.nt,
-                                         j.ly32, j.ry32, j.ca, csm);
-    __syncthreads();  // the next item stages in the forward layout again
+    sweep_strided_body<float, float, float, VAR, false, EPI, true>(sg.first + (it - sg.prefix), j.g32, j.g32, j.g32,
+                                                                   j.nx, j.ny, j.nx, j.nt, j.ly32, j.ry32,
+                                                                   SourceArgs{}, j.ca);
   }
 }
 
@@ -829,6 +837,15 @@ __global__ void copy_inc_kernel(long long n, const double* __restrict__ src, dou
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(nonfinite, 1);
 }
 
+int g_sm_count = 0;
+int sm_count() {
+  if (!g_sm_count) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+  }
+  return g_sm_count;
+}
 int g_max_smem = 0;
 int max_dyn_smem() {
   if (!g_max_smem) {
@@ -870,7 +887,8 @@ void launch_strided(const Geom& g, int m, int nslices, const Tc* fl, const Tc* f
   if constexpr (std::is_same<Tin, Tc>::value && std::is_same<Tout, Tc>::value && !SRC &&
                 (sizeof(Tc) == 8 ? EPI != 3 : EPI != 1)) {
     // the loads pipelined through shared memory (same arithmetic as sweep_strided_body)
-    const long long cblocks = (lines + SC_T - 1) / SC_T;
+    long long cblocks = (lines + SC_T - 1) / SC_T;
+    if (chain_ctas_per_sm > 0) cblocks = std::min<long long>(cblocks, (long long)sm_count() * chain_ctas_per_sm);
     sweep_strided_chunk_kernel<Tc, VAR, EPI><<<(unsigned)cblocks, SC_T, kScSmem, st>>>(
         in, out, tmp, lines, nm, S, g.nt, fl, fr, ca);
     PS_CUDA(cudaGetLastError());
@@ -1037,11 +1055,11 @@ void coarse_x32_grouped(const XWarpJob* jobs, const WorkSeg* segs, const int* ns
 void coarse_y32_grouped(bool var, int epi, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
                         cudaStream_t st) {
   if (var) {
-    if (epi == 3) sweep_y32_grouped_kernel<true, 3><<<grid, SC_T, kScSmem, st>>>(jobs, segs, nseg);
-    else sweep_y32_grouped_kernel<true, 2><<<grid, SC_T, kScSmem, st>>>(jobs, segs, nseg);
+    if (epi == 3) sweep_y32_grouped_kernel<true, 3><<<grid, SC_T, 0, st>>>(jobs, segs, nseg);
+    else sweep_y32_grouped_kernel<true, 2><<<grid, SC_T, 0, st>>>(jobs, segs, nseg);
   } else {
-    if (epi == 3) sweep_y32_grouped_kernel<false, 3><<<grid, SC_T, kScSmem, st>>>(jobs, segs, nseg);
-    else sweep_y32_grouped_kernel<false, 2><<<grid, SC_T, kScSmem, st>>>(jobs, segs, nseg);
+    if (epi == 3) sweep_y32_grouped_kernel<false, 3><<<grid, SC_T, 0, st>>>(jobs, segs, nseg);
+    else sweep_y32_grouped_kernel<false, 2><<<grid, SC_T, 0, st>>>(jobs, segs, nseg);
   }
   PS_CUDA(cudaGetLastError());
 }

@@ -169,6 +169,7 @@ struct ps_problem {
   // per group, an event after its pack (its inputs U^{k-1} have been read) and after its unpack
   // (its F results are in Fout)
   cudaStream_t side = nullptr;
+  cudaStream_t hi = nullptr;  // high-priority stream of the coarse chain beside the fine phase
   std::vector<cudaEvent_t> ev_pack, ev_done;
   cudaEvent_t ev_fine[2] = {nullptr, nullptr};
   bool overlap = false;  // run the fine phase beside the chain when it spans several slot groups
@@ -184,6 +185,7 @@ struct ps_problem {
     for (auto e : ev_pack) cudaEventDestroy(e);
     for (auto e : ev_done) cudaEventDestroy(e);
     if (side) cudaStreamDestroy(side);
+    if (hi) cudaStreamDestroy(hi);
   }
 };
 

@@ -179,6 +179,16 @@ void sweep_x_warp(const Geom& g, const LineFactors& f, const Tin* in, T* out, co
 // false (nothing launched) for rows shorter than 16 nodes or without FP64 x factors.
 bool sweep_x_chunked(const Geom& g, int nslices, const LineFactors& f, const double* in, double* out,
                      const SourceArgs& sa, cudaStream_t st);
+// CTAs per SM that the chunked FP64 sweeps (x warp chunks, strided chunks) may keep resident
+// on the calling host thread: 0 = as many as fit (one launch wave); > 0 = a persistent grid of
+// that many CTAs per SM, each walking its share of the work.  Set while the coarse chain runs
+// beside the fine phase, so that the fine tiles keep most of every SM's shared memory.
+extern thread_local int chain_ctas_per_sm;
+struct ChainResidency {
+  int saved;
+  explicit ChainResidency(int cap) : saved(chain_ctas_per_sm) { chain_ctas_per_sm = cap; }
+  ~ChainResidency() { chain_ctas_per_sm = saved; }
+};
 // Coarse-propagator sweep of direction f.m on ONE slice, staged through shared memory
 // (ps_coarse.cu); in may alias out.  T = double: x, y, z (x carries the source, y/z the
 // epilogues of CorrArgs modes 0-2); T = float: y, z with modes 0, 2, 3.  Returns false (nothing
@@ -212,7 +222,7 @@ void copy_with_increment(long long nt, const double* src, double* dst, unsigned 
 // Grouped coarse-step launches (persistent grids of `grid` CTAs; *nseg work segments).
 // x (ps_coarse.cu): a work item is coarse_x_grouped_rows() rows of one job, warp-private
 // Thomas chunks as the single-problem FP64 x-sweep; y: an item is coarse_y_grouped_lines()
-// lines, pipelined as the single-problem strided sweeps.
+// lines (FP64: pipelined as the single-problem strided sweeps; FP32: one chunk ahead).
 int coarse_x_grouped_rows();
 int coarse_y_grouped_lines();
 void coarse_x_grouped(bool var, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid,

@@ -964,6 +964,10 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
                            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw Error(PS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  r = encode_fn()(&tp.map_grp, elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, W, dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(PS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
   const int lines = tp.TS * tp.P;
   const int Lp = (L + 3) & ~3;
   // stages x (tile + factor rows l, r) + alignment + barriers; the source, when added, takes
@@ -980,7 +984,8 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
 
 template <typename T>
 void tile_sweep(const Geom& g, const TilePlan& tp, const LineFactors& f, int S_pad, int s_first, int nsl,
-                const SourceArgs& sa, const T* srcrow, int* err, cudaStream_t st) {
+                const SourceArgs& sa, const T* srcrow, int* err, cudaStream_t st, bool part_of_slots) {
+  const CUtensorMap& map = part_of_slots ? tp.map_grp : tp.map;
   TileArgs a{};
   a.axis = tp.axis;
   a.L = tp.L;
@@ -1027,12 +1032,12 @@ void tile_sweep(const Geom& g, const TilePlan& tp, const LineFactors& f, int S_p
     auto kern = tp.V == 2 ? (src ? tile_sweep_piped_kernel<T, 2, true> : tile_sweep_piped_kernel<T, 2, false>)
                           : (src ? tile_sweep_piped_kernel<T, 1, true> : tile_sweep_piped_kernel<T, 1, false>);
     PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<(unsigned)tiles, tp.threads, smem, st>>>(tp.map, a);
+    kern<<<(unsigned)tiles, tp.threads, smem, st>>>(map, a);
   } else if (!tp.pipe) {
     auto kern = tp.V == 2 ? (src ? tile_sweep_kernel<T, 2, true> : tile_sweep_kernel<T, 2, false>)
                           : (src ? tile_sweep_kernel<T, 1, true> : tile_sweep_kernel<T, 1, false>);
     PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<(unsigned)tiles, tp.threads, smem, st>>>(tp.map, a);
+    kern<<<(unsigned)tiles, tp.threads, smem, st>>>(map, a);
   } else {
     auto kern = tp.V == 2 ? (src ? tile_sweep_pipe_kernel<T, 2, true> : tile_sweep_pipe_kernel<T, 2, false>)
                           : (src ? tile_sweep_pipe_kernel<T, 1, true> : tile_sweep_pipe_kernel<T, 1, false>);
@@ -1043,15 +1048,15 @@ void tile_sweep(const Geom& g, const TilePlan& tp, const LineFactors& f, int S_p
     PS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     per_sm = std::max(per_sm, 1);
     const long long grid = std::min<long long>(tiles, (long long)per_sm * sms);
-    kern<<<(unsigned)grid, tp.threads, smem, st>>>(tp.map, a, (int)tiles);
+    kern<<<(unsigned)grid, tp.threads, smem, st>>>(map, a, (int)tiles);
   }
   PS_CUDA(cudaGetLastError());
 }
 
 template void tile_sweep<float>(const Geom&, const TilePlan&, const LineFactors&, int, int, int, const SourceArgs&,
-                                const float*, int*, cudaStream_t);
+                                const float*, int*, cudaStream_t, bool);
 template void tile_sweep<double>(const Geom&, const TilePlan&, const LineFactors&, int, int, int, const SourceArgs&,
-                                 const double*, int*, cudaStream_t);
+                                 const double*, int*, cudaStream_t, bool);
 
 // Line-major copies [line][Lp] (zero padded) of a direction's factors, in the tile's
 // precision.  Line numbering: c * n_b + b, with (b, c) = (y, z) for x-lines, (x, z) for

@@ -10,6 +10,7 @@ namespace ps {
 // Tile shape and TMA tensor map of one sweep direction over W[z][y][x][S_pad].
 struct TilePlan {
   CUtensorMap map;
+  CUtensorMap map_grp;  // the same box with 128-byte L2 promotion: launches over part of the slots
   int axis = 0, L = 0, TS = 32, P = 1, chunks = 1, chunk = 0, threads = 0;
   int V = 1;         // adjacent slots (lines) per thread
   int pipe = 1;      // persistent double-buffered CTAs (1) or one tile per CTA (0)
@@ -25,9 +26,11 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
                int slots = 0, int vec = 0);
 // One substep along tp.axis on slots [s_first, s_first + nsl) (whole TS-slot groups are
 // processed).  `err` is set when a tile's TMA load does not arrive within the wait limit.
+// part_of_slots: the launch covers only some slot groups (the fine phase beside the chain):
+// tiles use map_grp, whose L2 promotion fetches no neighbouring group's bytes.
 template <typename T>
 void tile_sweep(const Geom& g, const TilePlan& tp, const LineFactors& f, int S_pad, int s_first, int nsl,
-                const SourceArgs& sa, const T* srcrow, int* err, cudaStream_t st);
+                const SourceArgs& sa, const T* srcrow, int* err, cudaStream_t st, bool part_of_slots = false);
 // Line-major, zero-padded copies of a direction's factors for the tile sweeps (f.lt*, f.rt*).
 void factor_lines(const Geom& g, LineFactors& f, bool fp32, cudaStream_t st);
 // Source rows along x, line-major [z*ny + y][Lp], in precision elem (4 or 8 bytes).
