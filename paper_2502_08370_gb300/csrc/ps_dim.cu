@@ -1054,12 +1054,13 @@ void coarse_x32_grouped(const XWarpJob* jobs, const WorkSeg* segs, const int* ns
 }
 void coarse_y32_grouped(bool var, int epi, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
                         cudaStream_t st) {
+  // twice the CTAs of 128 lines: as many resident lines as the other grouped launches' 256-thread CTAs
   if (var) {
-    if (epi == 3) sweep_y32_grouped_kernel<true, 3><<<grid, SC_T, 0, st>>>(jobs, segs, nseg);
-    else sweep_y32_grouped_kernel<true, 2><<<grid, SC_T, 0, st>>>(jobs, segs, nseg);
+    if (epi == 3) sweep_y32_grouped_kernel<true, 3><<<grid * 2, SC_T, 0, st>>>(jobs, segs, nseg);
+    else sweep_y32_grouped_kernel<true, 2><<<grid * 2, SC_T, 0, st>>>(jobs, segs, nseg);
   } else {
-    if (epi == 3) sweep_y32_grouped_kernel<false, 3><<<grid, SC_T, 0, st>>>(jobs, segs, nseg);
-    else sweep_y32_grouped_kernel<false, 2><<<grid, SC_T, 0, st>>>(jobs, segs, nseg);
+    if (epi == 3) sweep_y32_grouped_kernel<false, 3><<<grid * 2, SC_T, 0, st>>>(jobs, segs, nseg);
+    else sweep_y32_grouped_kernel<false, 2><<<grid * 2, SC_T, 0, st>>>(jobs, segs, nseg);
   }
   PS_CUDA(cudaGetLastError());
 }
