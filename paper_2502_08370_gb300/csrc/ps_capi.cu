@@ -1340,8 +1340,12 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
     // line's chunks pipelined
     std::vector<Cand> cands = {{32, 2, 0, 2}, {32, 1, 0, 2}, {32, 1, 0, 1}, {32, 2, 0, 1}, {64, 1, 0, 2},
                                {16, 1, 0, 1}, {32, 1, 1, 2}, {32, 1, 1, 1}, {32, 1, 2, 1}, {32, 1, 2, 2}};
-    if (p->batched > 0)  // the grouped kernels of a batch run one tile per item, one line per thread
-      cands.erase(std::remove_if(cands.begin(), cands.end(), [](const Cand& c) { return c.pipe || c.vec == 2; }),
+    // the grouped kernels of a batch run one tile per item, one line per thread, and every item
+    // of a launch with the largest shared-memory tile of the batch: one line position per tile
+    // keeps six tiles per SM for all of them (a single problem on two positions would halve that)
+    if (p->batched > 0)
+      cands.erase(std::remove_if(cands.begin(), cands.end(),
+                                 [](const Cand& c) { return c.pipe || c.vec == 2 || c.positions != 1; }),
                   cands.end());
     // FP32 tiles of 16 slots (64-byte rows) are valid for one-box tiles but measured far slower
     // on GB300 (the z-sweep's 64-byte rows): not timed
