@@ -280,9 +280,12 @@ int ps_problem_update_coefficients(ps_problem* p, const double* a_nodal_dev, uin
  * recomputes the fine steps inside every slice from the forward checkpoints U_n (all slices
  * at once, FP64) and accumulates -tau (nu_Q - nu_P)(w_Q - w_P)/h^2 over every edge of every
  * substep, half to each end node.  Needs a preceding ps_run_parareal on this problem (its
- * states are the checkpoints, so run it to a tight tolerance, e.g. tol_mode = 1); FP64
- * precision and dimensional splitting for the coefficient gradient.  The problem's states
- * are the forward ones again on return; *iters_out = adjoint parareal iterations. */
+ * states are the checkpoints, so run it to a tight tolerance, e.g. tol_mode = 1).  dL/du0
+ * is available in every FIE form (FP64 or FP32 fine line solves, dimensional or DD
+ * splitting, FP64 coarse propagator); the coefficient gradient needs FP64 precision and the
+ * dimensional splitting, the increment-form coarse propagator and DR fine steps are refused
+ * (PS_ERR_UNSUPPORTED).  The problem's states are the forward ones again on return;
+ * *iters_out = adjoint parareal iterations. */
 int ps_adjoint_vjp(ps_problem* p, const double* gN_dev, double tol, int max_iter, double* grad_u0_dev,
                    double* grad_a_dev, uintptr_t stream, int* iters_out);
 /* Gradient of the loss J = 1/2 ||U_N - u_target||^2 (sum over interior nodes) of the last

@@ -228,3 +228,53 @@ def test_adjoint_long_lines_matches_oracle(ps, n):
     J, gu_ref, ga_ref = orc.adjoint(orc.Problem(n, a=a), T, N, s, u0, tgt)
     assert relmax(gu.cpu().numpy(), gu_ref) < 1e-9
     assert relmax(ga.cpu().numpy(), ga_ref) < 1e-9
+
+
+def oracle_u0_gradient(orp, orp_nosrc, T, N, s, u0, tgt):
+    """dJ/du0 for J = 1/2 ||U_N - target||^2 with U_N the sequential fine solution: every FIE
+    substep solve is symmetric, so the transposed fine step is the step's substeps in reverse
+    order without the source, applied to U_N - target from the last step to the first."""
+    U = orc.fine_sequential(orp, T, N, s, u0)
+    lam = U[N] - tgt
+    tau = T / N / s
+    for _ in range(N * s):
+        lam = orc.fie_step(orp_nosrc, tau, lam, reversed_order=True)
+    return 0.5 * float(np.sum((U[N] - tgt) ** 2)), lam
+
+
+@pytest.mark.parametrize("form", ["mixed", "dd"])
+def test_u0_gradient_fp32_form_and_dd_splitting(ps, form):
+    """dJ/du0 through the adjoint parareal in the FP32 form (FP32 fine line solves) and with the
+    DD splitting (FP64): against the transposed oracle fine propagator, itself pinned here by a
+    central difference of the quadratic J (exact up to rounding).  Bars: the FP32 bound of the
+    forward solve (4 s N M 2^-24, relative to max |dJ/du0|); 1e-9 in FP64.  The coefficient
+    gradient of these forms is refused (PS_ERR_UNSUPPORTED)."""
+    n, N, s, T = (23, 19), 4, 5, 0.3
+    rng = np.random.default_rng(81)
+    a = np.exp(0.3 * rng.standard_normal((n[1] + 2, n[0] + 2)))
+    src = rng.standard_normal(n[::-1])
+    src_t = 1.0 + 0.2 * np.sin(np.arange(N * s + 1))
+    u0 = rng.standard_normal(n[::-1])
+    tgt = rng.standard_normal(n[::-1])
+    split, boxes, ov = ("dd", (3, 2), 3.0 / 24) if form == "dd" else ("dim", (1, 1), 0.0)
+    orp = orc.Problem(n, a=a, src=src, src_t=src_t, split=split, boxes=boxes, overlap=ov)
+    orp0 = orc.Problem(n, a=a, split=split, boxes=boxes, overlap=ov)
+    J_ref, g_ref = oracle_u0_gradient(orp, orp0, T, N, s, u0, tgt)
+    # pin: J is quadratic in u0, so the central difference is exact up to rounding
+    d = rng.standard_normal(n[::-1])
+    eps = 1e-3
+    Jp = 0.5 * np.sum((orc.fine_sequential(orp, T, N, s, u0 + eps * d)[N] - tgt) ** 2)
+    Jm = 0.5 * np.sum((orc.fine_sequential(orp, T, N, s, u0 - eps * d)[N] - tgt) ** 2)
+    assert abs((Jp - Jm) / (2 * eps) - np.sum(g_ref * d)) <= 1e-8 * abs(np.sum(g_ref * d))
+    grid = ps.Grid(n)
+    op = ps.Operator(grid, a=dev(a), src=dev(src), src_t=src_t)
+    sp = ps.Splitting(op, split, boxes, ov)
+    prob = ps.Problem(sp, T, N, 1, s, tol_mode=1, precision="mixed" if form == "mixed" else "fp64")
+    prob.run(dev(u0), 1e-13)
+    J, gu, _ = prob.adjoint(dev(tgt), 1e-13, want_a=False)
+    bar = 4.0 * s * N * 2 * 2.0 ** -24 if form == "mixed" else 1e-9
+    assert abs(J - J_ref) <= bar * J_ref * 10
+    assert relmax(gu.cpu().numpy(), g_ref) < bar
+    with pytest.raises(ps.PsError) as e:
+        prob.adjoint(dev(tgt), 1e-13, want_a=True)
+    assert e.value.code == 6
