@@ -192,7 +192,7 @@ def make_problem(ps, torch, cfg, precision, timing, coarse_mode="fp64", fine_met
     prob = ps.Problem(sp, cfg["T"], cfg["N"], cfg["g"], cfg["s"], coarse=spc, precision=precision, timing=timing,
                       coarse_mode=coarse_mode, fine_method=fine_method, **TILE_KW, **PROB_KW)
     prob._keep = (grid, op, sp, spc, a, src)
-    if tune and AUTOTUNE["on"] and cfg["split"] == "dim" and not any(v not in (0, "auto") for v in TILE_KW.values()):
+    if tune and AUTOTUNE["on"] and not any(v not in (0, "auto") for v in TILE_KW.values()):
         t0 = time.perf_counter()
         prob.autotune(budget_ms=150)
         AUTOTUNE["seconds"] += time.perf_counter() - t0
