@@ -356,7 +356,7 @@ int ps_problem_kernel_times(const ps_problem* p, ps_kernel_time* out, int cap, i
  * line solves of every slice of every problem, then each coarse step with its correction),
  * the whole iteration is one CUDA graph replayed until every problem has converged, and only
  * small work tables change between replays.  Results equal each problem's own
- * ps_run_parareal bitwise.  Problems: 2-D, dimensional splitting, PS_PREC_MIXED, one coarse
+ * ps_run_parareal bitwise.  Problems: all 2-D or all 3-D, dimensional splitting, PS_PREC_MIXED, one coarse
  * step per slice, with or without a source term, all with the same coarse form (PS_COARSE_FP64,
  * or PS_COARSE_DELTA32 with rows of at most 1024 nodes) and the default coarse x-sweep
  * schedule of that form, all with a nodal coefficient or all without (PS_ERR_UNSUPPORTED

@@ -37,15 +37,16 @@ struct ps_batch {
   std::vector<XWarpJob> h_xjobs32;
   int span_max = 0;
   // device tables
-  DevBuf<unsigned char> tile_jobs;  // [2][count] TileJob
-  DevBuf<WorkSeg> tile_segs;        // [2][count]
-  DevBuf<int> tile_nseg;            // [maxS][2]
+  int dims = 2;                     // the problems' dimension (all the same)
+  DevBuf<unsigned char> tile_jobs;  // [dims][count] TileJob
+  DevBuf<WorkSeg> tile_segs;        // [dims][count]
+  DevBuf<int> tile_nseg;            // [maxS][dims]
   DevBuf<PackJob> pack_jobs, unpack_jobs;
   DevBuf<WorkSeg> pack_segs, unpack_segs;
   DevBuf<CoarseJob> copy_jobs;
   DevBuf<WorkSeg> copy_segs;
   DevBuf<CoarseJob> cjobs;          // [maxN][count]
-  DevBuf<WorkSeg> xsegs, ysegs;     // [maxN][count]
+  DevBuf<WorkSeg> xsegs, ysegs, zsegs;  // [maxN][count]
   DevBuf<int> nseg_misc;            // [0] pack, [1] unpack, [2] copy, [3 + n] coarse step n
   DevBuf<unsigned long long> inc;   // per problem
   DevBuf<int> flag, tmo;
@@ -57,7 +58,7 @@ struct ps_batch {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // host staging
   std::vector<unsigned char> h_tile_jobs;
-  std::vector<WorkSeg> h_tile_segs, h_pack_segs, h_unpack_segs, h_copy_segs, h_xsegs, h_ysegs;
+  std::vector<WorkSeg> h_tile_segs, h_pack_segs, h_unpack_segs, h_copy_segs, h_xsegs, h_ysegs, h_zsegs;
   std::vector<int> h_tile_nseg, h_nseg_misc;
   std::vector<PackJob> h_pack, h_unpack;
   std::vector<CoarseJob> h_copy, h_cjobs;
@@ -104,12 +105,17 @@ CoarseJob coarse_job(ps_batch* b, int i, int n) {
   j.xout = p->gtmp.p;
   j.nx = p->g.n[0];
   j.ny = p->g.n[1];
-  j.rows = p->g.n[1];
+  j.nz = p->g.dim == 3 ? p->g.n[2] : 1;
+  j.rows = (long long)j.ny * j.nz;
   j.nt = nt;
   j.lx = p->G.dim[0]->l64.p;
   j.rx = p->G.dim[0]->r64.p;
   j.ly = p->G.dim[1]->l64.p;
   j.ry = p->G.dim[1]->r64.p;
+  if (p->g.dim == 3) {
+    j.lz = p->G.dim[2]->l64.p;
+    j.rz = p->G.dim[2]->r64.p;
+  }
   j.ca.U_next = p->U.p + (n + 1) * nt;
   j.ca.Fout = p->Fout.p + n * nt;
   j.ca.Gold = p->Gold.p + n * nt;
@@ -141,13 +147,14 @@ void fill_coarse_tables(ps_batch* b, const std::vector<int>& active, int k) {
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->probs[a]->N > b->probs[c]->N; });
   const int P = b->count;
   for (int n = 0; n < b->maxN; ++n) {
-    int cnt = 0, px = 0, py = 0;
+    int cnt = 0, px = 0, py = 0, pz = 0;
     if (n >= k)
       for (int i : order) {
         ps_problem* p = b->probs[i];
         if (p->N <= n) break;
         b->h_cjobs[(size_t)n * P + cnt] = coarse_job(b, i, n);
-        int bx = (p->g.n[1] + coarse_x_grouped_rows() - 1) / coarse_x_grouped_rows();
+        const long long xrows = b->h_cjobs[(size_t)n * P + cnt].rows;
+        int bx = (int)((xrows + coarse_x_grouped_rows() - 1) / coarse_x_grouped_rows());
         if (b->delta32) {
           // the increment form, as the problem's own run_G32: x by warp rows (eight per item)
           // from U_n with the source (initial sweep) or from the FP32 increment, y in place on
@@ -158,7 +165,7 @@ void fill_coarse_tables(ps_batch* b, const std::vector<int>& active, int k) {
           xj.in64 = k == 0 ? p->U.p + n * nt : nullptr;
           xj.in32 = k == 0 ? nullptr : p->d32.p;
           xj.out = p->g32.p;
-          xj.rows = p->g.n[1];
+          xj.rows = xrows;
           xj.nx = nx;
           xj.m = ((nx + 31) / 32 + 1) & ~1;
           xj.span = nx + nx / xj.m + 2;
@@ -172,6 +179,10 @@ void fill_coarse_tables(ps_batch* b, const std::vector<int>& active, int k) {
           cj.g32 = p->g32.p;
           cj.ly32 = p->G.dim[1]->l32.p;
           cj.ry32 = p->G.dim[1]->r32.p;
+          if (p->g.dim == 3) {
+            cj.lz32 = p->G.dim[2]->l32.p;
+            cj.rz32 = p->G.dim[2]->r32.p;
+          }
           cj.ca.Gold = nullptr;
           if (k == 0) {
             cj.ca.mode = 2;
@@ -180,11 +191,16 @@ void fill_coarse_tables(ps_batch* b, const std::vector<int>& active, int k) {
             cj.ca.dnext = p->d32.p;
           }
         }
-        const int by = (p->g.n[0] + coarse_y_grouped_lines() - 1) / coarse_y_grouped_lines();
+        const CoarseJob& cj0 = b->h_cjobs[(size_t)n * P + cnt];
+        const long long ylines = (long long)cj0.nx * cj0.nz, zlines = (long long)cj0.nx * cj0.ny;
+        const int by = (int)((ylines + coarse_y_grouped_lines() - 1) / coarse_y_grouped_lines());
+        const int bz = (int)((zlines + coarse_y_grouped_lines() - 1) / coarse_y_grouped_lines());
         b->h_xsegs[(size_t)n * P + cnt] = WorkSeg{cnt, 0, bx, px};  // job index within step n
         b->h_ysegs[(size_t)n * P + cnt] = WorkSeg{cnt, 0, by, py};
+        b->h_zsegs[(size_t)n * P + cnt] = WorkSeg{cnt, 0, bz, pz};
         px += bx;
         py += by;
+        pz += bz;
         ++cnt;
       }
     b->h_nseg_misc[3 + n] = cnt;
@@ -199,13 +215,14 @@ void fill_iteration_tables(ps_batch* b, const std::vector<int>& active, int k) {
   // fine tiles, problems in order of decreasing s
   std::vector<int> order(active);
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->probs[a]->fs > b->probs[c]->fs; });
-  for (int m = 0; m < 2; ++m) {
+  const int D = b->dims;
+  for (int m = 0; m < D; ++m) {
     int prefix = 0;
     for (size_t r = 0; r < order.size(); ++r) {
       ps_problem* p = b->probs[order[r]];
       const int nsl = p->N - (k - 1);
       Geom g3 = p->g;
-      g3.n[2] = 1;
+      if (g3.dim == 2) g3.n[2] = 1;
       SourceArgs sa;
       if (p->op->src.p && m == 0) {
         sa.src = p->op->src.p;
@@ -223,7 +240,7 @@ void fill_iteration_tables(ps_batch* b, const std::vector<int>& active, int k) {
       int cnt = 0;
       for (int i : order)
         if (b->probs[i]->fs > j) ++cnt;
-      b->h_tile_nseg[(size_t)j * 2 + m] = cnt;
+      b->h_tile_nseg[(size_t)j * D + m] = cnt;
     }
   }
   // pack / unpack / copy, any order
@@ -270,6 +287,7 @@ void upload_tables(ps_batch* b, cudaStream_t st) {
   if (b->delta32) upload(b->xjobs32, b->h_xjobs32, st);
   upload(b->xsegs, b->h_xsegs, st);
   upload(b->ysegs, b->h_ysegs, st);
+  upload(b->zsegs, b->h_zsegs, st);
   upload(b->nseg_misc, b->h_nseg_misc, st);
 }
 
@@ -282,9 +300,10 @@ int enqueue_sequence(ps_batch* b, int mode, cudaStream_t st) {
     pack_grouped(true, b->pack_jobs.p, b->pack_segs.p, b->nseg_misc.p + 0, grid, st);
     ++n_launch;
     for (int j = 0; j < b->maxS; ++j)
-      for (int m = 0; m < 2; ++m) {
+      for (int m = 0; m < b->dims; ++m) {
         tile_sweep_grouped(b->tile_jobs.p + (size_t)m * P * tile_job_bytes(), b->tile_segs.p + (size_t)m * P,
-                           b->tile_nseg.p + (size_t)j * 2 + m, grid, b->tile_threads, b->tile_smem, b->tmo.p, j, st);
+                           b->tile_nseg.p + (size_t)j * b->dims + m, grid, b->tile_threads, b->tile_smem, b->tmo.p,
+                           j, st);
         ++n_launch;
       }
     pack_grouped(false, b->unpack_jobs.p, b->unpack_segs.p, b->nseg_misc.p + 1, grid, st);
@@ -295,16 +314,27 @@ int enqueue_sequence(ps_batch* b, int mode, cudaStream_t st) {
     if (b->delta32) {
       coarse_x32_grouped(b->xjobs32.p + (size_t)n * P, b->xsegs.p + (size_t)n * P, b->nseg_misc.p + 3 + n, grid,
                          b->span_max, st);
-      coarse_y32_grouped(b->var, mode == 2 ? 2 : 3, b->cjobs.p + (size_t)n * P, b->ysegs.p + (size_t)n * P,
-                         b->nseg_misc.p + 3 + n, grid, st);
+      const int epi32 = mode == 2 ? 2 : 3;  // the last sweep carries the epilogue
+      coarse_y32_grouped(b->var, b->dims == 3 ? 0 : epi32, b->cjobs.p + (size_t)n * P, b->ysegs.p + (size_t)n * P,
+                         b->nseg_misc.p + 3 + n, grid, st, 1);
       n_launch += 2;
+      if (b->dims == 3) {
+        coarse_y32_grouped(b->var, epi32, b->cjobs.p + (size_t)n * P, b->zsegs.p + (size_t)n * P,
+                           b->nseg_misc.p + 3 + n, grid, st, 2);
+        ++n_launch;
+      }
       continue;
     }
     coarse_x_grouped(b->var, b->cjobs.p + (size_t)n * P, b->xsegs.p + (size_t)n * P, b->nseg_misc.p + 3 + n, grid,
                      st);
-    coarse_y_grouped(b->var, mode, b->cjobs.p + (size_t)n * P, b->ysegs.p + (size_t)n * P, b->nseg_misc.p + 3 + n,
-                     grid, st);
+    coarse_y_grouped(b->var, b->dims == 3 ? 0 : mode, b->cjobs.p + (size_t)n * P, b->ysegs.p + (size_t)n * P,
+                     b->nseg_misc.p + 3 + n, grid, st, 1);
     n_launch += 2;
+    if (b->dims == 3) {
+      coarse_y_grouped(b->var, mode, b->cjobs.p + (size_t)n * P, b->zsegs.p + (size_t)n * P, b->nseg_misc.p + 3 + n,
+                       grid, st, 2);
+      ++n_launch;
+    }
   }
   return n_launch;
 }
@@ -333,8 +363,8 @@ cudaGraphExec_t capture(ps_batch* b, int mode) {
 void batch_check(const ps_batch* b, const ps_problem* p) {
   PS_REQUIRE(p, "null problem");
   PS_REQUIRE(p->N >= 1, "the problem has no slices");
-  if (p->g.dim != 2 || p->fine->kind != PS_SPLIT_DIM || p->coarse->kind != PS_SPLIT_DIM)
-    throw Error(PS_ERR_UNSUPPORTED, "batches hold 2-D problems with dimensional splitting");
+  if (p->fine->kind != PS_SPLIT_DIM || p->coarse->kind != PS_SPLIT_DIM)
+    throw Error(PS_ERR_UNSUPPORTED, "batches hold problems with dimensional splitting");
   if (p->prm.precision != PS_PREC_MIXED)
     throw Error(PS_ERR_UNSUPPORTED, "batches run the FP32 line-solve form (PS_PREC_MIXED)");
   if (p->gs != 1) throw Error(PS_ERR_UNSUPPORTED, "batches use one coarse step per slice");
@@ -347,6 +377,7 @@ void batch_check(const ps_batch* b, const ps_problem* p) {
   if (!b->probs.empty()) {
     PS_REQUIRE(var == (b->probs[0]->op->a.p != nullptr), "all problems of a batch need a nodal coefficient, or none");
     PS_REQUIRE(p->delta32 == b->probs[0]->delta32, "all problems of a batch need the same coarse propagator form");
+    PS_REQUIRE(p->g.dim == b->probs[0]->g.dim, "all problems of a batch need the same dimension (2-D or 3-D)");
   }
   for (const ps_problem* q : b->probs) PS_REQUIRE(q != p, "a problem appears twice in the batch");
 }
@@ -360,6 +391,7 @@ void batch_layout(ps_batch* b) {
   b->tile_threads = 0;
   b->var = P > 0 ? b->probs[0]->op->a.p != nullptr : true;
   b->delta32 = P > 0 && b->probs[0]->delta32;
+  b->dims = P > 0 ? b->probs[0]->g.dim : 2;
   b->span_max = 0;
   for (ps_problem* p : b->probs) {
     const int nx = p->g.n[0], m = ((nx + 31) / 32 + 1) & ~1;
@@ -369,10 +401,10 @@ void batch_layout(ps_batch* b) {
     b->maxS = std::max(b->maxS, p->fs);
     b->maxN = std::max(b->maxN, p->N);
     b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[0], p->op->src.p != nullptr));
-    b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[1], false));
     // the grouped kernel runs one line per thread, whatever the plan's own split
-    b->tile_threads = std::max(b->tile_threads, std::max(p->F.tiles[0].TS * p->F.tiles[0].P,
-                                                         p->F.tiles[1].TS * p->F.tiles[1].P));
+    for (int m = 1; m < p->g.dim; ++m) b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[m], false));
+    for (int m = 0; m < p->g.dim; ++m)
+      b->tile_threads = std::max(b->tile_threads, p->F.tiles[m].TS * p->F.tiles[m].P);
   }
   b->tile_threads = (b->tile_threads + 31) / 32 * 32;
   if (b->iter_graph) {
@@ -384,9 +416,9 @@ void batch_layout(ps_batch* b) {
     b->init_graph = nullptr;
   }
   const size_t Pz = (size_t)std::max(P, 1);
-  b->tile_jobs.alloc((size_t)2 * Pz * tile_job_bytes());
-  b->tile_segs.alloc((size_t)2 * Pz);
-  b->tile_nseg.alloc((size_t)2 * std::max(b->maxS, 1));
+  b->tile_jobs.alloc((size_t)b->dims * Pz * tile_job_bytes());
+  b->tile_segs.alloc((size_t)b->dims * Pz);
+  b->tile_nseg.alloc((size_t)b->dims * std::max(b->maxS, 1));
   b->pack_jobs.alloc(Pz);
   b->unpack_jobs.alloc(Pz);
   b->pack_segs.alloc(Pz);
@@ -398,14 +430,15 @@ void batch_layout(ps_batch* b) {
   else b->xjobs32.reset();
   b->xsegs.alloc((size_t)std::max(b->maxN, 1) * Pz);
   b->ysegs.alloc((size_t)std::max(b->maxN, 1) * Pz);
+  b->zsegs.alloc((size_t)std::max(b->maxN, 1) * Pz);
   b->nseg_misc.alloc((size_t)3 + b->maxN);
   b->inc.alloc(Pz);
   b->flag.alloc(Pz);
   b->tmo.alloc(1);
   PS_CUDA(cudaMemset(b->tmo.p, 0, sizeof(int)));
-  b->h_tile_jobs.assign((size_t)2 * P * tile_job_bytes(), 0);
-  b->h_tile_segs.assign((size_t)2 * P, WorkSeg{});
-  b->h_tile_nseg.assign((size_t)2 * b->maxS, 0);
+  b->h_tile_jobs.assign((size_t)b->dims * P * tile_job_bytes(), 0);
+  b->h_tile_segs.assign((size_t)b->dims * P, WorkSeg{});
+  b->h_tile_nseg.assign((size_t)b->dims * b->maxS, 0);
   b->h_pack.assign(P, PackJob{});
   b->h_unpack.assign(P, PackJob{});
   b->h_pack_segs.assign(P, WorkSeg{});
@@ -416,6 +449,7 @@ void batch_layout(ps_batch* b) {
   b->h_xjobs32.assign(b->delta32 ? (size_t)b->maxN * P : 0, XWarpJob{});
   b->h_xsegs.assign((size_t)b->maxN * P, WorkSeg{});
   b->h_ysegs.assign((size_t)b->maxN * P, WorkSeg{});
+  b->h_zsegs.assign((size_t)b->maxN * P, WorkSeg{});
   b->h_nseg_misc.assign((size_t)3 + b->maxN, 0);
   b->h_inc.assign(P, 0);
   b->h_flag.assign(P, 0);
@@ -503,10 +537,12 @@ int ps_batch_run(ps_batch* b, const double* const* u0_devs, double tol, int max_
     b->tile_smem = 0;
     b->tile_threads = 0;
     for (ps_problem* p : b->probs) {
-      b->tile_smem = std::max(b->tile_smem, std::max(tile_grouped_smem(p->F.tiles[0], p->op->src.p != nullptr), tile_grouped_smem(p->F.tiles[1], false)));
+      b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[0], p->op->src.p != nullptr));
       // the grouped kernel runs one line per thread, whatever the plan's own split
-      b->tile_threads = std::max(b->tile_threads, std::max(p->F.tiles[0].TS * p->F.tiles[0].P,
-                                                           p->F.tiles[1].TS * p->F.tiles[1].P));
+      for (int m = 1; m < p->g.dim; ++m)
+        b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[m], false));
+      for (int m = 0; m < p->g.dim; ++m)
+        b->tile_threads = std::max(b->tile_threads, p->F.tiles[m].TS * p->F.tiles[m].P);
     }
     b->tile_threads = (b->tile_threads + 31) / 32 * 32;
     b->init_graph = capture(b, 2);

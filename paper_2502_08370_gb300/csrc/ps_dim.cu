@@ -704,7 +704,7 @@ __device__ __forceinline__ int find_segment(const WorkSeg* segs, int nseg, long 
 }
 
 
-template <bool VAR, int EPI>
+template <bool VAR, int EPI, int AX>
 __global__ void __launch_bounds__(SC_T, 4) sweep_y_grouped_kernel(const CoarseJob* __restrict__ jobs,
                                                                   const WorkSeg* __restrict__ segs,
                                                                   const int* __restrict__ nseg_ptr) {
@@ -715,8 +715,12 @@ __global__ void __launch_bounds__(SC_T, 4) sweep_y_grouped_kernel(const CoarseJo
   for (long long it = blockIdx.x; it < total; it += gridDim.x) {
     const WorkSeg sg = segs[find_segment(segs, nseg, it)];
     const CoarseJob& j = jobs[sg.job];
-    strided_chunk_lines<double, VAR, EPI>(sg.first + (it - sg.prefix), j.xout, j.xout, j.xout, j.nx, j.ny, j.nx,
-                                          j.nt, j.ly, j.ry, j.ca, csm);
+    // AX 1: y-lines (nx * nz, stride nx); AX 2: z-lines (nx * ny, stride nx * ny)
+    const long long S = AX == 1 ? (long long)j.nx : (long long)j.nx * j.ny;
+    const long long lines = AX == 1 ? (long long)j.nx * j.nz : (long long)j.nx * j.ny;
+    strided_chunk_lines<double, VAR, EPI>(sg.first + (it - sg.prefix), j.xout, j.xout, j.xout, lines,
+                                          AX == 1 ? j.ny : j.nz, S, j.nt, AX == 1 ? j.ly : j.lz,
+                                          AX == 1 ? j.ry : j.rz, j.ca, csm);
     __syncthreads();  // the next item stages in the forward layout again
   }
 }
@@ -756,7 +760,7 @@ __global__ void __launch_bounds__(256) sweep_x32_grouped_kernel(const XWarpJob* 
   }
 }
 
-template <bool VAR, int EPI>
+template <bool VAR, int EPI, int AX>
 __global__ void __launch_bounds__(SC_T) sweep_y32_grouped_kernel(const CoarseJob* __restrict__ jobs,
                                                                  const WorkSeg* __restrict__ segs,
                                                                  const int* __restrict__ nseg_ptr) {
@@ -769,9 +773,12 @@ __global__ void __launch_bounds__(SC_T) sweep_y32_grouped_kernel(const CoarseJob
   for (long long it = blockIdx.x; it < total; it += gridDim.x) {
     const WorkSeg sg = segs[find_segment(segs, nseg, it)];
     const CoarseJob& j = jobs[sg.job];
+    const long long S = AX == 1 ? (long long)j.nx : (long long)j.nx * j.ny;
+    const long long lines = AX == 1 ? (long long)j.nx * j.nz : (long long)j.nx * j.ny;
     sweep_strided_body<float, float, float, VAR, false, EPI, true>(sg.first + (it - sg.prefix), j.g32, j.g32, j.g32,
-                                                                   j.nx, j.ny, j.nx, j.nt, j.ly32, j.ry32,
-                                                                   SourceArgs{}, j.ca);
+                                                                   lines, AX == 1 ? j.ny : j.nz, S, j.nt,
+                                                                   AX == 1 ? j.ly32 : j.lz32,
+                                                                   AX == 1 ? j.ry32 : j.rz32, SourceArgs{}, j.ca);
   }
 }
 
@@ -1035,13 +1042,26 @@ int max_dyn_smem_public() { return max_dyn_smem(); }
 int coarse_y_grouped_lines() { return SC_T; }
 
 void coarse_y_grouped(bool var, int epi, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
-                      cudaStream_t st) {
-  if (var) {
-    if (epi == 1) sweep_y_grouped_kernel<true, 1><<<grid, SC_T, kScSmem, st>>>(jobs, segs, nseg);
-    else sweep_y_grouped_kernel<true, 2><<<grid, SC_T, kScSmem, st>>>(jobs, segs, nseg);
+                      cudaStream_t st, int axis) {
+  auto go = [&](auto kern) { kern<<<grid, SC_T, kScSmem, st>>>(jobs, segs, nseg); };
+  if (axis == 1) {
+    if (var) {
+      if (epi == 1) go(sweep_y_grouped_kernel<true, 1, 1>);
+      else if (epi == 2) go(sweep_y_grouped_kernel<true, 2, 1>);
+      else go(sweep_y_grouped_kernel<true, 0, 1>);
+    } else {
+      if (epi == 1) go(sweep_y_grouped_kernel<false, 1, 1>);
+      else if (epi == 2) go(sweep_y_grouped_kernel<false, 2, 1>);
+      else go(sweep_y_grouped_kernel<false, 0, 1>);
+    }
   } else {
-    if (epi == 1) sweep_y_grouped_kernel<false, 1><<<grid, SC_T, kScSmem, st>>>(jobs, segs, nseg);
-    else sweep_y_grouped_kernel<false, 2><<<grid, SC_T, kScSmem, st>>>(jobs, segs, nseg);
+    if (var) {
+      if (epi == 1) go(sweep_y_grouped_kernel<true, 1, 2>);
+      else go(sweep_y_grouped_kernel<true, 2, 2>);
+    } else {
+      if (epi == 1) go(sweep_y_grouped_kernel<false, 1, 2>);
+      else go(sweep_y_grouped_kernel<false, 2, 2>);
+    }
   }
   PS_CUDA(cudaGetLastError());
 }
@@ -1053,14 +1073,27 @@ void coarse_x32_grouped(const XWarpJob* jobs, const WorkSeg* segs, const int* ns
   PS_CUDA(cudaGetLastError());
 }
 void coarse_y32_grouped(bool var, int epi, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
-                        cudaStream_t st) {
+                        cudaStream_t st, int axis) {
   // twice the CTAs of 128 lines: as many resident lines as the other grouped launches' 256-thread CTAs
-  if (var) {
-    if (epi == 3) sweep_y32_grouped_kernel<true, 3><<<grid * 2, SC_T, 0, st>>>(jobs, segs, nseg);
-    else sweep_y32_grouped_kernel<true, 2><<<grid * 2, SC_T, 0, st>>>(jobs, segs, nseg);
+  auto go = [&](auto kern) { kern<<<grid * 2, SC_T, 0, st>>>(jobs, segs, nseg); };
+  if (axis == 1) {
+    if (var) {
+      if (epi == 3) go(sweep_y32_grouped_kernel<true, 3, 1>);
+      else if (epi == 2) go(sweep_y32_grouped_kernel<true, 2, 1>);
+      else go(sweep_y32_grouped_kernel<true, 0, 1>);
+    } else {
+      if (epi == 3) go(sweep_y32_grouped_kernel<false, 3, 1>);
+      else if (epi == 2) go(sweep_y32_grouped_kernel<false, 2, 1>);
+      else go(sweep_y32_grouped_kernel<false, 0, 1>);
+    }
   } else {
-    if (epi == 3) sweep_y32_grouped_kernel<false, 3><<<grid * 2, SC_T, 0, st>>>(jobs, segs, nseg);
-    else sweep_y32_grouped_kernel<false, 2><<<grid * 2, SC_T, 0, st>>>(jobs, segs, nseg);
+    if (var) {
+      if (epi == 3) go(sweep_y32_grouped_kernel<true, 3, 2>);
+      else go(sweep_y32_grouped_kernel<true, 2, 2>);
+    } else {
+      if (epi == 3) go(sweep_y32_grouped_kernel<false, 3, 2>);
+      else go(sweep_y32_grouped_kernel<false, 2, 2>);
+    }
   }
   PS_CUDA(cudaGetLastError());
 }

@@ -133,18 +133,22 @@ struct WorkSeg {
 struct CoarseJob {
   const double* xin;
   double* xout;
-  long long rows, nt;
-  int nx, ny;
+  long long rows, nt;  // rows = x-lines (ny * nz)
+  int nx, ny, nz;      // nz = 1 in 2-D
   const double* lx;
   const double* rx;
   const double* ly;
   const double* ry;
+  const double* lz;    // 3-D: z factors
+  const double* rz;
   CorrArgs ca;
   SourceArgs sa;  // the coarse step's source (added on the x-sweep), or sa.src == null
   // FP32 increment form: the y-sweep runs in place on g32 with the FP32 factors
   float* g32;
   const float* ly32;
   const float* ry32;
+  const float* lz32;
+  const float* rz32;
 };
 
 // One batched problem's FP32 x-sweep of coarse step n (increment form): rows of the FP64 state
@@ -227,13 +231,15 @@ int coarse_x_grouped_rows();
 int coarse_y_grouped_lines();
 void coarse_x_grouped(bool var, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
                       cudaStream_t st);
+// axis 1: the y-lines (nx * nz of them), axis 2: the z-lines (nx * ny); epi: the correction
+// epilogue of the last sweep (0 on a 3-D problem's y-sweep)
 void coarse_y_grouped(bool var, int epi, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
-                      cudaStream_t st);
+                      cudaStream_t st, int axis = 1);
 void copy_inc_grouped(const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid, cudaStream_t st);
 void coarse_x32_grouped(const XWarpJob* jobs, const WorkSeg* segs, const int* nseg, int grid, int span_max,
                         cudaStream_t st);
 void coarse_y32_grouped(bool var, int epi, const CoarseJob* jobs, const WorkSeg* segs, const int* nseg, int grid,
-                        cudaStream_t st);
+                        cudaStream_t st, int axis = 1);
 int max_dyn_smem_public();
 
 }  // namespace ps

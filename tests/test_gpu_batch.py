@@ -181,3 +181,43 @@ def test_batch_with_sources_both_coarse_forms_bitwise(ps, coarse):
     U_ref, _, _ = orc.parareal(orp, c["T"], c["N"], 1, c["s"], c["u0"], 1e-8)
     err = np.abs(ref[0][2][-1] - U_ref[-1]).max() / np.abs(U_ref[-1]).max()
     assert err < 4.0 * c["s"] * c["N"] * 2 * 2.0 ** -24
+
+
+@pytest.mark.parametrize("coarse", ["fp64", "delta32"])
+def test_3d_batch_equals_individual_runs_bitwise(ps, coarse):
+    """Batches of 3-D problems (three fine tile directions, coarse x rows over y and z, y- and
+    z-line sweeps with the epilogue on z): every state, history and iteration count equal the
+    problems' own runs bitwise, for both coarse forms, with a source on some problems."""
+    rng = np.random.default_rng(91)
+    shapes = [(17, 13, 11), (23, 9, 15), (31, 17, 9), (12, 20, 7)]
+    probs, u0s = [], []
+    for i, n in enumerate(shapes):
+        a = np.exp(0.3 * rng.standard_normal([v + 2 for v in reversed(n)]))
+        src = rng.standard_normal(n[::-1]) if i % 2 == 0 else None
+        N, s = (4, 8)[i % 2], 3 + i
+        grid = ps.Grid(n)
+        op = ps.Operator(grid, a=dev(a), src=None if src is None else dev(src))
+        sp = ps.Splitting(op)
+        prob = ps.Problem(sp, 0.4, N, 1, s, precision="mixed", coarse_mode=coarse)
+        prob._keep = (grid, op, sp)
+        probs.append(prob)
+        u0s.append(dev(rng.standard_normal(n[::-1])))
+    ref = []
+    for p, u in zip(probs, u0s):
+        it = p.run(u, 1e-9)
+        ref.append((it, snapshot(p), p.history()))
+    batch = ps.Batch(probs)
+    for _ in range(2):
+        its = batch.run(u0s, 1e-9)
+        assert its == [r[0] for r in ref]
+        for p, (it, st, h) in zip(probs, ref):
+            got = snapshot(p)
+            for n in range(p.N + 1):
+                assert np.array_equal(got[n], st[n]), n
+            assert np.array_equal(p.history(), h)
+    # mixed dimensions are refused
+    g2 = ps.Grid((9, 8))
+    op2 = ps.Operator(g2)
+    p2 = ps.Problem(ps.Splitting(op2), 0.4, 4, 1, 3, precision="mixed", coarse_mode=coarse)
+    with pytest.raises(ps.PsError):
+        batch.add(p2)
