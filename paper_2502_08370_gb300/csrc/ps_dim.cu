@@ -844,14 +844,12 @@ __global__ void copy_inc_kernel(long long n, const double* __restrict__ src, dou
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(nonfinite, 1);
 }
 
-int g_sm_count = 0;
+// SMs of the current device, queried per call (the device may differ between calls)
 int sm_count() {
-  if (!g_sm_count) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
-  }
-  return g_sm_count;
+  int dev = 0, n = 0;
+  PS_CUDA(cudaGetDevice(&dev));
+  PS_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  return n;
 }
 int g_max_smem = 0;
 int max_dyn_smem() {
