@@ -766,53 +766,41 @@ __global__ void tile_sweep_pipe_kernel(const __grid_constant__ CUtensorMap map, 
 }
 
 // U (slice-major, FP64, slices [s_first, s_first+nsl)) <-> W (interleaved, S_pad slots).
-// Pack / unpack: a CTA moves 32 grid positions x 64 slots through shared memory ([position]
-// [slot], pitch 65 doubles: distinct bank pairs for both access patterns).  Every warp access
-// to U is a 256-byte row segment of one slice; every access to W covers a position's 64 slots
-// (256 bytes in FP32), so a node's slot vector is written (or read) whole by one CTA.
-constexpr int kPackSl = 64, kPackPitch = 65;
 template <typename T>
-__global__ void __launch_bounds__(256) to_interleaved_kernel(const double* __restrict__ U, T* __restrict__ W,
-                                                             long long nt, int S_pad, int s_first, int nsl, int rev) {
-  __shared__ double tile[32 * kPackPitch];
+__global__ void to_interleaved_kernel(const double* __restrict__ U, T* __restrict__ W, long long nt, int S_pad,
+                                      int s_first, int nsl, int rev) {
+  __shared__ double tile[32][33];
   const long long pos0 = (long long)blockIdx.x * 32;
-  const int sl0 = blockIdx.y * kPackSl;
-  const int lane = threadIdx.x, w = threadIdx.y;  // 32 x 8
-  for (int r = w; r < kPackSl; r += 8) {
+  const int sl0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int sl = sl0 + r;
-    const long long pos = pos0 + lane;
+    const long long pos = pos0 + threadIdx.x;
     const long long src = rev ? (long long)(nsl - 1 - sl) : (long long)sl;  // slot s_first + sl <- state src
-    tile[lane * kPackPitch + r] = (sl < nsl && pos < nt) ? U[src * nt + pos] : 0.0;
+    tile[r][threadIdx.x] = (sl < nsl && pos < nt) ? U[src * nt + pos] : 0.0;
   }
   __syncthreads();
-  for (int p = w; p < 32; p += 8) {
-    const long long pos = pos0 + p;
-    if (pos >= nt) continue;
-    for (int r = lane; r < kPackSl; r += 32) {
-      const int sl = sl0 + r;
-      if (sl < nsl) W[pos * S_pad + s_first + sl] = (T)tile[p * kPackPitch + r];
-    }
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const long long pos = pos0 + r;
+    const int sl = sl0 + threadIdx.x;
+    if (sl < nsl && pos < nt) W[pos * S_pad + s_first + sl] = (T)tile[threadIdx.x][r];
   }
 }
 template <typename T>
-__global__ void __launch_bounds__(256) from_interleaved_kernel(const T* __restrict__ W, double* __restrict__ U,
-                                                               long long nt, int S_pad, int s_first, int nsl) {
-  __shared__ double tile[32 * kPackPitch];
+__global__ void from_interleaved_kernel(const T* __restrict__ W, double* __restrict__ U, long long nt, int S_pad,
+                                        int s_first, int nsl) {
+  __shared__ double tile[32][33];
   const long long pos0 = (long long)blockIdx.x * 32;
-  const int sl0 = blockIdx.y * kPackSl;
-  const int lane = threadIdx.x, w = threadIdx.y;
-  for (int p = w; p < 32; p += 8) {
-    const long long pos = pos0 + p;
-    for (int r = lane; r < kPackSl; r += 32) {
-      const int sl = sl0 + r;
-      tile[p * kPackPitch + r] = (sl < nsl && pos < nt) ? (double)W[pos * S_pad + s_first + sl] : 0.0;
-    }
+  const int sl0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const long long pos = pos0 + r;
+    const int sl = sl0 + threadIdx.x;
+    tile[r][threadIdx.x] = (sl < nsl && pos < nt) ? (double)W[pos * S_pad + s_first + sl] : 0.0;
   }
   __syncthreads();
-  for (int r = w; r < kPackSl; r += 8) {
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int sl = sl0 + r;
-    const long long pos = pos0 + lane;
-    if (sl < nsl && pos < nt) U[(long long)sl * nt + pos] = tile[lane * kPackPitch + r];
+    const long long pos = pos0 + threadIdx.x;
+    if (sl < nsl && pos < nt) U[(long long)sl * nt + pos] = tile[threadIdx.x][r];
   }
 }
 
@@ -1198,13 +1186,13 @@ void source_rows(const Geom& g, const double* src, void* out, int elem, cudaStre
 
 template <typename T>
 void to_interleaved(const Geom& g, const double* U, T* W, int S_pad, int s_first, int nsl, cudaStream_t st, bool rev) {
-  dim3 grid((unsigned)((g.nt + 31) / 32), (unsigned)((nsl + kPackSl - 1) / kPackSl));
+  dim3 grid((unsigned)((g.nt + 31) / 32), (unsigned)((nsl + 31) / 32));
   to_interleaved_kernel<T><<<grid, dim3(32, 8), 0, st>>>(U, W, g.nt, S_pad, s_first, nsl, rev ? 1 : 0);
   PS_CUDA(cudaGetLastError());
 }
 template <typename T>
 void from_interleaved(const Geom& g, const T* W, double* U, int S_pad, int s_first, int nsl, cudaStream_t st) {
-  dim3 grid((unsigned)((g.nt + 31) / 32), (unsigned)((nsl + kPackSl - 1) / kPackSl));
+  dim3 grid((unsigned)((g.nt + 31) / 32), (unsigned)((nsl + 31) / 32));
   from_interleaved_kernel<T><<<grid, dim3(32, 8), 0, st>>>(W, U, g.nt, S_pad, s_first, nsl);
   PS_CUDA(cudaGetLastError());
 }
