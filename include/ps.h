@@ -182,9 +182,7 @@ typedef struct {
   int tile_positions;      /* fine line solves: line positions per TMA tile (1, 2, 4); 0 = auto
                               (FP32: 1; FP64: as many as fit 96 KB, up to 4) */
   int tile_pipeline;       /* fine line solves: 1 persistent CTAs with a ring of three stages,
-                              2 one tile per CTA, 3 one tile per one-warp CTA whose line chunks
-                              arrive, solve and leave pipelined (lines of more than 128 nodes, one
-                              position per tile), 0 = auto (one tile per CTA) */
+                              2 one tile per CTA, 0 = auto (one tile per CTA) */
   int tile_slots;          /* fine line solves: time slices per TMA tile (16, 32, 64); 0 = auto */
   int tol_mode;            /* stopping test: 0 = max_n ||U_n^k - U_n^{k-1}||_inf < tol (absolute);
                               1 = max_n ||U_n^k - U_n^{k-1}||_inf / ||U_n^k||_inf < tol (per slice) */
@@ -399,7 +397,7 @@ int ps_batch_destroy(ps_batch* b);
  * same arithmetic per slice in every case). */
 int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out);
 /* The timing record of the last ps_autotune on this problem: one entry per candidate timed,
- * name "fine:<slots>x<positions>/v<lines per thread>/<tile|ring|chunks>", "coarse:<staged|streamed>",
+ * name "fine:<slots>x<positions>/v<lines per thread>/<tile|ring>", "coarse:<staged|streamed>",
  * "coarse-x32:<thomas|pcr|hybrid>" (increment form) or "coarse-x64:<thomas|hybrid>",
  * "coarse-corr:<fused|split>" (FP64 coarse form: the correction in the last sweep's epilogue or
  * as its own pass; the same values either way), "dd:<S>-slices-per-cta" (DD), and its

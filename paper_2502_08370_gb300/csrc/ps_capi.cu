@@ -700,7 +700,7 @@ void configure_slices(ps_problem* p, int N, int g_steps, int f_steps, cudaStream
     if (g3.dim == 2) g3.n[2] = 1;
     for (int m = 0; m < p->g.dim; ++m) {
       tile_plan(g3, p->S_pad, elem, m, p->F.tiles[m], W, p->prm.tile_positions,
-                p->prm.tile_pipeline == 1 ? 1 : (p->prm.tile_pipeline == 3 ? 2 : 0), p->prm.tile_slots,
+                p->prm.tile_pipeline == 1 ? 1 : 0, p->prm.tile_slots,
                 p->prm.tile_lines_per_thread);
       factor_lines(g3, *p->F.dim[m], mixed, st);
     }
@@ -1276,7 +1276,7 @@ void rebuild_tiles(ps_problem* p, int slots, int positions, int pipe, int vec) {
   for (int m = 0; m < p->g.dim; ++m) p->F.tiles[m] = tmp[m];
   p->prm.tile_slots = slots;
   p->prm.tile_positions = positions;
-  p->prm.tile_pipeline = pipe == 1 ? 1 : (pipe == 2 ? 3 : 2);
+  p->prm.tile_pipeline = pipe == 1 ? 1 : 2;
   p->prm.tile_lines_per_thread = vec;
 }
 }  // namespace
@@ -1336,10 +1336,9 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
       int slots, positions, pipe, vec;
     };
     // slots per tile, line positions per tile, persistent double-buffered CTAs, lines per thread
-    // pipe: 0 one tile per CTA, 1 persistent ring of stages, 2 one tile per one-warp CTA with the
-    // line's chunks pipelined
+    // pipe: 0 one tile per CTA, 1 persistent ring of stages
     std::vector<Cand> cands = {{32, 2, 0, 2}, {32, 1, 0, 2}, {32, 1, 0, 1}, {32, 2, 0, 1}, {64, 1, 0, 2},
-                               {16, 1, 0, 1}, {32, 1, 1, 2}, {32, 1, 1, 1}, {32, 1, 2, 1}, {32, 1, 2, 2}};
+                               {16, 1, 0, 1}, {32, 1, 1, 2}, {32, 1, 1, 1}};
     // the grouped kernels of a batch run one tile per item, one line per thread, and every item
     // of a launch with the largest shared-memory tile of the batch: one line position per tile
     // keeps six tiles per SM for all of them (a single problem on two positions would halve that)
@@ -1354,7 +1353,7 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
                   cands.end());
     auto cand_name = [](const Cand& c) {
       return "fine:" + std::to_string(c.slots) + "x" + std::to_string(c.positions) + "/v" + std::to_string(c.vec) +
-             (c.pipe == 1 ? "/ring" : c.pipe == 2 ? "/chunks" : "/tile");
+             (c.pipe == 1 ? "/ring" : "/tile");
     };
     tile_flag_reset(p, st);
     p->tune_log.clear();
@@ -1527,7 +1526,7 @@ int ps_autotune(ps_problem* p, int budget_ms, uintptr_t stream, int* choice_out)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (bestc.slots == 0) {
-      rebuild_tiles(p, old_slots, old_pos, old_pipe == 1 ? 1 : (old_pipe == 3 ? 2 : 0), old_vec);
+      rebuild_tiles(p, old_slots, old_pos, old_pipe == 1 ? 1 : 0, old_vec);
       if (choice_out) *choice_out = coarse_choice * 100000;
       return;
     }
@@ -1561,7 +1560,7 @@ int ps_copy_schedule(const ps_problem* src, ps_problem* dst) {
   return guarded([&] {
     PS_REQUIRE(src && dst, "null argument");
     rebuild_tiles(dst, src->prm.tile_slots, src->prm.tile_positions,
-                  src->prm.tile_pipeline == 1 ? 1 : (src->prm.tile_pipeline == 3 ? 2 : 0),
+                  src->prm.tile_pipeline == 1 ? 1 : 0,
                   src->prm.tile_lines_per_thread);
     dst->coarse_staged = src->coarse_staged;
     dst->prm.coarse_sweep = src->prm.coarse_sweep;

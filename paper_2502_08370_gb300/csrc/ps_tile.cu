@@ -363,217 +363,6 @@ __global__ void tile_sweep_kernel(const __grid_constant__ CUtensorMap map, TileA
   tile_body<T, V, SRC>(&map, a, blockIdx.x, tile, bar, 0, a.t_first);
 }
 
-// One tile by one warp (P = 1, at most 32 threads) with its line chunks pipelined: chunk k of
-// the line lands on its own mbarrier, the forward recurrence starts on chunk 0 while the later
-// chunks are still in flight, and the backward recurrence hands every chunk to a TMA store as
-// soon as its lowest node is final.  Load, solve and store of a tile then overlap instead of
-// following one another, so more of each tile's bytes are moving at any time.  The arithmetic
-// is line_solve's, node for node (the same helpers, the same order).
-template <typename T, int V, bool SRC>
-__device__ __forceinline__ bool tile_body_piped(const CUtensorMap* map, const TileArgs& a, int t, T* tile,
-                                                uint64_t* bars, int t_first) {
-  using VT = VecT<T, V>;
-  using QT = Quad<T>;
-  const int lines = a.TS;
-  const int L = a.L, CH = a.chunk, NC = a.chunks, Lp = a.Lp;
-  T* fl_s = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(tile + (size_t)lines * L) + 31) & ~(uintptr_t)31);
-  T* fr_s = fl_s + Lp;
-  T* src_s = fr_s + Lp;
-  int s0, b0, c;
-  tile_coords(a, t, &s0, &b0, &c);
-  const int lane = threadIdx.x;
-  const unsigned mask = blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
-  if (lane == 0) {
-    for (int k = 0; k < NC; ++k) {
-      const int i0 = k * CH;
-      mbar_expect_tx(&bars[k], (uint32_t)(CH * lines * (int)sizeof(T)) + (k == 0 ? side_bytes<T, SRC>(a, 1) : 0u));
-      if (k == 0) issue_side_loads<T, SRC>(a, b0, c, 1, fl_s, fr_s, src_s, &bars[0]);
-      T* dst = tile + (size_t)i0 * lines;
-      if (a.axis == 0) tma_load_4d(dst, map, &bars[k], s0, i0, b0, c);
-      else if (a.axis == 1) tma_load_4d(dst, map, &bars[k], s0, b0, i0, c);
-      else tma_load_4d(dst, map, &bars[k], s0, b0, c, i0);
-    }
-  }
-  // every lane polls the barriers of the chunks it is about to read; a wait that runs out of
-  // time abandons the tile (no store has been issued by then: stores start in the backward pass)
-  // (one compare per four-node group on the fast path: the next chunk's first node is kept)
-  int waited = -1, wait_at = 0;  // chunks [0, waited] have landed; node wait_at starts the next
-  auto need = [&](int node) -> bool {
-    while (node >= wait_at) {
-      const bool got = mbar_wait(&bars[waited + 1], 0);
-      if (!__all_sync(mask, got)) {
-        if (lane == 0) atomicExch(a.err, 1);
-        return false;
-      }
-      ++waited;
-      wait_at = waited + 1 < NC ? (waited + 1) * CH : 0x7fffffff;
-    }
-    return true;
-  };
-  int stored = NC;                  // chunks [stored, NC) are with the TMA engine
-  int release_at = (NC - 1) * CH;   // first node of chunk stored - 1
-  auto release = [&](int lowest_final) {
-    while (lowest_final <= release_at) {
-      --stored;
-      release_at = stored > 0 ? (stored - 1) * CH : -1;
-      fence_async_smem();
-      __syncwarp(mask);
-      if (lane == 0) {
-        const int i0 = stored * CH;
-        const T* srcp = tile + (size_t)i0 * lines;
-        if (a.axis == 0) tma_store_4d(map, srcp, s0, i0, b0, c);
-        else if (a.axis == 1) tma_store_4d(map, srcp, s0, b0, i0, c);
-        else tma_store_4d(map, srcp, s0, b0, c, i0);
-        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-      }
-    }
-  };
-  if (!need(0)) return false;  // chunk 0 and the factor / source rows
-  const int sl = lane * V;
-  T ft[V];
-#pragma unroll
-  for (int v = 0; v < V; ++v) ft[v] = SRC ? slot_time_factor<T>(a, s0 + sl + v, t_first) : T(0);
-  T* x = tile + sl;
-  const int st = lines;
-  const T* Lf = fl_s;
-  const T* Rf = fr_s;
-  const T* S = src_s;
-  // forward
-  T y[V];
-#pragma unroll
-  for (int v = 0; v < V; ++v) y[v] = T(0);
-  const int nq = L / 4;
-  QT l4n{}, s4n{};
-  VT bn[4];
-  if (nq > 0) {
-    if (!need(3)) return false;
-    l4n = *reinterpret_cast<const QT*>(Lf);
-    if (SRC) s4n = *reinterpret_cast<const QT*>(S);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) bn[u] = *reinterpret_cast<const VT*>(x + u * st);
-  }
-  for (int cq = 0; cq < nq; ++cq) {
-    const int i0 = 4 * cq;
-    const QT l4 = l4n;
-    const QT s4 = s4n;
-    VT b[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) b[u] = bn[u];
-    if (cq + 1 < nq) {
-      if (!need(i0 + 7)) return false;
-      l4n = *reinterpret_cast<const QT*>(Lf + i0 + 4);
-      if (SRC) s4n = *reinterpret_cast<const QT*>(S + i0 + 4);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) bn[u] = *reinterpret_cast<const VT*>(x + (i0 + 4 + u) * st);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        T bb = b[u].v[v];
-        if (SRC) bb = rhs_node(bb, s4.q[u], ft[v]);
-        y[v] = fwd_node(y[v], bb, l4.q[u]);
-        b[u].v[v] = y[v];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) *reinterpret_cast<VT*>(x + (i0 + u) * st) = b[u];
-  }
-  for (int i = 4 * nq; i < L; ++i) {
-    if (!need(i)) return false;
-    VT b = *reinterpret_cast<const VT*>(x + i * st);
-    const T li = Lf[i];
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      T bb = b.v[v];
-      if (SRC) bb = rhs_node(bb, S[i], ft[v]);
-      y[v] = fwd_node(y[v], bb, li);
-      b.v[v] = y[v];
-    }
-    *reinterpret_cast<VT*>(x + i * st) = b;
-  }
-  // backward, releasing chunks to the TMA stores from the top down
-  T xn[V];
-#pragma unroll
-  for (int v = 0; v < V; ++v) xn[v] = T(0);
-  T lnext = T(0);
-  for (int i = L - 1; i >= 4 * nq; --i) {
-    VT yy = *reinterpret_cast<const VT*>(x + i * st);
-    const T ri = Rf[i];
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      xn[v] = bwd_node(xn[v], yy.v[v], ri, lnext);
-      yy.v[v] = xn[v];
-    }
-    *reinterpret_cast<VT*>(x + i * st) = yy;
-    lnext = Lf[i];
-  }
-  release(4 * nq);
-  QT r4n{};
-  VT yyn[4];
-  if (nq > 0) {
-    const int i0 = 4 * (nq - 1);
-    r4n = *reinterpret_cast<const QT*>(Rf + i0);
-    l4n = *reinterpret_cast<const QT*>(Lf + i0);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) yyn[u] = *reinterpret_cast<const VT*>(x + (i0 + u) * st);
-  }
-  for (int cq = nq - 1; cq >= 0; --cq) {
-    const int i0 = 4 * cq;
-    const QT r4 = r4n;
-    const QT l4 = l4n;
-    VT yy[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) yy[u] = yyn[u];
-    if (cq > 0) {
-      r4n = *reinterpret_cast<const QT*>(Rf + i0 - 4);
-      l4n = *reinterpret_cast<const QT*>(Lf + i0 - 4);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) yyn[u] = *reinterpret_cast<const VT*>(x + (i0 - 4 + u) * st);
-    }
-#pragma unroll
-    for (int u = 3; u >= 0; --u) {
-      const T l1 = u == 3 ? lnext : l4.q[u + 1];
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        xn[v] = bwd_node(xn[v], yy[u].v[v], r4.q[u], l1);
-        yy[u].v[v] = xn[v];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) *reinterpret_cast<VT*>(x + (i0 + u) * st) = yy[u];
-    lnext = l4.q[0];
-    release(i0);
-  }
-  release(0);
-  if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-  __syncwarp(mask);
-  return true;
-}
-
-// Shared memory: [chunk barriers (up to 16, 128 bytes) | tile ...].
-template <typename T, int V, bool SRC>
-__global__ void tile_sweep_piped_kernel(const __grid_constant__ CUtensorMap map, TileArgs a) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
-  T* tile = reinterpret_cast<T*>(smem_raw + 128);
-  __shared__ int s_abort;
-  if (threadIdx.x == 0) {
-    s_abort = *reinterpret_cast<volatile int*>(a.err);
-    if (smem_addr(tile) & 127) {
-      atomicExch(a.err, 2);
-      s_abort = 1;
-    }
-    if (!s_abort) {
-      for (int k = 0; k < a.chunks; ++k) mbar_init(&bars[k], 1);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-  }
-  __syncthreads();
-  if (s_abort) return;
-  tile_body_piped<T, V, SRC>(&map, a, blockIdx.x, tile, bars, a.t_first);
-}
-
 // Grouped, persistent form: many problems' tiles in one launch.  jobs[j] holds one
 // (problem, direction)'s tensor map and tile arguments (in global memory, 64-byte aligned);
 // the first *nseg segments of `segs` list which tiles of which job run, with running
@@ -895,8 +684,7 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
     }
   }
   PS_REQUIRE((tp.TS * elem) % 128 == 0 || short_rows, "tile rows must be a multiple of 128 bytes");
-  const bool want_chunks = pipe == 2;  // one-warp tiles with the line's chunks pipelined
-  tp.pipe = pipe < 0 ? 1 : (pipe == 2 ? 0 : pipe);
+  tp.pipe = pipe < 0 ? 1 : pipe;
   {
     // long lines: fewer slots per tile (down to 128-byte rows) until one tile fits in shared memory
     int dev = 0, maxsm = 0;
@@ -933,18 +721,6 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
   tp.chunks = (L + 255) / 256;
   while (L % tp.chunks) ++tp.chunks;
   tp.chunk = L / tp.chunks;
-  // one-warp tiles of long lines: equal chunks of about 40-80 nodes, each on its own barrier,
-  // so that the solve starts on the first chunk and the stores leave chunk by chunk
-  tp.piped = 0;
-  if (want_chunks && !short_rows && !tp.pipe && tp.P == 1 && L > 128 && tp.TS / tp.V <= 32) {
-    for (int nc = (L + 79) / 80; nc <= 16 && L / nc >= 8; ++nc)
-      if (L % nc == 0) {
-        tp.chunks = nc;
-        tp.chunk = L / nc;
-        tp.piped = 1;
-        break;
-      }
-  }
   // globals: dims (S_pad, nx, ny, nz), strides in bytes of dims 1..3
   cuuint64_t dims[4] = {(cuuint64_t)S_pad, (cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
   cuuint64_t strides[3] = {(cuuint64_t)S_pad * elem, (cuuint64_t)S_pad * elem * g.n[0],
@@ -1028,12 +804,7 @@ void tile_sweep(const Geom& g, const TilePlan& tp, const LineFactors& f, int S_p
   const int stages = tp.pipe ? kPipeStages : 1;
   const int Lp = (tp.L + 3) & ~3;
   const size_t smem = tp.smem + (src ? (size_t)stages * tp.P * Lp * sizeof(T) : 0);
-  if (!tp.pipe && tp.piped) {
-    auto kern = tp.V == 2 ? (src ? tile_sweep_piped_kernel<T, 2, true> : tile_sweep_piped_kernel<T, 2, false>)
-                          : (src ? tile_sweep_piped_kernel<T, 1, true> : tile_sweep_piped_kernel<T, 1, false>);
-    PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<(unsigned)tiles, tp.threads, smem, st>>>(map, a);
-  } else if (!tp.pipe) {
+  if (!tp.pipe) {
     auto kern = tp.V == 2 ? (src ? tile_sweep_kernel<T, 2, true> : tile_sweep_kernel<T, 2, false>)
                           : (src ? tile_sweep_kernel<T, 1, true> : tile_sweep_kernel<T, 1, false>);
     PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -14,14 +14,12 @@ struct TilePlan {
   int axis = 0, L = 0, TS = 32, P = 1, chunks = 1, chunk = 0, threads = 0;
   int V = 1;         // adjacent slots (lines) per thread
   int pipe = 1;      // persistent double-buffered CTAs (1) or one tile per CTA (0)
-  int piped = 0;     // one tile per one-warp CTA with its line chunks on separate barriers
   int ctas_per_sm = 1;
   size_t smem = 0;   // dynamic shared memory per CTA without the source staging
 };
 
 // positions: 1, 2 or 4 line positions per tile (0 = largest that fits); pipe: 1 persistent
-// double-buffered, 0 one tile per CTA, 2 one tile per one-warp CTA with the line's chunks
-// pipelined (lines longer than 128 nodes, one position; else as 0), -1 auto.
+// double-buffered, 0 one tile per CTA, -1 auto.
 void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void* W, int positions = 0, int pipe = -1,
                int slots = 0, int vec = 0);
 // One substep along tp.axis on slots [s_first, s_first + nsl) (whole TS-slot groups are
