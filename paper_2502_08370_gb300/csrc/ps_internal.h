@@ -77,10 +77,9 @@ struct LineFactors {
   int var = 0;
   DevBuf<double> l64, r64;
   DevBuf<float> l32, r32;
-  // line-major copies [line][L rounded up to 4] for the fine propagator's tile sweeps, and the
-  // influence rows of their two-half solve (lines of 64 nodes or more)
-  DevBuf<double> lt64, rt64, at64;
-  DevBuf<float> lt32, rt32, at32;
+  // line-major copies [line][L rounded up to 4] for the fine propagator's tile sweeps
+  DevBuf<double> lt64, rt64;
+  DevBuf<float> lt32, rt32;
 };
 
 // Geometry of a state on the grid (x fastest).

@@ -63,7 +63,6 @@ struct TileArgs {
   long long rows_x;  // ny*nz: leading dimension of the transposed x-factors
   const void* fl;       // factor rows l of every line: [line][Lp], line = c * nb + b
   const void* fr;       // factor rows r, same layout
-  const void* fa;       // influence rows of the two-half solve (line_split), same layout, or null
   const void* srcrow;   // source rows (x-lines of a step's first substep) [line][Lp] or null
   int Lp;               // row length: L rounded up to 4, zero padded
   const double* src;    // non-null when the source is added
@@ -86,39 +85,20 @@ __device__ __forceinline__ int tile_off(const TileArgs& a, int s, int p, int i) 
   return a.axis == 0 ? (p * a.L + i) * a.TS + s : (i * a.P + p) * a.TS + s;
 }
 
-// Side rows of a tile, per position, in shared memory: l, r, the influence row (two-half
-// solve), the source; each row set P * Lp entries apart.
-struct SideRows {
-  void* l;
-  void* r;
-  void* a;  // null without the two-half solve
-  void* src;
-};
-template <typename T>
-__device__ __forceinline__ SideRows side_rows(const TileArgs& a, T* base) {
-  const size_t stride = (size_t)a.P * a.Lp;
-  SideRows sr;
-  sr.l = base;
-  sr.r = base + stride;
-  sr.a = a.fa ? base + 2 * stride : nullptr;
-  sr.src = base + (a.fa ? 3 : 2) * stride;
-  return sr;
-}
 // Bytes the factor (and source) rows of a tile add to its barrier's transaction count.
 template <typename T, bool SRC>
 __device__ __forceinline__ uint32_t side_bytes(const TileArgs& a, int nvalid) {
-  return (uint32_t)((2 + (a.fa ? 1 : 0) + (SRC ? 1 : 0)) * nvalid * a.Lp * (int)sizeof(T));
+  return (uint32_t)((SRC ? 3 : 2) * nvalid * a.Lp * (int)sizeof(T));
 }
 // Factor (and source) rows of the tile's valid positions: nvalid consecutive lines.
 template <typename T, bool SRC>
-__device__ __forceinline__ void issue_side_loads(const TileArgs& a, int b0, int c, int nvalid, const SideRows& sr,
-                                                 uint64_t* bar) {
+__device__ __forceinline__ void issue_side_loads(const TileArgs& a, int b0, int c, int nvalid, T* fl_s, T* fr_s,
+                                                 T* src_s, uint64_t* bar) {
   const long long row = (long long)c * a.nb + b0;
   const uint32_t bytes = (uint32_t)(nvalid * a.Lp * (int)sizeof(T));
-  bulk_load(sr.l, reinterpret_cast<const T*>(a.fl) + row * a.Lp, bytes, bar);
-  bulk_load(sr.r, reinterpret_cast<const T*>(a.fr) + row * a.Lp, bytes, bar);
-  if (a.fa) bulk_load(sr.a, reinterpret_cast<const T*>(a.fa) + row * a.Lp, bytes, bar);
-  if (SRC) bulk_load(sr.src, reinterpret_cast<const T*>(a.srcrow) + row * a.Lp, bytes, bar);
+  bulk_load(fl_s, reinterpret_cast<const T*>(a.fl) + row * a.Lp, bytes, bar);
+  bulk_load(fr_s, reinterpret_cast<const T*>(a.fr) + row * a.Lp, bytes, bar);
+  if (SRC) bulk_load(src_s, reinterpret_cast<const T*>(a.srcrow) + row * a.Lp, bytes, bar);
 }
 // tau * src_t at the end time of the step, for interleaved slot `slot`.
 template <typename T>
@@ -140,7 +120,7 @@ struct alignas(sizeof(T) * 4) Quad {
 };
 
 // The three roundings of a node, written as explicit FMAs so that every kernel that solves a
-// line (one tile per CTA, persistent, grouped) computes the same bits:
+// line (one tile per CTA, pipelined chunks, persistent, grouped) computes the same bits:
 //     b + f * ft (source),   y = b - l y,   x = r y - l' x
 template <typename T>
 __device__ __forceinline__ T fmat(T a, T b, T c) {
@@ -162,8 +142,7 @@ __device__ __forceinline__ T bwd_node(T x, T yv, T r, T ln) { return fmat(-ln, x
 //     backward  x_i = r_i y_i - l_{i+1} x_{i+1}    (x_L = 0, l_L = 0)
 // The source, when present, enters the right-hand side: b_i += src_i * ft[v].
 template <typename T, int V, bool SRC>
-__device__ __forceinline__ void line_solve_seq(T* x, int st, int L, const T* Lf, const T* Rf, const T* S,
-                                               const T* ft) {
+__device__ __forceinline__ void line_solve(T* x, int st, int L, const T* Lf, const T* Rf, const T* S, const T* ft) {
   using VT = VecT<T, V>;
   using QT = Quad<T>;
   // Each chunk of four nodes is loaded one chunk ahead, into registers, before the previous
@@ -272,188 +251,6 @@ __device__ __forceinline__ void line_solve_seq(T* x, int st, int L, const T* Lf,
   }
 }
 
-// Lines of at least 64 nodes are solved as two halves at once (two independent dependent
-// chains per thread instead of one: on long lines a tile's solve, not its copies, is the
-// longer part of its life in shared memory).  With h = line_split(L) (a multiple of 4):
-//   forward:  y_i for i < h as usual; for i >= h the local recurrence from y_{h-1} = 0, then
-//             y_i = local_i + A_i y_{h-1},  A_i = prod_{j=h..i} (-l_j);
-//   backward: x_i for i >= h as usual (with the corrected y_i); for i < h the local recurrence
-//             from x_h = 0, then x_i = local_i + B_i x_h,  B_i = prod_{j=i+1..h} (-l_j).
-// A (i >= h) and B (i < h) are one precomputed row per line (influence_rows_kernel).  The
-// same exact solution, other roundings: |l_j| < 1 makes both products decay along the line.
-__host__ __device__ __forceinline__ int line_split(int L) { return L >= 64 ? ((L / 2) & ~3) : 0; }
-
-template <typename T, int V, bool SRC>
-__device__ __forceinline__ void line_solve_split(T* x, int st, int L, const T* Lf, const T* Rf, const T* S,
-                                                 const T* ft, const T* Af) {
-  using VT = VecT<T, V>;
-  using QT = Quad<T>;
-  const int h = line_split(L), ng = h / 4;
-  T y1[V], y2[V];
-#pragma unroll
-  for (int v = 0; v < V; ++v) y1[v] = y2[v] = T(0);
-  // forward: groups g of both halves together (nodes 4g.. and h+4g..), loaded one group ahead
-  QT l1n = *reinterpret_cast<const QT*>(Lf), l2n = *reinterpret_cast<const QT*>(Lf + h), s1n{}, s2n{};
-  if (SRC) {
-    s1n = *reinterpret_cast<const QT*>(S);
-    s2n = *reinterpret_cast<const QT*>(S + h);
-  }
-  VT b1n[4], b2n[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    b1n[u] = *reinterpret_cast<const VT*>(x + u * st);
-    b2n[u] = *reinterpret_cast<const VT*>(x + (h + u) * st);
-  }
-  for (int g = 0; g < ng; ++g) {
-    const int i1 = 4 * g, i2 = h + 4 * g;
-    const QT l1 = l1n, l2 = l2n, s1 = s1n, s2 = s2n;
-    VT b1[4], b2[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      b1[u] = b1n[u];
-      b2[u] = b2n[u];
-    }
-    if (g + 1 < ng) {
-      l1n = *reinterpret_cast<const QT*>(Lf + i1 + 4);
-      l2n = *reinterpret_cast<const QT*>(Lf + i2 + 4);
-      if (SRC) {
-        s1n = *reinterpret_cast<const QT*>(S + i1 + 4);
-        s2n = *reinterpret_cast<const QT*>(S + i2 + 4);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        b1n[u] = *reinterpret_cast<const VT*>(x + (i1 + 4 + u) * st);
-        b2n[u] = *reinterpret_cast<const VT*>(x + (i2 + 4 + u) * st);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        T bb1 = b1[u].v[v], bb2 = b2[u].v[v];
-        if (SRC) {
-          bb1 = rhs_node(bb1, s1.q[u], ft[v]);
-          bb2 = rhs_node(bb2, s2.q[u], ft[v]);
-        }
-        y1[v] = fwd_node(y1[v], bb1, l1.q[u]);
-        y2[v] = fwd_node(y2[v], bb2, l2.q[u]);
-        b1[u].v[v] = y1[v];
-        b2[u].v[v] = y2[v];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      *reinterpret_cast<VT*>(x + (i1 + u) * st) = b1[u];
-      *reinterpret_cast<VT*>(x + (i2 + u) * st) = b2[u];
-    }
-  }
-  for (int i = 2 * h; i < L; ++i) {  // the second half's nodes past 2h (L - 2h < 8)
-    VT b = *reinterpret_cast<const VT*>(x + i * st);
-    const T li = Lf[i];
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      T bb = b.v[v];
-      if (SRC) bb = rhs_node(bb, S[i], ft[v]);
-      y2[v] = fwd_node(y2[v], bb, li);
-      b.v[v] = y2[v];
-    }
-    *reinterpret_cast<VT*>(x + i * st) = b;
-  }
-  // y1 = y_{h-1}, exact.  Backward: the second half exactly (its y corrected on the way), the
-  // first half from x_h = 0, both chains at once
-  T x1[V], x2[V];
-#pragma unroll
-  for (int v = 0; v < V; ++v) x1[v] = x2[v] = T(0);
-  T ln2 = T(0);  // l_{i+1} of the second half's next step
-  for (int i = L - 1; i >= 2 * h; --i) {
-    VT yy = *reinterpret_cast<const VT*>(x + i * st);
-    const T ri = Rf[i], ai = Af[i];
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const T yc = fmat(ai, y1[v], yy.v[v]);
-      x2[v] = bwd_node(x2[v], yc, ri, ln2);
-      yy.v[v] = x2[v];
-    }
-    *reinterpret_cast<VT*>(x + i * st) = yy;
-    ln2 = Lf[i];
-  }
-  T ln1 = T(0);  // l_{i+1} of the first half's next step (0 at i = h - 1: x_h is taken as 0)
-  {
-    const int j1 = 4 * (ng - 1), j2 = h + 4 * (ng - 1);
-    QT r1n = *reinterpret_cast<const QT*>(Rf + j1), r2n = *reinterpret_cast<const QT*>(Rf + j2);
-    QT l1b = *reinterpret_cast<const QT*>(Lf + j1), l2b = *reinterpret_cast<const QT*>(Lf + j2);
-    QT a2n = *reinterpret_cast<const QT*>(Af + j2);
-    VT y1n[4], y2n[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      y1n[u] = *reinterpret_cast<const VT*>(x + (j1 + u) * st);
-      y2n[u] = *reinterpret_cast<const VT*>(x + (j2 + u) * st);
-    }
-    for (int g = ng - 1; g >= 0; --g) {
-      const int i1 = 4 * g, i2 = h + 4 * g;
-      const QT r1 = r1n, r2 = r2n, l1 = l1b, l2 = l2b, a2 = a2n;
-      VT yy1[4], yy2[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        yy1[u] = y1n[u];
-        yy2[u] = y2n[u];
-      }
-      if (g > 0) {
-        r1n = *reinterpret_cast<const QT*>(Rf + i1 - 4);
-        r2n = *reinterpret_cast<const QT*>(Rf + i2 - 4);
-        l1b = *reinterpret_cast<const QT*>(Lf + i1 - 4);
-        l2b = *reinterpret_cast<const QT*>(Lf + i2 - 4);
-        a2n = *reinterpret_cast<const QT*>(Af + i2 - 4);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          y1n[u] = *reinterpret_cast<const VT*>(x + (i1 - 4 + u) * st);
-          y2n[u] = *reinterpret_cast<const VT*>(x + (i2 - 4 + u) * st);
-        }
-      }
-#pragma unroll
-      for (int u = 3; u >= 0; --u) {
-        const T lb1 = u == 3 ? ln1 : l1.q[u + 1];
-        const T lb2 = u == 3 ? ln2 : l2.q[u + 1];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          const T yc = fmat(a2.q[u], y1[v], yy2[u].v[v]);
-          x2[v] = bwd_node(x2[v], yc, r2.q[u], lb2);
-          x1[v] = bwd_node(x1[v], yy1[u].v[v], r1.q[u], lb1);
-          yy2[u].v[v] = x2[v];
-          yy1[u].v[v] = x1[v];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        *reinterpret_cast<VT*>(x + (i1 + u) * st) = yy1[u];
-        *reinterpret_cast<VT*>(x + (i2 + u) * st) = yy2[u];
-      }
-      ln1 = l1.q[0];
-      ln2 = l2.q[0];
-    }
-  }
-  // x2 = x_h, exact: the first half's correction, independent per node
-  for (int g = 0; g < ng; ++g) {
-    const int i1 = 4 * g;
-    const QT bq = *reinterpret_cast<const QT*>(Af + i1);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      VT xx = *reinterpret_cast<const VT*>(x + (i1 + u) * st);
-#pragma unroll
-      for (int v = 0; v < V; ++v) xx.v[v] = fmat(bq.q[u], x2[v], xx.v[v]);
-      *reinterpret_cast<VT*>(x + (i1 + u) * st) = xx;
-    }
-  }
-}
-
-// One line: two halves at once when an influence row is given, else one chain.
-template <typename T, int V, bool SRC>
-__device__ __forceinline__ void line_solve(T* x, int st, int L, const T* Lf, const T* Rf, const T* S, const T* ft,
-                                           const T* Af) {
-  if (Af != nullptr && line_split(L) > 0) line_solve_split<T, V, SRC>(x, st, L, Lf, Rf, S, ft, Af);
-  else line_solve_seq<T, V, SRC>(x, st, L, Lf, Rf, S, ft);
-}
-
 // Tile t -> (first slot, first paired position, fixed coordinate).
 __device__ __forceinline__ void tile_coords(const TileArgs& a, int t, int* s0, int* b0, int* c) {
   const int ngroups = a.s_hi - a.s_lo;
@@ -474,12 +271,9 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* map, const TileArgs
   __shared__ int s_ok;
   const int lines = a.TS * a.P;
   const int Lp = a.Lp;
-  T* side0 = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(tile + (size_t)lines * a.L) + 31) & ~(uintptr_t)31);
-  const SideRows sr = side_rows<T>(a, side0);
-  const T* fl_s = static_cast<const T*>(sr.l);
-  const T* fr_s = static_cast<const T*>(sr.r);
-  const T* fa_s = static_cast<const T*>(sr.a);
-  const T* src_s = static_cast<const T*>(sr.src);
+  T* fl_s = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(tile + (size_t)lines * a.L) + 31) & ~(uintptr_t)31);
+  T* fr_s = fl_s + (size_t)a.P * Lp;
+  T* src_s = fr_s + (size_t)a.P * Lp;
   int s0, b0, c;
   tile_coords(a, t, &s0, &b0, &c);
   const int tid = threadIdx.x;
@@ -488,7 +282,7 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* map, const TileArgs
     if (a.axis == 0) {
       // x-lines: one box (TS slots x chunk nodes) per position and chunk
       mbar_expect_tx(bar, (uint32_t)(nvalid * a.L * a.TS * (int)sizeof(T)) + side_bytes<T, SRC>(a, nvalid));
-      issue_side_loads<T, SRC>(a, b0, c, nvalid, sr, bar);
+      issue_side_loads<T, SRC>(a, b0, c, nvalid, fl_s, fr_s, src_s, bar);
       for (int p = 0; p < nvalid; ++p)
         for (int k = 0; k < a.chunks; ++k) {
           const int i0 = k * a.chunk;
@@ -497,7 +291,7 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* map, const TileArgs
     } else {
       // y/z-lines: one box (TS slots x P positions x chunk nodes) per chunk
       mbar_expect_tx(bar, (uint32_t)(lines * a.L * (int)sizeof(T)) + side_bytes<T, SRC>(a, nvalid));
-      issue_side_loads<T, SRC>(a, b0, c, nvalid, sr, bar);
+      issue_side_loads<T, SRC>(a, b0, c, nvalid, fl_s, fr_s, src_s, bar);
       for (int k = 0; k < a.chunks; ++k) {
         const int i0 = k * a.chunk;
         T* dst = tile + (size_t)i0 * a.P * a.TS;
@@ -518,7 +312,7 @@ __device__ __forceinline__ bool tile_body(const CUtensorMap* map, const TileArgs
 #pragma unroll
     for (int v = 0; v < V; ++v) ft[v] = SRC ? slot_time_factor<T>(a, s0 + s + v, t_first) : T(0);
     line_solve<T, V, SRC>(tile + tile_off(a, s, p, 0), a.axis == 0 ? a.TS : a.P * a.TS, a.L, fl_s + p * Lp,
-                          fr_s + p * Lp, src_s + p * Lp, ft, fa_s ? fa_s + p * Lp : nullptr);
+                          fr_s + p * Lp, src_s + p * Lp, ft);
   }
   fence_async_smem();
   __syncthreads();
@@ -623,14 +417,14 @@ __global__ void tile_sweep_grouped_kernel(const TileJob* __restrict__ jobs, cons
 
 
 template <typename T, bool SRC>
-__device__ __forceinline__ void issue_tile_load(const CUtensorMap* map, const TileArgs& a, T* buf, const SideRows& sr,
-                                                uint64_t* bar, int t) {
+__device__ __forceinline__ void issue_tile_load(const CUtensorMap* map, const TileArgs& a, T* buf, T* fl_s, T* fr_s,
+                                                T* src_s, uint64_t* bar, int t) {
   int s0, b0, c;
   tile_coords(a, t, &s0, &b0, &c);
   const int nvalid = min(a.P, a.nb - b0);
   if (a.axis == 0) {
     mbar_expect_tx(bar, (uint32_t)(nvalid * a.L * a.TS * (int)sizeof(T)) + side_bytes<T, SRC>(a, nvalid));
-    issue_side_loads<T, SRC>(a, b0, c, nvalid, sr, bar);
+    issue_side_loads<T, SRC>(a, b0, c, nvalid, fl_s, fr_s, src_s, bar);
     for (int p = 0; p < nvalid; ++p)
       for (int k = 0; k < a.chunks; ++k) {
         const int i0 = k * a.chunk;
@@ -638,7 +432,7 @@ __device__ __forceinline__ void issue_tile_load(const CUtensorMap* map, const Ti
       }
   } else {
     mbar_expect_tx(bar, (uint32_t)(a.TS * a.P * a.L * (int)sizeof(T)) + side_bytes<T, SRC>(a, nvalid));
-    issue_side_loads<T, SRC>(a, b0, c, nvalid, sr, bar);
+    issue_side_loads<T, SRC>(a, b0, c, nvalid, fl_s, fr_s, src_s, bar);
     for (int k = 0; k < a.chunks; ++k) {
       const int i0 = k * a.chunk;
       T* dst = buf + (size_t)i0 * a.P * a.TS;
@@ -688,14 +482,14 @@ __global__ void tile_sweep_pipe_kernel(const __grid_constant__ CUtensorMap map, 
   T* buf0 = reinterpret_cast<T*>(smem_raw);
   // per stage: l, r (and source) of the tile's positions, rows of Lp entries, 32-byte aligned
   T* fac0 = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(buf0 + R * tile_elems) + 31) & ~(uintptr_t)31);
-  const size_t fac_stride = (size_t)(2 + (a.fa ? 1 : 0) + (SRC ? 1 : 0)) * side;
+  const size_t fac_stride = SRC ? 3 * side : 2 * side;
   uint64_t* bars = reinterpret_cast<uint64_t*>(
       (reinterpret_cast<uintptr_t>(fac0 + R * fac_stride) + 15) & ~(uintptr_t)15);
   __shared__ int s_ok;
   const int tid = threadIdx.x;
   auto stage_load = [&](int stage, int t) {
     T* fl = fac0 + stage * fac_stride;
-    issue_tile_load<T, SRC>(&map, a, buf0 + stage * tile_elems, side_rows<T>(a, fl), &bars[stage], t);
+    issue_tile_load<T, SRC>(&map, a, buf0 + stage * tile_elems, fl, fl + side, fl + 2 * side, &bars[stage], t);
   };
   if (tid == 0) {
     s_ok = *reinterpret_cast<volatile int*>(a.err) ? 0 : 1;
@@ -717,11 +511,9 @@ __global__ void tile_sweep_pipe_kernel(const __grid_constant__ CUtensorMap map, 
     const int stage = k % R;
     const uint32_t parity = (uint32_t)((k / R) & 1);
     T* buf = buf0 + stage * tile_elems;
-    const SideRows sr = side_rows<T>(a, fac0 + stage * fac_stride);
-    const T* fl_s = static_cast<const T*>(sr.l);
-    const T* fr_s = static_cast<const T*>(sr.r);
-    const T* fa_s = static_cast<const T*>(sr.a);
-    const T* src_s = static_cast<const T*>(sr.src);
+    T* fl_s = fac0 + stage * fac_stride;
+    T* fr_s = fl_s + side;
+    T* src_s = fr_s + side;
     int s0, b0, c;
     tile_coords(a, t, &s0, &b0, &c);
     if (tid == 0) s_ok = mbar_wait(&bars[stage], parity) ? 1 : 0;
@@ -745,7 +537,7 @@ __global__ void tile_sweep_pipe_kernel(const __grid_constant__ CUtensorMap map, 
 #pragma unroll
       for (int v = 0; v < V; ++v) ft[v] = SRC ? slot_time_factor<T>(a, s0 + s + v, a.t_first) : T(0);
       line_solve<T, V, SRC>(buf + tile_off(a, s, p, 0), a.axis == 0 ? a.TS : a.P * a.TS, a.L, fl_s + p * Lp,
-                            fr_s + p * Lp, src_s + p * Lp, ft, fa_s ? fa_s + p * Lp : nullptr);
+                            fr_s + p * Lp, src_s + p * Lp, ft);
     }
     fence_async_smem();
     __syncthreads();
@@ -901,8 +693,7 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
     const int Lp4 = (L + 3) & ~3;
     const int st = tp.pipe ? kPipeStages : 1;
     while (!short_rows && tp.TS * elem > 128 && S_pad % (tp.TS / 2) == 0 &&
-           (size_t)st * ((size_t)tp.TS * L * elem + (line_split(L) ? 4 : 3) * (size_t)Lp4 * elem + 64) + 512 >
-               (size_t)maxsm)
+           (size_t)st * ((size_t)tp.TS * L * elem + 3 * (size_t)Lp4 * elem + 64) + 512 > (size_t)maxsm)
       tp.TS /= 2;
   }
   const int stages = tp.pipe ? kPipeStages : 1;
@@ -957,9 +748,7 @@ void tile_plan(const Geom& g, int S_pad, int elem, int axis, TilePlan& tp, void*
   const int Lp = (L + 3) & ~3;
   // stages x (tile + factor rows l, r) + alignment + barriers; the source, when added, takes
   // one more factor row per position and stage
-  // (l, r and, for the two-half solve, the influence row)
-  const int frows = line_split(L) ? 3 : 2;
-  tp.smem = (size_t)stages * ((size_t)lines * L * elem + frows * (size_t)tp.P * Lp * elem + 64) + 64 + 128;
+  tp.smem = (size_t)stages * ((size_t)lines * L * elem + 2 * (size_t)tp.P * Lp * elem + 64) + 64 + 128;
   tp.threads = lines / tp.V;
   int dev = 0, maxsm = 0;
   PS_CUDA(cudaGetDevice(&dev));
@@ -995,13 +784,10 @@ void tile_sweep(const Geom& g, const TilePlan& tp, const LineFactors& f, int S_p
   if (sizeof(T) == 4) {
     a.fl = f.lt32.p;
     a.fr = f.rt32.p;
-    a.fa = f.at32.p;
   } else {
     a.fl = f.lt64.p;
     a.fr = f.rt64.p;
-    a.fa = f.at64.p;
   }
-  if (!line_split(tp.L)) a.fa = nullptr;
   a.src = sa.src;
   a.srcrow = srcrow;
   a.src_t = sa.src_t;
@@ -1072,28 +858,6 @@ __global__ void line_major_kernel(const T* __restrict__ l, const T* __restrict__
   lt[e] = lv;
   rt[e] = rv;
 }
-// Influence rows of the two-half line solve (line_split): per line, A_i = prod_{j=h..i}(-l_j)
-// for i >= h and B_i = prod_{j=i+1..h}(-l_j) for i < h, from the line-major factors the tiles
-// use (products in FP64, rounded once).  One thread per line.
-template <typename T>
-__global__ void influence_rows_kernel(const T* __restrict__ lt, T* __restrict__ at, long long lines, int L, int Lp) {
-  const long long line = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (line >= lines) return;
-  const int h = line_split(L);
-  const T* l = lt + line * Lp;
-  T* a = at + line * Lp;
-  double p = 1.0;
-  for (int i = h; i < L; ++i) {
-    p *= -(double)l[i];
-    a[i] = (T)p;
-  }
-  p = 1.0;
-  for (int i = h - 1; i >= 0; --i) {
-    p *= -(double)l[i + 1];
-    a[i] = (T)p;
-  }
-  for (int i = L; i < Lp; ++i) a[i] = T(0);
-}
 __global__ void src_rows_kernel(const double* __restrict__ src, void* out, int elem, long long rows, int nx, int Lp) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= rows * Lp) return;
@@ -1109,25 +873,16 @@ void factor_lines(const Geom& g, LineFactors& f, bool fp32, cudaStream_t st) {
   const long long lines = g.nt / L;
   const long long total = lines * Lp;
   const unsigned blocks = (unsigned)((total + 255) / 256);
-  const unsigned lblocks = (unsigned)((lines + 127) / 128);
   if (fp32) {
     f.lt32.alloc((size_t)total);
     f.rt32.alloc((size_t)total);
     line_major_kernel<float><<<blocks, 256, 0, st>>>(f.l32.p, f.r32.p, f.lt32.p, f.rt32.p, m, g.n[0], g.n[1], g.n[2],
                                                      lines, L, Lp, f.var);
-    if (line_split(L)) {
-      f.at32.alloc((size_t)total);
-      influence_rows_kernel<float><<<lblocks, 128, 0, st>>>(f.lt32.p, f.at32.p, lines, L, Lp);
-    }
   } else {
     f.lt64.alloc((size_t)total);
     f.rt64.alloc((size_t)total);
     line_major_kernel<double><<<blocks, 256, 0, st>>>(f.l64.p, f.r64.p, f.lt64.p, f.rt64.p, m, g.n[0], g.n[1],
                                                       g.n[2], lines, L, Lp, f.var);
-    if (line_split(L)) {
-      f.at64.alloc((size_t)total);
-      influence_rows_kernel<double><<<lblocks, 128, 0, st>>>(f.lt64.p, f.at64.p, lines, L, Lp);
-    }
   }
   PS_CUDA(cudaGetLastError());
 }
@@ -1158,7 +913,6 @@ long long tile_job_fill(const Geom& g, const TilePlan& tp, const LineFactors& f,
   a.Lp = (tp.L + 3) & ~3;
   a.fl = f.lt32.p;
   a.fr = f.rt32.p;
-  a.fa = line_split(tp.L) ? f.at32.p : nullptr;
   a.err = err;
   PS_REQUIRE(a.fl && a.fr, "line-major FP32 factors missing");
   if (sa.src && tp.axis == 0) {
