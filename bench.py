@@ -57,9 +57,9 @@ FP64_PEAK_TFLOPS = 1.19
 # (127^3 x 64 slices, scaled to any launch by the node-slices it processes).  A kernel whose
 # source changed since is reported with traffic null.
 _UNITS_127 = 127 ** 3 * 64
-TRAFFIC = {"F.x.f32": {"bytes_per_node_slice": (549.215744e6 + 463.143680e6) / _UNITS_127, "tile_src_sha": "b4be5a9e65cc44b5"},
-           "F.y.f32": {"bytes_per_node_slice": (541.017344e6 + 463.126016e6) / _UNITS_127, "tile_src_sha": "b4be5a9e65cc44b5"},
-           "F.z.f32": {"bytes_per_node_slice": (541.020672e6 + 462.866688e6) / _UNITS_127, "tile_src_sha": "b4be5a9e65cc44b5"}}
+TRAFFIC = {"F.x.f32": {"bytes_per_node_slice": (549.214464e6 + 463.244544e6) / _UNITS_127, "tile_src_sha": "b27d5c80c1ebe8be"},
+           "F.y.f32": {"bytes_per_node_slice": (541.012224e6 + 463.005696e6) / _UNITS_127, "tile_src_sha": "b27d5c80c1ebe8be"},
+           "F.z.f32": {"bytes_per_node_slice": (541.032448e6 + 462.982912e6) / _UNITS_127, "tile_src_sha": "b27d5c80c1ebe8be"}}
 
 
 def tile_src_sha():
