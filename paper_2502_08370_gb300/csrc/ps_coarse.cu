@@ -1,5 +1,6 @@
-// ps_coarse.cu -- the coarse propagator's line sweeps on one slice, staged through shared
-// memory.
+// ps_coarse.cu -- the coarse propagator's line sweeps on one slice: the FP64 x-sweep by
+// warp-private Thomas chunks (the default; also the batches' grouped x-sweep), the sweeps
+// staged whole through shared memory (an autotuner candidate), and the FP32 PCR x-sweep.
 //
 // The coarse chain of parareal (Sec. 3) advances one slice at a time, U_{n+1} = G(U_n) +
 // correction, so its sweeps see only the lines of one slice (n^{d-1} lines per direction) and
