@@ -306,7 +306,7 @@ int ps_adjoint(ps_problem* p, const double* u_target_dev, double tol, int max_it
  *  - Grids with more than PS_NOALLOC_MAX_UNKNOWNS interior unknowns are rejected with
  *    PS_ERR_INVALID before any GPU work.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *    with that device current; make that first call before any stream capture.
+ *    with that device current.
  *  - Like the allocating version, the call waits for `stream` before it returns: it reads the
  *    device-side error flag of its kernels back to the host.
  *  - All calls share the one array: calls that overlap on the GPU (other streams, other
