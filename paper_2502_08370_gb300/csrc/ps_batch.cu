@@ -50,8 +50,10 @@ struct ps_batch {
   DevBuf<int> nseg_misc;            // [0] pack, [1] unpack, [2] copy, [3 + n] coarse step n
   DevBuf<unsigned long long> inc;   // per problem
   DevBuf<int> flag, tmo;
+  std::vector<TilePlan> bplans;     // [count][dims] the batch's tile shapes (batch_tile_plans)
   size_t tile_smem = 0;
   int tile_threads = 0;
+  int tile_grid = 0;                // CTAs of a grouped tile launch: one wave
   int sms = 152;
   cudaStream_t cs = nullptr;
   cudaGraphExec_t iter_graph = nullptr, init_graph = nullptr;
@@ -65,7 +67,7 @@ struct ps_batch {
   std::vector<unsigned long long> h_inc;
   std::vector<int> h_flag;
   double updates = 0.0;
-  int launches_per_iter = 0, launches = 0;
+  int launches_per_iter = 0, launches_init = 0, launches = 0;
   bool registered = false;  // counted in its problems' `batched`
   ~ps_batch() {
     if (registered)
@@ -231,7 +233,8 @@ void fill_iteration_tables(ps_batch* b, const std::vector<int>& active, int k) {
         sa.src_t_len = p->op->src_t_len;
         sa.tau = p->F.tau;
       }
-      const long long tiles = tile_job_fill(g3, p->F.tiles[m], *p->F.dim[m], p->S_pad, k - 1, nsl, b->tmo.p,
+      const long long tiles = tile_job_fill(g3, b->bplans[(size_t)order[r] * D + m], *p->F.dim[m], p->S_pad, k - 1,
+                                            nsl, b->tmo.p,
                                             b->h_tile_jobs.data() + ((size_t)m * P + r) * jb, sa, p->srcrow32.p);
       b->h_tile_segs[(size_t)m * P + r] = WorkSeg{(int)r, 0, (int)tiles, prefix};  // job index within axis m
       prefix += (int)tiles;
@@ -302,7 +305,8 @@ int enqueue_sequence(ps_batch* b, int mode, cudaStream_t st) {
     for (int j = 0; j < b->maxS; ++j)
       for (int m = 0; m < b->dims; ++m) {
         tile_sweep_grouped(b->tile_jobs.p + (size_t)m * P * tile_job_bytes(), b->tile_segs.p + (size_t)m * P,
-                           b->tile_nseg.p + (size_t)j * b->dims + m, grid, b->tile_threads, b->tile_smem, b->tmo.p,
+                           b->tile_nseg.p + (size_t)j * b->dims + m, b->tile_grid, b->tile_threads, b->tile_smem,
+                           b->tmo.p,
                            j, st);
         ++n_launch;
       }
@@ -356,6 +360,7 @@ cudaGraphExec_t capture(ps_batch* b, int mode) {
   cudaGraphDestroy(g);
   PS_CUDA(e);
   if (mode == 1) b->launches_per_iter = n;
+  else b->launches_init = n;
   return ex;
 }
 
@@ -382,13 +387,64 @@ void batch_check(const ps_batch* b, const ps_problem* p) {
   for (const ps_problem* q : b->probs) PS_REQUIRE(q != p, "a problem appears twice in the batch");
 }
 
+// The batch's tile shapes.  One grouped launch serves every problem, so every CTA reserves
+// the largest tile of the batch (and at least what six tiles per SM take: one position of
+// 255-node FP32 lines, the best single-problem shape).  A problem with shorter lines takes as
+// many line positions per tile (up to 4) as fit in that reservation, so that its CTAs keep
+// as many bytes in flight as those of the longest lines; with one position per tile a CTA of
+// 63-node lines would move an eighth of them.  The number of positions per tile changes no
+// line's arithmetic.  Each problem keeps its own plans for its own runs.  The grouped launch
+// then takes one wave of CTAs (as many as fit on every SM): its CTAs walk equal shares of the
+// tiles, so a second, partial wave would leave SMs idle at the end of each launch.
+void batch_tile_plans(ps_batch* b) {
+  const int D = b->dims;
+  size_t budget = 0;
+  for (ps_problem* p : b->probs)
+    for (int m = 0; m < D; ++m)
+      budget = std::max(budget, tile_grouped_smem(p->F.tiles[m], m == 0 && p->op->src.p != nullptr));
+  int dev = 0, per_sm = 0;
+  PS_CUDA(cudaGetDevice(&dev));
+  PS_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  budget = std::max(budget, (size_t)per_sm / 6 - 1024);
+  b->bplans.assign(b->probs.size() * D, TilePlan{});
+  b->tile_smem = 0;
+  b->tile_threads = 0;
+  for (size_t i = 0; i < b->probs.size(); ++i) {
+    ps_problem* p = b->probs[i];
+    Geom g3 = p->g;
+    if (g3.dim == 2) g3.n[2] = 1;
+    for (int m = 0; m < D; ++m) {
+      const TilePlan& own = p->F.tiles[m];
+      const bool src = m == 0 && p->op->src.p != nullptr;
+      TilePlan tp = own;
+      for (int q = 4; q > own.P; q /= 2) {
+        TilePlan c;
+        try {
+          tile_plan(g3, p->S_pad, 4, m, c, p->W.p, q, 0, own.TS, 1);
+        } catch (const Error&) {
+          continue;  // no such shape for these lines: keep fewer positions
+        }
+        if (c.TS == own.TS && c.P > own.P && tile_grouped_smem(c, src) <= budget) {
+          tp = c;
+          break;
+        }
+      }
+      b->bplans[i * D + m] = tp;
+      b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(tp, src));
+      // the grouped kernel runs one line per thread, whatever the plan's own split
+      b->tile_threads = std::max(b->tile_threads, tp.TS * tp.P);
+    }
+  }
+  b->tile_threads = (b->tile_threads + 31) / 32 * 32;
+  b->tile_grid = b->sms;
+  if (b->tile_threads > 0) b->tile_grid *= std::max(1, tile_grouped_ctas_per_sm(b->tile_threads, b->tile_smem));
+}
+
 // Sizes of the batch's tables from its problems, and the device tables and host staging.
 void batch_layout(ps_batch* b) {
   const int P = (int)b->probs.size();
   b->count = P;
   b->maxS = b->maxN = 0;
-  b->tile_smem = 0;
-  b->tile_threads = 0;
   b->var = P > 0 ? b->probs[0]->op->a.p != nullptr : true;
   b->delta32 = P > 0 && b->probs[0]->delta32;
   b->dims = P > 0 ? b->probs[0]->g.dim : 2;
@@ -400,13 +456,8 @@ void batch_layout(ps_batch* b) {
   for (ps_problem* p : b->probs) {
     b->maxS = std::max(b->maxS, p->fs);
     b->maxN = std::max(b->maxN, p->N);
-    b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[0], p->op->src.p != nullptr));
-    // the grouped kernel runs one line per thread, whatever the plan's own split
-    for (int m = 1; m < p->g.dim; ++m) b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[m], false));
-    for (int m = 0; m < p->g.dim; ++m)
-      b->tile_threads = std::max(b->tile_threads, p->F.tiles[m].TS * p->F.tiles[m].P);
   }
-  b->tile_threads = (b->tile_threads + 31) / 32 * 32;
+  batch_tile_plans(b);
   if (b->iter_graph) {
     cudaGraphExecDestroy(b->iter_graph);
     b->iter_graph = nullptr;
@@ -520,6 +571,7 @@ int ps_batch_destroy(ps_batch* b) {
 int ps_batch_run(ps_batch* b, const double* const* u0_devs, double tol, int max_iter, uintptr_t stream,
                  int* iters_out) {
   return bguarded([&] {
+    TraceRange whole("ps.batch");
     PS_REQUIRE(b && u0_devs, "null argument");
     PS_REQUIRE(b->count > 0, "the batch holds no problem");
     cudaStream_t ust = reinterpret_cast<cudaStream_t>(stream);
@@ -534,17 +586,7 @@ int ps_batch_run(ps_batch* b, const double* const* u0_devs, double tol, int max_
       cudaGraphExecDestroy(b->init_graph);
       b->init_graph = nullptr;
     }
-    b->tile_smem = 0;
-    b->tile_threads = 0;
-    for (ps_problem* p : b->probs) {
-      b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[0], p->op->src.p != nullptr));
-      // the grouped kernel runs one line per thread, whatever the plan's own split
-      for (int m = 1; m < p->g.dim; ++m)
-        b->tile_smem = std::max(b->tile_smem, tile_grouped_smem(p->F.tiles[m], false));
-      for (int m = 0; m < p->g.dim; ++m)
-        b->tile_threads = std::max(b->tile_threads, p->F.tiles[m].TS * p->F.tiles[m].P);
-    }
-    b->tile_threads = (b->tile_threads + 31) / 32 * 32;
+    batch_tile_plans(b);
     b->init_graph = capture(b, 2);
     b->iter_graph = capture(b, 1);
     PS_CUDA(cudaEventRecord(b->ev_in, ust));
@@ -567,7 +609,7 @@ int ps_batch_run(ps_batch* b, const double* const* u0_devs, double tol, int max_
     fill_coarse_tables(b, active, 0);
     upload_tables(b, st);
     PS_CUDA(cudaGraphLaunch(b->init_graph, st));
-    b->launches += 2 * b->maxN;
+    b->launches += b->launches_init;
     int k = 0;
     const int cap = max_iter <= 0 ? (1 << 30) : max_iter;
     while (!active.empty()) {

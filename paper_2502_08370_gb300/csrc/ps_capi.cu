@@ -18,7 +18,6 @@
 #include <string>
 #include <vector>
 
-#include <nvtx3/nvToolsExt.h>
 
 #include "ps_adjoint.h"
 #include "ps_async.h"
@@ -428,14 +427,6 @@ void check_state_len(const ps_problem* p, int slice) {
   require_slices(p);
   PS_REQUIRE(slice >= 0 && slice <= p->N, "slice out of range");
 }
-
-// Host-side trace ranges (NVTX; free when no tool is attached), one per parareal phase.
-struct TraceRange {
-  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
-  ~TraceRange() { nvtxRangePop(); }
-  TraceRange(const TraceRange&) = delete;
-  TraceRange& operator=(const TraceRange&) = delete;
-};
 
 // resume_k < 0: a new run from u0.  resume_k >= 0: continue after iteration resume_k from the
 // problem's states U^k, coarse values Gold and history (a stopped run, or a loaded checkpoint).

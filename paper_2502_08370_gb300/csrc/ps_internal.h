@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <stdexcept>
@@ -187,6 +188,14 @@ bool sweep_x_chunked(const Geom& g, int nslices, const LineFactors& f, const dou
 // on the calling host thread: 0 = as many as fit (one launch wave); > 0 = a persistent grid of
 // that many CTAs per SM, each walking its share of the work.  Set while the coarse chain runs
 // beside the fine phase, so that the fine tiles keep most of every SM's shared memory.
+// Host-side trace range (NVTX; free when no tool is attached): one per parareal phase, and
+// one around each batched run.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 extern thread_local int chain_ctas_per_sm;
 struct ChainResidency {
   int saved;

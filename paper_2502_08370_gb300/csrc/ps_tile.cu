@@ -932,6 +932,14 @@ size_t tile_grouped_smem(const TilePlan& tp, bool src) {
   return tp.smem + (src ? (size_t)tp.P * ((tp.L + 3) & ~3) * sizeof(float) + 64 : 0);
 }
 
+int tile_grouped_ctas_per_sm(int threads, size_t smem) {
+  auto kern = tile_sweep_grouped_kernel<float, 1>;
+  PS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int n = 0;
+  PS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem));
+  return n;
+}
+
 void tile_sweep_grouped(const void* jobs, const WorkSeg* segs, const int* nseg, int grid, int threads, size_t smem,
                         int* err, int step, cudaStream_t st) {
   auto kern = tile_sweep_grouped_kernel<float, 1>;  // one line per thread, as the default single-problem plan

@@ -58,6 +58,8 @@ long long tile_job_fill(const Geom& g, const TilePlan& tp, const LineFactors& f,
                         int* err, void* job_out, const SourceArgs& sa, const float* srcrow);
 size_t tile_job_bytes();
 size_t tile_grouped_smem(const TilePlan& tp, bool src);
+// CTAs of the grouped tile kernel resident per SM at `threads` threads and `smem` bytes
+int tile_grouped_ctas_per_sm(int threads, size_t smem);
 // step: the fine step of the launch (the source's time index is step + 1 + slot * t_slice)
 void tile_sweep_grouped(const void* jobs, const WorkSeg* segs, const int* nseg, int grid, int threads, size_t smem,
                         int* err, int step, cudaStream_t st);
