@@ -361,7 +361,11 @@ int ps_problem_kernel_times(const ps_problem* p, ps_kernel_time* out, int cap, i
  * otherwise).  The batch keeps pointers to the problems
  * (destroy it first); states and histories are read per problem afterwards (ps_get_state,
  * ...).  While a problem belongs to a batch, ps_autotune only considers the tile shapes
- * the batch's grouped kernels run (one tile per work item, one line per thread). */
+ * the batch's grouped kernels run (one tile per work item, one line per thread, one line
+ * position per tile).  From those, each ps_batch_run derives the batch's own tile shapes:
+ * every tile of a launch reserves as much shared memory as the batch's largest, and
+ * problems with shorter lines take up to four line positions per tile to fill it (the
+ * problems' own plans, and every result, stay as they are). */
 typedef struct ps_batch ps_batch;
 /* count >= 0 problems (problems may be NULL when count = 0); more join with ps_batch_add. */
 int ps_batch_create(ps_problem* const* problems, int count, uintptr_t stream, ps_batch** out);
