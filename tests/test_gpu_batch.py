@@ -221,3 +221,39 @@ def test_3d_batch_equals_individual_runs_bitwise(ps, coarse):
     p2 = ps.Problem(ps.Splitting(op2), 0.4, 4, 1, 3, precision="mixed", coarse_mode=coarse)
     with pytest.raises(ps.PsError):
         batch.add(p2)
+
+
+@pytest.mark.parametrize("coarse", ["fp64", "delta32"])
+def test_batch_tile_shapes_of_mixed_line_lengths_bitwise(ps, coarse):
+    """A batch whose lines range from 9 to 511 nodes: every tile of the grouped launch reserves
+    the largest tile (511-node x lines with a source), so the batch gives the shorter lines more
+    positions per tile (two for 255 nodes, four for 127 and fewer), with ragged last tiles
+    (21, 127, 255 and 17 positions).  States, histories and iteration counts equal each
+    problem's own run (one position per tile) bitwise."""
+    rng = np.random.default_rng(93)
+    shapes = [(511, 9), (255, 21), (63, 127), (17, 255)]
+    probs, u0s = [], []
+    for i, n in enumerate(shapes):
+        a = np.exp(0.3 * rng.standard_normal([v + 2 for v in reversed(n)]))
+        src = rng.standard_normal(n[::-1]) if i % 2 == 0 else None
+        N, s = (4, 8)[i % 2], 3 + i
+        grid = ps.Grid(n)
+        op = ps.Operator(grid, a=dev(a), src=None if src is None else dev(src))
+        sp = ps.Splitting(op)
+        prob = ps.Problem(sp, 0.4, N, 1, s, precision="mixed", coarse_mode=coarse, tile_positions=1)
+        prob._keep = (grid, op, sp)
+        probs.append(prob)
+        u0s.append(dev(rng.standard_normal(n[::-1])))
+    ref = []
+    for p, u in zip(probs, u0s):
+        it = p.run(u, 1e-9)
+        ref.append((it, snapshot(p), p.history()))
+    batch = ps.Batch(probs)
+    for _ in range(2):
+        its = batch.run(u0s, 1e-9)
+        assert its == [r[0] for r in ref]
+        for p, (it, st, h) in zip(probs, ref):
+            got = snapshot(p)
+            for n in range(p.N + 1):
+                assert np.array_equal(got[n], st[n]), n
+            assert np.array_equal(p.history(), h)
