@@ -13,8 +13,10 @@
 // The launches read their work from device tables (which problems, which tiles or blocks),
 // so the sequence is captured once as a CUDA graph and replayed every iteration; between
 // replays the host only rewrites the tables (converged problems drop out) and reads back
-// the per-problem increments.  Each problem's arithmetic is the same as in its own
-// ps_run_parareal, so batched and individual results agree bitwise.
+// the per-problem increments.  The tile launches take the batch's own tile shapes (problems
+// with shorter lines get more line positions per tile, batch_tile_plans).  Each problem's
+// arithmetic is the same as in its own ps_run_parareal, so batched and individual results
+// agree bitwise.
 #include <cuda_runtime.h>
 
 #include <algorithm>
